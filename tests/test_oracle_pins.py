@@ -1,0 +1,459 @@
+"""Pins for the FP64 oracle: each check compares it with something other than
+itself -- hand-derived closed forms (tests/golden), an independent
+quaternion-based kinematics, brute-force surface sampling, brute-force dense
+edge sampling, and library routines (scipy cKDTree) for special cases.
+
+No GPU needed.  Chosen so that a dropped term, a wrong sign or index, or a
+transposed operand anywhere in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+from scipy.spatial.transform import Rotation
+
+from paper_2609_30644_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------
+# independent kinematics used as pins
+# ----------------------------------------------------------------------------
+
+def planar_closed_form(robot, theta):
+    """Textbook planar chain: phi_j = yaw + sum_{i<=j} theta_i; link j starts
+    at base + sum_{i<j} L_i (cos phi_i, sin phi_i)."""
+    yaw = math.atan2(robot.base[4], robot.base[0])
+    bx, by = float(robot.base[3]), float(robot.base[7])
+    L = robot.dh[:, 0].astype(float)
+    out = []
+    for s in range(robot.n_spheres):
+        j = int(robot.sphere_link[s])
+        f = float(robot.sphere_xyzr[s, 0]) / L[j]
+        x, y, phi = bx, by, yaw
+        for i in range(j):
+            phi_i = yaw + sum(theta[: i + 1])
+            x += L[i] * math.cos(phi_i)
+            y += L[i] * math.sin(phi_i)
+        phi = yaw + sum(theta[: j + 1])
+        out.append((x + f * L[j] * math.cos(phi), y + f * L[j] * math.sin(phi), 0.0,
+                    float(robot.sphere_xyzr[s, 3])))
+    return np.array(out)
+
+
+def quaternion_fk(robot, q):
+    """DH chain composed with rotation objects and explicit translations in the
+    base frame: F_j' = F_{j-1} Rz(theta_j + off_j); next origin = origin +
+    R_j' (a_j, 0, d_j); next rotation = R_j' Rx(alpha_j); sphere = origin_{j-1}
+    + R_j' p.  The (float32, not exactly orthonormal) base matrix is applied
+    last, as given.  Returns world spheres and per-link (R, origin) in world."""
+    B = robot.base.astype(float).reshape(3, 4)
+    BR, Bt = B[:, :3], B[:, 3]
+    rot = Rotation.identity()
+    org = np.zeros(3)
+    frames = []
+    for j in range(robot.dof):
+        a, al, d, off = robot.dh[j].astype(float)
+        rj = rot * Rotation.from_euler("z", q[j] + off)
+        frames.append((rj, org.copy()))
+        org = org + rj.apply([a, 0.0, d])
+        rot = rj * Rotation.from_euler("x", al)
+    out = []
+    for s in range(robot.n_spheres):
+        rj, o = frames[int(robot.sphere_link[s])]
+        p = BR @ (o + rj.apply(robot.sphere_xyzr[s, :3].astype(float))) + Bt
+        out.append((*p, float(robot.sphere_xyzr[s, 3])))
+    world = [(BR @ rj.as_matrix(), BR @ o + Bt) for rj, o in frames]
+    return np.array(out), world
+
+
+def box_clearance_bruteforce(c, r, cub, n=161):
+    """Min distance from c to a dense sample of the box surface, or -r when
+    c is inside (inside test in box coordinates)."""
+    ctr = cub[:3].astype(float)
+    h = cub[3:6].astype(float)
+    R = cub[6:].astype(float).reshape(3, 3)
+    p = R.T @ (np.asarray(c, float) - ctr)
+    if np.all(np.abs(p) <= h):
+        return -r
+    u = np.linspace(-1, 1, n)
+    U, V = np.meshgrid(u, u)
+    pts = []
+    for ax in range(3):
+        o1, o2 = [a for a in range(3) if a != ax]
+        for sgn in (-1, 1):
+            P = np.zeros((U.size, 3))
+            P[:, ax] = sgn * h[ax]
+            P[:, o1] = U.ravel() * h[o1]
+            P[:, o2] = V.ravel() * h[o2]
+            pts.append(P)
+    P = np.concatenate(pts)
+    return float(np.min(np.linalg.norm(P - p[None], axis=1))) - r
+
+
+# ----------------------------------------------------------------------------
+# forward kinematics
+# ----------------------------------------------------------------------------
+
+def test_planar_fk_golden(orc):
+    scene = synth.planar_pair_scene(0)
+    o = orc.OracleScene(scene)
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "planar_fk.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 8
+    for row in rows:
+        th = [float(x) for x in row[:3]]
+        link, k = int(row[3]), int(row[4])
+        x, y = float(row[5]), float(row[6])
+        w = o.fk_robot(0, th)
+        s = link * 4 + k
+        # scene parameters are float32 (|rounding| < 3e-8 per value)
+        assert w[s, 0] == pytest.approx(x, abs=2e-7)
+        assert w[s, 1] == pytest.approx(y, abs=2e-7)
+        assert w[s, 2] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_planar_fk_closed_form(orc):
+    """DH with alpha = d = 0 reduces to the textbook planar chain."""
+    scene = synth.planar_pair_scene(3)
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        q = rng.uniform(-math.pi, math.pi, 6)
+        for k in range(2):
+            ref = planar_closed_form(scene.robots[k], q[3 * k:3 * k + 3])
+            got = o.fk_robot(k, q[3 * k:3 * k + 3])
+            np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("make", [synth.table_pair_scene, synth.grid4_scene])
+def test_spatial_fk_vs_quaternion_chain(orc, make):
+    scene = make(1)
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        for k, rb in enumerate(scene.robots):
+            q = rng.uniform(rb.q_lo, rb.q_hi)
+            ref, frames = quaternion_fk(rb, q)
+            np.testing.assert_allclose(o.fk_robot(k, q), ref, atol=1e-12)
+            F = o.link_frames(k, q)
+            for j, (rj, org) in enumerate(frames):
+                np.testing.assert_allclose(F[j, :3, :3], rj, atol=1e-12)
+                np.testing.assert_allclose(F[j, :3, 3], org, atol=1e-12)
+                # joint rotations are exact rotations: the frame is as
+                # orthonormal as the float32 base rotation it starts from
+                Rm = F[j, :3, :3]
+                B = rb.base.astype(float).reshape(3, 4)[:, :3]
+                base_err = np.abs(B.T @ B - np.eye(3)).max()
+                assert np.abs(Rm.T @ Rm - np.eye(3)).max() <= base_err + 1e-12
+                np.testing.assert_array_equal(F[j, 3], [0, 0, 0, 1])
+
+
+def test_fk_theta_offset_is_added(orc):
+    """theta_offset shifts the joint angle: q + off with off=0 equals q' = q + off."""
+    scene = synth.table_pair_scene(0)
+    rb = scene.robots[0]
+    rng = np.random.default_rng(3)
+    q = rng.uniform(-1, 1, rb.dof)
+    off = rng.uniform(-1, 1, rb.dof).astype(np.float32)
+    rb2 = synth.Robot(rb.dof, rb.dh.copy(), rb.q_lo, rb.q_hi, rb.sphere_link,
+                      rb.sphere_xyzr, rb.base)
+    rb2.dh[:, 3] = off
+    s1 = synth.Scene([rb2], scene.obs_spheres, scene.obs_cuboids)
+    s0 = synth.Scene([rb], scene.obs_spheres, scene.obs_cuboids)
+    a = orc.OracleScene(s1).fk_robot(0, q)
+    b = orc.OracleScene(s0).fk_robot(0, q + off.astype(float))
+    np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# distances
+# ----------------------------------------------------------------------------
+
+def test_clearance_golden(orc):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "clearance_cases.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 8
+    for row in rows:
+        v = [float(x) for x in row[1:]]
+        if row[0] == "ss":
+            got = orc.sphere_sphere_clearance(v[0:3], v[3], v[4:7], v[7])
+            assert got == pytest.approx(v[8], abs=1e-12)
+        else:
+            cub = np.array(v[4:19], dtype=np.float32)
+            got = orc.sphere_cuboid_clearance(v[0:3], v[3], cub)
+            assert got == pytest.approx(v[19], abs=1e-7)
+
+
+def test_sphere_cuboid_vs_bruteforce(orc):
+    rng = np.random.default_rng(4)
+    scene = synth.table_pair_scene(0)
+    for i in range(40):
+        cub = scene.obs_cuboids[1 + i % 31]
+        c = cub[:3].astype(float) + rng.uniform(-0.25, 0.25, 3)
+        r = float(rng.uniform(0.0, 0.05))
+        got = orc.sphere_cuboid_clearance(c, r, cub)
+        ref = box_clearance_bruteforce(c, r, cub)
+        # surface grid spacing 2h/160 <= 1.25e-3 m
+        if ref > -r:
+            assert got <= ref + 1e-9
+            assert got == pytest.approx(ref, abs=1.5e-3)
+        else:
+            assert got == pytest.approx(-r, abs=1e-12)
+
+
+def test_sphere_sphere_symmetric_and_scaled(orc):
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        a, b = rng.normal(size=3), rng.normal(size=3)
+        r1, r2 = rng.uniform(0, 1, 2)
+        d = orc.sphere_sphere_clearance(a, r1, b, r2)
+        assert d == pytest.approx(orc.sphere_sphere_clearance(b, r2, a, r1), abs=1e-15)
+        assert d == pytest.approx(np.linalg.norm(a - b) - r1 - r2, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# configuration validity (composite free space)
+# ----------------------------------------------------------------------------
+
+def _planar_min_clearance(scene, q):
+    """All-pairs clearance with closed-form planar FK and scipy-free numpy."""
+    w = [planar_closed_form(rb, q[3 * k:3 * k + 3]) for k, rb in enumerate(scene.robots)]
+    mc = np.inf
+    for k, wk in enumerate(w):
+        oc = scene.obs_spheres.astype(float)
+        d = np.linalg.norm(wk[:, None, :3] - oc[None, :, :3], axis=2) - wk[:, None, 3] - oc[None, :, 3]
+        mc = min(mc, d.min())
+        for j in range(k + 1, len(w)):
+            d = (np.linalg.norm(wk[:, None, :3] - w[j][None, :, :3], axis=2)
+                 - wk[:, None, 3] - w[j][None, :, 3])
+            mc = min(mc, d.min())
+    return mc
+
+
+def test_config_valid_planar_allpairs(orc):
+    scene = synth.planar_pair_scene(0)
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(6)
+    n_valid = 0
+    for _ in range(200):
+        q = rng.uniform(-math.pi, math.pi, 6)
+        ok, mc = o.config_valid(q, 0.0)
+        ref = _planar_min_clearance(scene, q)
+        assert mc == pytest.approx(ref, abs=1e-12)
+        assert ok == (ref >= 0.0)
+        n_valid += ok
+        # margin shifts the threshold
+        ok2, _ = o.config_valid(q, 0.05)
+        assert ok2 == (ref >= 0.05)
+    assert 20 < n_valid < 180
+
+
+def test_config_valid_spatial_composition(orc):
+    """Spatial scene: quaternion FK spheres, numpy sphere-sphere and robot-robot
+    pairs, oracle box clearance (pinned above) -> same minimum and verdict."""
+    scene = synth.table_pair_scene(2)
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        q = synth.uniform_configs(scene, 1, rng)[:, 0].astype(float)
+        w = [quaternion_fk(rb, q[off:off + rb.dof])[0]
+             for rb, off in zip(scene.robots, scene.dof_offsets)]
+        mc = np.inf
+        for k, wk in enumerate(w):
+            oc = scene.obs_spheres.astype(float)
+            d = np.linalg.norm(wk[:, None, :3] - oc[None, :, :3], axis=2) - wk[:, None, 3] - oc[None, :, 3]
+            mc = min(mc, d.min())
+            for s in range(wk.shape[0]):
+                for cub in scene.obs_cuboids:
+                    mc = min(mc, orc.sphere_cuboid_clearance(wk[s, :3], wk[s, 3], cub))
+            for j in range(k + 1, len(w)):
+                d = (np.linalg.norm(wk[:, None, :3] - w[j][None, :, :3], axis=2)
+                     - wk[:, None, 3] - w[j][None, :, 3])
+                mc = min(mc, d.min())
+        ok, got = o.config_valid(q, 1e-4)
+        assert got == pytest.approx(mc, abs=1e-10)
+        assert ok == (mc >= 1e-4)
+
+
+def test_no_self_collision_tests(orc):
+    """A single robot whose own spheres overlap (adjacent links) is valid in
+    free space: only robot-obstacle and robot-robot pairs count."""
+    scene = synth.planar_pair_scene(0)
+    one = synth.Scene([scene.robots[0]], np.zeros((0, 4), np.float32),
+                      np.zeros((0, 15), np.float32))
+    o = orc.OracleScene(one)
+    ok, mc = o.config_valid([0.0, math.pi, 0.0], 0.0)   # folded arm
+    assert ok and mc == np.finfo(float).max
+
+
+# ----------------------------------------------------------------------------
+# edges: interpolation count and verdicts
+# ----------------------------------------------------------------------------
+
+def test_edge_npoints_exact_cases(orc):
+    scene = synth.planar_pair_scene(0)
+    o = orc.OracleScene(scene)
+    z = np.zeros(6, np.float32)
+    assert o.edge_npoints(z, z, 0.02) == 1                       # zero-length edge
+    qb = z.copy(); qb[0], qb[1] = 0.75, 1.0                      # |dq| = 1.25 exactly
+    assert o.edge_npoints(z, qb, 0.25) == 5
+    assert o.edge_npoints(z, qb, 0.5) == 3                       # ceil(2.5)
+    qb = z.copy(); qb[3] = 1e-3
+    assert o.edge_npoints(z, qb, 0.02) == 1
+    rng = np.random.default_rng(8)
+    for _ in range(500):
+        qa = rng.uniform(-3, 3, 6).astype(np.float32)
+        qb = (qa + rng.normal(0, 0.5, 6)).astype(np.float32)
+        n = o.edge_npoints(qa, qb, 0.02)
+        L = np.linalg.norm(qb.astype(float) - qa.astype(float))
+        # spacing never exceeds the resolution (up to FP32 rounding of L)
+        assert n * 0.02 >= L * (1 - 1e-6)
+        assert (n - 1) * 0.02 < L * (1 + 1e-6) or n == 1
+
+
+def test_edge_verdict_vs_dense_bruteforce(orc):
+    """Oracle edge verdict at res against 64x denser sampling with the
+    closed-form planar pipeline: a collision found at res is found densely
+    (the res points are a subset); a valid edge at res with clearance above the
+    largest sphere displacement between samples stays valid densely."""
+    scene = synth.planar_pair_scene(1)
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, 60, seed=3)
+    res = 0.02
+    for e in range(qa.shape[1]):
+        ok, mc, fh, n = o.edge_valid(qa[:, e], qb[:, e], res, 0.0)
+        a, b = qa[:, e].astype(float), qb[:, e].astype(float)
+        nf = 64 * n
+        clear = [_planar_min_clearance(scene, a + (k / nf) * (b - a)) for k in range(nf + 1)]
+        dense_ok = min(clear) >= 0.0
+        coarse = min(clear[::64])
+        assert mc == pytest.approx(coarse, abs=1e-12)
+        if not ok:
+            assert not dense_ok
+            assert clear[64 * fh] < 0 and all(c >= 0 for c in clear[:64 * fh:64])
+        # sphere displacement between coarse samples <= 0.9 m * |dq|/n (lever x angle)
+        step = 0.9 * np.abs(b - a).sum() / n
+        if ok and mc > step:
+            assert dense_ok
+
+
+def test_edge_early_exit_consistent(orc):
+    scene = synth.table_pair_scene(0)
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, 40, seed=4)
+    full = o.validate_edges(qa, qb, 0.02, 1e-4, early_exit=False)
+    fast = o.validate_edges(qa, qb, 0.02, 1e-4, early_exit=True)
+    np.testing.assert_array_equal(full["valid"], fast["valid"])
+    np.testing.assert_array_equal(full["first_hit"], fast["first_hit"])
+    assert 0 < full["valid"].sum() < 40
+
+
+def test_stay_put_robot_constant(orc):
+    """An edge where robot 2 stays put: robot 2's spheres are identical at all
+    points, so its verdict depends on robot 1 only (Prop. 1: stay-put edges)."""
+    scene = synth.table_pair_scene(0)
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(9)
+    qa = synth.uniform_configs(scene, 1, rng)[:, 0]
+    qb = qa.copy()
+    qb[:7] += 0.3
+    n = o.edge_npoints(qa, qb, 0.02)
+    w0 = o.fk_robot(1, qa[7:].astype(float))
+    for k in range(n + 1):
+        qk = qa.astype(float) + (k / n) * (qb.astype(float) - qa.astype(float))
+        np.testing.assert_array_equal(o.fk_robot(1, qk[7:]), w0)
+
+
+# ----------------------------------------------------------------------------
+# nearest / neighbours
+# ----------------------------------------------------------------------------
+
+def _nearest_bruteforce(tree, q, c):
+    D = tree.shape[0] - 1
+    d = np.linalg.norm(tree[:D].astype(float) - q.astype(float)[:, None], axis=0)
+    g = tree[D].astype(float)
+    adm = np.nonzero(g + d < c)[0]
+    if adm.size == 0:
+        return -1
+    order = np.lexsort((adm, g[adm], d[adm]))   # last key is primary
+    return int(adm[order[0]])
+
+
+def test_nearest_vs_bruteforce_with_ties(orc):
+    D = 14
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, 600, lo, hi, seed=1, dup_frac=0.1)
+    qs, cs = synth.nn_queries(D, 300, lo, hi, seed=2, budget_lo=0, budget_hi=25)
+    n_empty = 0
+    for i in range(qs.shape[1]):
+        idx = orc.nearest(tree, qs[:, i], cs[i])[0]
+        assert idx == _nearest_bruteforce(tree, qs[:, i], cs[i])
+        n_empty += idx < 0
+    assert 0 < n_empty < 300
+    # exact duplicates: query at a duplicated configuration -> lowest g, then index
+    dup = np.nonzero(np.all(tree[:D, :, None] == tree[:D, None, :], axis=0).sum(1) > 1)[0]
+    assert dup.size > 0
+    for v in dup[:20]:
+        q = tree[:D, v].copy()
+        same = np.nonzero(np.all(tree[:D] == q[:, None], axis=0))[0]
+        g = tree[D, same]
+        expect = same[np.lexsort((same, g))[0]]
+        assert orc.nearest(tree, q, np.float32(1e9))[0] == expect
+
+
+def test_nearest_unbounded_is_plain_nn(orc):
+    """With c = +inf the filter admits everything: plain nearest neighbour."""
+    D = 7
+    rng = np.random.default_rng(10)
+    tree = np.zeros((D + 1, 2000), np.float32)
+    tree[:D] = rng.uniform(-1, 1, (D, 2000))
+    tree[D] = rng.uniform(0, 5, 2000)
+    kd = cKDTree(tree[:D].T.astype(float))
+    for _ in range(200):
+        q = rng.uniform(-1, 1, D).astype(np.float32)
+        d, i = kd.query(q.astype(float))
+        got, bd, _, _ = orc.nearest(tree, q, np.inf)
+        assert got == i and bd == pytest.approx(d, abs=1e-12)
+
+
+def test_nearest_filter_strict(orc):
+    tree = np.array([[0.0, 1.0], [0.0, 0.0], [1.0, 0.0]], np.float32)  # D=2, g=(1,0)
+    q = np.array([0.0, 0.0], np.float32)
+    # vertex 0: g + d = 1 + 0 = 1; vertex 1: 0 + 1 = 1
+    assert orc.nearest(tree, q, 1.0)[0] == -1          # strict <: neither admitted
+    assert orc.nearest(tree, q, 1.0000001)[0] == 0     # both admitted, 0 is closer
+    tree[2, 0] = 1.5
+    assert orc.nearest(tree, q, 1.2)[0] == 1           # vertex 0 filtered out
+
+
+def test_neighbors_vs_kdtree(orc):
+    D = 7
+    rng = np.random.default_rng(11)
+    tree = np.zeros((D + 1, 3000), np.float32)
+    tree[:D] = rng.uniform(-2.9, 2.9, (D, 3000))
+    kd = cKDTree(tree[:D].T.astype(float))
+    for _ in range(100):
+        q = rng.uniform(-2.9, 2.9, D).astype(np.float32)
+        delta = float(rng.uniform(1.0, 3.0))
+        ref = sorted(kd.query_ball_point(q.astype(float), delta))
+        got, cnt, _ = orc.neighbors(tree, q, np.float32(delta), k_max=32)
+        assert cnt == len(ref)
+        assert list(got) == ref[:32]
+
+
+def test_path_cost(orc):
+    rng = np.random.default_rng(12)
+    a, b = rng.normal(size=14), rng.normal(size=14)
+    ts = np.sort(rng.uniform(0, 1, 10))
+    ts[0], ts[-1] = 0.0, 1.0
+    path = np.stack([a + t * (b - a) for t in ts]).astype(np.float32)
+    L = np.linalg.norm(path[-1].astype(float) - path[0].astype(float))
+    assert orc.path_cost(path) == pytest.approx(L, rel=1e-6)   # collinear: no detour
+    path = rng.normal(size=(7, 5)).astype(np.float32)
+    ref = sum(np.linalg.norm(path[j + 1].astype(float) - path[j].astype(float)) for j in range(6))
+    assert orc.path_cost(path) == pytest.approx(ref, rel=1e-14)
+    assert orc.path_cost(path[:1]) == 0.0
