@@ -1,0 +1,462 @@
+#!/usr/bin/env python3
+"""Throughput of the MR. POP motion-validation hot path on one GB300.
+
+Workload (2 synthetic 7-DOF arms facing each other over a table, 32 cuboids +
+32 spheres, composite 14-DOF; edge resolution 0.02 rad, contact margin 1e-4 m):
+one step is one pass of the whole hot path over one batch of synthetic input:
+
+  1. mrpop_validate_edges   65,536 candidate composite edges (interpolation,
+                            per-robot FK to spheres, sphere-vs-obstacle and
+                            robot-vs-robot tests, early exit)
+  2. mrpop_nearest          65,536 cost-filtered NEAREST queries (one per
+                            candidate edge) over a 16,384-vertex state-cost tree
+  3. mrpop_neighbors        1,024 radius queries (delta = 1.2 rad, k_max = 32)
+                            over a 4,096-vertex 7-DOF per-robot roadmap
+  4. mrpop_path_cost        cost of a 65,537-vertex composite path
+
+metric: edge checks/s = 65,536 / step time (device time, CUDA events, inputs
+resident in HBM, L2 flushed between steps).  All data are synthetic.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank validates its own
+batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+E_EDGES = 65536
+NN_TREE = 16384
+NN_QUERIES = 65536
+RM_VERTS = 4096
+RM_QUERIES = 1024
+RM_DELTA = 1.2
+RM_KMAX = 32
+PATH_M = 65537
+RES = 0.02
+MARGIN = 1e-4
+METRIC = "edge checks/sec"
+UNIT = "edges/s"
+WORKLOAD = "table_pair_14dof_65536_edges"
+
+# FP32 arithmetic per counted unit (FMA = 2 flops; compares and the
+# transcendental sincosf excluded), matching the kernel's formulas.
+FLOPS_PER = {
+    "joint_transform": 51,      # interpolate, add offset, F = T Rz, T = F Tz Tx Rx
+    "bound_test": 10,           # |c - c_o|^2 vs (r + r_o + m)^2
+    "sphere_obstacle_test": 11,
+    "cuboid_test": 31,          # R^T (c - c_b), clamp excess, squared norm
+    "pair_test": 11,
+    "point_transform": 18,      # R p + t
+}
+
+
+def algorithmic_flops(cnt) -> float:
+    c = [int(x) for x in cnt]
+    return (c[1] * FLOPS_PER["joint_transform"]
+            + (c[2] + c[3]) * FLOPS_PER["bound_test"]
+            + c[4] * FLOPS_PER["sphere_obstacle_test"]
+            + c[5] * FLOPS_PER["cuboid_test"]
+            + c[6] * FLOPS_PER["pair_test"]
+            + c[7] * FLOPS_PER["point_transform"])
+
+
+def make_inputs(rank: int):
+    """Seeded synthetic inputs of one step (numpy, host)."""
+    import numpy as np
+
+    from paper_2609_30644_gb300 import synth
+    scene = synth.table_pair_scene(0)
+    qa, qb = synth.candidate_edges(scene, E_EDGES, seed=rank)
+    D = scene.D
+    lo, hi = scene.q_lo, scene.q_hi
+    tree = synth.random_tree_fast(D, NN_TREE, lo, hi, seed=100 + rank)
+    qs, cs = synth.nn_queries(D, NN_QUERIES, lo, hi, seed=200 + rank,
+                              budget_lo=10.0, budget_hi=40.0)
+    r0 = scene.robots[0]
+    roadmap = synth.random_tree_fast(r0.dof, RM_VERTS, r0.q_lo, r0.q_hi, seed=300 + rank)
+    rq, _ = synth.nn_queries(r0.dof, RM_QUERIES, r0.q_lo, r0.q_hi, seed=400 + rank)
+    rng = np.random.default_rng(500 + rank)
+    path = np.ascontiguousarray(
+        rng.uniform(lo, hi, (PATH_M, D)).astype(np.float32))
+    return scene, dict(qa=qa, qb=qb, tree=tree, qs=qs, cs=cs, roadmap=roadmap, rq=rq, path=path)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the oracle as it stands, on the host cores)
+# ---------------------------------------------------------------------------
+
+_WORKER_CACHE = {}
+
+
+def _oracle_chunk(args):
+    """Worker: runs the oracle over one slice of the sampled step and returns
+    the time of the oracle calls alone (inputs are generated once per worker
+    process, outside the timing)."""
+    rank, e_idx, q_idx, r_idx, path_len = args
+    import numpy as np
+
+    import oracle
+    if rank not in _WORKER_CACHE:
+        scene, x = make_inputs(rank)
+        _WORKER_CACHE[rank] = (oracle.OracleScene(scene), x)
+    o, x = _WORKER_CACHE[rank]
+    t0 = time.perf_counter()
+    qa = np.ascontiguousarray(x["qa"][:, e_idx])
+    qb = np.ascontiguousarray(x["qb"][:, e_idx])
+    o.validate_edges(qa, qb, RES, MARGIN, early_exit=True)
+    for i in q_idx:
+        oracle.nearest(x["tree"], x["qs"][:, i], x["cs"][i])
+    for i in r_idx:
+        oracle.neighbors(x["roadmap"], x["rq"][:, i], RM_DELTA, RM_KMAX)
+    if path_len > 1:
+        oracle.path_cost(x["path"][:path_len])
+    return time.perf_counter() - t0
+
+
+def oracle_sample(n_edges: int, workers: int, rank: int = 0):
+    """Times the oracle on a bounded sample of the step with the same
+    per-edge composition (1 nearest query per edge, 1 radius query per 64
+    edges, path vertices = edges + 1), spread over ``workers`` processes."""
+    import multiprocessing as mpr
+
+    import numpy as np
+    stride = max(1, E_EDGES // n_edges)
+    e_all = np.arange(0, stride * n_edges, stride)[:n_edges]
+    q_all = e_all.copy()
+    r_all = np.arange(0, RM_QUERIES, max(1, RM_QUERIES // max(1, n_edges // 64)))[:max(1, n_edges // 64)]
+    chunks = []
+    for w in range(workers):
+        chunks.append((rank, e_all[w::workers], q_all[w::workers], r_all[w::workers],
+                       (n_edges + 1) if w == 0 else 0))
+    ctx = mpr.get_context("spawn")
+    import oracle
+    oracle.build()
+    with ctx.Pool(workers) as pool:
+        # warm every worker (input generation), then time the slices; the
+        # slices run concurrently, one per process, so the step takes as long
+        # as the slowest slice
+        pool.map(_oracle_chunk, [(rank, e_all[:1], q_all[:1], r_all[:1], 2)] * (4 * workers),
+                 chunksize=1)
+        times = pool.map(_oracle_chunk, chunks, chunksize=1)
+    wall = max(times)
+    return n_edges / wall, wall
+
+
+def run_reference(args) -> None:
+    """--impl reference: the FP64 oracle (this method's only reference
+    implementation) timed on the host cores, on the same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    workers = os.cpu_count() or 1
+    n = max(64, 16 * workers)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(min(n, 64), workers)
+    walls = []
+    for _ in range(args.steps):
+        v, w = oracle_sample(n, workers)
+        vals.append(v)
+        walls.append(w)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.median(walls), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "edges_per_step_sample": n, "res_rad": RES,
+                   "margin_m": MARGIN},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": f"{n} edges (+{n} nearest queries over {NN_TREE} vertices, "
+                                   f"{max(1, n // 64)} radius queries, {n + 1}-vertex path "
+                                   f"cost) of the {E_EDGES}-edge batch per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200", "-f", self.path]
+            if self.uuid:
+                cmd.insert(1, f"--id={self.uuid}")
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx),
+                       reasons=sorted(reasons), samples=len(sm))
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args) -> None:
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = os.cpu_count() or 1
+        n = 256 * workers
+        v, wall = oracle_sample(n, workers)
+        cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": f"{n} edges (every {E_EDGES // n}th of the batch) with {n} nearest "
+                         f"queries over {NN_TREE} vertices, {n // 64} radius queries and a "
+                         f"{n + 1}-vertex path cost; {wall:.1f} s wall on {workers} processes"}
+
+    import numpy as np
+    import torch
+
+    import paper_2609_30644_gb300 as mp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    scene, x = make_inputs(rank)
+    prob = mp.Problem(scene, resolution=RES, margin=MARGIN)
+    g = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in x.items()}
+    valid = torch.empty(E_EDGES, dtype=torch.uint8, device=dev)
+    nn_out = torch.empty(NN_QUERIES, dtype=torch.int64, device=dev)
+    cost = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(inp, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        mp.validate_edges(prob, inp["qa"], inp["qb"], valid)
+        if ev is not None:
+            ev[1].record(stream)
+        mp.nearest(g["tree"], inp["qs"], inp["cs"], out=nn_out)
+        if ev is not None:
+            ev[2].record(stream)
+        idx, cnt = mp.neighbors(g["roadmap"], inp["rq"], RM_DELTA, RM_KMAX, dim=scene.robots[0].dof)
+        if ev is not None:
+            ev[3].record(stream)
+        mp.path_cost(inp["path"], out=cost)
+        if ev is not None:
+            ev[4].record(stream)
+        return idx, cnt
+
+    # algorithmic work of the validation launch on this batch (untimed)
+    counters = mp.validate_work(prob, g["qa"], g["qb"]).cpu().numpy()
+    flops_per_launch = algorithmic_flops(counters)
+
+    for _ in range(max(args.warmup, 0)):
+        step(g)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flush (256 MB > 129 MB L2), untimed
+        step(g, evs[i])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    val_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    nn_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    rm_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    pc_ms = [e[3].elapsed_time(e[4]) for e in evs]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * E_EDGES / (ms_per_step / 1000.0)
+
+    # ---- end to end through the public API with host buffers -------------
+    pin = {k: torch.from_numpy(np.ascontiguousarray(x[k])).pin_memory()
+           for k in ("qa", "qb", "qs", "cs", "rq", "path")}
+    h_valid = torch.empty(E_EDGES, dtype=torch.uint8).pin_memory()
+    h_nn = torch.empty(NN_QUERIES, dtype=torch.int64).pin_memory()
+    h_idx = torch.empty((RM_QUERIES, RM_KMAX), dtype=torch.int64).pin_memory()
+    h_cnt = torch.empty(RM_QUERIES, dtype=torch.int64).pin_memory()
+    h_cost = torch.empty(1, dtype=torch.float64).pin_memory()
+    d_in = {k: torch.empty_like(v, device=dev) for k, v in pin.items()}
+    h2d = sum(v.numel() * v.element_size() for v in pin.values())
+    d2h = sum(t.numel() * t.element_size() for t in (h_valid, h_nn, h_idx, h_cnt, h_cost))
+
+    def e2e_step():
+        for k, v in pin.items():
+            d_in[k].copy_(v, non_blocking=True)
+        idx, cnt = step(d_in)
+        h_valid.copy_(valid, non_blocking=True)
+        h_nn.copy_(nn_out, non_blocking=True)
+        h_idx.copy_(idx, non_blocking=True)
+        h_cnt.copy_(cnt, non_blocking=True)
+        h_cost.copy_(cost, non_blocking=True)
+
+    for _ in range(max(args.warmup, 1)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = float(sum(e2e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * E_EDGES / (e2e_total / args.steps / 1000.0)
+
+    # sanity: the e2e results equal the resident-input results
+    assert torch.equal(h_valid, valid.cpu())
+
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        peaks = measured_peaks()
+        sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+        peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        val_avg_s = statistics.mean(val_ms) / 1000.0
+        achieved = flops_per_launch / val_avg_s / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "edges": E_EDGES, "robots": 2, "dof": scene.D,
+                       "obstacles": "32 cuboids + 32 spheres", "res_rad": RES,
+                       "margin_m": MARGIN, "nearest": f"{NN_QUERIES} queries x {NN_TREE} vertices",
+                       "neighbors": f"{RM_QUERIES} queries x {RM_VERTS} vertices, 7-DOF",
+                       "path_vertices": PATH_M, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "kernel": "validate_kernel",
+                         "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": None,
+                         "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x "
+                                        f"2 flop x {sm_max:.0f} MHz",
+                         "flops_per_launch": flops_per_launch},
+            "kernel_ms": {"validate": statistics.mean(val_ms), "nearest": statistics.mean(nn_ms),
+                          "neighbors": statistics.mean(rm_ms), "path_cost": statistics.mean(pc_ms)},
+            "valid_fraction": float(valid.float().mean().item()),
+            "work_counters": [int(c) for c in counters],
+            "nearest_queries_per_s": NN_QUERIES / (statistics.mean(nn_ms) / 1000.0),
+            "wall_s_timed_loop": t_wall,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 4 * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

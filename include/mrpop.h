@@ -1,0 +1,207 @@
+/*
+ * mrpop.h -- C ABI of the GB300 motion-validation library for MR. POP
+ * (multi-robot parallel optimizing planner, dRRT + AO-x).
+ *
+ * The library implements the data-parallel hot path of the planner:
+ * interpolation of composite edges, forward kinematics of serial arms to
+ * collision-sphere sets, sphere-vs-obstacle and robot-vs-robot sphere tests
+ * with early exit, cost-filtered nearest-neighbour and radius queries over
+ * state-cost trees, and path cost.
+ *
+ * Conventions for every call
+ *   - Every call returns an mrpop_status and never aborts; on failure a
+ *     message is available from mrpop_last_error() (thread-local).
+ *   - "device" pointers are CUDA global-memory pointers on the current device
+ *     (for example from torch tensors); "host" pointers are CPU memory.  The
+ *     caller owns every buffer it passes and keeps it alive until the work on
+ *     the given stream has completed.
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Kernels
+ *     are enqueued asynchronously on it; outputs are valid once the stream
+ *     reaches that point.
+ *   - Composite configurations q = (q^1, ..., q^K) concatenate the robots'
+ *     joint vectors in robot order (Sec. III-A); D = sum of the robots' dof.
+ *     Batches are SoA float32 [D][n]: element (i, e) at ptr[i * n + e].
+ *   - A problem handle owns device copies of its robots and obstacles; it may
+ *     be used from one host thread at a time.
+ */
+#ifndef MRPOP_H
+#define MRPOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MRPOP_OK = 0,
+    MRPOP_EINVAL = 1,      /* an argument is out of range or inconsistent      */
+    MRPOP_ENOMEM = 2,      /* a host or device allocation failed               */
+    MRPOP_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed      */
+    MRPOP_ECAPACITY = 4,   /* a tree, roadmap or path buffer is full           */
+    MRPOP_ETIMEOUT = 5,    /* a bounded device wait gave up                    */
+    MRPOP_ENOSOLUTION = 6, /* no path was found within the budget             */
+    MRPOP_EBUSY = 7        /* the object is in use by another request          */
+} mrpop_status;
+
+/* Limits checked by mrpop_create_problem. */
+#define MRPOP_MAX_ROBOTS 16
+#define MRPOP_MAX_DOF 16             /* joints per robot                     */
+#define MRPOP_MAX_LINKS 64           /* sum of dof over robots (= max D)     */
+#define MRPOP_MAX_SPHERES_PER_LINK 16
+#define MRPOP_MAX_OBSTACLES 1024     /* spheres + cuboids                    */
+/* Edges needing more interpolation intervals than this (|qb - qa| >
+ * MRPOP_MAX_EDGE_INTERVALS * resolution), or with non-finite coordinates, are
+ * reported invalid without being checked. */
+#define MRPOP_MAX_EDGE_INTERVALS (1 << 20)
+
+typedef struct mrpop_problem mrpop_problem; /* opaque, library-owned */
+
+/* A serial arm of revolute joints with standard DH rows (Sec. III-E: robots
+ * are approximated by collision spheres attached to their links).
+ *   dh          host [dof][4]  a, alpha, d, theta_offset of each joint
+ *   q_lo, q_hi  host [dof]     joint limits (rad)
+ *   sphere_link host [n_spheres] link (joint) index of each sphere,
+ *               non-decreasing; at most MRPOP_MAX_SPHERES_PER_LINK per link
+ *   sphere_xyzr host [n_spheres][4] centre in frame F_j' (joint j's frame
+ *               after its rotation Rz(q_j + theta_offset_j)) and radius
+ *   base        row-major 3x4 [R | t] pose of the first joint's frame.
+ * The frame after joint j is F_j' * Tz(d_j) * Tx(a_j) * Rx(alpha_j). */
+typedef struct {
+    int32_t dof;
+    int32_t n_spheres;
+    const float *dh;
+    const float *q_lo;
+    const float *q_hi;
+    const int32_t *sphere_link;
+    const float *sphere_xyzr;
+    float base[12];
+} mrpop_robot;
+
+/* Obstacles (host arrays): spheres [n][4] = cx, cy, cz, r; cuboids [n][15] =
+ * centre c[3], half extents h[3], R[9] row-major whose columns are the box
+ * axes in the world frame. */
+typedef struct {
+    int32_t n_spheres;
+    const float *spheres;
+    int32_t n_cuboids;
+    const float *cuboids;
+} mrpop_obstacles;
+
+/* Planner and checker parameters.
+ *   resolution   edge discretisation step (rad); an edge qa->qb is checked at
+ *                q_k = qa + (k/n)(qb - qa), k = 0..n, n = max(1, ceil(|qb-qa|_2
+ *                / resolution)) computed in FP32 (Sec. III-E discretisation)
+ *   margin       contact inflation (m): a pair is in contact when its centre
+ *                distance is below r1 + r2 + margin
+ *   delta        per-robot roadmap connection radius (rad) (Sec. III-A)
+ *   n_per_round  roadmap samples per robot per ROADMAP call (Alg. 2)
+ *   tree_cap, roadmap_cap   vertex capacities of planner trees / roadmaps
+ *   max_iters    planner iteration cap per search call
+ *   seed         planner random seed */
+typedef struct {
+    float resolution;
+    float margin;
+    float delta;
+    int32_t n_per_round;
+    int64_t tree_cap;
+    int64_t roadmap_cap;
+    int64_t max_iters;
+    uint64_t seed;
+} mrpop_config;
+
+/* Message of the last failed call on this thread ("" when none). */
+const char *mrpop_last_error(void);
+
+/* Creates a problem (Sec. III-A problem setup: K robots, obstacles, q_start,
+ * q_goal).  robots: host [K]; obs: host; start, goal: host [D] (may be NULL
+ * when only the primitives are used); cfg: host.  Copies every table to the
+ * current CUDA device; the handle owns those copies.  Errors: EINVAL when a
+ * limit above is exceeded or a table is malformed; ENOMEM / ECUDA from the
+ * device copies. */
+mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t K,
+                                  const mrpop_obstacles *obs, const float *start,
+                                  const float *goal, const mrpop_config *cfg,
+                                  mrpop_problem **out);
+
+/* Releases the handle and its device memory after synchronising the device
+ * work that may still use it.  NULL is accepted. */
+mrpop_status mrpop_destroy_problem(mrpop_problem *p);
+
+/* Composite dimension D, robot count K and total sphere count S. */
+mrpop_status mrpop_problem_dims(const mrpop_problem *p, int32_t *D, int32_t *K,
+                                int32_t *S);
+
+/* Forward kinematics (Sec. III-E FK tracing) of n composite configurations
+ * q (device SoA [D][n]) to world sphere centres out (device [3][S][n]:
+ * coordinate c of sphere s of configuration i at out[(c * S + s) * n + i]).
+ * Spheres are ordered by robot, then as given. */
+mrpop_status mrpop_fk(mrpop_problem *p, const float *q, int64_t n, float *out,
+                      void *cuda_stream);
+
+/* Motion validation of n_edges composite edges (Alg. 2: (q_near, q_new) in
+ * C^f; Sec. III-E two-stage check).  qa, qb: device SoA [D][n_edges].
+ * valid: device uint8 [n_edges], 1 when every interpolated configuration is
+ * free of robot-obstacle and robot-robot contact, else 0.  Work stops for an
+ * edge at its first colliding checkpoint tile. */
+mrpop_status mrpop_validate_edges(mrpop_problem *p, const float *qa, const float *qb,
+                                  int64_t n_edges, uint8_t *valid, void *cuda_stream);
+
+/* Same check with optional by-products (NULL to skip):
+ *   length   device float [n_edges]  |qb - qa|_2 (FP32), the edge cost
+ *   npoints  device int32 [n_edges]  interval count n of each edge */
+mrpop_status mrpop_validate_edges_ex(mrpop_problem *p, const float *qa, const float *qb,
+                                     int64_t n_edges, uint8_t *valid, float *length,
+                                     int32_t *npoints, void *cuda_stream);
+
+/* Minimum signed clearance (surface distance minus margin-free radii) over
+ * every checkpoint and every tested pair of each edge, without culling or
+ * early exit: device float [n_edges].  A diagnostic for distance parity; the
+ * edge is valid exactly when this is >= margin. */
+mrpop_status mrpop_edge_clearance(mrpop_problem *p, const float *qa, const float *qb,
+                                  int64_t n_edges, float *min_clear, void *cuda_stream);
+
+/* Work counters of mrpop_validate_edges on the same inputs, summed over the
+ * batch, for roofline accounting (device int64 [8], overwritten):
+ *   [0] checkpoints evaluated        [1] joint transforms
+ *   [2] link-vs-obstacle bound tests [3] link-vs-link bound tests
+ *   [4] sphere-vs-sphere-obstacle tests  [5] sphere-vs-cuboid tests
+ *   [6] robot-robot sphere-pair tests    [7] point transforms (coarse centres
+ *       and sphere centres)
+ * Counts are per checkpoint: a sphere-level test is counted only where that
+ * checkpoint's own link-level test hit (the kernel may run more, warp-wide). */
+mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, const float *qb,
+                                 int64_t n_edges, int64_t *counters, void *cuda_stream);
+
+/* NEAREST(V, q, c) of Alg. 2 for n_queries queries: among tree vertices with
+ * g_v + |q - q_v| < c, the one closest to q; ties go to the lowest g, then the
+ * lowest index (Sec. III-D); -1 when no vertex qualifies.
+ *   tree      device SoA [dim+1][ld]: rows 0..dim-1 configuration, row dim g
+ *   n_vertices  vertices 0..n_vertices-1 are scanned (n_vertices <= ld)
+ *   queries   device SoA [dim][n_queries];  budgets device float [n_queries]
+ *   out_idx   device int64 [n_queries]
+ * dim <= MRPOP_MAX_LINKS.  Distances are FP32. */
+mrpop_status mrpop_nearest(const float *tree, int64_t n_vertices, int64_t ld, int32_t dim,
+                           const float *queries, const float *budgets, int64_t n_queries,
+                           int64_t *out_idx, void *cuda_stream);
+
+/* NEIGHBORS(V, q, delta) of Alg. 2: indices of the vertices with |q - q_v| <=
+ * delta, in ascending index order.  The first k_max of them go to
+ * out_idx[i * k_max + j] (device int64 [n_queries][k_max], unused slots -1);
+ * out_cnt (device int64 [n_queries]) receives the full count, which may exceed
+ * k_max.  tree rows 0..dim-1 are read (a g row, if any, is ignored). */
+mrpop_status mrpop_neighbors(const float *tree, int64_t n_vertices, int64_t ld, int32_t dim,
+                             const float *queries, int64_t n_queries, float delta,
+                             int64_t k_max, int64_t *out_idx, int64_t *out_cnt,
+                             void *cuda_stream);
+
+/* C(sigma) = sum_j |q_{j+1} - q_j| (Sec. III-A) of a path of M vertices
+ * (device [M][dim], row-major per vertex), segment lengths in FP32 summed in
+ * FP64, written to cost_out (device double [1]). */
+mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim, double *cost_out,
+                             void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRPOP_H */

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 from typing import Optional
@@ -21,7 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrpop_oracle.c")
 _HDR = os.path.join(_HERE, "mrpop_oracle.h")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_LIB = os.path.join(_HERE, f"liboracle.{platform.machine()}.so")
 _lock = threading.Lock()
 _lib = None
 

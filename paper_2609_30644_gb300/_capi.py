@@ -1,0 +1,280 @@
+"""ctypes binding of libmrpop.so with the C ABI's names.
+
+Argument marshalling only: tensors must already live on the right device with
+the right dtype and layout; this module checks that and passes raw pointers
+and the current torch stream to the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libmrpop.so")
+
+# Every symbol declared in include/mrpop.h.
+EXPORTS = (
+    "mrpop_last_error",
+    "mrpop_create_problem",
+    "mrpop_destroy_problem",
+    "mrpop_problem_dims",
+    "mrpop_fk",
+    "mrpop_validate_edges",
+    "mrpop_validate_edges_ex",
+    "mrpop_edge_clearance",
+    "mrpop_validate_work",
+    "mrpop_nearest",
+    "mrpop_neighbors",
+    "mrpop_path_cost",
+)
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
+          6: "ENOSOLUTION", 7: "EBUSY"}
+
+
+class MrpopError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mrpop {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Robot(C.Structure):
+    _fields_ = [("dof", C.c_int32), ("n_spheres", C.c_int32), ("dh", C.c_void_p),
+                ("q_lo", C.c_void_p), ("q_hi", C.c_void_p), ("sphere_link", C.c_void_p),
+                ("sphere_xyzr", C.c_void_p), ("base", C.c_float * 12)]
+
+
+class _Obstacles(C.Structure):
+    _fields_ = [("n_spheres", C.c_int32), ("spheres", C.c_void_p),
+                ("n_cuboids", C.c_int32), ("cuboids", C.c_void_p)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("resolution", C.c_float), ("margin", C.c_float), ("delta", C.c_float),
+                ("n_per_round", C.c_int32), ("tree_cap", C.c_int64),
+                ("roadmap_cap", C.c_int64), ("max_iters", C.c_int64), ("seed", C.c_uint64)]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(library_path):
+        raise ImportError(
+            f"{library_path} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a). "
+            "There is no CPU fallback.")
+    L = C.CDLL(library_path)
+    vp, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+    sig = {
+        "mrpop_last_error": (C.c_char_p, []),
+        "mrpop_create_problem": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+        "mrpop_destroy_problem": (i32, [vp]),
+        "mrpop_problem_dims": (i32, [vp, vp, vp, vp]),
+        "mrpop_fk": (i32, [vp, vp, i64, vp, vp]),
+        "mrpop_validate_edges": (i32, [vp, vp, vp, i64, vp, vp]),
+        "mrpop_validate_edges_ex": (i32, [vp, vp, vp, i64, vp, vp, vp, vp]),
+        "mrpop_edge_clearance": (i32, [vp, vp, vp, i64, vp, vp]),
+        "mrpop_validate_work": (i32, [vp, vp, vp, i64, vp, vp]),
+        "mrpop_nearest": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
+        "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
+        "mrpop_path_cost": (i32, [vp, i64, i32, vp, vp]),
+    }
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        fn.restype, fn.argtypes = sig[name]
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise MrpopError(status, lib.mrpop_last_error().decode())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dptr(t: Optional[torch.Tensor], dtype: torch.dtype, name: str) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _host(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Problem:
+    """Owns an ``mrpop_problem`` handle built from a ``synth.Scene``-like
+    object (robots with dh/q_lo/q_hi/sphere_link/sphere_xyzr/base, and
+    obs_spheres/obs_cuboids) on the current CUDA device."""
+
+    def __init__(self, scene, resolution: float = 0.02, margin: float = 0.0,
+                 delta: float = 1.0, n_per_round: int = 64, tree_cap: int = 1 << 16,
+                 roadmap_cap: int = 1 << 14, max_iters: int = 4096, seed: int = 0,
+                 start: Optional[Sequence[float]] = None,
+                 goal: Optional[Sequence[float]] = None):
+        keep = []
+        robots = (_Robot * len(scene.robots))()
+        for i, r in enumerate(scene.robots):
+            arrs = [_host(r.dh, np.float32), _host(r.q_lo, np.float32),
+                    _host(r.q_hi, np.float32), _host(r.sphere_link, np.int32),
+                    _host(r.sphere_xyzr, np.float32)]
+            keep += arrs
+            robots[i].dof = int(r.dof)
+            robots[i].n_spheres = int(len(r.sphere_link))
+            robots[i].dh, robots[i].q_lo, robots[i].q_hi = (a.ctypes.data for a in arrs[:3])
+            robots[i].sphere_link, robots[i].sphere_xyzr = arrs[3].ctypes.data, arrs[4].ctypes.data
+            for j, v in enumerate(np.asarray(r.base, dtype=np.float32).reshape(12)):
+                robots[i].base[j] = float(v)
+        osph = _host(np.asarray(scene.obs_spheres).reshape(-1, 4), np.float32)
+        ocub = _host(np.asarray(scene.obs_cuboids).reshape(-1, 15), np.float32)
+        keep += [osph, ocub]
+        obs = _Obstacles(osph.shape[0], osph.ctypes.data if osph.size else None,
+                         ocub.shape[0], ocub.ctypes.data if ocub.size else None)
+        cfg = _Config(resolution, margin, delta, n_per_round, tree_cap, roadmap_cap,
+                      max_iters, seed)
+        st = _host(start, np.float32) if start is not None else None
+        gl = _host(goal, np.float32) if goal is not None else None
+        keep += [a for a in (st, gl) if a is not None]
+        h = C.c_void_p()
+        _check(lib.mrpop_create_problem(robots, len(scene.robots), C.byref(obs),
+                                        st.ctypes.data if st is not None else None,
+                                        gl.ctypes.data if gl is not None else None,
+                                        C.byref(cfg), C.byref(h)))
+        self._h = h
+        D, K, S = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib.mrpop_problem_dims(h, C.byref(D), C.byref(K), C.byref(S)))
+        self.D, self.K, self.S = D.value, K.value, S.value
+        self.resolution, self.margin = resolution, margin
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise ValueError("problem destroyed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            lib.mrpop_destroy_problem(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _edges(p: Problem, qa: torch.Tensor, qb: torch.Tensor) -> int:
+    if qa.shape != qb.shape or qa.dim() != 2 or qa.shape[0] != p.D:
+        raise ValueError(f"qa, qb must both be [D={p.D}, n]")
+    return int(qa.shape[1])
+
+
+def fk(p: Problem, q: torch.Tensor, out: Optional[torch.Tensor] = None,
+       stream=None) -> torch.Tensor:
+    """World sphere centres [3, S, n] of configurations q [D, n]."""
+    n = int(q.shape[1])
+    if out is None:
+        out = torch.empty((3, p.S, n), dtype=torch.float32, device=q.device)
+    _check(lib.mrpop_fk(p.handle, _dptr(q, torch.float32, "q"), n,
+                        _dptr(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def validate_edges(p: Problem, qa: torch.Tensor, qb: torch.Tensor,
+                   valid: Optional[torch.Tensor] = None, length: Optional[torch.Tensor] = None,
+                   npoints: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    n = _edges(p, qa, qb)
+    if valid is None:
+        valid = torch.empty(n, dtype=torch.uint8, device=qa.device)
+    _check(lib.mrpop_validate_edges_ex(
+        p.handle, _dptr(qa, torch.float32, "qa"), _dptr(qb, torch.float32, "qb"), n,
+        _dptr(valid, torch.uint8, "valid"), _dptr(length, torch.float32, "length"),
+        _dptr(npoints, torch.int32, "npoints"), _stream(stream)))
+    return valid
+
+
+def edge_clearance(p: Problem, qa: torch.Tensor, qb: torch.Tensor,
+                   out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    n = _edges(p, qa, qb)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=qa.device)
+    _check(lib.mrpop_edge_clearance(p.handle, _dptr(qa, torch.float32, "qa"),
+                                    _dptr(qb, torch.float32, "qb"), n,
+                                    _dptr(out, torch.float32, "min_clear"), _stream(stream)))
+    return out
+
+
+def validate_work(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -> torch.Tensor:
+    n = _edges(p, qa, qb)
+    out = torch.zeros(8, dtype=torch.int64, device=qa.device)
+    _check(lib.mrpop_validate_work(p.handle, _dptr(qa, torch.float32, "qa"),
+                                   _dptr(qb, torch.float32, "qb"), n,
+                                   _dptr(out, torch.int64, "counters"), _stream(stream)))
+    return out
+
+
+def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
+            n_vertices: Optional[int] = None, out: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+    """tree [dim+1, ld] (row dim = g), queries [dim, Q], budgets [Q] -> int64 [Q]."""
+    dim = int(tree.shape[0]) - 1
+    ld = int(tree.shape[1])
+    N = ld if n_vertices is None else int(n_vertices)
+    Q = int(queries.shape[1])
+    if queries.shape[0] != dim or budgets.shape != (Q,):
+        raise ValueError("queries must be [dim, Q] and budgets [Q]")
+    if out is None:
+        out = torch.empty(Q, dtype=torch.int64, device=queries.device)
+    _check(lib.mrpop_nearest(_dptr(tree, torch.float32, "tree"), N, ld, dim,
+                             _dptr(queries, torch.float32, "queries"),
+                             _dptr(budgets, torch.float32, "budgets"), Q,
+                             _dptr(out, torch.int64, "out_idx"), _stream(stream)))
+    return out
+
+
+def neighbors(tree: torch.Tensor, queries: torch.Tensor, delta: float, k_max: int,
+              dim: Optional[int] = None, n_vertices: Optional[int] = None,
+              stream=None) -> tuple:
+    """Radius query: returns (idx [Q, k_max] int64 with -1 padding, count [Q])."""
+    dim = int(queries.shape[0]) if dim is None else dim
+    ld = int(tree.shape[1])
+    N = ld if n_vertices is None else int(n_vertices)
+    Q = int(queries.shape[1])
+    idx = torch.empty((Q, k_max), dtype=torch.int64, device=queries.device)
+    cnt = torch.empty(Q, dtype=torch.int64, device=queries.device)
+    _check(lib.mrpop_neighbors(_dptr(tree, torch.float32, "tree"), N, ld, dim,
+                               _dptr(queries, torch.float32, "queries"), Q, float(delta),
+                               k_max, _dptr(idx, torch.int64, "out_idx") if k_max else None,
+                               _dptr(cnt, torch.int64, "out_cnt"), _stream(stream)))
+    return idx, cnt
+
+
+def path_cost(path: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """C(sigma) of a path [M, dim] -> float64 tensor [1] on the device."""
+    M, dim = int(path.shape[0]), int(path.shape[1])
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=path.device)
+    _check(lib.mrpop_path_cost(_dptr(path, torch.float32, "path"), M, dim,
+                               _dptr(out, torch.float64, "cost"), _stream(stream)))
+    return out

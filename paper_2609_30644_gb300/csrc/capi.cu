@@ -1,0 +1,361 @@
+// C ABI entry points: problem creation (geometry tables), argument checking
+// and dispatch to the kernel launchers.  Every entry point returns a status
+// and records a message for mrpop_last_error(); nothing here aborts.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mrpop_internal.cuh"
+
+namespace mrpop {
+
+static thread_local char g_err[512] = "";
+
+mrpop_status set_error(mrpop_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+mrpop_status cuda_error(cudaError_t e, const char *what) {
+    return set_error(e == cudaErrorMemoryAllocation ? MRPOP_ENOMEM : MRPOP_ECUDA,
+                     "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static bool finite_all(const float *v, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+static float f_of_i(int v) {
+    float f;
+    std::memcpy(&f, &v, sizeof(f));
+    return f;
+}
+
+}  // namespace mrpop
+
+using namespace mrpop;
+
+extern "C" const char *mrpop_last_error(void) { return g_err; }
+
+// Coarse sphere of one link, in the link frame F_j': centre at the midpoint of
+// the axis-aligned box around the link's fine spheres, radius the largest
+// |centre - c_s| + r_s plus a slack that absorbs FP32 rounding of both the
+// coarse and the fine sphere positions (coarse culling never changes a
+// verdict, Sec. III-E two-stage check).
+static void coarse_sphere(const float *xyzr, int n, float out[4]) {
+    if (n == 0) {
+        out[0] = out[1] = out[2] = 0.f;
+        out[3] = 0.f;
+        return;
+    }
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int s = 0; s < n; ++s)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::fmin(lo[a], (double)xyzr[4 * s + a] - xyzr[4 * s + 3]);
+            hi[a] = std::fmax(hi[a], (double)xyzr[4 * s + a] + xyzr[4 * s + 3]);
+        }
+    double c[3], r = 0.0;
+    for (int a = 0; a < 3; ++a) c[a] = 0.5 * (lo[a] + hi[a]);
+    for (int s = 0; s < n; ++s) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = (double)xyzr[4 * s + a] - c[a];
+            d2 += d * d;
+        }
+        r = std::fmax(r, std::sqrt(d2) + xyzr[4 * s + 3]);
+    }
+    for (int a = 0; a < 3; ++a) out[a] = (float)c[a];
+    out[3] = (float)(r + 1e-4);
+}
+
+extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t K,
+                                             const mrpop_obstacles *obs, const float *start,
+                                             const float *goal, const mrpop_config *cfg,
+                                             mrpop_problem **out) {
+    if (!out) return set_error(MRPOP_EINVAL, "mrpop_create_problem: out is NULL");
+    *out = nullptr;
+    if (!robots || !obs || !cfg)
+        return set_error(MRPOP_EINVAL, "mrpop_create_problem: robots, obs and cfg are required");
+    if (K < 1 || K > MRPOP_MAX_ROBOTS)
+        return set_error(MRPOP_EINVAL, "K=%d outside [1, %d]", K, MRPOP_MAX_ROBOTS);
+    if (!(cfg->resolution > 0.f) || !std::isfinite(cfg->resolution))
+        return set_error(MRPOP_EINVAL, "resolution must be positive and finite");
+    if (!(cfg->margin >= 0.f) || !std::isfinite(cfg->margin))
+        return set_error(MRPOP_EINVAL, "margin must be >= 0 and finite");
+
+    Tables t;
+    t.K = K;
+    int L = 0, S = 0;
+    for (int k = 0; k < K; ++k) {
+        const mrpop_robot &r = robots[k];
+        if (r.dof < 1 || r.dof > MRPOP_MAX_DOF)
+            return set_error(MRPOP_EINVAL, "robot %d: dof=%d outside [1, %d]", k, r.dof,
+                             MRPOP_MAX_DOF);
+        if (r.n_spheres < 0) return set_error(MRPOP_EINVAL, "robot %d: n_spheres < 0", k);
+        if (!r.dh || !r.q_lo || !r.q_hi || (r.n_spheres > 0 && (!r.sphere_link || !r.sphere_xyzr)))
+            return set_error(MRPOP_EINVAL, "robot %d: missing table pointer", k);
+        if (!finite_all(r.dh, 4 * r.dof) || !finite_all(r.q_lo, r.dof) ||
+            !finite_all(r.q_hi, r.dof) || !finite_all(r.base, 12) ||
+            (r.n_spheres > 0 && !finite_all(r.sphere_xyzr, 4 * (int64_t)r.n_spheres)))
+            return set_error(MRPOP_EINVAL, "robot %d: non-finite table entry", k);
+        for (int j = 0; j < r.dof; ++j)
+            if (!(r.q_lo[j] <= r.q_hi[j]))
+                return set_error(MRPOP_EINVAL, "robot %d joint %d: q_lo > q_hi", k, j);
+        int prev = 0;
+        for (int s = 0; s < r.n_spheres; ++s) {
+            const int l = r.sphere_link[s];
+            if (l < prev || l >= r.dof)
+                return set_error(MRPOP_EINVAL,
+                                 "robot %d sphere %d: link %d not non-decreasing in [0, %d)",
+                                 k, s, l, r.dof);
+            if (r.sphere_xyzr[4 * s + 3] < 0.f)
+                return set_error(MRPOP_EINVAL, "robot %d sphere %d: negative radius", k, s);
+            prev = l;
+        }
+        t.link0[k] = L;
+        L += r.dof;
+        S += r.n_spheres;
+    }
+    if (L > MRPOP_MAX_LINKS)
+        return set_error(MRPOP_EINVAL, "total dof %d exceeds %d", L, MRPOP_MAX_LINKS);
+    t.link0[K] = L;
+    t.L = L;
+    t.S = S;
+    if (obs->n_spheres < 0 || obs->n_cuboids < 0 ||
+        obs->n_spheres + (int64_t)obs->n_cuboids > MRPOP_MAX_OBSTACLES)
+        return set_error(MRPOP_EINVAL, "obstacle counts (%d spheres, %d cuboids) outside [0, %d]",
+                         obs->n_spheres, obs->n_cuboids, MRPOP_MAX_OBSTACLES);
+    if ((obs->n_spheres > 0 && !obs->spheres) || (obs->n_cuboids > 0 && !obs->cuboids))
+        return set_error(MRPOP_EINVAL, "missing obstacle table pointer");
+    if ((obs->n_spheres > 0 && !finite_all(obs->spheres, 4 * (int64_t)obs->n_spheres)) ||
+        (obs->n_cuboids > 0 && !finite_all(obs->cuboids, 15 * (int64_t)obs->n_cuboids)))
+        return set_error(MRPOP_EINVAL, "non-finite obstacle entry");
+    for (int o = 0; o < obs->n_spheres; ++o)
+        if (obs->spheres[4 * o + 3] < 0.f)
+            return set_error(MRPOP_EINVAL, "obstacle sphere %d: negative radius", o);
+    for (int o = 0; o < obs->n_cuboids; ++o)
+        for (int a = 0; a < 3; ++a)
+            if (obs->cuboids[15 * o + 3 + a] < 0.f)
+                return set_error(MRPOP_EINVAL, "cuboid %d: negative half extent", o);
+    t.NS = obs->n_spheres;
+    t.NC = obs->n_cuboids;
+
+    // --- pack the blob ---------------------------------------------------
+    t.off_base = 0;
+    t.off_link = t.off_base + 3 * K;
+    t.off_sph = t.off_link + kLinkF4 * L;
+    t.off_os = t.off_sph + S;
+    t.off_oc = t.off_os + t.NS;
+    t.n_f4 = t.off_oc + kCuboidF4 * t.NC;
+    std::vector<float> blob(4 * (size_t)t.n_f4, 0.f);
+    auto f4 = [&](int i) { return blob.data() + 4 * (size_t)i; };
+    int s_glob = 0;
+    for (int k = 0; k < K; ++k) {
+        const mrpop_robot &r = robots[k];
+        std::memcpy(f4(t.off_base + 3 * k), r.base, 12 * sizeof(float));
+        int s = 0;
+        for (int j = 0; j < r.dof; ++j) {
+            const int l = t.link0[k] + j;
+            const int first = s;
+            while (s < r.n_spheres && r.sphere_link[s] == j) ++s;
+            const int cnt = s - first;
+            if (cnt > MRPOP_MAX_SPHERES_PER_LINK)
+                return set_error(MRPOP_EINVAL, "robot %d link %d: %d spheres exceed %d", k, j,
+                                 cnt, MRPOP_MAX_SPHERES_PER_LINK);
+            t.max_spheres_per_link = cnt > t.max_spheres_per_link ? cnt : t.max_spheres_per_link;
+            const float *dh = r.dh + 4 * j;  // a, alpha, d, theta_offset
+            float *A = f4(t.off_link + kLinkF4 * l);
+            A[0] = dh[0];
+            A[1] = dh[2];
+            A[2] = (float)std::cos((double)dh[1]);
+            A[3] = (float)std::sin((double)dh[1]);
+            A[4] = dh[3];
+            A[5] = f_of_i(s_glob + first);
+            A[6] = f_of_i(cnt);
+            A[7] = f_of_i(k);
+            coarse_sphere(r.sphere_xyzr + 4 * first, cnt, A + 8);
+        }
+        std::memcpy(f4(t.off_sph + s_glob), r.sphere_xyzr, 4 * sizeof(float) * r.n_spheres);
+        s_glob += r.n_spheres;
+    }
+    if (t.NS > 0) std::memcpy(f4(t.off_os), obs->spheres, 4 * sizeof(float) * t.NS);
+    for (int o = 0; o < t.NC; ++o) {
+        const float *c = obs->cuboids + 15 * o;
+        float *B = f4(t.off_oc + kCuboidF4 * o);
+        const double hb = std::sqrt((double)c[3] * c[3] + (double)c[4] * c[4] + (double)c[5] * c[5]);
+        B[0] = c[0]; B[1] = c[1]; B[2] = c[2]; B[3] = (float)(hb + 1e-4);
+        B[4] = c[3]; B[5] = c[4]; B[6] = c[5]; B[7] = 0.f;
+        for (int a = 0; a < 3; ++a) {  // axis a = column a of the row-major R
+            B[8 + 4 * a + 0] = c[6 + 0 * 3 + a];
+            B[8 + 4 * a + 1] = c[6 + 1 * 3 + a];
+            B[8 + 4 * a + 2] = c[6 + 2 * 3 + a];
+            B[8 + 4 * a + 3] = 0.f;
+        }
+    }
+
+    mrpop_problem *p = new (std::nothrow) mrpop_problem();
+    if (!p) return set_error(MRPOP_ENOMEM, "host allocation failed");
+    p->dev.t = t;
+    p->cfg = *cfg;
+    p->D = L;
+    p->h_blob.swap(blob);
+    for (int k = 0; k < K; ++k)
+        for (int j = 0; j < robots[k].dof; ++j) {
+            p->q_lo.push_back(robots[k].q_lo[j]);
+            p->q_hi.push_back(robots[k].q_hi[j]);
+        }
+    if (start) p->start.assign(start, start + L);
+    if (goal) p->goal.assign(goal, goal + L);
+
+    auto fail = [&](mrpop_status st) {
+        mrpop_destroy_problem(p);
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaGetDevice"));
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, p->device);
+    p->num_sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    p->smem_optin = (size_t)v;
+    if ((e = cudaMalloc(&p->dev.blob, p->h_blob.size() * sizeof(float))) != cudaSuccess)
+        return fail(cuda_error(e, "cudaMalloc(tables)"));
+    if ((e = cudaMemcpy(p->dev.blob, p->h_blob.data(), p->h_blob.size() * sizeof(float),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(cuda_error(e, "cudaMemcpy(tables)"));
+    if ((e = cudaMalloc(&p->dev.q_lo, sizeof(float) * L)) != cudaSuccess ||
+        (e = cudaMalloc(&p->dev.q_hi, sizeof(float) * L)) != cudaSuccess)
+        return fail(cuda_error(e, "cudaMalloc(limits)"));
+    cudaMemcpy(p->dev.q_lo, p->q_lo.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(p->dev.q_hi, p->q_hi.data(), sizeof(float) * L,
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(cuda_error(e, "cudaMemcpy(limits)"));
+    if ((e = cudaMalloc(&p->dev.edge_counter, sizeof(int) * 4)) != cudaSuccess)
+        return fail(cuda_error(e, "cudaMalloc(counter)"));
+    if ((e = cudaMemset(p->dev.edge_counter, 0, sizeof(int) * 4)) != cudaSuccess)
+        return fail(cuda_error(e, "cudaMemset(counter)"));
+    *out = p;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_destroy_problem(mrpop_problem *p) {
+    if (!p) return MRPOP_OK;
+    if (p->dev.blob || p->dev.edge_counter) cudaDeviceSynchronize();
+    cudaFree(p->dev.blob);
+    cudaFree(p->dev.q_lo);
+    cudaFree(p->dev.q_hi);
+    cudaFree(p->dev.edge_counter);
+    delete p;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_problem_dims(const mrpop_problem *p, int32_t *D, int32_t *K,
+                                           int32_t *S) {
+    if (!p) return set_error(MRPOP_EINVAL, "problem is NULL");
+    if (D) *D = p->D;
+    if (K) *K = p->dev.t.K;
+    if (S) *S = p->dev.t.S;
+    return MRPOP_OK;
+}
+
+static mrpop_status check_edges(mrpop_problem *p, const float *qa, const float *qb,
+                                int64_t n, const void *out, const char *fn) {
+    if (!p) return set_error(MRPOP_EINVAL, "%s: problem is NULL", fn);
+    if (n < 0) return set_error(MRPOP_EINVAL, "%s: n_edges < 0", fn);
+    if (n > (int64_t)INT32_MAX)
+        return set_error(MRPOP_EINVAL, "%s: n_edges exceeds %d", fn, INT32_MAX);
+    if (n > 0 && (!qa || !qb || !out))
+        return set_error(MRPOP_EINVAL, "%s: NULL buffer", fn);
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_fk(mrpop_problem *p, const float *q, int64_t n, float *out,
+                                 void *stream) {
+    mrpop_status st = check_edges(p, q, q, n, out, "mrpop_fk");
+    if (st != MRPOP_OK || n == 0) return st;
+    return launch_fk(p, q, n, out, (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_validate_edges_ex(mrpop_problem *p, const float *qa,
+                                                const float *qb, int64_t n, uint8_t *valid,
+                                                float *length, int32_t *npoints,
+                                                void *stream) {
+    mrpop_status st = check_edges(p, qa, qb, n, valid, "mrpop_validate_edges");
+    if (st != MRPOP_OK || n == 0) return st;
+    return launch_validate(p, qa, qb, n, valid, length, npoints, nullptr, nullptr,
+                           (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_validate_edges(mrpop_problem *p, const float *qa,
+                                             const float *qb, int64_t n, uint8_t *valid,
+                                             void *stream) {
+    return mrpop_validate_edges_ex(p, qa, qb, n, valid, nullptr, nullptr, stream);
+}
+
+extern "C" mrpop_status mrpop_edge_clearance(mrpop_problem *p, const float *qa,
+                                             const float *qb, int64_t n, float *min_clear,
+                                             void *stream) {
+    mrpop_status st = check_edges(p, qa, qb, n, min_clear, "mrpop_edge_clearance");
+    if (st != MRPOP_OK || n == 0) return st;
+    return launch_validate(p, qa, qb, n, nullptr, nullptr, nullptr, min_clear, nullptr,
+                           (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, const float *qb,
+                                            int64_t n, int64_t *counters, void *stream) {
+    mrpop_status st = check_edges(p, qa, qb, n, counters, "mrpop_validate_work");
+    if (st != MRPOP_OK) return st;
+    if (!counters) return set_error(MRPOP_EINVAL, "mrpop_validate_work: counters is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    MRPOP_CUDA_TRY(cudaMemsetAsync(counters, 0, 8 * sizeof(int64_t), s));
+    if (n == 0) return MRPOP_OK;
+    return launch_validate(p, qa, qb, n, nullptr, nullptr, nullptr, nullptr,
+                           (unsigned long long *)counters, s);
+}
+
+extern "C" mrpop_status mrpop_nearest(const float *tree, int64_t N, int64_t ld, int32_t dim,
+                                      const float *queries, const float *budgets, int64_t Q,
+                                      int64_t *out_idx, void *stream) {
+    if (dim < 1 || dim > MRPOP_MAX_LINKS)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest: dim=%d outside [1, %d]", dim,
+                         MRPOP_MAX_LINKS);
+    if (N < 0 || Q < 0 || ld < N || N > (int64_t)INT32_MAX || Q > (int64_t)INT32_MAX)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest: bad sizes N=%lld ld=%lld Q=%lld",
+                         (long long)N, (long long)ld, (long long)Q);
+    if (Q == 0) return MRPOP_OK;
+    if (!queries || !budgets || !out_idx || (N > 0 && !tree))
+        return set_error(MRPOP_EINVAL, "mrpop_nearest: NULL buffer");
+    return launch_nearest(tree, N, ld, dim, queries, budgets, Q, out_idx, (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_neighbors(const float *tree, int64_t N, int64_t ld, int32_t dim,
+                                        const float *queries, int64_t Q, float delta,
+                                        int64_t k_max, int64_t *out_idx, int64_t *out_cnt,
+                                        void *stream) {
+    if (dim < 1 || dim > MRPOP_MAX_LINKS)
+        return set_error(MRPOP_EINVAL, "mrpop_neighbors: dim=%d outside [1, %d]", dim,
+                         MRPOP_MAX_LINKS);
+    if (N < 0 || Q < 0 || ld < N || k_max < 0 || N > (int64_t)INT32_MAX ||
+        Q > (int64_t)INT32_MAX)
+        return set_error(MRPOP_EINVAL, "mrpop_neighbors: bad sizes");
+    if (!std::isfinite(delta)) return set_error(MRPOP_EINVAL, "mrpop_neighbors: delta not finite");
+    if (Q == 0) return MRPOP_OK;
+    if (!queries || !out_cnt || (k_max > 0 && !out_idx) || (N > 0 && !tree))
+        return set_error(MRPOP_EINVAL, "mrpop_neighbors: NULL buffer");
+    return launch_neighbors(tree, N, ld, dim, queries, Q, delta, k_max, out_idx, out_cnt,
+                            (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim,
+                                        double *cost_out, void *stream) {
+    if (dim < 1 || M < 0) return set_error(MRPOP_EINVAL, "mrpop_path_cost: bad sizes");
+    if (!cost_out || (M > 0 && !path)) return set_error(MRPOP_EINVAL, "mrpop_path_cost: NULL buffer");
+    return launch_path_cost(path, M, dim, cost_out, (cudaStream_t)stream);
+}

@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mrpop.h"
+
+namespace mrpop {
+
+// ---------------------------------------------------------------------------
+// Geometry tables.  Everything a validation kernel reads about a problem lives
+// in one contiguous float4 blob that each block stages into shared memory:
+//
+//   base     K x 3 float4   rows of the 3x4 base pose [R | t]
+//   link     L x 3 float4   (a, d, cos alpha, sin alpha)
+//                           (theta_offset, first sphere, sphere count, robot)
+//                           (coarse centre x, y, z in F_j', coarse radius)
+//   sphere   S x 1 float4   (x, y, z in F_j', r), grouped by link
+//   osphere  NS x 1 float4  (cx, cy, cz, r)
+//   cuboid   NC x 5 float4  (cx, cy, cz, bounding radius |h|), (hx, hy, hz, 0),
+//                           box axis 0, axis 1, axis 2 as (x, y, z, 0)
+//
+// Integer fields are stored as float bit patterns (__int_as_float).
+// "Link" j of the composite chain is joint j: link index == q index.
+// ---------------------------------------------------------------------------
+struct Tables {
+    int K = 0, L = 0, S = 0, NS = 0, NC = 0;
+    int link0[MRPOP_MAX_ROBOTS + 1] = {0};  // first link of robot k; link0[K] = L
+    int max_spheres_per_link = 0;
+    int off_base = 0, off_link = 0, off_sph = 0, off_os = 0, off_oc = 0, n_f4 = 0;
+};
+
+constexpr int kLinkF4 = 3;
+constexpr int kCuboidF4 = 5;
+constexpr int kXfFloats = 15;  // stored link frame: R (9), t (3), coarse centre (3)
+
+struct DeviceProblem {
+    Tables t;
+    float4 *blob = nullptr;       // device copy of the table blob
+    float *q_lo = nullptr;        // device [D]
+    float *q_hi = nullptr;        // device [D]
+    int *edge_counter = nullptr;  // device work counter for persistent launches
+};
+
+}  // namespace mrpop
+
+struct mrpop_problem {
+    mrpop::DeviceProblem dev;
+    mrpop_config cfg{};
+    int device = 0;
+    int D = 0;
+    std::vector<float> h_blob;  // host copy of the table blob
+    std::vector<float> start, goal, q_lo, q_hi;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+};
+
+namespace mrpop {
+
+// Thread-local error reporting.
+mrpop_status set_error(mrpop_status st, const char *fmt, ...);
+mrpop_status cuda_error(cudaError_t e, const char *what);
+
+#define MRPOP_CUDA_TRY(expr)                                          \
+    do {                                                              \
+        cudaError_t _e = (expr);                                      \
+        if (_e != cudaSuccess) return ::mrpop::cuda_error(_e, #expr); \
+    } while (0)
+
+// Kernel launchers (defined in the kernel translation units).
+mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
+                             uint8_t *valid, float *length, int32_t *npoints,
+                             float *min_clear, unsigned long long *counters,
+                             cudaStream_t st);
+mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st);
+mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
+                            const float *queries, const float *budgets, int64_t Q,
+                            int64_t *out_idx, cudaStream_t st);
+mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
+                              const float *queries, int64_t Q, float delta, int64_t k_max,
+                              int64_t *out_idx, int64_t *out_cnt, cudaStream_t st);
+mrpop_status launch_path_cost(const float *path, int64_t M, int dim, double *out,
+                              cudaStream_t st);
+
+}  // namespace mrpop

@@ -1,0 +1,267 @@
+// Cost-filtered nearest neighbour (Alg. 2 NEAREST), radius query (Alg. 2
+// NEIGHBORS) and path cost (Sec. III-A) over SoA state-cost trees.
+//
+// NEAREST: a block owns QB queries (staged in shared memory) and a slice of
+// the tree.  Each thread streams vertices of the slice through registers
+// (coalesced SoA rows), evaluates all QB queries against the vertex with
+// float4 broadcast reads of the queries, and keeps a running best per query
+// under the key (d^2, g, index).  A warp-shuffle argmin and a cross-warp pass
+// finish the block; when the tree is split across blocks (few queries, large
+// tree), partial bests go to stream-ordered scratch and a second kernel
+// reduces them.
+#include <cfloat>
+
+#include "mrpop_internal.cuh"
+
+namespace mrpop {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNNThreads = 256;
+constexpr int kQB = 8;
+
+struct Best {
+    float d2;
+    float g;
+    int idx;
+};
+
+// Lexicographic (d^2, g, index); idx < 0 marks "none" (d2 = +inf).
+__device__ __forceinline__ bool better(const Best &a, const Best &b) {
+    if (a.d2 != b.d2) return a.d2 < b.d2;
+    if (a.g != b.g) return a.g < b.g;
+    return (unsigned)a.idx < (unsigned)b.idx;
+}
+
+__device__ __forceinline__ Best shfl_best(const Best &b, int off) {
+    Best o;
+    o.d2 = __shfl_xor_sync(kFull, b.d2, off);
+    o.g = __shfl_xor_sync(kFull, b.g, off);
+    o.idx = __shfl_xor_sync(kFull, b.idx, off);
+    return o;
+}
+
+template <int DP>
+__global__ void __launch_bounds__(kNNThreads)
+nearest_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
+               const float *__restrict__ queries, const float *__restrict__ budgets, int Q,
+               int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial) {
+    __shared__ __align__(16) float qs[kQB][DP];
+    __shared__ float cs[kQB];
+    __shared__ Best wbest[kNNThreads / 32][kQB];
+    const int q0 = blockIdx.x * kQB;
+    const int nq = min(kQB, Q - q0);
+    for (int i = threadIdx.x; i < kQB * DP; i += blockDim.x) {
+        const int j = i / DP, d = i % DP;
+        qs[j][d] = (j < nq && d < dim) ? queries[(size_t)d * Q + q0 + j] : 0.f;
+    }
+    if (threadIdx.x < kQB) cs[threadIdx.x] = threadIdx.x < nq ? budgets[q0 + threadIdx.x] : -FLT_MAX;
+    __syncthreads();
+
+    Best best[kQB];
+#pragma unroll
+    for (int j = 0; j < kQB; ++j) best[j] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+
+    const int vs = blockIdx.y * chunk;
+    const int ve = min(N, vs + chunk);
+    for (int v = vs + threadIdx.x; v < ve; v += blockDim.x) {
+        float x[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) x[d] = d < dim ? __ldg(tree + (size_t)d * ld + v) : 0.f;
+        const float g = __ldg(tree + (size_t)dim * ld + v);
+#pragma unroll
+        for (int j = 0; j < kQB; ++j) {
+            const float4 *q4 = reinterpret_cast<const float4 *>(qs[j]);
+            float d2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < DP / 4; ++d) {
+                const float4 qq = q4[d];
+                const float a0 = qq.x - x[4 * d], a1 = qq.y - x[4 * d + 1];
+                const float a2 = qq.z - x[4 * d + 2], a3 = qq.w - x[4 * d + 3];
+                d2 = fmaf(a0, a0, d2);
+                d2 = fmaf(a1, a1, d2);
+                d2 = fmaf(a2, a2, d2);
+                d2 = fmaf(a3, a3, d2);
+            }
+            if (d2 <= best[j].d2) {
+                // filter of Alg. 2: g_v + |q - q_v| < c (strict)
+                if (g + __fsqrt_rn(d2) < cs[j] && (d2 < best[j].d2 || g < best[j].g)) {
+                    best[j].d2 = d2;
+                    best[j].g = g;
+                    best[j].idx = v;
+                }
+            }
+        }
+    }
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kQB; ++j) {
+        Best b = best[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const Best o = shfl_best(b, off);
+            if (better(o, b)) b = o;
+        }
+        if (lane == 0) wbest[warp][j] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        const int j = threadIdx.x;
+        Best b = wbest[0][j];
+        for (int w = 1; w < kNNThreads / 32; ++w)
+            if (better(wbest[w][j], b)) b = wbest[w][j];
+        if (partial)
+            partial[(size_t)blockIdx.y * Q + q0 + j] = b;
+        else
+            out_idx[q0 + j] = b.idx;
+    }
+}
+
+__global__ void nearest_reduce_kernel(const Best *__restrict__ partial, int splits, int Q,
+                                      int64_t *__restrict__ out_idx) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    Best b = partial[q];
+    for (int s = 1; s < splits; ++s) {
+        const Best o = partial[(size_t)s * Q + q];
+        if (better(o, b)) b = o;
+    }
+    out_idx[q] = b.idx;
+}
+
+template <int DP>
+mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const float *queries,
+                        const float *budgets, int Q, int64_t *out_idx, cudaStream_t st) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int groups = (Q + kQB - 1) / kQB;
+    const int target = sms * 8;
+    int splits = 1;
+    if (groups < target && N > 4 * kNNThreads) {
+        splits = (target + groups - 1) / groups;
+        splits = std::min(splits, (N + 4 * kNNThreads - 1) / (4 * kNNThreads));
+        splits = std::max(splits, 1);
+        splits = std::min(splits, 65535);
+    }
+    int chunk = (N + splits - 1) / splits;
+    chunk = ((chunk + kNNThreads - 1) / kNNThreads) * kNNThreads;
+    if (chunk == 0) chunk = kNNThreads;
+    splits = std::max(1, (N + chunk - 1) / chunk);
+    Best *partial = nullptr;
+    if (splits > 1)
+        MRPOP_CUDA_TRY(cudaMallocAsync((void **)&partial, sizeof(Best) * (size_t)splits * Q, st));
+    dim3 grid(groups, splits);
+    nearest_kernel<DP><<<grid, kNNThreads, 0, st>>>(tree, N, ld, dim, queries, budgets, Q, chunk,
+                                                    out_idx, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && splits > 1) {
+        nearest_reduce_kernel<<<(Q + 255) / 256, 256, 0, st>>>(partial, splits, Q, out_idx);
+        e = cudaGetLastError();
+    }
+    if (partial) cudaFreeAsync(partial, st);
+    if (e != cudaSuccess) return cuda_error(e, "nearest kernel launch");
+    return MRPOP_OK;
+}
+
+// NEIGHBORS: one warp per query, lanes over 32 consecutive vertices, in
+// ascending order; ballot + prefix popcount keeps the output sorted.
+__global__ void neighbors_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
+                                 const float *__restrict__ queries, int Q, float delta,
+                                 int64_t k_max, int64_t *__restrict__ out_idx,
+                                 int64_t *__restrict__ out_cnt) {
+    __shared__ float qs[8][MRPOP_MAX_LINKS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = blockIdx.x * 8 + warp;
+    if (q >= Q) return;
+    for (int d = lane; d < dim; d += 32) qs[warp][d] = queries[(size_t)d * Q + q];
+    __syncwarp();
+    int64_t count = 0;
+    for (int v0 = 0; v0 < N; v0 += 32) {
+        const int v = v0 + lane;
+        bool in = false;
+        if (v < N) {
+            float d2 = 0.f;
+            for (int d = 0; d < dim; ++d) {
+                const float a = qs[warp][d] - __ldg(tree + (size_t)d * ld + v);
+                d2 = fmaf(a, a, d2);
+            }
+            in = __fsqrt_rn(d2) <= delta;
+        }
+        const unsigned bal = __ballot_sync(kFull, in);
+        if (in) {
+            const int64_t pos = count + __popc(bal & ((1u << lane) - 1u));
+            if (pos < k_max) out_idx[(size_t)q * k_max + pos] = v;
+        }
+        count += __popc(bal);
+    }
+    for (int64_t pos = count + lane; pos < k_max; pos += 32) out_idx[(size_t)q * k_max + pos] = -1;
+    if (lane == 0) out_cnt[q] = count;
+}
+
+// C(sigma): one block; FP32 segment lengths, FP64 accumulation.
+__global__ void path_cost_kernel(const float *__restrict__ path, int64_t M, int dim,
+                                 double *__restrict__ out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j + 1 < M; j += blockDim.x) {
+        float s = 0.f;
+        for (int d = 0; d < dim; ++d) {
+            const float a = path[(j + 1) * dim + d] - path[j * dim + d];
+            s = fmaf(a, a, s);
+        }
+        acc += (double)__fsqrt_rn(s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
+}  // namespace
+
+mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
+                            const float *queries, const float *budgets, int64_t Q,
+                            int64_t *out_idx, cudaStream_t st) {
+    const int n = (int)N, q = (int)Q;
+    const int dp = (dim + 3) & ~3;
+    switch (dp) {
+        case 4: return nearest_dp<4>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 8: return nearest_dp<8>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 12: return nearest_dp<12>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 16: return nearest_dp<16>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 20: return nearest_dp<20>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 24: return nearest_dp<24>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 28: return nearest_dp<28>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        case 32: return nearest_dp<32>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+        default: break;
+    }
+    if (dp <= 48) return nearest_dp<48>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+    return nearest_dp<64>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+}
+
+mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
+                              const float *queries, int64_t Q, float delta, int64_t k_max,
+                              int64_t *out_idx, int64_t *out_cnt, cudaStream_t st) {
+    const int blocks = (int)((Q + 7) / 8);
+    neighbors_kernel<<<blocks, 256, 0, st>>>(tree, (int)N, ld, dim, queries, (int)Q, delta, k_max,
+                                             out_idx, out_cnt);
+    MRPOP_CUDA_TRY(cudaGetLastError());
+    return MRPOP_OK;
+}
+
+mrpop_status launch_path_cost(const float *path, int64_t M, int dim, double *out,
+                              cudaStream_t st) {
+    path_cost_kernel<<<1, 512, 0, st>>>(path, M, dim, out);
+    MRPOP_CUDA_TRY(cudaGetLastError());
+    return MRPOP_OK;
+}
+
+}  // namespace mrpop

@@ -1,0 +1,538 @@
+// Motion validation of composite edges (Sec. III-E) and forward kinematics.
+//
+// Design (sm_103a, FP32 SIMT; not a dense contraction, so no tensor cores):
+//  * One warp per edge, fetched dynamically from a self-resetting work
+//    counter.  The edge's q_a and q_b - q_a are staged in shared memory and the
+//    interval count n is computed once per warp.
+//  * Checkpoints across lanes: tile t of an edge with n+1 points and
+//    T = ceil((n+1)/32) tiles assigns point k = t + T*lane to each lane, so
+//    every tile samples the whole edge and a collision anywhere ends the edge
+//    after few tiles (early exit with __any_sync).
+//  * Per link, forward kinematics in registers (Rz, then the d/a/alpha
+//    offsets), a link-level ("coarse") sphere test against every obstacle's
+//    bounding sphere and against the stored link frames of earlier robots,
+//    warp-wide OR of the per-lane hit masks (__reduce_or_sync), then
+//    sphere-level ("fine") tests only for the union mask, on a register cache
+//    of the link's world spheres.  Culling never changes a verdict: coarse
+//    spheres enclose their fine spheres with a slack above FP32 rounding.
+//  * The paper's own design (4 threads per motion, then threads reassigned in
+//    proportion to the fine-test load) balances work across motions; here the
+//    warp-uniform union mask keeps all 32 lanes busy on the same tests instead.
+//  * Geometry tables are staged once per block into shared memory; link
+//    frames of robots 0..K-2 go to a per-warp shared scratch [link][15][lane]
+//    (lane-contiguous, conflict-free) for the robot-robot tests.
+#include <cfloat>
+
+#include "mrpop_internal.cuh"
+
+namespace mrpop {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsMax = 4;
+
+enum Mode { kVerdict = 0, kClearance = 1, kCount = 2 };
+
+struct VParams {
+    Tables t;
+    const float4 *blob;
+    const float *qa;
+    const float *qb;
+    int64_t E;
+    float res;
+    float margin;
+    uint8_t *valid;
+    float *length;
+    int32_t *npoints;
+    float *min_clear;
+    unsigned long long *counters;
+    int *work;  // [0] next edge, [1] finished warps; both return to 0 at exit
+    int total_warps;
+    int warp_floats;
+    int dpad;
+};
+
+struct Frame {
+    float r[9];  // row-major rotation
+    float t[3];
+};
+
+// F = T * Rz(theta): columns 0 and 1 rotate, column 2 and t are unchanged.
+__device__ __forceinline__ Frame rotz(const Frame &T, float c, float s) {
+    Frame F;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float a = T.r[3 * i], b = T.r[3 * i + 1];
+        F.r[3 * i] = fmaf(c, a, s * b);
+        F.r[3 * i + 1] = fmaf(c, b, -s * a);
+        F.r[3 * i + 2] = T.r[3 * i + 2];
+        F.t[i] = T.t[i];
+    }
+    return F;
+}
+
+// T = F * Tz(d) * Tx(a) * Rx(alpha)
+__device__ __forceinline__ Frame advance(const Frame &F, float a, float d, float ca, float sa) {
+    Frame T;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float c0 = F.r[3 * i], c1 = F.r[3 * i + 1], c2 = F.r[3 * i + 2];
+        T.t[i] = fmaf(a, c0, fmaf(d, c2, F.t[i]));
+        T.r[3 * i] = c0;
+        T.r[3 * i + 1] = fmaf(ca, c1, sa * c2);
+        T.r[3 * i + 2] = fmaf(ca, c2, -sa * c1);
+    }
+    return T;
+}
+
+__device__ __forceinline__ float3 apply(const Frame &F, float x, float y, float z) {
+    return make_float3(fmaf(F.r[0], x, fmaf(F.r[1], y, fmaf(F.r[2], z, F.t[0]))),
+                       fmaf(F.r[3], x, fmaf(F.r[4], y, fmaf(F.r[5], z, F.t[1]))),
+                       fmaf(F.r[6], x, fmaf(F.r[7], y, fmaf(F.r[8], z, F.t[2]))));
+}
+
+__device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, float by,
+                                       float bz) {
+    const float dx = ax - bx, dy = ay - by, dz = az - bz;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+__device__ __forceinline__ Frame load_base(const float4 *tab, const Tables &t, int b) {
+    const float4 r0 = tab[t.off_base + 3 * b], r1 = tab[t.off_base + 3 * b + 1],
+                 r2 = tab[t.off_base + 3 * b + 2];
+    Frame T;
+    T.r[0] = r0.x; T.r[1] = r0.y; T.r[2] = r0.z; T.t[0] = r0.w;
+    T.r[3] = r1.x; T.r[4] = r1.y; T.r[5] = r1.z; T.t[1] = r1.w;
+    T.r[6] = r2.x; T.r[7] = r2.y; T.r[8] = r2.z; T.t[2] = r2.w;
+    return T;
+}
+
+__device__ __forceinline__ unsigned low_mask(int n) { return n >= 32 ? kFull : ((1u << n) - 1u); }
+
+// Interval count n = max(1, ceil(|dq|_2 / res)) in FP32 with a sequential
+// fused multiply-add sum (the oracle takes the same integer decision in FP32).
+__device__ __forceinline__ int interval_count(const float *dq, int D, float res, float *len_out) {
+    float acc = 0.f;
+    for (int i = 0; i < D; ++i) acc = __fmaf_rn(dq[i], dq[i], acc);
+    const float len = __fsqrt_rn(acc);
+    const float nf = ceilf(__fdiv_rn(len, res));
+    *len_out = len;
+    if (!(nf >= 1.f)) return 1;
+    return nf > 1073741824.f ? 1073741824 : (int)nf;
+}
+
+template <int MODE, int SPL>
+__global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams P) {
+    extern __shared__ float4 sm4[];
+    float4 *tab = sm4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *ws = reinterpret_cast<float *>(sm4 + P.t.n_f4) + (size_t)warp * P.warp_floats;
+    float *qa_s = ws, *dq_s = ws + P.dpad, *xf = ws + 2 * P.dpad;
+
+    for (int i = threadIdx.x; i < P.t.n_f4; i += blockDim.x) tab[i] = P.blob[i];
+    __syncthreads();
+
+    const Tables &t = P.t;
+    const int K = t.K, D = t.L, NS = t.NS, NC = t.NC;
+    const float m = P.margin;
+    unsigned long long cnt[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cnt[c] = 0ull;
+
+    for (;;) {
+        int e = 0;
+        if (lane == 0) e = atomicAdd(&P.work[0], 1);
+        e = __shfl_sync(kFull, e, 0);
+        if (e >= P.E) break;
+        __syncwarp();
+        for (int i = lane; i < D; i += 32) {
+            const float a = __ldg(P.qa + (size_t)i * P.E + e);
+            const float b = __ldg(P.qb + (size_t)i * P.E + e);
+            qa_s[i] = a;
+            dq_s[i] = __fsub_rn(b, a);
+        }
+        __syncwarp();
+        float len;
+        const int n = interval_count(dq_s, D, P.res, &len);
+        // Edges beyond MRPOP_MAX_EDGE_INTERVALS intervals (or with non-finite
+        // coordinates) are reported invalid without being checked.
+        const bool too_long = !(len <= P.res * (float)MRPOP_MAX_EDGE_INTERVALS);
+        const int T = too_long ? 0 : (n >> 5) + 1;  // ceil((n + 1) / 32)
+        bool edge_hit = too_long;
+        float minc = too_long ? -FLT_MAX : FLT_MAX;
+
+        for (int tile = 0; tile < T; ++tile) {
+            int k = tile + T * lane;
+            const bool active = k <= n;
+            if (!active) k = n;
+            const float tk = __fdiv_rn((float)k, (float)n);
+            bool hit = false;
+            if (MODE == kCount && active) cnt[0] += 1;
+
+            for (int b = 0; b < K; ++b) {
+                const int l0 = t.link0[b], l1 = t.link0[b + 1];
+                const bool store = b < K - 1;
+                Frame Tm = load_base(tab, t, b);
+                for (int l = l0; l < l1; ++l) {
+                    const float4 LA = tab[t.off_link + kLinkF4 * l];
+                    const float4 LB = tab[t.off_link + kLinkF4 * l + 1];
+                    const float4 LC = tab[t.off_link + kLinkF4 * l + 2];
+                    const float th = __fmaf_rn(tk, dq_s[l], qa_s[l]) + LB.x;
+                    float sn, cs;
+                    sincosf(th, &sn, &cs);
+                    const Frame F = rotz(Tm, cs, sn);
+                    const float3 cc = apply(F, LC.x, LC.y, LC.z);
+                    if (store) {
+                        float *x = xf + (size_t)l * kXfFloats * 32 + lane;
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) x[c * 32] = F.r[c];
+                        x[9 * 32] = F.t[0];
+                        x[10 * 32] = F.t[1];
+                        x[11 * 32] = F.t[2];
+                        x[12 * 32] = cc.x;
+                        x[13 * 32] = cc.y;
+                        x[14 * 32] = cc.z;
+                    }
+                    const int sf = __float_as_int(LB.y), ns = __float_as_int(LB.z);
+                    if (MODE == kCount && active) cnt[1] += 1;
+                    if (ns > 0) {
+                        float4 pw[SPL];
+                        bool have = false;
+                        bool own_any = false;
+                        auto ensure = [&]() {
+                            if (!have) {
+#pragma unroll
+                                for (int s = 0; s < SPL; ++s)
+                                    if (s < ns) {
+                                        const float4 sp = tab[t.off_sph + sf + s];
+                                        const float3 p = apply(F, sp.x, sp.y, sp.z);
+                                        pw[s] = make_float4(p.x, p.y, p.z, sp.w);
+                                    }
+                                have = true;
+                            }
+                        };
+                        if (MODE == kCount && active) cnt[7] += 1;  // coarse centre
+                        const float rc = LC.w + m;
+
+                        // ---- robot vs obstacle spheres
+                        for (int c0 = 0; c0 < NS; c0 += 32) {
+                            const int cn = min(32, NS - c0);
+                            unsigned own = 0;
+                            if (MODE == kClearance) {
+                                own = low_mask(cn);
+                            } else {
+                                for (int o = 0; o < cn; ++o) {
+                                    const float4 ob = tab[t.off_os + c0 + o];
+                                    const float d2 = dist2(cc.x, cc.y, cc.z, ob.x, ob.y, ob.z);
+                                    const float th2 = rc + ob.w;
+                                    own |= (d2 < th2 * th2) ? (1u << o) : 0u;
+                                }
+                            }
+                            const unsigned wm =
+                                MODE == kClearance ? own : __reduce_or_sync(kFull, own);
+                            if (MODE == kCount && active) {
+                                cnt[2] += cn;
+                                cnt[4] += (unsigned long long)__popc(own) * ns;
+                                own_any |= own != 0;
+                            }
+                            if (wm) {
+                                ensure();
+                                unsigned mm = wm;
+                                while (mm) {
+                                    const int o = __ffs(mm) - 1;
+                                    mm &= mm - 1;
+                                    const float4 ob = tab[t.off_os + c0 + o];
+#pragma unroll
+                                    for (int s = 0; s < SPL; ++s)
+                                        if (s < ns) {
+                                            const float d2 =
+                                                dist2(pw[s].x, pw[s].y, pw[s].z, ob.x, ob.y, ob.z);
+                                            if (MODE == kClearance) {
+                                                minc = fminf(minc, __fsqrt_rn(d2) - pw[s].w - ob.w);
+                                            } else {
+                                                const float th2 = pw[s].w + ob.w + m;
+                                                hit |= d2 < th2 * th2;
+                                            }
+                                        }
+                                }
+                            }
+                        }
+
+                        // ---- robot vs obstacle cuboids (oriented boxes)
+                        for (int c0 = 0; c0 < NC; c0 += 32) {
+                            const int cn = min(32, NC - c0);
+                            unsigned own = 0;
+                            if (MODE == kClearance) {
+                                own = low_mask(cn);
+                            } else {
+                                for (int o = 0; o < cn; ++o) {
+                                    const float4 cb = tab[t.off_oc + kCuboidF4 * (c0 + o)];
+                                    const float d2 = dist2(cc.x, cc.y, cc.z, cb.x, cb.y, cb.z);
+                                    const float th2 = rc + cb.w;
+                                    own |= (d2 < th2 * th2) ? (1u << o) : 0u;
+                                }
+                            }
+                            const unsigned wm =
+                                MODE == kClearance ? own : __reduce_or_sync(kFull, own);
+                            if (MODE == kCount && active) {
+                                cnt[2] += cn;
+                                cnt[5] += (unsigned long long)__popc(own) * ns;
+                                own_any |= own != 0;
+                            }
+                            if (wm) {
+                                ensure();
+                                unsigned mm = wm;
+                                while (mm) {
+                                    const int o = __ffs(mm) - 1;
+                                    mm &= mm - 1;
+                                    const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + o);
+                                    const float4 C = cbp[0], H = cbp[1], A0 = cbp[2], A1 = cbp[3],
+                                                 A2 = cbp[4];
+#pragma unroll
+                                    for (int s = 0; s < SPL; ++s)
+                                        if (s < ns) {
+                                            const float vx = pw[s].x - C.x, vy = pw[s].y - C.y,
+                                                        vz = pw[s].z - C.z;
+                                            const float p0 = fmaf(A0.x, vx, fmaf(A0.y, vy, A0.z * vz));
+                                            const float p1 = fmaf(A1.x, vx, fmaf(A1.y, vy, A1.z * vz));
+                                            const float p2 = fmaf(A2.x, vx, fmaf(A2.y, vy, A2.z * vz));
+                                            const float u0 = fmaxf(fabsf(p0) - H.x, 0.f);
+                                            const float u1 = fmaxf(fabsf(p1) - H.y, 0.f);
+                                            const float u2 = fmaxf(fabsf(p2) - H.z, 0.f);
+                                            const float d2 = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+                                            if (MODE == kClearance) {
+                                                minc = fminf(minc, __fsqrt_rn(d2) - pw[s].w);
+                                            } else {
+                                                const float th2 = pw[s].w + m;
+                                                hit |= d2 < th2 * th2;
+                                            }
+                                        }
+                                }
+                            }
+                        }
+
+                        // ---- robot vs earlier robots (links 0 .. l0-1)
+                        if (l0 > 0) {
+                            unsigned own0 = 0, own1 = 0;
+                            if (MODE == kClearance) {
+                                own0 = low_mask(l0);
+                                own1 = l0 > 32 ? low_mask(l0 - 32) : 0u;
+                            } else {
+                                for (int i = 0; i < l0; ++i) {
+                                    const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
+                                    const float ri = tab[t.off_link + kLinkF4 * i + 2].w;
+                                    const float d2 = dist2(cc.x, cc.y, cc.z, x[12 * 32], x[13 * 32],
+                                                           x[14 * 32]);
+                                    const float th2 = LC.w + ri + m;
+                                    const unsigned bit = d2 < th2 * th2 ? 1u : 0u;
+                                    if (i < 32)
+                                        own0 |= bit << i;
+                                    else
+                                        own1 |= bit << (i - 32);
+                                }
+                            }
+                            const unsigned w0 = MODE == kClearance ? own0 : __reduce_or_sync(kFull, own0);
+                            const unsigned w1 = MODE == kClearance ? own1 : __reduce_or_sync(kFull, own1);
+                            if (MODE == kCount && active) {
+                                cnt[3] += l0;
+                                own_any |= (own0 | own1) != 0;
+                                for (int w = 0; w < 2; ++w) {
+                                    unsigned mm = w == 0 ? own0 : own1;
+                                    while (mm) {
+                                        const int i = __ffs(mm) - 1 + 32 * w;
+                                        mm &= mm - 1;
+                                        const int nsi =
+                                            __float_as_int(tab[t.off_link + kLinkF4 * i + 1].z);
+                                        cnt[6] += (unsigned long long)nsi * ns;
+                                        cnt[7] += nsi;
+                                    }
+                                }
+                            }
+                            for (int w = 0; w < 2; ++w) {
+                                unsigned mm = w == 0 ? w0 : w1;
+                                if (mm) ensure();
+                                while (mm) {
+                                    const int i = __ffs(mm) - 1 + 32 * w;
+                                    mm &= mm - 1;
+                                    const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
+                                    Frame Fi;
+#pragma unroll
+                                    for (int c = 0; c < 9; ++c) Fi.r[c] = x[c * 32];
+                                    Fi.t[0] = x[9 * 32];
+                                    Fi.t[1] = x[10 * 32];
+                                    Fi.t[2] = x[11 * 32];
+                                    const float4 LBi = tab[t.off_link + kLinkF4 * i + 1];
+                                    const int sfi = __float_as_int(LBi.y), nsi = __float_as_int(LBi.z);
+                                    for (int s2 = 0; s2 < nsi; ++s2) {
+                                        const float4 sp = tab[t.off_sph + sfi + s2];
+                                        const float3 pa = apply(Fi, sp.x, sp.y, sp.z);
+#pragma unroll
+                                        for (int s = 0; s < SPL; ++s)
+                                            if (s < ns) {
+                                                const float d2 =
+                                                    dist2(pw[s].x, pw[s].y, pw[s].z, pa.x, pa.y, pa.z);
+                                                if (MODE == kClearance) {
+                                                    minc = fminf(minc,
+                                                                 __fsqrt_rn(d2) - pw[s].w - sp.w);
+                                                } else {
+                                                    const float th2 = pw[s].w + sp.w + m;
+                                                    hit |= d2 < th2 * th2;
+                                                }
+                                            }
+                                    }
+                                }
+                            }
+                        }
+                        if (MODE == kCount && active && own_any) cnt[7] += ns;
+                    }
+                    Tm = advance(F, LA.x, LA.y, LA.z, LA.w);
+                    if (MODE != kClearance && __any_sync(kFull, hit)) goto tile_done;
+                }
+            }
+        tile_done:
+            if (MODE != kClearance && __any_sync(kFull, hit)) {
+                edge_hit = true;
+                break;
+            }
+        }
+
+        if (MODE == kClearance) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                minc = fminf(minc, __shfl_xor_sync(kFull, minc, off));
+            if (lane == 0) P.min_clear[e] = minc;
+        } else if (MODE == kVerdict) {
+            if (lane == 0) {
+                P.valid[e] = edge_hit ? 0 : 1;
+                if (P.length) P.length[e] = len;
+                if (P.npoints) P.npoints[e] = n;
+            }
+        }
+    }
+
+    if (MODE == kCount) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            unsigned long long v = cnt[c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+            if (lane == 0 && v) atomicAdd(P.counters + c, v);
+        }
+    }
+    // The last warp to leave resets the work counter for the next launch on
+    // this problem (every warp has made its final fetch before counting out).
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&P.work[1], 1) == P.total_warps - 1) {
+            atomicExch(&P.work[0], 0);
+            atomicExch(&P.work[1], 0);
+        }
+    }
+}
+
+template <int MODE, int SPL>
+mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
+                         cudaStream_t st) {
+    auto kern = validate_kernel<MODE, SPL>;
+    MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    int bps = 0;
+    MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, warps * 32, smem));
+    if (bps < 1) return set_error(MRPOP_EINVAL, "validation kernel does not fit on an SM");
+    const int64_t want = (V.E + warps - 1) / warps;
+    const int grid = (int)std::min<int64_t>((int64_t)p->num_sms * bps, want);
+    V.total_warps = grid * warps;
+    kern<<<grid, warps * 32, smem, st>>>(V);
+    MRPOP_CUDA_TRY(cudaGetLastError());
+    return MRPOP_OK;
+}
+
+template <int MODE>
+mrpop_status launch_spl(mrpop_problem *p, VParams &V, int warps, size_t smem,
+                        cudaStream_t st) {
+    const int spl = p->dev.t.max_spheres_per_link;
+    if (spl <= 4) return launch_mode<MODE, 4>(p, V, warps, smem, st);
+    if (spl <= 8) return launch_mode<MODE, 8>(p, V, warps, smem, st);
+    if (spl <= 12) return launch_mode<MODE, 12>(p, V, warps, smem, st);
+    return launch_mode<MODE, 16>(p, V, warps, smem, st);
+}
+
+// ---------------------------------------------------------------------------
+// Forward kinematics of a batch of configurations: one thread per config.
+// ---------------------------------------------------------------------------
+__global__ void fk_kernel(const float4 *__restrict__ tab, const Tables t,
+                          const float *__restrict__ q, int64_t n, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t S = t.S;
+    for (int b = 0; b < t.K; ++b) {
+        Frame Tm = load_base(tab, t, b);
+        for (int l = t.link0[b]; l < t.link0[b + 1]; ++l) {
+            const float4 LA = tab[t.off_link + kLinkF4 * l];
+            const float4 LB = tab[t.off_link + kLinkF4 * l + 1];
+            float sn, cs;
+            sincosf(q[(size_t)l * n + i] + LB.x, &sn, &cs);
+            const Frame F = rotz(Tm, cs, sn);
+            const int sf = __float_as_int(LB.y), ns = __float_as_int(LB.z);
+            for (int s = 0; s < ns; ++s) {
+                const float4 sp = tab[t.off_sph + sf + s];
+                const float3 pw = apply(F, sp.x, sp.y, sp.z);
+                out[((size_t)0 * S + sf + s) * n + i] = pw.x;
+                out[((size_t)1 * S + sf + s) * n + i] = pw.y;
+                out[((size_t)2 * S + sf + s) * n + i] = pw.z;
+            }
+            Tm = advance(F, LA.x, LA.y, LA.z, LA.w);
+        }
+    }
+}
+
+}  // namespace
+
+mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
+                             uint8_t *valid, float *length, int32_t *npoints,
+                             float *min_clear, unsigned long long *counters,
+                             cudaStream_t st) {
+    const Tables &t = p->dev.t;
+    VParams V;
+    V.t = t;
+    V.blob = p->dev.blob;
+    V.qa = qa;
+    V.qb = qb;
+    V.E = n;
+    V.res = p->cfg.resolution;
+    V.margin = p->cfg.margin;
+    V.valid = valid;
+    V.length = length;
+    V.npoints = npoints;
+    V.min_clear = min_clear;
+    V.counters = counters;
+    V.work = p->dev.edge_counter;
+    V.dpad = (t.L + 3) & ~3;
+    const int nstore = t.link0[t.K - 1];
+    V.warp_floats = 2 * V.dpad + nstore * kXfFloats * 32;
+    const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
+    int warps = kWarpsMax;
+    size_t smem = 0;
+    for (; warps >= 1; warps >>= 1) {
+        smem = tab_bytes + (size_t)warps * V.warp_floats * sizeof(float);
+        if (smem <= p->smem_optin) break;
+    }
+    if (warps < 1)
+        return set_error(MRPOP_EINVAL,
+                         "problem too large for the validation kernel's shared memory "
+                         "(%zu bytes of tables + %d bytes per warp)",
+                         tab_bytes, V.warp_floats * 4);
+    if (min_clear) return launch_spl<kClearance>(p, V, warps, smem, st);
+    if (counters) return launch_spl<kCount>(p, V, warps, smem, st);
+    return launch_spl<kVerdict>(p, V, warps, smem, st);
+}
+
+mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st) {
+    const int threads = 128;
+    const int64_t blocks = (n + threads - 1) / threads;
+    fk_kernel<<<(unsigned)blocks, threads, 0, st>>>(p->dev.blob, p->dev.t, q, n, out);
+    MRPOP_CUDA_TRY(cudaGetLastError());
+    return MRPOP_OK;
+}
+
+}  // namespace mrpop

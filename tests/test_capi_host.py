@@ -1,0 +1,91 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every symbol that include/*.h declares, and rejects malformed
+problems with MRPOP_EINVAL before touching the device."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2609_30644_gb300 import build as B
+    B.build()
+    import paper_2609_30644_gb300 as m
+    return m
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(mrpop_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for n in ("mrpop_create_problem", "mrpop_validate_edges", "mrpop_nearest",
+              "mrpop_neighbors", "mrpop_path_cost", "mrpop_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = C.CDLL(capi.library_path)
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(capi.EXPORTS) == declared_symbols()
+
+
+def _scene():
+    from paper_2609_30644_gb300 import synth
+    return synth.planar_pair_scene(0)
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda s: s.robots[0].__setattr__("dof", 0), "dof"),
+    (lambda s: s.robots[0].__setattr__("dof", 17), "dof"),
+    (lambda s: s.robots[0].sphere_link.__setitem__(0, 2), "non-decreasing"),
+    (lambda s: s.robots[0].sphere_xyzr.__setitem__((0, 3), -1.0), "radius"),
+    (lambda s: s.obs_spheres.__setitem__((0, 3), np.nan), "non-finite"),
+    (lambda s: s.robots[1].base.__setitem__(3, np.inf), "non-finite"),
+])
+def test_create_rejects_malformed(capi, mutate, msg):
+    s = _scene()
+    mutate(s)
+    with pytest.raises(capi.MrpopError) as ei:
+        capi.Problem(s)
+    assert ei.value.status == 1 and msg in str(ei.value)
+
+
+def test_create_rejects_too_many_spheres_per_link(capi):
+    from paper_2609_30644_gb300 import synth
+    rb = synth.planar_arm(np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32),
+                          spheres_per_link=17)
+    s = synth.Scene([rb], np.zeros((0, 4), np.float32), np.zeros((0, 15), np.float32))
+    with pytest.raises(capi.MrpopError) as ei:
+        capi.Problem(s)
+    assert ei.value.status == 1
+
+
+def test_create_rejects_bad_config(capi):
+    with pytest.raises(capi.MrpopError) as ei:
+        capi.Problem(_scene(), resolution=0.0)
+    assert ei.value.status == 1
+    with pytest.raises(capi.MrpopError):
+        capi.Problem(_scene(), margin=-1.0)
+
+
+def test_nearest_rejects_bad_dim(capi):
+    lib = capi.lib
+    st = lib.mrpop_nearest(None, 0, 0, 0, None, None, 1, None, None)
+    assert st == 1 and b"dim" in lib.mrpop_last_error()
+    st = lib.mrpop_nearest(None, 10, 5, 3, None, None, 1, None, None)   # ld < N
+    assert st == 1
+    assert lib.mrpop_nearest(None, 0, 0, 3, None, None, 0, None, None) == 0  # Q = 0: no-op

@@ -1,0 +1,150 @@
+"""GPU parity of NEAREST (cost-filtered), NEIGHBORS (radius) and path cost
+against the FP64 oracle, through the C ABI.
+
+Indices must match exactly, ties included (key: distance, then g, then
+index).  The one allowance is a genuine FP32/FP64 near-tie: when the oracle's
+best and runner-up distances, or some vertex's filter value g + d and the
+budget c, are within 1e-5 relative, the GPU must still return a vertex that
+is admissible and as close as the oracle's best within that tolerance.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_30644_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2609_30644_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _check_nearest(orc, tree, qs, cs, got, N=None, sample=None):
+    D = tree.shape[0] - 1
+    N = tree.shape[1] if N is None else N
+    idxs = range(qs.shape[1]) if sample is None else sample
+    n_tie = 0
+    for i in idxs:
+        ref, bd, sd, gap = orc.nearest(tree, qs[:, i], cs[i], n_vertices=N)
+        if got[i] == ref:
+            continue
+        scale = max(1.0, abs(float(cs[i])))
+        near_tie = (np.isfinite(sd) and sd - bd <= REL * max(bd, 1e-30)) or gap <= REL * scale
+        assert near_tie, (i, got[i], ref, bd, sd, gap)
+        n_tie += 1
+        if got[i] >= 0:
+            v = tree[:D, got[i]].astype(float)
+            d = np.linalg.norm(v - qs[:, i].astype(float))
+            assert tree[D, got[i]] + d < cs[i] + REL * scale
+            assert d <= bd * (1 + REL) + 1e-12 or ref < 0
+    return n_tie
+
+
+@pytest.mark.parametrize("D,N,Q", [(14, 3000, 500), (28, 2000, 200), (6, 5000, 300),
+                                   (7, 777, 129), (3, 1000, 64), (64, 600, 40), (21, 1, 16)])
+def test_nearest_parity(mp, orc, D, N, Q):
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, N, lo, hi, seed=D, dup_frac=0.05)
+    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=D + 1, budget_lo=0.0, budget_hi=20.0)
+    got = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    ties = _check_nearest(orc, tree, qs, cs, got)
+    assert ties <= max(2, Q // 50)
+    assert (got >= -1).all() and (got < N).all()
+
+
+def test_nearest_exact_ties(mp, orc):
+    """Queries placed exactly on duplicated vertices: the tie must go to the
+    lowest g, then the lowest index (Sec. III-D), bit-exactly."""
+    D = 14
+    rng = np.random.default_rng(5)
+    base = rng.uniform(-2, 2, (D, 50)).astype(np.float32)
+    tree = np.zeros((D + 1, 400), np.float32)
+    for j in range(400):
+        tree[:D, j] = base[:, j % 50]
+        tree[D, j] = np.float32([0.5, 0.25, 0.25, 1.0][(j // 50) % 4])
+    qs = np.ascontiguousarray(base[:, :50])
+    cs = np.full(50, 100.0, np.float32)
+    got = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    for i in range(50):
+        assert got[i] == orc.nearest(tree, qs[:, i], cs[i])[0]
+        assert got[i] == 50 + i      # g = 0.25 first appears at block 1
+
+
+def test_nearest_empty_and_filtered(mp, orc):
+    D = 7
+    lo, hi = -np.ones(D), np.ones(D)
+    tree = synth.random_tree(D, 500, lo, hi, seed=3)
+    qs, _ = synth.nn_queries(D, 64, lo, hi, seed=4)
+    cs = np.zeros(64, np.float32)                     # nothing admissible
+    got = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    assert (got == -1).all()
+    empty = torch.empty((D + 1, 0), dtype=torch.float32, device="cuda")
+    got = mp.nearest(empty, _dev(qs), _dev(np.full(64, 1e9, np.float32))).cpu().numpy()
+    assert (got == -1).all()
+
+
+def test_nearest_split_tree_few_queries(mp, orc):
+    """Few queries over a large tree: the tree is split across blocks and the
+    partial minima are reduced; also ld > n_vertices."""
+    D = 14
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    N, ld = 200_000, 200_064
+    tree = np.zeros((D + 1, ld), np.float32)
+    tree[:, :N] = synth.random_tree_fast(D, N, lo, hi, seed=9)
+    tree[:, N:] = -7.0                                 # must never be read
+    qs, cs = synth.nn_queries(D, 5, lo, hi, seed=10, budget_lo=5, budget_hi=30)
+    got = mp.nearest(_dev(tree), _dev(qs), _dev(cs), n_vertices=N).cpu().numpy()
+    _check_nearest(orc, tree, qs, cs, got, N=N)
+
+
+def test_nearest_full_size_sampled(mp, orc):
+    """65,536 queries against a 16,384-vertex 14-D tree (the benchmark's
+    launch configuration), 200 sampled queries re-checked by the oracle."""
+    D = 14
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree_fast(D, 16384, lo, hi, seed=1)
+    qs, cs = synth.nn_queries(D, 65536, lo, hi, seed=2, budget_lo=10, budget_hi=40)
+    got = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    sample = np.random.default_rng(0).choice(65536, 200, replace=False)
+    _check_nearest(orc, tree, qs, cs, got, sample=sample)
+
+
+@pytest.mark.parametrize("D,N,Q,k_max", [(7, 3000, 200, 32), (14, 1000, 64, 8), (6, 65, 33, 100),
+                                         (3, 10, 5, 0)])
+def test_neighbors_parity(mp, orc, D, N, Q, k_max):
+    rng = np.random.default_rng(D)
+    tree = np.zeros((D + 1, N), np.float32)
+    tree[:D] = rng.uniform(-2.9, 2.9, (D, N))
+    tree[D] = rng.uniform(0, 5, N)
+    qs = rng.uniform(-2.9, 2.9, (D, Q)).astype(np.float32)
+    delta = np.float32(1.2 * np.sqrt(D))
+    idx, cnt = mp.neighbors(_dev(tree), _dev(qs), float(delta), k_max)
+    idx, cnt = idx.cpu().numpy(), cnt.cpu().numpy()
+    for i in range(Q):
+        ref, rc, gap = orc.neighbors(tree, qs[:, i], delta, k_max)
+        if gap > REL * delta:
+            assert cnt[i] == rc
+            np.testing.assert_array_equal(idx[i, :len(ref)], ref)
+        else:
+            assert abs(int(cnt[i]) - rc) <= 2
+        row = idx[i, :min(int(cnt[i]), k_max)]
+        assert (np.diff(row) > 0).all()
+        assert (idx[i, min(int(cnt[i]), k_max):] == -1).all()
+
+
+def test_path_cost_parity(mp, orc):
+    rng = np.random.default_rng(7)
+    for M, D in [(2, 14), (17, 6), (65537, 14), (1, 28)]:
+        path = rng.uniform(-2.9, 2.9, (M, D)).astype(np.float32)
+        got = float(mp.path_cost(_dev(path)).cpu().numpy()[0])
+        ref = orc.path_cost(path)
+        assert got == pytest.approx(ref, rel=1e-6, abs=1e-12)

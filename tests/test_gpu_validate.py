@@ -1,0 +1,224 @@
+"""GPU parity of forward kinematics and motion validation against the FP64
+oracle, through the C ABI.
+
+Tolerances (stated by the method's target, derived for FP32):
+  * sphere centres and clearances: |gpu - oracle| <= 1e-5 * (1 + |oracle|)
+    (FP32 distances within 1e-5 relative at the ~1 m workspace scale);
+  * verdicts: bit-exact for every edge whose oracle minimum clearance lies
+    outside [margin - 1e-4, margin + 1e-4] m (the contact band, where FP32
+    and FP64 may legitimately disagree);
+  * interval counts: bit-exact (an integer both sides decide in FP32).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_30644_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-4
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2609_30644_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return m
+
+
+SCENES = {
+    "planar_pair": lambda: synth.planar_pair_scene(0),
+    "table_pair": lambda: synth.table_pair_scene(0),
+    "grid4": lambda: synth.grid4_scene(0),
+}
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _check_verdicts(valid_gpu, ref, margin):
+    inband = np.abs(ref["min_clear"] - margin) <= BAND
+    bad = (valid_gpu != ref["valid"]) & ~inband
+    assert not bad.any(), f"{bad.sum()} verdict mismatches outside the contact band: {np.nonzero(bad)[0][:10]}"
+    return int(inband.sum())
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_fk_parity(mp, orc, name):
+    scene = SCENES[name]()
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(0)
+    q = synth.uniform_configs(scene, 257, rng)
+    with mp.Problem(scene) as p:
+        out = mp.fk(p, _dev(q)).cpu().numpy()
+    for i in range(0, 257, 16):
+        ref = o.fk(q[:, i])
+        got = out[:, :, i].T
+        err = np.abs(got - ref[:, :3])
+        assert (err <= REL * (1 + np.abs(ref[:, :3]))).all(), err.max()
+
+
+@pytest.mark.parametrize("name,n_edges", [("planar_pair", 300), ("table_pair", 160), ("grid4", 40)])
+def test_clearance_parity(mp, orc, name, n_edges):
+    scene = SCENES[name]()
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, n_edges, seed=5, step_hi=1.5)
+    ref = o.validate_edges(qa, qb, 0.02, 0.0, early_exit=False)
+    with mp.Problem(scene, resolution=0.02) as p:
+        got = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref["min_clear"])
+    assert (err <= REL * (1 + np.abs(ref["min_clear"]))).all(), err.max()
+
+
+@pytest.mark.parametrize("margin", [0.0, 1e-4, 0.02])
+@pytest.mark.parametrize("name,n_edges", [("planar_pair", 600), ("table_pair", 300), ("grid4", 60)])
+def test_verdict_parity(mp, orc, name, n_edges, margin):
+    """Mixed candidate edges, long enough to span several 32-point tiles with
+    ragged tails (step up to 3 rad)."""
+    scene = SCENES[name]()
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, n_edges, seed=11, step_hi=3.0)
+    ref = o.validate_edges(qa, qb, 0.02, margin, early_exit=False)
+    assert ref["npoints"].max() >= 64            # several tiles
+    assert 0 < ref["valid"].sum() < n_edges      # a real mix
+    with mp.Problem(scene, resolution=0.02, margin=margin) as p:
+        n = qa.shape[1]
+        valid = torch.empty(n, dtype=torch.uint8, device="cuda")
+        length = torch.empty(n, dtype=torch.float32, device="cuda")
+        npts = torch.empty(n, dtype=torch.int32, device="cuda")
+        mp.validate_edges(p, _dev(qa), _dev(qb), valid, length, npts)
+        v = valid.cpu().numpy()
+        np.testing.assert_array_equal(npts.cpu().numpy(), ref["npoints"])
+        L = np.linalg.norm(qb.astype(np.float64) - qa.astype(np.float64), axis=0)
+        np.testing.assert_allclose(length.cpu().numpy(), L, rtol=1e-6, atol=1e-7)
+        # repeated launches reuse the self-resetting work counter
+        v2 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+        np.testing.assert_array_equal(v, v2)
+    _check_verdicts(v, ref, margin)
+
+
+def test_verdict_matches_gpu_clearance(mp):
+    """Culling never changes a verdict: the culled early-exit kernel agrees
+    with the unculled full-clearance kernel wherever FP32 itself is decided."""
+    scene = synth.table_pair_scene(1)
+    qa, qb = synth.candidate_edges(scene, 8192, seed=13)
+    with mp.Problem(scene, margin=1e-4) as p:
+        v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+        c = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy()
+    decided = np.abs(c - 1e-4) > 1e-6
+    np.testing.assert_array_equal(v[decided], (c[decided] >= 1e-4).astype(np.uint8))
+
+
+def test_full_size_batch_sampled(mp, orc):
+    """65,536-edge batch of the 2 x 7-DOF table scene in the benchmark's launch
+    configuration; a seeded sample of edges is re-checked by the oracle."""
+    scene = synth.table_pair_scene(0)
+    qa, qb = synth.candidate_edges(scene, 65536, seed=0)
+    with mp.Problem(scene, resolution=0.02, margin=1e-4) as p:
+        v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(65536, 256, replace=False))
+    o = orc.OracleScene(scene)
+    ref = o.validate_edges(qa[:, idx], qb[:, idx], 0.02, 1e-4, early_exit=False)
+    _check_verdicts(v[idx], ref, 1e-4)
+    assert 0.2 < v.mean() < 0.8
+
+
+def test_edge_cases(mp, orc):
+    scene = synth.table_pair_scene(0)
+    o = orc.OracleScene(scene)
+    rng = np.random.default_rng(3)
+    with mp.Problem(scene) as p:
+        # empty batch: no launch, no error
+        z = torch.empty((p.D, 0), dtype=torch.float32, device="cuda")
+        assert mp.validate_edges(p, z, z).numel() == 0
+        # zero-length edges (n = 1, both checkpoints equal) and single edge
+        q = synth.uniform_configs(scene, 33, rng)
+        v = mp.validate_edges(p, _dev(q), _dev(q)).cpu().numpy()
+        for i in range(33):
+            assert v[i] == o.config_valid(q[:, i], 0.0)[0] or abs(o.config_valid(q[:, i])[1]) <= BAND
+        v1 = mp.validate_edges(p, _dev(q[:, :1]), _dev(q[:, 1:2])).cpu().numpy()
+        ref = o.validate_edges(q[:, :1], q[:, 1:2], 0.02, 0.0)
+        _check_verdicts(v1, ref, 0.0)
+
+
+def test_single_robot_and_obstacle_variants(mp, orc):
+    """K = 1 (no robot-robot tests), no obstacles, cuboids only, and a link
+    with 16 spheres (the per-link maximum)."""
+    base = synth.table_pair_scene(0)
+    arm = base.robots[0]
+    big = synth.planar_arm(np.array([0, -1, 0, 0.1, 1, 0, 0, -0.2, 0, 0, 1, 0], np.float32),
+                           spheres_per_link=16, radius=0.02)
+    empty4 = np.zeros((0, 4), np.float32)
+    empty15 = np.zeros((0, 15), np.float32)
+    variants = [
+        synth.Scene([arm], base.obs_spheres, base.obs_cuboids),
+        synth.Scene(base.robots, empty4, empty15),
+        synth.Scene(base.robots, empty4, base.obs_cuboids),
+        synth.Scene([big, arm], base.obs_spheres, empty15),
+    ]
+    for sc in variants:
+        o = orc.OracleScene(sc)
+        qa, qb = synth.candidate_edges(sc, 120, seed=21, step_hi=2.0)
+        ref = o.validate_edges(qa, qb, 0.02, 0.0)
+        with mp.Problem(sc) as p:
+            v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+            c = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy().astype(np.float64)
+        _check_verdicts(v, ref, 0.0)
+        fin = ref["min_clear"] < 1e300
+        assert np.all(np.abs(c[fin] - ref["min_clear"][fin]) <= REL * (1 + np.abs(ref["min_clear"][fin])))
+
+
+def test_batched_scene_eight_arms(mp, orc):
+    """Largest composite problem of the batched workload (up to 8 arms,
+    56-DOF, hundreds of obstacles): fewer warps per block, same verdicts."""
+    for idx in range(40):
+        sc = synth.batched_scene(idx)
+        if sc.K >= 7:
+            break
+    o = orc.OracleScene(sc)
+    qa, qb = synth.candidate_edges(sc, 24, seed=2, step_lo=0.02, step_hi=0.2)
+    ref = o.validate_edges(qa, qb, 0.02, 0.0)
+    with mp.Problem(sc) as p:
+        v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+    _check_verdicts(v, ref, 0.0)
+
+
+def test_work_counters_structure(mp, orc):
+    """Counters on edges the oracle finds valid (no early exit): every
+    checkpoint is evaluated once and every link tests every obstacle bound."""
+    scene = synth.table_pair_scene(0)
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, 400, seed=17, step_hi=0.3)
+    ref = o.validate_edges(qa, qb, 0.02, 0.0)
+    keep = np.nonzero((ref["valid"] == 1) & (ref["min_clear"] > 1e-3))[0][:64]
+    assert keep.size >= 8
+    qa, qb = np.ascontiguousarray(qa[:, keep]), np.ascontiguousarray(qb[:, keep])
+    with mp.Problem(scene) as p:
+        cnt = mp.validate_work(p, _dev(qa), _dev(qb)).cpu().numpy()
+    pts = int((ref["npoints"][keep] + 1).sum())
+    L = scene.D
+    assert cnt[0] == pts
+    assert cnt[1] == pts * L
+    n_obs = len(scene.obs_spheres) + len(scene.obs_cuboids)
+    assert cnt[2] == pts * L * n_obs
+    assert cnt[3] == pts * 7 * 7          # links of robot 1 against robot 0's 7 links
+    assert cnt[7] >= pts * L
+
+
+def test_overlong_and_nonfinite_edges_are_invalid(mp):
+    scene = synth.table_pair_scene(0)
+    rng = np.random.default_rng(4)
+    qa = synth.uniform_configs(scene, 4, rng)
+    qb = qa.copy()
+    qb[0, 0] = np.inf
+    qb[1, 1] = np.nan
+    qb[2, 2] = qa[2, 2] + 0.02 * (1 << 20) * 1.5   # beyond the interval limit
+    with mp.Problem(scene) as p:
+        v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+        c = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy()
+    assert (v[:3] == 0).all()
+    assert (c[:3] < -1e30).all()
