@@ -185,6 +185,31 @@ mrpop_status mrpop_nearest(const float *tree, int64_t n_vertices, int64_t ld, in
                            const float *queries, const float *budgets, int64_t n_queries,
                            int64_t *out_idx, void *cuda_stream);
 
+/* Largest n_queries accepted by mrpop_nearest_noalloc. */
+#define MRPOP_NEAREST_NOALLOC_MAX_QUERIES 65536
+
+/* NEAREST with no device allocation.  The paper has no counterpart: this is a
+ * library convenience for callers that cannot allocate device memory while
+ * they plan -- a real-time replanning loop that must neither stall on the
+ * allocator nor risk an out-of-memory failure mid-cycle, or a process whose
+ * device memory is already reserved by another framework's caching allocator.
+ * Same arguments, results and errors as mrpop_nearest (the caller still passes
+ * every input and output), but the partial minima live in one fixed device
+ * array of 2 * MRPOP_NEAREST_NOALLOC_MAX_QUERIES records (1.5 MiB) that every
+ * GPU loading this library holds until the process exits.
+ *   - n_queries > MRPOP_NEAREST_NOALLOC_MAX_QUERIES is rejected with
+ *     MRPOP_EINVAL; nothing is launched.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture.
+ *   - All calls share the array: calls that overlap on the GPU (for example
+ *     on two streams) race and must be serialised by the caller.  Each call
+ *     writes every record it reads, so nothing needs clearing between calls.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+mrpop_status mrpop_nearest_noalloc(const float *tree, int64_t n_vertices, int64_t ld,
+                                   int32_t dim, const float *queries, const float *budgets,
+                                   int64_t n_queries, int64_t *out_idx, void *cuda_stream);
+
 /* NEIGHBORS(V, q, delta) of Alg. 2: indices of the vertices with |q - q_v| <=
  * delta, in ascending index order.  The first k_max of them go to
  * out_idx[i * k_max + j] (device int64 [n_queries][k_max], unused slots -1);

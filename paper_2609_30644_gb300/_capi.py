@@ -28,6 +28,7 @@ EXPORTS = (
     "mrpop_edge_clearance",
     "mrpop_validate_work",
     "mrpop_nearest",
+    "mrpop_nearest_noalloc",
     "mrpop_neighbors",
     "mrpop_path_cost",
 )
@@ -78,6 +79,7 @@ def _load() -> C.CDLL:
         "mrpop_edge_clearance": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_validate_work": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_nearest": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
+        "mrpop_nearest_noalloc": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
         "mrpop_path_cost": (i32, [vp, i64, i32, vp, vp]),
     }

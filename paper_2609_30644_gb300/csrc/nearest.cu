@@ -9,7 +9,9 @@
 // finish the block; when the tree is split across blocks (few queries, large
 // tree), partial bests go to stream-ordered scratch and a second kernel
 // reduces them.
+#include <algorithm>
 #include <cfloat>
+#include <mutex>
 
 #include "mrpop_internal.cuh"
 
@@ -265,3 +267,127 @@ mrpop_status launch_path_cost(const float *path, int64_t M, int dim, double *out
 }
 
 }  // namespace mrpop
+
+namespace mrpop {
+
+// ---------------------------------------------------------------------------
+// Allocation-free NEAREST (mrpop_nearest_noalloc).
+//
+// mrpop_nearest may take stream-ordered scratch for the partial minima of a
+// split tree.  Some callers cannot allocate device memory at query time: a
+// real-time replanning loop that must neither stall on the allocator nor risk
+// an out-of-memory failure in the middle of a control cycle, or a process whose
+// device memory has already been reserved by another framework's caching
+// allocator.  For them this variant keeps its partial minima in one fixed
+// file-scope device array, g_nearest_noalloc_scratch, which every GPU that
+// loads this library holds until the process exits.
+//
+// Host code cannot use the array's name as a device address (it is a host-side
+// stand-in), so the first call on each device, with that device current, looks
+// the address up with cudaGetSymbolAddress and caches it.  That first call
+// should therefore come before any stream capture.  All calls share the array;
+// two calls that overlap on the GPU (for example on two streams) race on it.
+// Every partial record a call reads was written earlier by the same call, so
+// nothing needs clearing between calls.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocRecords = 2 * MRPOP_NEAREST_NOALLOC_MAX_QUERIES;
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) Best g_nearest_noalloc_scratch[kNoAllocRecords];
+
+std::mutex g_noalloc_mu;
+Best *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+mrpop_status noalloc_scratch(Best **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_noalloc: device ordinal %d >= %d", dev,
+                         kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_nearest_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(nearest scratch)");
+        g_noalloc_ptr[dev] = static_cast<Best *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return MRPOP_OK;
+}
+
+template <int DP>
+mrpop_status nearest_noalloc_dp(const float *tree, int N, int64_t ld, int dim,
+                                const float *queries, const float *budgets, int Q,
+                                int64_t *out_idx, Best *scratch, cudaStream_t st) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int groups = (Q + kQB - 1) / kQB;
+    const int target = sms * 8;
+    int splits = 1;
+    if (groups < target && N > 4 * kNNThreads) {
+        splits = (target + groups - 1) / groups;
+        splits = std::min(splits, (N + 4 * kNNThreads - 1) / (4 * kNNThreads));
+    }
+    splits = std::max(1, std::min(splits, kNoAllocRecords / Q));
+    int chunk = (N + splits - 1) / splits;
+    chunk = ((chunk + kNNThreads - 1) / kNNThreads) * kNNThreads;
+    if (chunk == 0) chunk = kNNThreads;
+    splits = std::max(1, (N + chunk - 1) / chunk);
+    dim3 grid(groups, splits);
+    nearest_kernel<DP><<<grid, kNNThreads, 0, st>>>(tree, N, ld, dim, queries, budgets, Q, chunk,
+                                                    out_idx, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "nearest (no-alloc) kernel launch");
+    nearest_reduce_kernel<<<(Q + 255) / 256, 256, 0, st>>>(scratch, splits, Q, out_idx);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "nearest (no-alloc) reduce launch");
+    return MRPOP_OK;
+}
+
+}  // namespace
+}  // namespace mrpop
+
+extern "C" mrpop_status mrpop_nearest_noalloc(const float *tree, int64_t N, int64_t ld,
+                                              int32_t dim, const float *queries,
+                                              const float *budgets, int64_t Q,
+                                              int64_t *out_idx, void *stream) {
+    using namespace mrpop;
+    if (dim < 1 || dim > MRPOP_MAX_LINKS)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_noalloc: dim=%d outside [1, %d]", dim,
+                         MRPOP_MAX_LINKS);
+    if (N < 0 || Q < 0 || ld < N || N > (int64_t)INT32_MAX)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_noalloc: bad sizes N=%lld ld=%lld Q=%lld",
+                         (long long)N, (long long)ld, (long long)Q);
+    if (Q > MRPOP_NEAREST_NOALLOC_MAX_QUERIES)
+        return set_error(MRPOP_EINVAL,
+                         "mrpop_nearest_noalloc: %lld queries exceed the fixed scratch limit of %d "
+                         "(MRPOP_NEAREST_NOALLOC_MAX_QUERIES); split the batch or use mrpop_nearest",
+                         (long long)Q, MRPOP_NEAREST_NOALLOC_MAX_QUERIES);
+    if (Q == 0) return MRPOP_OK;
+    if (!queries || !budgets || !out_idx || (N > 0 && !tree))
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_noalloc: NULL buffer");
+    Best *scratch = nullptr;
+    mrpop_status s = noalloc_scratch(&scratch);
+    if (s != MRPOP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N, q = (int)Q;
+    switch ((dim + 3) & ~3) {
+        case 4: return nearest_noalloc_dp<4>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 8: return nearest_noalloc_dp<8>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 12: return nearest_noalloc_dp<12>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 16: return nearest_noalloc_dp<16>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 20: return nearest_noalloc_dp<20>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 24: return nearest_noalloc_dp<24>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 28: return nearest_noalloc_dp<28>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        case 32: return nearest_noalloc_dp<32>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+        default: break;
+    }
+    if (((dim + 3) & ~3) <= 48)
+        return nearest_noalloc_dp<48>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+    return nearest_noalloc_dp<64>(tree, n, ld, dim, queries, budgets, q, out_idx, scratch, st);
+}
+
