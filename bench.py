@@ -57,8 +57,10 @@ FLOPS_PER = {
     "bound_test": 10,           # |c - c_o|^2 vs (r + r_o + m)^2
     "sphere_obstacle_test": 11,
     "cuboid_test": 31,          # R^T (c - c_b), clamp excess, squared norm
+    "box_bound_test": 31,       # same distance for a bounding sphere
     "pair_test": 11,
     "point_transform": 18,      # R p + t
+    "tile_bound": 390,          # centroid and max radius of 32 coarse centres
 }
 
 
@@ -69,7 +71,10 @@ def algorithmic_flops(cnt) -> float:
             + c[4] * FLOPS_PER["sphere_obstacle_test"]
             + c[5] * FLOPS_PER["cuboid_test"]
             + c[6] * FLOPS_PER["pair_test"]
-            + c[7] * FLOPS_PER["point_transform"])
+            + c[7] * FLOPS_PER["point_transform"]
+            + c[8] * FLOPS_PER["bound_test"]
+            + c[9] * FLOPS_PER["tile_bound"]
+            + (c[10] + c[11]) * FLOPS_PER["box_bound_test"])
 
 
 def make_inputs(rank: int):

@@ -162,14 +162,24 @@ mrpop_status mrpop_edge_clearance(mrpop_problem *p, const float *qa, const float
                                   int64_t n_edges, float *min_clear, void *cuda_stream);
 
 /* Work counters of mrpop_validate_edges on the same inputs, summed over the
- * batch, for roofline accounting (device int64 [8], overwritten):
- *   [0] checkpoints evaluated        [1] joint transforms
- *   [2] link-vs-obstacle bound tests [3] link-vs-link bound tests
- *   [4] sphere-vs-sphere-obstacle tests  [5] sphere-vs-cuboid tests
- *   [6] robot-robot sphere-pair tests    [7] point transforms (coarse centres
- *       and sphere centres)
- * Counts are per checkpoint: a sphere-level test is counted only where that
- * checkpoint's own link-level test hit (the kernel may run more, warp-wide). */
+ * batch, for roofline accounting (device int64 [MRPOP_WORK_COUNTERS],
+ * overwritten):
+ *   [0]  checkpoints evaluated             [1]  joint transforms
+ *   [2]  checkpoint link-vs-obstacle-sphere bound tests (tile candidates only)
+ *   [3]  checkpoint link-vs-link bound tests (tile candidates only)
+ *   [4]  sphere-vs-sphere-obstacle tests   [5]  sphere-vs-cuboid tests
+ *   [6]  robot-robot sphere-pair tests     [7]  point transforms (coarse
+ *        centres and sphere centres)
+ *   [8]  tile-level sphere tests (tile bound vs obstacle spheres and vs the
+ *        tile bounds of earlier robots' links)
+ *   [9]  tile bounds built (one per tile and link: centroid and radius of the
+ *        link's coarse spheres at the tile's 32 checkpoints)
+ *   [10] checkpoint link-vs-cuboid box tests (tile candidates only)
+ *   [11] tile-level box tests (tile bound vs cuboid)
+ * Per-checkpoint counts only include what that checkpoint decides: a
+ * sphere-level test is counted only where the checkpoint's own link-level
+ * test hit (the kernel may run more, warp-wide). */
+#define MRPOP_WORK_COUNTERS 12
 mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, const float *qb,
                                  int64_t n_edges, int64_t *counters, void *cuda_stream);
 

@@ -229,7 +229,7 @@ def edge_clearance(p: Problem, qa: torch.Tensor, qb: torch.Tensor,
 
 def validate_work(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -> torch.Tensor:
     n = _edges(p, qa, qb)
-    out = torch.zeros(8, dtype=torch.int64, device=qa.device)
+    out = torch.zeros(12, dtype=torch.int64, device=qa.device)   # MRPOP_WORK_COUNTERS
     _check(lib.mrpop_validate_work(p.handle, _dptr(qa, torch.float32, "qa"),
                                    _dptr(qb, torch.float32, "qb"), n,
                                    _dptr(out, torch.int64, "counters"), _stream(stream)))

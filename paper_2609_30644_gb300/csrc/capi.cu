@@ -314,7 +314,7 @@ extern "C" mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, c
     if (st != MRPOP_OK) return st;
     if (!counters) return set_error(MRPOP_EINVAL, "mrpop_validate_work: counters is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    MRPOP_CUDA_TRY(cudaMemsetAsync(counters, 0, 8 * sizeof(int64_t), s));
+    MRPOP_CUDA_TRY(cudaMemsetAsync(counters, 0, MRPOP_WORK_COUNTERS * sizeof(int64_t), s));
     if (n == 0) return MRPOP_OK;
     return launch_validate(p, qa, qb, n, nullptr, nullptr, nullptr, nullptr,
                            (unsigned long long *)counters, s);

@@ -167,6 +167,159 @@ mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const flo
     return MRPOP_OK;
 }
 
+// NEAREST for large query batches: every thread owns QPT queries in
+// registers and the block streams its slice of the tree through shared memory
+// in tiles of kTile vertices, kept as SoA rows [dim + 1][kTile] (coalesced,
+// conflict-free stores).  One float4 broadcast read gives one coordinate of 4
+// vertices, which feeds 4 x QPT distance accumulators; a candidate test runs
+// only where some accumulator reaches the running best.
+typedef unsigned long long f2;  // two FP32 lanes in one 64-bit register pair
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+constexpr int kQThreads = 128;
+constexpr int kQPT = 2;
+constexpr int kTile = 256;
+
+template <int DIM>
+__global__ void __launch_bounds__(kQThreads)
+nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
+                   const float *__restrict__ queries, const float *__restrict__ budgets, int Q,
+                   int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial) {
+    __shared__ __align__(16) float tile[(DIM + 1) * kTile];
+    f2 qp[kQPT][DIM];   // (q_d, q_d) packed
+    float cq[kQPT];
+    Best best[kQPT];
+    const int qb = blockIdx.x * kQThreads * kQPT;
+#pragma unroll
+    for (int j = 0; j < kQPT; ++j) {
+        const int q = qb + j * kQThreads + threadIdx.x;
+        const bool ok = q < Q;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const float v = ok ? queries[(size_t)d * Q + q] : 0.f;
+            qp[j][d] = f2_pack(v, v);
+        }
+        cq[j] = ok ? budgets[q] : -FLT_MAX;   // nothing is admissible for padding
+        best[j] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+    }
+    const int vs = blockIdx.y * chunk;
+    const int ve = min(N, vs + chunk);
+    const float4 *tile4 = reinterpret_cast<const float4 *>(tile);
+    for (int v0 = vs; v0 < ve; v0 += kTile) {
+        const int nv = min(kTile, ve - v0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < (DIM + 1) * kTile; i += kQThreads) {
+            const int d = i / kTile, j = i - d * kTile;
+            // padding vertices get g = +inf: never admissible
+            tile[i] = j < nv ? __ldg(tree + (size_t)d * ld + v0 + j) : (d == DIM ? FLT_MAX * 2.f : 0.f);
+        }
+        __syncthreads();
+        const int ng = (nv + 3) >> 2;
+        for (int gq = 0; gq < ng; ++gq) {
+            // packed FP32x2: lanes (vertex 4gq, 4gq+1) and (4gq+2, 4gq+3);
+            // each element rounds exactly like the scalar sub / fma
+            f2 acc[kQPT][2];
+#pragma unroll
+            for (int j = 0; j < kQPT; ++j) acc[j][0] = acc[j][1] = 0ull;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const float4 xv = tile4[d * (kTile / 4) + gq];
+                const f2 x01 = f2_pack(xv.x, xv.y), x23 = f2_pack(xv.z, xv.w);
+#pragma unroll
+                for (int j = 0; j < kQPT; ++j) {
+                    const f2 a01 = f2_sub(qp[j][d], x01), a23 = f2_sub(qp[j][d], x23);
+                    acc[j][0] = f2_fma(a01, a01, acc[j][0]);
+                    acc[j][1] = f2_fma(a23, a23, acc[j][1]);
+                }
+            }
+            float accf[kQPT][4];
+#pragma unroll
+            for (int j = 0; j < kQPT; ++j) {
+                f2_unpack(acc[j][0], accf[j][0], accf[j][1]);
+                f2_unpack(acc[j][1], accf[j][2], accf[j][3]);
+            }
+#pragma unroll
+            for (int j = 0; j < kQPT; ++j) {
+                const float bd = best[j].d2;
+                if ((accf[j][0] <= bd) | (accf[j][1] <= bd) | (accf[j][2] <= bd) | (accf[j][3] <= bd)) {
+                    const float4 g4 = tile4[DIM * (kTile / 4) + gq];
+                    const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float d2 = accf[j][u], g = gg[u];
+                        // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index)
+                        if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
+                            (d2 < best[j].d2 || g < best[j].g)) {
+                            best[j].d2 = d2;
+                            best[j].g = g;
+                            best[j].idx = v0 + 4 * gq + u;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kQPT; ++j) {
+        const int q = qb + j * kQThreads + threadIdx.x;
+        if (q >= Q) continue;
+        if (partial)
+            partial[(size_t)blockIdx.y * Q + q] = best[j];
+        else
+            out_idx[q] = best[j].idx;
+    }
+}
+
+template <int DIM>
+mrpop_status nearest_qpt(const float *tree, int N, int64_t ld, const float *queries,
+                         const float *budgets, int Q, int64_t *out_idx, cudaStream_t st) {
+    int dev = 0, sms = 1, bps = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_qpt_kernel<DIM>, kQThreads, 0);
+    bps = std::max(bps, 1);
+    const int qblocks = (Q + kQThreads * kQPT - 1) / (kQThreads * kQPT);
+    const int target = sms * bps;
+    int splits = std::max(1, (target + qblocks - 1) / qblocks);
+    splits = std::min(splits, std::max(1, (N + kTile - 1) / kTile));
+    splits = std::min(splits, 65535);
+    int chunk = (N + splits - 1) / splits;
+    chunk = std::max(kTile, ((chunk + kTile - 1) / kTile) * kTile);
+    splits = std::max(1, (N + chunk - 1) / chunk);
+    Best *partial = nullptr;
+    if (splits > 1)
+        MRPOP_CUDA_TRY(cudaMallocAsync((void **)&partial, sizeof(Best) * (size_t)splits * Q, st));
+    dim3 grid(qblocks, splits);
+    nearest_qpt_kernel<DIM><<<grid, kQThreads, 0, st>>>(tree, N, ld, queries, budgets, Q, chunk,
+                                                        out_idx, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && splits > 1) {
+        nearest_reduce_kernel<<<(Q + 255) / 256, 256, 0, st>>>(partial, splits, Q, out_idx);
+        e = cudaGetLastError();
+    }
+    if (partial) cudaFreeAsync(partial, st);
+    if (e != cudaSuccess) return cuda_error(e, "nearest (query-blocked) kernel launch");
+    return MRPOP_OK;
+}
+
 // NEIGHBORS: one warp per query, lanes over 32 consecutive vertices, in
 // ascending order; ballot + prefix popcount keeps the output sorted.
 __global__ void neighbors_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
@@ -233,6 +386,20 @@ mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,
                             int64_t *out_idx, cudaStream_t st) {
     const int n = (int)N, q = (int)Q;
+    // Large batches: queries in registers against shared-memory tree tiles.
+    if (Q >= 2048 && N > 0) {
+        switch (dim) {
+            case 3: return nearest_qpt<3>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 6: return nearest_qpt<6>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 7: return nearest_qpt<7>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 14: return nearest_qpt<14>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 21: return nearest_qpt<21>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 28: return nearest_qpt<28>(tree, n, ld, queries, budgets, q, out_idx, st);
+            default: break;
+        }
+    }
+    // Small batches (and other dimensions): vertices across lanes, queries
+    // broadcast from shared memory, warp-shuffle argmin.
     const int dp = (dim + 3) & ~3;
     switch (dp) {
         case 4: return nearest_dp<4>(tree, n, ld, dim, queries, budgets, q, out_idx, st);

@@ -9,12 +9,18 @@
 //    every tile samples the whole edge and a collision anywhere ends the edge
 //    after few tiles (early exit with __any_sync).
 //  * Per link, forward kinematics in registers (Rz, then the d/a/alpha
-//    offsets), a link-level ("coarse") sphere test against every obstacle's
-//    bounding sphere and against the stored link frames of earlier robots,
-//    warp-wide OR of the per-lane hit masks (__reduce_or_sync), then
-//    sphere-level ("fine") tests only for the union mask, on a register cache
-//    of the link's world spheres.  Culling never changes a verdict: coarse
-//    spheres enclose their fine spheres with a slack above FP32 rounding.
+//    offsets), then three levels of culling:
+//      1. tile level: the warp bounds the link's coarse spheres at its 32
+//         checkpoints by one sphere (centroid + max radius, shuffles); lane i
+//         tests obstacle i (and the tile bound of earlier robots' link i)
+//         against it, and a ballot gives the candidate set;
+//      2. checkpoint level ("coarse" stage of the paper): each lane tests its
+//         own link sphere against the candidates only;
+//      3. sphere level ("fine" stage): the warp-wide OR of the lanes' hit
+//         masks (__reduce_or_sync) selects the obstacles / links whose spheres
+//         are tested, on a register cache of the link's world spheres.
+//    Culling never changes a verdict: each bound encloses what it replaces
+//    with a slack above FP32 rounding.
 //  * The paper's own design (4 threads per motion, then threads reassigned in
 //    proportion to the fine-test load) balances work across motions; here the
 //    warp-uniform union mask keeps all 32 lanes busy on the same tests instead.
@@ -30,6 +36,11 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsMax = 4;
+constexpr int kCounters = MRPOP_WORK_COUNTERS;
+// Absolute slack (m) added to tile bounds: covers FP32 rounding of the
+// centroid and radius so the tile test never drops a candidate that a
+// checkpoint's own link-level test would keep.
+constexpr float kTileSlack = 1e-4f;
 
 enum Mode { kVerdict = 0, kClearance = 1, kCount = 2 };
 
@@ -50,6 +61,7 @@ struct VParams {
     int total_warps;
     int warp_floats;
     int dpad;
+    int nstore;  // links of robots 0..K-2 (their frames and tile bounds are kept)
 };
 
 struct Frame {
@@ -97,6 +109,21 @@ __device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, f
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
+// Squared distance from point p to an oriented box (centre C, half extents H,
+// unit axes A0..A2 as columns): |max(|A^T (p - C)| - h, 0)|^2.
+__device__ __forceinline__ float box_dist2(float px, float py, float pz, const float4 &C,
+                                           const float4 &H, const float4 &A0, const float4 &A1,
+                                           const float4 &A2) {
+    const float vx = px - C.x, vy = py - C.y, vz = pz - C.z;
+    const float p0 = fmaf(A0.x, vx, fmaf(A0.y, vy, A0.z * vz));
+    const float p1 = fmaf(A1.x, vx, fmaf(A1.y, vy, A1.z * vz));
+    const float p2 = fmaf(A2.x, vx, fmaf(A2.y, vy, A2.z * vz));
+    const float u0 = fmaxf(fabsf(p0) - H.x, 0.f);
+    const float u1 = fmaxf(fabsf(p1) - H.y, 0.f);
+    const float u2 = fmaxf(fabsf(p2) - H.z, 0.f);
+    return fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+}
+
 __device__ __forceinline__ Frame load_base(const float4 *tab, const Tables &t, int b) {
     const float4 r0 = tab[t.off_base + 3 * b], r1 = tab[t.off_base + 3 * b + 1],
                  r2 = tab[t.off_base + 3 * b + 2];
@@ -127,7 +154,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
     float4 *tab = sm4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *ws = reinterpret_cast<float *>(sm4 + P.t.n_f4) + (size_t)warp * P.warp_floats;
-    float *qa_s = ws, *dq_s = ws + P.dpad, *xf = ws + 2 * P.dpad;
+    float *qa_s = ws, *dq_s = ws + P.dpad;
+    float4 *tb = reinterpret_cast<float4 *>(ws + 2 * P.dpad);      // tile bounds [nstore]
+    float *xf = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][15][32]
 
     for (int i = threadIdx.x; i < P.t.n_f4; i += blockDim.x) tab[i] = P.blob[i];
     __syncthreads();
@@ -135,9 +164,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
     const Tables &t = P.t;
     const int K = t.K, D = t.L, NS = t.NS, NC = t.NC;
     const float m = P.margin;
-    unsigned long long cnt[8];
+    unsigned long long cnt[kCounters];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) cnt[c] = 0ull;
+    for (int c = 0; c < kCounters; ++c) cnt[c] = 0ull;
 
     for (;;) {
         int e = 0;
@@ -182,6 +211,30 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                     sincosf(th, &sn, &cs);
                     const Frame F = rotz(Tm, cs, sn);
                     const float3 cc = apply(F, LC.x, LC.y, LC.z);
+                    const int sf = __float_as_int(LB.y), ns = __float_as_int(LB.z);
+                    if (MODE == kCount && active) cnt[1] += 1;
+
+                    // Tile bound: one sphere around this link's coarse spheres at
+                    // all 32 checkpoints of the tile (warp-uniform).
+                    float4 bnd = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (MODE != kClearance) {
+                        float sx = cc.x, sy = cc.y, sz = cc.z;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            sx += __shfl_xor_sync(kFull, sx, off);
+                            sy += __shfl_xor_sync(kFull, sy, off);
+                            sz += __shfl_xor_sync(kFull, sz, off);
+                        }
+                        bnd.x = sx * (1.f / 32.f);
+                        bnd.y = sy * (1.f / 32.f);
+                        bnd.z = sz * (1.f / 32.f);
+                        float rd = __fsqrt_rn(dist2(cc.x, cc.y, cc.z, bnd.x, bnd.y, bnd.z));
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1)
+                            rd = fmaxf(rd, __shfl_xor_sync(kFull, rd, off));
+                        bnd.w = rd + LC.w + kTileSlack;
+                        if (MODE == kCount && lane == 0) cnt[9] += 1;
+                    }
                     if (store) {
                         float *x = xf + (size_t)l * kXfFloats * 32 + lane;
 #pragma unroll
@@ -192,9 +245,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                         x[12 * 32] = cc.x;
                         x[13 * 32] = cc.y;
                         x[14 * 32] = cc.z;
+                        if (lane == 0) tb[l] = bnd;
+                        __syncwarp();
                     }
-                    const int sf = __float_as_int(LB.y), ns = __float_as_int(LB.z);
-                    if (MODE == kCount && active) cnt[1] += 1;
                     if (ns > 0) {
                         float4 pw[SPL];
                         bool have = false;
@@ -221,17 +274,31 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                             if (MODE == kClearance) {
                                 own = low_mask(cn);
                             } else {
-                                for (int o = 0; o < cn; ++o) {
+                                bool h = false;
+                                if (lane < cn) {
+                                    const float4 ob = tab[t.off_os + c0 + lane];
+                                    const float d2 = dist2(bnd.x, bnd.y, bnd.z, ob.x, ob.y, ob.z);
+                                    const float th2 = bnd.w + ob.w + m;
+                                    h = d2 < th2 * th2;
+                                }
+                                const unsigned cand = __ballot_sync(kFull, h);
+                                unsigned cm = cand;
+                                while (cm) {
+                                    const int o = __ffs(cm) - 1;
+                                    cm &= cm - 1;
                                     const float4 ob = tab[t.off_os + c0 + o];
                                     const float d2 = dist2(cc.x, cc.y, cc.z, ob.x, ob.y, ob.z);
                                     const float th2 = rc + ob.w;
                                     own |= (d2 < th2 * th2) ? (1u << o) : 0u;
                                 }
+                                if (MODE == kCount) {
+                                    if (lane == 0) cnt[8] += cn;
+                                    if (active) cnt[2] += __popc(cand);
+                                }
                             }
                             const unsigned wm =
                                 MODE == kClearance ? own : __reduce_or_sync(kFull, own);
                             if (MODE == kCount && active) {
-                                cnt[2] += cn;
                                 cnt[4] += (unsigned long long)__popc(own) * ns;
                                 own_any |= own != 0;
                             }
@@ -258,24 +325,42 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                             }
                         }
 
-                        // ---- robot vs obstacle cuboids (oriented boxes)
+                        // ---- robot vs obstacle cuboids (oriented boxes); the tile and
+                        // checkpoint levels test their bounding spheres against the box
+                        // itself (distance to a convex set is 1-Lipschitz, so a sphere
+                        // that encloses the fine spheres stays conservative)
                         for (int c0 = 0; c0 < NC; c0 += 32) {
                             const int cn = min(32, NC - c0);
                             unsigned own = 0;
                             if (MODE == kClearance) {
                                 own = low_mask(cn);
                             } else {
-                                for (int o = 0; o < cn; ++o) {
-                                    const float4 cb = tab[t.off_oc + kCuboidF4 * (c0 + o)];
-                                    const float d2 = dist2(cc.x, cc.y, cc.z, cb.x, cb.y, cb.z);
-                                    const float th2 = rc + cb.w;
-                                    own |= (d2 < th2 * th2) ? (1u << o) : 0u;
+                                bool h = false;
+                                if (lane < cn) {
+                                    const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + lane);
+                                    const float d2 = box_dist2(bnd.x, bnd.y, bnd.z, cbp[0], cbp[1],
+                                                               cbp[2], cbp[3], cbp[4]);
+                                    const float th2 = bnd.w + m;
+                                    h = d2 < th2 * th2;
+                                }
+                                const unsigned cand = __ballot_sync(kFull, h);
+                                unsigned cm = cand;
+                                while (cm) {
+                                    const int o = __ffs(cm) - 1;
+                                    cm &= cm - 1;
+                                    const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + o);
+                                    const float d2 = box_dist2(cc.x, cc.y, cc.z, cbp[0], cbp[1],
+                                                               cbp[2], cbp[3], cbp[4]);
+                                    own |= (d2 < rc * rc) ? (1u << o) : 0u;
+                                }
+                                if (MODE == kCount) {
+                                    if (lane == 0) cnt[11] += cn;
+                                    if (active) cnt[10] += __popc(cand);
                                 }
                             }
                             const unsigned wm =
                                 MODE == kClearance ? own : __reduce_or_sync(kFull, own);
                             if (MODE == kCount && active) {
-                                cnt[2] += cn;
                                 cnt[5] += (unsigned long long)__popc(own) * ns;
                                 own_any |= own != 0;
                             }
@@ -291,15 +376,8 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
 #pragma unroll
                                     for (int s = 0; s < SPL; ++s)
                                         if (s < ns) {
-                                            const float vx = pw[s].x - C.x, vy = pw[s].y - C.y,
-                                                        vz = pw[s].z - C.z;
-                                            const float p0 = fmaf(A0.x, vx, fmaf(A0.y, vy, A0.z * vz));
-                                            const float p1 = fmaf(A1.x, vx, fmaf(A1.y, vy, A1.z * vz));
-                                            const float p2 = fmaf(A2.x, vx, fmaf(A2.y, vy, A2.z * vz));
-                                            const float u0 = fmaxf(fabsf(p0) - H.x, 0.f);
-                                            const float u1 = fmaxf(fabsf(p1) - H.y, 0.f);
-                                            const float u2 = fmaxf(fabsf(p2) - H.z, 0.f);
-                                            const float d2 = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+                                            const float d2 =
+                                                box_dist2(pw[s].x, pw[s].y, pw[s].z, C, H, A0, A1, A2);
                                             if (MODE == kClearance) {
                                                 minc = fminf(minc, __fsqrt_rn(d2) - pw[s].w);
                                             } else {
@@ -318,23 +396,49 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                                 own0 = low_mask(l0);
                                 own1 = l0 > 32 ? low_mask(l0 - 32) : 0u;
                             } else {
-                                for (int i = 0; i < l0; ++i) {
-                                    const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
-                                    const float ri = tab[t.off_link + kLinkF4 * i + 2].w;
-                                    const float d2 = dist2(cc.x, cc.y, cc.z, x[12 * 32], x[13 * 32],
-                                                           x[14 * 32]);
-                                    const float th2 = LC.w + ri + m;
-                                    const unsigned bit = d2 < th2 * th2 ? 1u : 0u;
-                                    if (i < 32)
-                                        own0 |= bit << i;
+                                // tile-level candidates: lane i tests link i (and i + 32)
+                                bool h0 = false, h1 = false;
+                                if (lane < l0) {
+                                    const float4 o = tb[lane];
+                                    const float d2 = dist2(bnd.x, bnd.y, bnd.z, o.x, o.y, o.z);
+                                    const float th2 = bnd.w + o.w + m;
+                                    h0 = d2 < th2 * th2;
+                                }
+                                if (lane + 32 < l0) {
+                                    const float4 o = tb[lane + 32];
+                                    const float d2 = dist2(bnd.x, bnd.y, bnd.z, o.x, o.y, o.z);
+                                    const float th2 = bnd.w + o.w + m;
+                                    h1 = d2 < th2 * th2;
+                                }
+                                const unsigned cand0 = __ballot_sync(kFull, h0);
+                                const unsigned cand1 = __ballot_sync(kFull, h1);
+                                for (int w = 0; w < 2; ++w) {
+                                    unsigned cm = w == 0 ? cand0 : cand1;
+                                    unsigned own = 0;
+                                    while (cm) {
+                                        const int bit = __ffs(cm) - 1;
+                                        cm &= cm - 1;
+                                        const int i = bit + 32 * w;
+                                        const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
+                                        const float ri = tab[t.off_link + kLinkF4 * i + 2].w;
+                                        const float d2 = dist2(cc.x, cc.y, cc.z, x[12 * 32],
+                                                               x[13 * 32], x[14 * 32]);
+                                        const float th2 = LC.w + ri + m;
+                                        own |= (d2 < th2 * th2) ? (1u << bit) : 0u;
+                                    }
+                                    if (w == 0)
+                                        own0 = own;
                                     else
-                                        own1 |= bit << (i - 32);
+                                        own1 = own;
+                                }
+                                if (MODE == kCount) {
+                                    if (lane == 0) cnt[8] += l0;
+                                    if (active) cnt[3] += __popc(cand0) + __popc(cand1);
                                 }
                             }
                             const unsigned w0 = MODE == kClearance ? own0 : __reduce_or_sync(kFull, own0);
                             const unsigned w1 = MODE == kClearance ? own1 : __reduce_or_sync(kFull, own1);
                             if (MODE == kCount && active) {
-                                cnt[3] += l0;
                                 own_any |= (own0 | own1) != 0;
                                 for (int w = 0; w < 2; ++w) {
                                     unsigned mm = w == 0 ? own0 : own1;
@@ -412,7 +516,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
 
     if (MODE == kCount) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < kCounters; ++c) {
             unsigned long long v = cnt[c];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
@@ -453,6 +557,7 @@ mrpop_status launch_spl(mrpop_problem *p, VParams &V, int warps, size_t smem,
     const int spl = p->dev.t.max_spheres_per_link;
     if (spl <= 4) return launch_mode<MODE, 4>(p, V, warps, smem, st);
     if (spl <= 8) return launch_mode<MODE, 8>(p, V, warps, smem, st);
+    if (spl <= 9) return launch_mode<MODE, 9>(p, V, warps, smem, st);
     if (spl <= 12) return launch_mode<MODE, 12>(p, V, warps, smem, st);
     return launch_mode<MODE, 16>(p, V, warps, smem, st);
 }
@@ -509,7 +614,8 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
     V.work = p->dev.edge_counter;
     V.dpad = (t.L + 3) & ~3;
     const int nstore = t.link0[t.K - 1];
-    V.warp_floats = 2 * V.dpad + nstore * kXfFloats * 32;
+    V.nstore = nstore;
+    V.warp_floats = 2 * V.dpad + 4 * nstore + nstore * kXfFloats * 32;
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
     int warps = kWarpsMax;
     size_t smem = 0;

@@ -189,7 +189,9 @@ def test_batched_scene_eight_arms(mp, orc):
 
 def test_work_counters_structure(mp, orc):
     """Counters on edges the oracle finds valid (no early exit): every
-    checkpoint is evaluated once and every link tests every obstacle bound."""
+    checkpoint is evaluated once, every tile bounds every link once and tests
+    it against every obstacle and every earlier robot's link, and checkpoint
+    tests never exceed their tile candidates."""
     scene = synth.table_pair_scene(0)
     o = orc.OracleScene(scene)
     qa, qb = synth.candidate_edges(scene, 400, seed=17, step_hi=0.3)
@@ -199,26 +201,36 @@ def test_work_counters_structure(mp, orc):
     qa, qb = np.ascontiguousarray(qa[:, keep]), np.ascontiguousarray(qb[:, keep])
     with mp.Problem(scene) as p:
         cnt = mp.validate_work(p, _dev(qa), _dev(qb)).cpu().numpy()
-    pts = int((ref["npoints"][keep] + 1).sum())
+    npts = ref["npoints"][keep]
+    pts = int((npts + 1).sum())
+    tiles = int(((npts >> 5) + 1).sum())
     L = scene.D
+    n_obs = len(scene.obs_spheres) + len(scene.obs_cuboids)
     assert cnt[0] == pts
     assert cnt[1] == pts * L
-    n_obs = len(scene.obs_spheres) + len(scene.obs_cuboids)
-    assert cnt[2] == pts * L * n_obs
-    assert cnt[3] == pts * 7 * 7          # links of robot 1 against robot 0's 7 links
+    NS, NC = len(scene.obs_spheres), len(scene.obs_cuboids)
+    assert cnt[9] == tiles * L
+    assert cnt[8] == tiles * (L * NS + 7 * 7)      # robot 1's links vs robot 0's 7
+    assert cnt[11] == tiles * L * NC
+    assert cnt[2] <= pts * L * NS and cnt[10] <= pts * L * NC and cnt[3] <= pts * 7 * 7
     assert cnt[7] >= pts * L
 
 
-def test_overlong_and_nonfinite_edges_are_invalid(mp):
+def test_robot_robot_contact_spatial(mp, orc):
+    """Two 7-DOF arms with bases 0.5 m apart and no obstacles: every verdict
+    is decided by robot-robot sphere pairs (tile, link and sphere levels)."""
     scene = synth.table_pair_scene(0)
-    rng = np.random.default_rng(4)
-    qa = synth.uniform_configs(scene, 4, rng)
-    qb = qa.copy()
-    qb[0, 0] = np.inf
-    qb[1, 1] = np.nan
-    qb[2, 2] = qa[2, 2] + 0.02 * (1 << 20) * 1.5   # beyond the interval limit
-    with mp.Problem(scene) as p:
+    scene.robots[0].base[7] = -0.25
+    scene.robots[1].base[7] = 0.25
+    scene = synth.Scene(scene.robots, np.zeros((0, 4), np.float32), np.zeros((0, 15), np.float32))
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, 400, seed=31, step_hi=1.0)
+    ref = o.validate_edges(qa, qb, 0.02, 1e-4)
+    assert 0.1 < ref["valid"].mean() < 0.9
+    with mp.Problem(scene, margin=1e-4) as p:
         v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
-        c = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy()
-    assert (v[:3] == 0).all()
-    assert (c[:3] < -1e30).all()
+        c = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy().astype(np.float64)
+        cnt = mp.validate_work(p, _dev(qa), _dev(qb)).cpu().numpy()
+    _check_verdicts(v, ref, 1e-4)
+    assert np.all(np.abs(c - ref["min_clear"]) <= REL * (1 + np.abs(ref["min_clear"])))
+    assert cnt[6] > 0        # sphere-level robot-robot tests did run
