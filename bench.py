@@ -440,7 +440,7 @@ def run_ours(args) -> None:
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,   # validate, nearest, neighbors, path cost (2)
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

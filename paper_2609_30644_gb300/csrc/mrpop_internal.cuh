@@ -36,7 +36,7 @@ struct Tables {
 
 constexpr int kLinkF4 = 3;
 constexpr int kCuboidF4 = 5;
-constexpr int kXfFloats = 15;  // stored link frame: R (9), t (3), coarse centre (3)
+constexpr int kXfFloats = 12;  // stored link frame: R (9), t (3)
 
 struct DeviceProblem {
     Tables t;

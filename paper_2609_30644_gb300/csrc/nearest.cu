@@ -167,12 +167,6 @@ mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const flo
     return MRPOP_OK;
 }
 
-// NEAREST for large query batches: every thread owns QPT queries in
-// registers and the block streams its slice of the tree through shared memory
-// in tiles of kTile vertices, kept as SoA rows [dim + 1][kTile] (coalesced,
-// conflict-free stores).  One float4 broadcast read gives one coordinate of 4
-// vertices, which feeds 4 x QPT distance accumulators; a candidate test runs
-// only where some accumulator reaches the running best.
 typedef unsigned long long f2;  // two FP32 lanes in one 64-bit register pair
 
 __device__ __forceinline__ f2 f2_pack(float lo, float hi) {
@@ -183,9 +177,9 @@ __device__ __forceinline__ f2 f2_pack(float lo, float hi) {
 __device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
     f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
@@ -194,6 +188,22 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
     return r;
 }
 
+// NEAREST for large query batches: every thread owns QPT queries in
+// registers and the block streams its slice of the tree through shared memory
+// in tiles of kTile vertices, kept as SoA rows [dim][kTile] (coalesced,
+// conflict-free stores) plus two rows per vertex: g and a scaled squared norm.
+//
+// Filter, then exact decision.  For each (query, vertex) the inner loop only
+// accumulates the dot product with -2q (one packed FP32x2 FMA per coordinate
+// for two vertices), which gives the expansion |q|^2 + |x|^2 - 2 q.x of the
+// squared distance.  Its FP32 error is at most (12 D + 24) u (|q|^2 + |x|^2)
+// (u = 2^-24: the dot product and both norms are D-term FMA sums, bounded by
+// Cauchy-Schwarz), and the exact FP32 distance below differs from the true one
+// by at most 4 (D + 2) u d^2.  A vertex whose expansion, lowered by that bound,
+// still exceeds the running best cannot become the best; every other vertex
+// is re-evaluated with the same exact formula as the other NEAREST kernels
+// (sum of fmaf((q_d - x_d)^2)), which alone decides.  Results are therefore
+// identical to the plain scan.
 constexpr int kQThreads = 128;
 constexpr int kQPT = 2;
 constexpr int kTile = 256;
@@ -203,22 +213,30 @@ __global__ void __launch_bounds__(kQThreads)
 nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
                    const float *__restrict__ queries, const float *__restrict__ budgets, int Q,
                    int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial) {
-    __shared__ __align__(16) float tile[(DIM + 1) * kTile];
-    f2 qp[kQPT][DIM];   // (q_d, q_d) packed
-    float cq[kQPT];
+    // rows 0..DIM-1 coordinates, row DIM g, row DIM+1 |x|^2 (1 - c3)
+    __shared__ __align__(16) float tile[(DIM + 2) * kTile];
+    constexpr float kU = 5.9604645e-8f;                   // 2^-24
+    constexpr float kC3 = (12.f * DIM + 24.f) * kU;       // expansion error / (|q|^2 + |x|^2)
+    constexpr float kC1 = 4.f * (DIM + 2.f) * kU;         // exact-distance relative error
+    f2 m2q[kQPT][DIM];   // (-2 q_d, -2 q_d) packed; q_d = -0.5 * (-2 q_d) exactly
+    float cq[kQPT], qn[kQPT], lim[kQPT];
     Best best[kQPT];
     const int qb = blockIdx.x * kQThreads * kQPT;
 #pragma unroll
     for (int j = 0; j < kQPT; ++j) {
         const int q = qb + j * kQThreads + threadIdx.x;
         const bool ok = q < Q;
+        float n2 = 0.f;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const float v = ok ? queries[(size_t)d * Q + q] : 0.f;
-            qp[j][d] = f2_pack(v, v);
+            m2q[j][d] = f2_pack(-2.f * v, -2.f * v);
+            n2 = fmaf(v, v, n2);
         }
+        qn[j] = n2;
         cq[j] = ok ? budgets[q] : -FLT_MAX;   // nothing is admissible for padding
         best[j] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+        lim[j] = FLT_MAX * 2.f;
     }
     const int vs = blockIdx.y * chunk;
     const int ve = min(N, vs + chunk);
@@ -232,45 +250,61 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
             tile[i] = j < nv ? __ldg(tree + (size_t)d * ld + v0 + j) : (d == DIM ? FLT_MAX * 2.f : 0.f);
         }
         __syncthreads();
+        for (int j = threadIdx.x; j < kTile; j += kQThreads) {
+            float n2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) n2 = fmaf(tile[d * kTile + j], tile[d * kTile + j], n2);
+            tile[(DIM + 1) * kTile + j] = n2 * (1.f - kC3);
+        }
+        __syncthreads();
         const int ng = (nv + 3) >> 2;
         for (int gq = 0; gq < ng; ++gq) {
-            // packed FP32x2: lanes (vertex 4gq, 4gq+1) and (4gq+2, 4gq+3);
-            // each element rounds exactly like the scalar sub / fma
+            const float4 w4 = tile4[(DIM + 1) * (kTile / 4) + gq];
+            const f2 w01 = f2_pack(w4.x, w4.y), w23 = f2_pack(w4.z, w4.w);
             f2 acc[kQPT][2];
 #pragma unroll
-            for (int j = 0; j < kQPT; ++j) acc[j][0] = acc[j][1] = 0ull;
+            for (int j = 0; j < kQPT; ++j) {
+                const f2 qq = f2_pack(qn[j], qn[j]);
+                acc[j][0] = f2_add(w01, qq);
+                acc[j][1] = f2_add(w23, qq);
+            }
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
                 const float4 xv = tile4[d * (kTile / 4) + gq];
                 const f2 x01 = f2_pack(xv.x, xv.y), x23 = f2_pack(xv.z, xv.w);
 #pragma unroll
                 for (int j = 0; j < kQPT; ++j) {
-                    const f2 a01 = f2_sub(qp[j][d], x01), a23 = f2_sub(qp[j][d], x23);
-                    acc[j][0] = f2_fma(a01, a01, acc[j][0]);
-                    acc[j][1] = f2_fma(a23, a23, acc[j][1]);
+                    acc[j][0] = f2_fma(m2q[j][d], x01, acc[j][0]);
+                    acc[j][1] = f2_fma(m2q[j][d], x23, acc[j][1]);
                 }
             }
-            float accf[kQPT][4];
 #pragma unroll
             for (int j = 0; j < kQPT; ++j) {
-                f2_unpack(acc[j][0], accf[j][0], accf[j][1]);
-                f2_unpack(acc[j][1], accf[j][2], accf[j][3]);
-            }
-#pragma unroll
-            for (int j = 0; j < kQPT; ++j) {
-                const float bd = best[j].d2;
-                if ((accf[j][0] <= bd) | (accf[j][1] <= bd) | (accf[j][2] <= bd) | (accf[j][3] <= bd)) {
-                    const float4 g4 = tile4[DIM * (kTile / 4) + gq];
-                    const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+                float e[4];
+                f2_unpack(acc[j][0], e[0], e[1]);
+                f2_unpack(acc[j][1], e[2], e[3]);
+                const float L = lim[j];
+                if ((e[0] <= L) | (e[1] <= L) | (e[2] <= L) | (e[3] <= L)) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float d2 = accf[j][u], g = gg[u];
+                        if (!(e[u] <= lim[j])) continue;
+                        const int vl = 4 * gq + u;
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d) {
+                            float lo, hi;
+                            f2_unpack(m2q[j][d], lo, hi);
+                            const float a = -0.5f * lo - tile[d * kTile + vl];
+                            d2 = fmaf(a, a, d2);
+                        }
+                        const float g = tile[DIM * kTile + vl];
                         // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index)
                         if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
                             (d2 < best[j].d2 || g < best[j].g)) {
                             best[j].d2 = d2;
                             best[j].g = g;
-                            best[j].idx = v0 + 4 * gq + u;
+                            best[j].idx = v0 + vl;
+                            lim[j] = fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU);
                         }
                     }
                 }
@@ -320,64 +354,102 @@ mrpop_status nearest_qpt(const float *tree, int N, int64_t ld, const float *quer
     return MRPOP_OK;
 }
 
-// NEIGHBORS: one warp per query, lanes over 32 consecutive vertices, in
-// ascending order; ballot + prefix popcount keeps the output sorted.
-__global__ void neighbors_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
-                                 const float *__restrict__ queries, int Q, float delta,
-                                 int64_t k_max, int64_t *__restrict__ out_idx,
-                                 int64_t *__restrict__ out_cnt) {
-    __shared__ float qs[8][MRPOP_MAX_LINKS];
+// NEIGHBORS: a block serves kNbWarps queries, one warp each, and streams the
+// tree through shared memory in tiles of kNbTile vertices (SoA rows, loaded
+// once for all of the block's queries).  Lanes take 32 consecutive vertices at
+// a time in ascending order; ballot + prefix popcount keep the output sorted.
+constexpr int kNbWarps = 8;
+constexpr int kNbTile = 256;
+
+__global__ void __launch_bounds__(kNbWarps * 32)
+neighbors_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
+                 const float *__restrict__ queries, int Q, float delta, int64_t k_max,
+                 int64_t *__restrict__ out_idx, int64_t *__restrict__ out_cnt) {
+    __shared__ float qs[kNbWarps][MRPOP_MAX_LINKS];
+    extern __shared__ float tile[];  // [dim][kNbTile]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int q = blockIdx.x * 8 + warp;
-    if (q >= Q) return;
-    for (int d = lane; d < dim; d += 32) qs[warp][d] = queries[(size_t)d * Q + q];
-    __syncwarp();
+    const int q = blockIdx.x * kNbWarps + warp;
+    const bool qok = q < Q;
+    for (int d = lane; d < dim; d += 32) qs[warp][d] = qok ? queries[(size_t)d * Q + q] : 0.f;
     int64_t count = 0;
-    for (int v0 = 0; v0 < N; v0 += 32) {
-        const int v = v0 + lane;
-        bool in = false;
-        if (v < N) {
-            float d2 = 0.f;
-            for (int d = 0; d < dim; ++d) {
-                const float a = qs[warp][d] - __ldg(tree + (size_t)d * ld + v);
-                d2 = fmaf(a, a, d2);
+    for (int v0 = 0; v0 < N; v0 += kNbTile) {
+        const int nv = min(kNbTile, N - v0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < dim * kNbTile; i += blockDim.x) {
+            const int d = i / kNbTile, j = i - d * kNbTile;
+            tile[i] = j < nv ? __ldg(tree + (size_t)d * ld + v0 + j) : 0.f;
+        }
+        __syncthreads();
+        if (!qok) continue;
+        for (int c = 0; c < nv; c += 32) {
+            const int v = c + lane;
+            bool in = false;
+            if (v < nv) {
+                float d2 = 0.f;
+                for (int d = 0; d < dim; ++d) {
+                    const float a = qs[warp][d] - tile[d * kNbTile + v];
+                    d2 = fmaf(a, a, d2);
+                }
+                in = __fsqrt_rn(d2) <= delta;
             }
-            in = __fsqrt_rn(d2) <= delta;
+            const unsigned bal = __ballot_sync(kFull, in);
+            if (in) {
+                const int64_t pos = count + __popc(bal & ((1u << lane) - 1u));
+                if (pos < k_max) out_idx[(size_t)q * k_max + pos] = v0 + v;
+            }
+            count += __popc(bal);
         }
-        const unsigned bal = __ballot_sync(kFull, in);
-        if (in) {
-            const int64_t pos = count + __popc(bal & ((1u << lane) - 1u));
-            if (pos < k_max) out_idx[(size_t)q * k_max + pos] = v;
-        }
-        count += __popc(bal);
     }
+    if (!qok) return;
     for (int64_t pos = count + lane; pos < k_max; pos += 32) out_idx[(size_t)q * k_max + pos] = -1;
     if (lane == 0) out_cnt[q] = count;
 }
 
-// C(sigma): one block; FP32 segment lengths, FP64 accumulation.
-__global__ void path_cost_kernel(const float *__restrict__ path, int64_t M, int dim,
-                                 double *__restrict__ out) {
-    __shared__ double red[32];
-    double acc = 0.0;
-    for (int64_t j = threadIdx.x; j + 1 < M; j += blockDim.x) {
-        float s = 0.f;
-        for (int d = 0; d < dim; ++d) {
-            const float a = path[(j + 1) * dim + d] - path[j * dim + d];
-            s = fmaf(a, a, s);
-        }
-        acc += (double)__fsqrt_rn(s);
-    }
+// C(sigma): segment lengths in FP32, sums in FP64 with a fixed reduction order
+// (each block sums a fixed range of segments; one warp adds the block sums in
+// block order), so the result is deterministic.
+__device__ __forceinline__ double block_sum(double acc, double *red) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
+    double v = 0.0;
     if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-        if (threadIdx.x == 0) *out = v;
     }
+    return v;  // valid in thread 0
+}
+
+__device__ __forceinline__ float segment_length(const float *__restrict__ path, int64_t j, int dim) {
+    float s = 0.f;
+    for (int d = 0; d < dim; ++d) {
+        const float a = path[(j + 1) * dim + d] - path[j * dim + d];
+        s = fmaf(a, a, s);
+    }
+    return __fsqrt_rn(s);
+}
+
+__global__ void path_cost_kernel(const float *__restrict__ path, int64_t M, int dim,
+                                 int64_t chunk, double *__restrict__ out) {
+    __shared__ double red[32];
+    const int64_t j0 = (int64_t)blockIdx.x * chunk;
+    const int64_t j1 = min(M - 1, j0 + chunk);
+    double acc = 0.0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+        acc += (double)segment_length(path, j, dim);
+    const double v = block_sum(acc, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ partial, int n,
+                                    double *__restrict__ out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) acc += partial[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if (threadIdx.x == 0) *out = acc;
 }
 
 }  // namespace
@@ -419,17 +491,39 @@ mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
 mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
                               const float *queries, int64_t Q, float delta, int64_t k_max,
                               int64_t *out_idx, int64_t *out_cnt, cudaStream_t st) {
-    const int blocks = (int)((Q + 7) / 8);
-    neighbors_kernel<<<blocks, 256, 0, st>>>(tree, (int)N, ld, dim, queries, (int)Q, delta, k_max,
-                                             out_idx, out_cnt);
+    const int blocks = (int)((Q + kNbWarps - 1) / kNbWarps);
+    const size_t smem = sizeof(float) * (size_t)dim * kNbTile;
+    if (smem > 48 * 1024)
+        MRPOP_CUDA_TRY(cudaFuncSetAttribute(neighbors_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    neighbors_kernel<<<blocks, kNbWarps * 32, smem, st>>>(tree, (int)N, ld, dim, queries, (int)Q,
+                                                          delta, k_max, out_idx, out_cnt);
     MRPOP_CUDA_TRY(cudaGetLastError());
     return MRPOP_OK;
 }
 
 mrpop_status launch_path_cost(const float *path, int64_t M, int dim, double *out,
                               cudaStream_t st) {
-    path_cost_kernel<<<1, 512, 0, st>>>(path, M, dim, out);
-    MRPOP_CUDA_TRY(cudaGetLastError());
+    const int threads = 256;
+    const int64_t segs = M > 1 ? M - 1 : 0;
+    int blocks = (int)std::min<int64_t>(1024, (segs + 4 * threads - 1) / (4 * threads));
+    if (blocks <= 1) {
+        path_cost_kernel<<<1, threads, 0, st>>>(path, M, dim, segs > 0 ? segs : 1, out);
+        MRPOP_CUDA_TRY(cudaGetLastError());
+        return MRPOP_OK;
+    }
+    const int64_t chunk = (segs + blocks - 1) / blocks;
+    blocks = (int)((segs + chunk - 1) / chunk);
+    double *partial = nullptr;
+    MRPOP_CUDA_TRY(cudaMallocAsync((void **)&partial, sizeof(double) * blocks, st));
+    path_cost_kernel<<<blocks, threads, 0, st>>>(path, M, dim, chunk, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        sum_partials_kernel<<<1, 32, 0, st>>>(partial, blocks, out);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(partial, st);
+    if (e != cudaSuccess) return cuda_error(e, "path cost kernel launch");
     return MRPOP_OK;
 }
 

@@ -11,7 +11,8 @@
 //  * Per link, forward kinematics in registers (Rz, then the d/a/alpha
 //    offsets), then three levels of culling:
 //      1. tile level: the warp bounds the link's coarse spheres at its 32
-//         checkpoints by one sphere (centroid + max radius, shuffles); lane i
+//         checkpoints by one sphere (around the box of the centres, from
+//         integer min/max warp reductions); lane i
 //         tests obstacle i (and the tile bound of earlier robots' link i)
 //         against it, and a ballot gives the candidate set;
 //      2. checkpoint level ("coarse" stage of the paper): each lane tests its
@@ -37,10 +38,16 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsMax = 4;
 constexpr int kCounters = MRPOP_WORK_COUNTERS;
-// Absolute slack (m) added to tile bounds: covers FP32 rounding of the
-// centroid and radius so the tile test never drops a candidate that a
-// checkpoint's own link-level test would keep.
-constexpr float kTileSlack = 1e-4f;
+// Absolute slack (m) added to tile bounds: covers the quantisation step and
+// FP32 rounding of the box centre and radius, so the tile test never drops a
+// candidate that a checkpoint's own link-level test would keep.
+constexpr float kTileSlack = 4e-4f;
+// Tile bounds quantise coarse centres to 0.1 mm integers so that min/max are
+// single warp reductions; within +-100 m the integers stay below 2^24 and
+// convert back to float exactly.  A tile with a centre beyond that range gets
+// an unbounded sphere (every obstacle becomes a candidate).
+constexpr float kQuant = 1e4f;
+constexpr float kQuantRange = 100.f;
 
 enum Mode { kVerdict = 0, kClearance = 1, kCount = 2 };
 
@@ -215,24 +222,31 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                     if (MODE == kCount && active) cnt[1] += 1;
 
                     // Tile bound: one sphere around this link's coarse spheres at
-                    // all 32 checkpoints of the tile (warp-uniform).
+                    // all 32 checkpoints of the tile (warp-uniform), built from the
+                    // axis-aligned box of the coarse centres quantised to 0.1 mm
+                    // (rounded outward) with single-instruction integer reductions.
                     float4 bnd = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (MODE != kClearance) {
-                        float sx = cc.x, sy = cc.y, sz = cc.z;
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            sx += __shfl_xor_sync(kFull, sx, off);
-                            sy += __shfl_xor_sync(kFull, sy, off);
-                            sz += __shfl_xor_sync(kFull, sz, off);
-                        }
-                        bnd.x = sx * (1.f / 32.f);
-                        bnd.y = sy * (1.f / 32.f);
-                        bnd.z = sz * (1.f / 32.f);
-                        float rd = __fsqrt_rn(dist2(cc.x, cc.y, cc.z, bnd.x, bnd.y, bnd.z));
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1)
-                            rd = fmaxf(rd, __shfl_xor_sync(kFull, rd, off));
-                        bnd.w = rd + LC.w + kTileSlack;
+                        const float qx = fminf(fmaxf(cc.x, -kQuantRange), kQuantRange) * kQuant;
+                        const float qy = fminf(fmaxf(cc.y, -kQuantRange), kQuantRange) * kQuant;
+                        const float qz = fminf(fmaxf(cc.z, -kQuantRange), kQuantRange) * kQuant;
+                        const int x0 = __reduce_min_sync(kFull, __float2int_rd(qx));
+                        const int x1 = __reduce_max_sync(kFull, __float2int_ru(qx));
+                        const int y0 = __reduce_min_sync(kFull, __float2int_rd(qy));
+                        const int y1 = __reduce_max_sync(kFull, __float2int_ru(qy));
+                        const int z0 = __reduce_min_sync(kFull, __float2int_rd(qz));
+                        const int z1 = __reduce_max_sync(kFull, __float2int_ru(qz));
+                        const float ex = (float)(x1 - x0) * (0.5f / kQuant);
+                        const float ey = (float)(y1 - y0) * (0.5f / kQuant);
+                        const float ez = (float)(z1 - z0) * (0.5f / kQuant);
+                        bnd.x = (float)(x0 + x1) * (0.5f / kQuant);
+                        bnd.y = (float)(y0 + y1) * (0.5f / kQuant);
+                        bnd.z = (float)(z0 + z1) * (0.5f / kQuant);
+                        bnd.w = __fsqrt_rn(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + LC.w + kTileSlack;
+                        // outside the quantisation range the bound admits everything
+                        const bool far = !(fmaxf(fabsf(cc.x), fmaxf(fabsf(cc.y), fabsf(cc.z))) <
+                                           kQuantRange);
+                        if (__any_sync(kFull, far)) bnd.w = FLT_MAX * 2.f;
                         if (MODE == kCount && lane == 0) cnt[9] += 1;
                     }
                     if (store) {
@@ -242,9 +256,6 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                         x[9 * 32] = F.t[0];
                         x[10 * 32] = F.t[1];
                         x[11 * 32] = F.t[2];
-                        x[12 * 32] = cc.x;
-                        x[13 * 32] = cc.y;
-                        x[14 * 32] = cc.z;
                         if (lane == 0) tb[l] = bnd;
                         __syncwarp();
                     }
@@ -420,10 +431,16 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
                                         cm &= cm - 1;
                                         const int i = bit + 32 * w;
                                         const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
-                                        const float ri = tab[t.off_link + kLinkF4 * i + 2].w;
-                                        const float d2 = dist2(cc.x, cc.y, cc.z, x[12 * 32],
-                                                               x[13 * 32], x[14 * 32]);
-                                        const float th2 = LC.w + ri + m;
+                                        const float4 LCi = tab[t.off_link + kLinkF4 * i + 2];
+                                        Frame Fi;
+#pragma unroll
+                                        for (int c = 0; c < 9; ++c) Fi.r[c] = x[c * 32];
+                                        Fi.t[0] = x[9 * 32];
+                                        Fi.t[1] = x[10 * 32];
+                                        Fi.t[2] = x[11 * 32];
+                                        const float3 ci = apply(Fi, LCi.x, LCi.y, LCi.z);
+                                        const float d2 = dist2(cc.x, cc.y, cc.z, ci.x, ci.y, ci.z);
+                                        const float th2 = LC.w + LCi.w + m;
                                         own |= (d2 < th2 * th2) ? (1u << bit) : 0u;
                                     }
                                     if (w == 0)

@@ -148,3 +148,23 @@ def test_path_cost_parity(mp, orc):
         got = float(mp.path_cost(_dev(path)).cpu().numpy()[0])
         ref = orc.path_cost(path)
         assert got == pytest.approx(ref, rel=1e-6, abs=1e-12)
+
+
+@pytest.mark.parametrize("D,N,Q", [(14, 3000, 4096), (28, 2000, 2048), (6, 5000, 3000),
+                                   (3, 700, 2500), (7, 257, 2049), (21, 1500, 2100)])
+def test_nearest_query_blocked_parity(mp, orc, D, N, Q):
+    """Batches of >= 2048 queries take the query-blocked kernel (expansion
+    filter + exact re-check); sampled queries against the oracle, duplicates
+    in the tree for ties, and the whole batch against the small-batch kernel
+    (called in chunks of < 2048 queries), which must agree index for index."""
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, N, lo, hi, seed=100 + D, dup_frac=0.1)
+    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=200 + D, budget_lo=0.0, budget_hi=25.0)
+    qs[:, :64] = tree[:D, :64]            # queries exactly on (duplicated) vertices
+    big = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    small = np.concatenate([
+        mp.nearest(_dev(tree), _dev(np.ascontiguousarray(qs[:, i:i + 1000])),
+                   _dev(cs[i:i + 1000])).cpu().numpy() for i in range(0, Q, 1000)])
+    np.testing.assert_array_equal(big, small)
+    sample = np.concatenate([np.arange(64), np.random.default_rng(D).choice(Q, 200, replace=False)])
+    _check_nearest(orc, tree, qs, cs, big, sample=sample)
