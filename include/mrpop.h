@@ -236,6 +236,31 @@ mrpop_status mrpop_neighbors(const float *tree, int64_t n_vertices, int64_t ld, 
 mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim, double *cost_out,
                              void *cuda_stream);
 
+/* MR. POP's anytime planner (Alg. 1): ROADMAP, then the initial dRRT search,
+ * then AO-X calls with the shrinking incumbent cost c_best (Alg. 2), until
+ * time_budget_s seconds of wall time have passed.  The problem must have been
+ * created with start and goal; both must be collision-free.  Planner state
+ * (roadmaps, trees, incumbent) stays on the device in the handle, so a later
+ * call continues where this one stopped.
+ *   path      host float [path_cap][D]: the best path found, q_start first,
+ *             q_goal last (may be NULL to query the length and cost only)
+ *   path_len  vertices of that path;  cost  C(sigma) = sum of segment lengths
+ *             (Sec. III-A) in FP64 from the returned FP32 vertices, +inf when
+ *             none.
+ * Every returned path has been re-checked at resolution / 4 with the
+ * problem's margin; incumbents only ever decrease strictly.
+ * Errors: EINVAL (no start/goal, or either in collision), ENOSOLUTION (no path
+ * within the budget), ECAPACITY (path_cap too small; path_len is set). */
+mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path, int64_t path_cap,
+                        int64_t *path_len, double *cost);
+
+/* Incumbent history of the problem's planner: times[i] (seconds since the
+ * start of the mrpop_plan call that found it) and costs[i], in order, at most
+ * cap entries; *n receives the full count and *iterations the planner
+ * iterations run so far (host arrays; any pointer may be NULL). */
+mrpop_status mrpop_plan_trace(const mrpop_problem *p, double *times, double *costs, int64_t cap,
+                              int64_t *n, int64_t *iterations);
+
 #ifdef __cplusplus
 }
 #endif

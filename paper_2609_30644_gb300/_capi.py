@@ -31,6 +31,8 @@ EXPORTS = (
     "mrpop_nearest_noalloc",
     "mrpop_neighbors",
     "mrpop_path_cost",
+    "mrpop_plan",
+    "mrpop_plan_trace",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -82,6 +84,8 @@ def _load() -> C.CDLL:
         "mrpop_nearest_noalloc": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
         "mrpop_path_cost": (i32, [vp, i64, i32, vp, vp]),
+        "mrpop_plan": (i32, [vp, C.c_double, vp, i64, vp, vp]),
+        "mrpop_plan_trace": (i32, [vp, vp, vp, i64, vp, vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -280,3 +284,26 @@ def path_cost(path: torch.Tensor, out: Optional[torch.Tensor] = None, stream=Non
     _check(lib.mrpop_path_cost(_dptr(path, torch.float32, "path"), M, dim,
                                _dptr(out, torch.float64, "cost"), _stream(stream)))
     return out
+
+
+def plan(p: Problem, time_budget_s: float, path_cap: int = 1 << 16) -> tuple:
+    """Runs the planner on p for time_budget_s seconds.  Returns (path
+    float32 [M, D] or None, cost); cost is +inf when no path was found."""
+    buf = np.zeros((path_cap, p.D), dtype=np.float32)
+    n, cost = C.c_int64(), C.c_double()
+    st = lib.mrpop_plan(p.handle, float(time_budget_s), buf.ctypes.data, path_cap,
+                        C.byref(n), C.byref(cost))
+    if st == 6:  # MRPOP_ENOSOLUTION
+        return None, float("inf")
+    _check(st)
+    return buf[:n.value].copy(), cost.value
+
+
+def plan_trace(p: Problem) -> tuple:
+    """(times, costs, iterations) of the incumbent history."""
+    n, it = C.c_int64(), C.c_int64()
+    _check(lib.mrpop_plan_trace(p.handle, None, None, 0, C.byref(n), C.byref(it)))
+    t = np.zeros(max(n.value, 1))
+    c = np.zeros(max(n.value, 1))
+    _check(lib.mrpop_plan_trace(p.handle, t.ctypes.data, c.ctypes.data, n.value, None, None))
+    return t[:n.value], c[:n.value], it.value

@@ -213,6 +213,23 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
         }
     if (start) p->start.assign(start, start + L);
     if (goal) p->goal.assign(goal, goal + L);
+    for (int k = 0; k < K; ++k) {
+        const mrpop_robot &r = robots[k];
+        HostRobot hr;
+        hr.dof = r.dof;
+        hr.dh.assign(r.dh, r.dh + 4 * r.dof);
+        hr.q_lo.assign(r.q_lo, r.q_lo + r.dof);
+        hr.q_hi.assign(r.q_hi, r.q_hi + r.dof);
+        if (r.n_spheres > 0) {
+            hr.sphere_xyzr.assign(r.sphere_xyzr, r.sphere_xyzr + 4 * r.n_spheres);
+            hr.sphere_link.assign(r.sphere_link, r.sphere_link + r.n_spheres);
+        }
+        std::memcpy(hr.base, r.base, sizeof(hr.base));
+        p->robots.push_back(std::move(hr));
+    }
+    if (obs->n_spheres > 0) p->obs_spheres.assign(obs->spheres, obs->spheres + 4 * obs->n_spheres);
+    if (obs->n_cuboids > 0)
+        p->obs_cuboids.assign(obs->cuboids, obs->cuboids + 15 * obs->n_cuboids);
 
     auto fail = [&](mrpop_status st) {
         mrpop_destroy_problem(p);
@@ -248,6 +265,8 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
 extern "C" mrpop_status mrpop_destroy_problem(mrpop_problem *p) {
     if (!p) return MRPOP_OK;
     if (p->dev.blob || p->dev.edge_counter) cudaDeviceSynchronize();
+    destroy_planner(p->planner);
+    p->planner = nullptr;
     cudaFree(p->dev.blob);
     cudaFree(p->dev.q_lo);
     cudaFree(p->dev.q_hi);

@@ -38,6 +38,27 @@ constexpr int kLinkF4 = 3;
 constexpr int kCuboidF4 = 5;
 constexpr int kXfFloats = 12;  // stored link frame: R (9), t (3)
 
+// Parameters of one validation launch (one problem, one batch of edges).
+struct VParams {
+    Tables t;
+    const float4 *blob;
+    const float *qa;
+    const float *qb;
+    int64_t E;
+    float res;
+    float margin;
+    uint8_t *valid;
+    float *length;
+    int32_t *npoints;
+    float *min_clear;
+    unsigned long long *counters;
+    int *work;  // [0] next edge, [1] finished warps; both return to 0 at exit
+    int total_warps;
+    int warp_floats;
+    int dpad;
+    int nstore;  // links of robots 0..K-2 (their frames and tile bounds are kept)
+};
+
 struct DeviceProblem {
     Tables t;
     float4 *blob = nullptr;       // device copy of the table blob
@@ -48,8 +69,22 @@ struct DeviceProblem {
 
 }  // namespace mrpop
 
+namespace mrpop {
+struct HostRobot {
+    int dof = 0;
+    std::vector<float> dh, q_lo, q_hi, sphere_xyzr;
+    std::vector<int32_t> sphere_link;
+    float base[12] = {0};
+};
+struct Planner;  // device-resident planner state (planner.cu)
+void destroy_planner(Planner *pl);
+}  // namespace mrpop
+
 struct mrpop_problem {
     mrpop::DeviceProblem dev;
+    std::vector<mrpop::HostRobot> robots;     // host copies (planner sub-problems)
+    std::vector<float> obs_spheres, obs_cuboids;
+    mrpop::Planner *planner = nullptr;
     mrpop_config cfg{};
     int device = 0;
     int D = 0;
@@ -76,6 +111,14 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
                              uint8_t *valid, float *length, int32_t *npoints,
                              float *min_clear, unsigned long long *counters,
                              cudaStream_t st);
+// Fills V for validating n edges of problem p (warps per block and dynamic
+// shared memory of the launch go to *warps_out / *smem_out).
+mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
+                          uint8_t *valid, VParams *V, size_t *smem_out, int *warps_out);
+// Validates every problem's batch in one launch: d_params is a device array
+// of nslots VParams whose total_warps equal blocks_per_slot * warps.
+mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int spl, int warps,
+                                   int blocks_per_slot, size_t smem, cudaStream_t st);
 mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st);
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,

@@ -257,38 +257,47 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
             tile[(DIM + 1) * kTile + j] = n2 * (1.f - kC3);
         }
         __syncthreads();
-        const int ng = (nv + 3) >> 2;
+        const int ng = (nv + 7) >> 3;   // groups of 8 vertices
         for (int gq = 0; gq < ng; ++gq) {
-            const float4 w4 = tile4[(DIM + 1) * (kTile / 4) + gq];
-            const f2 w01 = f2_pack(w4.x, w4.y), w23 = f2_pack(w4.z, w4.w);
-            f2 acc[kQPT][2];
+            const float4 wa = tile4[(DIM + 1) * (kTile / 4) + 2 * gq];
+            const float4 wb = tile4[(DIM + 1) * (kTile / 4) + 2 * gq + 1];
+            f2 acc[kQPT][4];
 #pragma unroll
             for (int j = 0; j < kQPT; ++j) {
                 const f2 qq = f2_pack(qn[j], qn[j]);
-                acc[j][0] = f2_add(w01, qq);
-                acc[j][1] = f2_add(w23, qq);
+                acc[j][0] = f2_add(f2_pack(wa.x, wa.y), qq);
+                acc[j][1] = f2_add(f2_pack(wa.z, wa.w), qq);
+                acc[j][2] = f2_add(f2_pack(wb.x, wb.y), qq);
+                acc[j][3] = f2_add(f2_pack(wb.z, wb.w), qq);
             }
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                const float4 xv = tile4[d * (kTile / 4) + gq];
-                const f2 x01 = f2_pack(xv.x, xv.y), x23 = f2_pack(xv.z, xv.w);
+                const float4 xa = tile4[d * (kTile / 4) + 2 * gq];
+                const float4 xb = tile4[d * (kTile / 4) + 2 * gq + 1];
+                const f2 x0 = f2_pack(xa.x, xa.y), x1 = f2_pack(xa.z, xa.w);
+                const f2 x2 = f2_pack(xb.x, xb.y), x3 = f2_pack(xb.z, xb.w);
 #pragma unroll
                 for (int j = 0; j < kQPT; ++j) {
-                    acc[j][0] = f2_fma(m2q[j][d], x01, acc[j][0]);
-                    acc[j][1] = f2_fma(m2q[j][d], x23, acc[j][1]);
+                    acc[j][0] = f2_fma(m2q[j][d], x0, acc[j][0]);
+                    acc[j][1] = f2_fma(m2q[j][d], x1, acc[j][1]);
+                    acc[j][2] = f2_fma(m2q[j][d], x2, acc[j][2]);
+                    acc[j][3] = f2_fma(m2q[j][d], x3, acc[j][3]);
                 }
             }
 #pragma unroll
             for (int j = 0; j < kQPT; ++j) {
-                float e[4];
-                f2_unpack(acc[j][0], e[0], e[1]);
-                f2_unpack(acc[j][1], e[2], e[3]);
-                const float L = lim[j];
-                if ((e[0] <= L) | (e[1] <= L) | (e[2] <= L) | (e[3] <= L)) {
+                float e[8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (!(e[u] <= lim[j])) continue;
-                        const int vl = 4 * gq + u;
+                for (int h = 0; h < 4; ++h) f2_unpack(acc[j][h], e[2 * h], e[2 * h + 1]);
+                unsigned cm = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cm |= (e[u] <= lim[j]) ? (1u << u) : 0u;
+                // survivors of the filter (a superset once lim shrinks below)
+                while (cm) {
+                    const int u = __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    {
+                        const int vl = 8 * gq + u;
                         float d2 = 0.f;
 #pragma unroll
                         for (int d = 0; d < DIM; ++d) {
@@ -332,7 +341,9 @@ mrpop_status nearest_qpt(const float *tree, int N, int64_t ld, const float *quer
     bps = std::max(bps, 1);
     const int qblocks = (Q + kQThreads * kQPT - 1) / (kQThreads * kQPT);
     const int target = sms * bps;
-    int splits = std::max(1, (target + qblocks - 1) / qblocks);
+    // as many tree slices as fit in one wave of resident blocks (a partial
+    // second wave would idle most SMs at the end)
+    int splits = std::max(1, target / qblocks);
     splits = std::min(splits, std::max(1, (N + kTile - 1) / kTile));
     splits = std::min(splits, 65535);
     int chunk = (N + splits - 1) / splits;

@@ -1,0 +1,998 @@
+// MR. POP planner (Alg. 1, Alg. 2) on device-resident roadmaps and trees.
+//
+// Outer loop (Alg. 1): ROADMAP, then the initial dRRT search, then AO-X calls
+// with a shrinking incumbent cost, until the time budget runs out.
+//
+// GB300 design: instead of one thread block per planner iteration, every
+// search *step* runs kStepIters iterations for every problem in the batch at
+// once, as a fixed sequence of launches whose grids have a problem ("slot")
+// dimension: sample -> NEAREST on the expanded tree -> dRRT / AO-X direction
+// oracle -> edge validation -> insert -> NEAREST on the opposite tree ->
+// connection validation -> incumbent candidates.  The sequence has a fixed
+// shape, so it is captured once in a CUDA graph and replayed; the host only
+// rewrites a small control block per slot and reads it back.
+//
+// Roadmaps (Alg. 2 ROADMAP): per robot, batches of uniform samples are
+// checked against the obstacles (a single-robot sub-problem), connected to
+// their neighbours within delta (NEIGHBORS) by checked edges, and grown until
+// start and goal are connected (BFS on the host).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#include "mrpop_internal.cuh"
+
+namespace mrpop {
+
+constexpr int kStepIters = 256;     // iterations per step and problem
+constexpr int kKmax = 32;           // roadmap degree cap
+constexpr int kOversample = 4;      // roadmap candidates per wanted sample
+constexpr int kInformedTries = 16;  // informed-sampling rejection limit
+
+struct Ctrl {
+    float c_best;                  // incumbent cost (+inf before the first solution)
+    int mode;                      // 0 dRRT search, 1 AO-X, 2 idle
+    int step;                      // RNG stream of the step
+    int tree_a;                    // tree expanded this step (set on device)
+    unsigned long long seed;
+    unsigned long long best_key;   // min over (cost bits << 32 | iteration)
+    int overflow;                  // a tree reached its capacity
+    int pad;
+};
+
+struct Slot {
+    int K, D, rcap, tcap;
+    int dof[MRPOP_MAX_ROBOTS];
+    int qoff[MRPOP_MAX_ROBOTS];
+    const float *q_lo, *q_hi, *start, *goal, *centre, *axis;
+    float c_min;
+    float *rm_q[MRPOP_MAX_ROBOTS];  // [dof][rcap]
+    int *rm_adj[MRPOP_MAX_ROBOTS];  // [rcap][kKmax]
+    int *rm_deg[MRPOP_MAX_ROBOTS];  // [rcap]
+    int *rm_n;                      // [K]
+    float *tq[2];                   // [D+1][tcap], row D = g
+    int *tpar[2];                   // [tcap]
+    int *trmv[2];                   // [K][tcap] roadmap vertex of each robot
+    int *tn;                        // [2]
+    float *qrand, *crand, *qnear, *qnew, *gnew, *budget2, *qconn;
+    int64_t *near, *conn;
+    int *rmvnew, *newidx;
+    uint8_t *valid1, *valid2;
+    Ctrl *ctrl;
+};
+
+// ---------------------------------------------------------------------------
+// counter-based random numbers (SplitMix64 finaliser)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct Rng {
+    unsigned long long key, ctr;
+    __device__ __forceinline__ float uniform() {  // [0, 1)
+        return (float)(mix64(key ^ mix64(ctr++)) >> 40) * (1.0f / 16777216.0f);
+    }
+    __device__ __forceinline__ float normal() {
+        const float u1 = 1.0f - uniform(), u2 = uniform();
+        return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+};
+
+__device__ __forceinline__ float nanf_() { return __int_as_float(0x7fc00000); }
+
+// ---------------------------------------------------------------------------
+// search step kernels (grid.y = slot)
+// ---------------------------------------------------------------------------
+
+// q_rand (uniform, or informed in the prolate hyperspheroid of c_best) and the
+// cost coordinate c_rand ~ U[g_lb(q_rand), c_best] (Alg. 2 AO-X).
+__global__ void k_sample(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Ctrl &C = *S.ctrl;
+    const int a = (S.tn[0] <= S.tn[1]) ? 0 : 1;  // expand the smaller tree
+    if (i == 0) S.ctrl->tree_a = a;
+    if (i >= kStepIters) return;
+    const int D = S.D, B = kStepIters;
+    if (C.mode == 2) {
+        S.crand[i] = -INFINITY;
+        return;
+    }
+    Rng rng{mix64(C.seed ^ 0x5851F42D4C957F2Dull), ((unsigned long long)C.step << 32) ^ (unsigned)i};
+    rng.ctr *= 977ull;
+    float x[MRPOP_MAX_LINKS];
+    const bool informed = C.mode == 1 && C.c_best < INFINITY && C.c_best > S.c_min;
+    bool ok = false;
+    if (informed) {
+        // Direct sampling of the prolate hyperspheroid (foci start and goal,
+        // transverse diameter c_best): uniform in the unit ball, scaled by the
+        // radii, reflected so that e1 maps to the start->goal axis, centred.
+        const float r1 = 0.5f * C.c_best;
+        const float r2 = 0.5f * sqrtf(fmaxf(C.c_best * C.c_best - S.c_min * S.c_min, 0.f));
+        for (int tr = 0; tr < kInformedTries && !ok; ++tr) {
+            float n2 = 0.f;
+            for (int d = 0; d < D; ++d) {
+                x[d] = rng.normal();
+                n2 = fmaf(x[d], x[d], n2);
+            }
+            const float rad = powf(rng.uniform(), 1.0f / (float)D) / sqrtf(fmaxf(n2, 1e-30f));
+            for (int d = 0; d < D; ++d) x[d] *= rad * (d == 0 ? r1 : r2);
+            // Householder reflection with w = e1 - axis
+            float ww = 0.f, wx = 0.f;
+            for (int d = 0; d < D; ++d) {
+                const float w = (d == 0 ? 1.f : 0.f) - S.axis[d];
+                ww = fmaf(w, w, ww);
+                wx = fmaf(w, x[d], wx);
+            }
+            const float f = ww > 1e-12f ? 2.f * wx / ww : 0.f;
+            ok = true;
+            for (int d = 0; d < D; ++d) {
+                const float w = (d == 0 ? 1.f : 0.f) - S.axis[d];
+                x[d] = S.centre[d] + x[d] - f * w;
+                ok = ok && x[d] >= S.q_lo[d] && x[d] <= S.q_hi[d];
+            }
+        }
+    }
+    if (!ok)
+        for (int d = 0; d < D; ++d) x[d] = S.q_lo[d] + rng.uniform() * (S.q_hi[d] - S.q_lo[d]);
+    for (int d = 0; d < D; ++d) S.qrand[(size_t)d * B + i] = x[d];
+    if (C.mode == 1) {
+        const float *root = a == 0 ? S.start : S.goal;
+        float g2 = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const float t = x[d] - root[d];
+            g2 = fmaf(t, t, g2);
+        }
+        const float glb = sqrtf(g2);
+        S.crand[i] = glb < C.c_best ? glb + rng.uniform() * (C.c_best - glb) : glb;
+    } else {
+        S.crand[i] = INFINITY;
+    }
+}
+
+// NEAREST over one of the slot's trees (pass 0: expanded tree with q_rand and
+// c_rand; pass 1: opposite tree with q_new and c_best - g_new).  Vertices
+// across the block's threads, 16 queries per block in shared memory, key
+// (d^2, g, index), warp-shuffle argmin then a cross-warp pass.
+constexpr int kPQB = 16;
+constexpr int kPThreads = 128;
+
+struct PBest {
+    float d2, g;
+    int idx;
+};
+__device__ __forceinline__ bool pbetter(const PBest &a, const PBest &b) {
+    if (a.d2 != b.d2) return a.d2 < b.d2;
+    if (a.g != b.g) return a.g < b.g;
+    return (unsigned)a.idx < (unsigned)b.idx;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kPThreads) k_nearest(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.y];
+    const Ctrl &C = *S.ctrl;
+    __shared__ float qs[kPQB][MRPOP_MAX_LINKS];
+    __shared__ float cs[kPQB];
+    __shared__ PBest wb[kPThreads / 32][kPQB];
+    const int B = kStepIters, D = S.D;
+    const int t = PASS == 0 ? C.tree_a : 1 - C.tree_a;
+    const float *tree = S.tq[t];
+    const int N = min(S.tn[t], S.tcap);
+    const int q0 = blockIdx.x * kPQB;
+    const float *Qs = PASS == 0 ? S.qrand : S.qnew;
+    const float *Cs = PASS == 0 ? S.crand : S.budget2;
+    for (int k = threadIdx.x; k < kPQB * D; k += blockDim.x) {
+        const int j = k / D, d = k % D;
+        qs[j][d] = Qs[(size_t)d * B + q0 + j];
+    }
+    if (threadIdx.x < kPQB) cs[threadIdx.x] = Cs[q0 + threadIdx.x];
+    __syncthreads();
+    PBest best[kPQB];
+#pragma unroll
+    for (int j = 0; j < kPQB; ++j) best[j] = PBest{INFINITY, INFINITY, -1};
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        float acc[kPQB];
+#pragma unroll
+        for (int j = 0; j < kPQB; ++j) acc[j] = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const float xv = tree[(size_t)d * S.tcap + v];
+#pragma unroll
+            for (int j = 0; j < kPQB; ++j) {
+                const float a = qs[j][d] - xv;
+                acc[j] = fmaf(a, a, acc[j]);
+            }
+        }
+        const float g = tree[(size_t)D * S.tcap + v];
+#pragma unroll
+        for (int j = 0; j < kPQB; ++j)
+            if (acc[j] <= best[j].d2 && g + __fsqrt_rn(acc[j]) < cs[j] &&
+                (acc[j] < best[j].d2 || g < best[j].g))
+                best[j] = PBest{acc[j], g, v};
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kPQB; ++j) {
+        PBest b = best[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            PBest o{__shfl_xor_sync(0xffffffffu, b.d2, off), __shfl_xor_sync(0xffffffffu, b.g, off),
+                    __shfl_xor_sync(0xffffffffu, b.idx, off)};
+            if (pbetter(o, b)) b = o;
+        }
+        if (lane == 0) wb[warp][j] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPQB) {
+        PBest b = wb[0][threadIdx.x];
+        for (int w = 1; w < kPThreads / 32; ++w)
+            if (pbetter(wb[w][threadIdx.x], b)) b = wb[w][threadIdx.x];
+        (PASS == 0 ? S.near : S.conn)[q0 + threadIdx.x] = b.idx;
+    }
+}
+
+// Direction oracle.  dRRT (Solovey et al.): per robot, the roadmap neighbour v
+// of q_near^r with the largest cos angle(v - q_near^r, q_rand^r - q_near^r);
+// the robot stays put when no neighbour has a positive cosine.  AO-X: the same
+// choice, kept only when the extension is admissible, g_near + |q_new - q_near|
+// <= c_rand (Sec. III-D).
+__global__ void k_oracle(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.y];
+    const Ctrl &C = *S.ctrl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kStepIters) return;
+    const int B = kStepIters, D = S.D, a = C.tree_a;
+    const int nr = (int)S.near[i];
+    bool active = C.mode != 2 && nr >= 0;
+    bool moved = false;
+    float len2 = 0.f;
+    if (active) {
+        for (int r = 0; r < S.K; ++r) {
+            const int u = S.trmv[a][(size_t)r * S.tcap + nr];
+            const int dof = S.dof[r], off = S.qoff[r];
+            const float *V = S.rm_q[r];
+            float dn = 0.f;
+            for (int d = 0; d < dof; ++d) {
+                const float t = S.qrand[(size_t)(off + d) * B + i] - V[(size_t)d * S.rcap + u];
+                dn = fmaf(t, t, dn);
+            }
+            int bestv = u;
+            float bestc = 0.f;
+            const int deg = min(S.rm_deg[r][u], kKmax);
+            for (int k = 0; k < deg; ++k) {
+                const int v = S.rm_adj[r][(size_t)u * kKmax + k];
+                float dot = 0.f, vn = 0.f;
+                for (int d = 0; d < dof; ++d) {
+                    const float e = V[(size_t)d * S.rcap + v] - V[(size_t)d * S.rcap + u];
+                    const float t = S.qrand[(size_t)(off + d) * B + i] - V[(size_t)d * S.rcap + u];
+                    dot = fmaf(e, t, dot);
+                    vn = fmaf(e, e, vn);
+                }
+                if (vn <= 0.f || dn <= 0.f) continue;
+                const float c = dot / sqrtf(vn * dn);
+                if (c > bestc || (c == bestc && bestv != u && v < bestv)) {
+                    bestc = c;
+                    bestv = v;
+                }
+            }
+            S.rmvnew[(size_t)r * B + i] = bestv;
+            moved |= bestv != u;
+            for (int d = 0; d < dof; ++d) {
+                const float qa = V[(size_t)d * S.rcap + u], qb = V[(size_t)d * S.rcap + bestv];
+                S.qnear[(size_t)(off + d) * B + i] = qa;
+                S.qnew[(size_t)(off + d) * B + i] = qb;
+                const float t = qb - qa;
+                len2 = fmaf(t, t, len2);
+            }
+        }
+    }
+    float gnew = INFINITY;
+    if (active && moved) {
+        gnew = S.tq[a][(size_t)D * S.tcap + nr] + sqrtf(len2);
+        if (C.mode == 1 && !(gnew <= S.crand[i])) active = false;
+    }
+    if (!(active && moved)) {
+        // inactive iteration: a NaN edge is rejected by validation at once
+        S.qnew[i] = nanf_();
+        S.qnear[i] = 0.f;
+        gnew = INFINITY;
+    }
+    S.gnew[i] = gnew;
+}
+
+// Insert z_new = (q_new, g_near + |q_new - q_near|) into the expanded tree and
+// prepare the connection budget c_best - g_new (AO-X) or +inf (dRRT).
+__global__ void k_insert(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.y];
+    Ctrl &C = *S.ctrl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kStepIters) return;
+    const int B = kStepIters, D = S.D, a = C.tree_a;
+    int idx = -1;
+    if (S.valid1[i] && S.gnew[i] < INFINITY) {
+        idx = atomicAdd(&S.tn[a], 1);
+        if (idx >= S.tcap) {
+            C.overflow = 1;
+            idx = -1;
+        } else {
+            for (int d = 0; d < D; ++d)
+                S.tq[a][(size_t)d * S.tcap + idx] = S.qnew[(size_t)d * B + i];
+            S.tq[a][(size_t)D * S.tcap + idx] = S.gnew[i];
+            S.tpar[a][idx] = (int)S.near[i];
+            for (int r = 0; r < S.K; ++r)
+                S.trmv[a][(size_t)r * S.tcap + idx] = S.rmvnew[(size_t)r * B + i];
+        }
+    }
+    S.newidx[i] = idx;
+    S.budget2[i] = idx < 0 ? -INFINITY : (C.mode == 1 ? C.c_best - S.gnew[i] : INFINITY);
+}
+
+__global__ void k_conn_prep(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kStepIters) return;
+    const int B = kStepIters, D = S.D, b = 1 - S.ctrl->tree_a;
+    const int c = (int)S.conn[i];
+    if (c >= 0 && S.newidx[i] >= 0) {
+        for (int d = 0; d < D; ++d) S.qconn[(size_t)d * B + i] = S.tq[b][(size_t)d * S.tcap + c];
+    } else {
+        S.qconn[i] = nanf_();
+    }
+}
+
+// A checked connection closes a path start -> ... -> z_new -> z_conn -> ...
+// -> goal; the cheapest of the step wins (packed cost | iteration key).
+__global__ void k_solution(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.y];
+    Ctrl &C = *S.ctrl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kStepIters) return;
+    const int B = kStepIters, D = S.D, b = 1 - C.tree_a;
+    const int c = (int)S.conn[i];
+    if (!S.valid2[i] || c < 0 || S.newidx[i] < 0) return;
+    float s2 = 0.f;
+    for (int d = 0; d < D; ++d) {
+        const float t = S.qconn[(size_t)d * B + i] - S.qnew[(size_t)d * B + i];
+        s2 = fmaf(t, t, s2);
+    }
+    const float cost = S.gnew[i] + sqrtf(s2) + S.tq[b][(size_t)D * S.tcap + c];
+    const unsigned long long key =
+        ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)i;
+    atomicMin(&C.best_key, key);
+}
+
+// Path of the winning iteration: root_a .. z_new, then z_conn .. root_b.
+// One thread follows the parents; the configurations are written to
+// out_q [cap][D] in that order (reversed to start -> goal by the host when the
+// expanded tree was the goal tree).
+__global__ void k_extract(const Slot *__restrict__ slots, int it, int *scratch, float *out_q,
+                          int cap, int *len_out) {
+    const Slot &S = slots[0];
+    const int a = S.ctrl->tree_a, b = 1 - a, D = S.D;
+    int na = 0;
+    for (int v = S.newidx[it]; v >= 0 && na < cap; v = S.tpar[a][v]) scratch[na++] = v;
+    int n = 0;
+    for (int k = na - 1; k >= 0; --k, ++n)
+        for (int d = 0; d < D; ++d) out_q[(size_t)n * D + d] = S.tq[a][(size_t)d * S.tcap + scratch[k]];
+    for (int v = (int)S.conn[it]; v >= 0 && n < cap; v = S.tpar[b][v], ++n)
+        for (int d = 0; d < D; ++d) out_q[(size_t)n * D + d] = S.tq[b][(size_t)d * S.tcap + v];
+    *len_out = n;
+}
+
+// ---------------------------------------------------------------------------
+// roadmap kernels (one robot of one slot)
+// ---------------------------------------------------------------------------
+__global__ void k_rm_sample(const float *lo, const float *hi, int dof, int n,
+                            unsigned long long key, unsigned long long ctr0, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Rng rng{key, ctr0 + (unsigned long long)i * 64ull};
+    for (int d = 0; d < dof; ++d) out[(size_t)d * n + i] = lo[d] + rng.uniform() * (hi[d] - lo[d]);
+}
+
+// Append up to `want` valid candidates (in candidate order) to V_r.
+__global__ void k_rm_append(const float *cand, const uint8_t *valid, int n, int dof, int want,
+                            float *V, int rcap, int *count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = *count, added = 0;
+    for (int i = 0; i < n && added < want && c < rcap; ++i) {
+        if (!valid[i]) continue;
+        for (int d = 0; d < dof; ++d) V[(size_t)d * rcap + c] = cand[(size_t)d * n + i];
+        ++c;
+        ++added;
+    }
+    *count = c;
+}
+
+__global__ void k_rm_gather(const float *V, int rcap, int dof, int first, int m, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    for (int d = 0; d < dof; ++d) out[(size_t)d * m + i] = V[(size_t)d * rcap + first + i];
+}
+
+// Candidate roadmap edges (new vertex, earlier neighbour within delta).
+__global__ void k_rm_edges(const float *V, int rcap, int dof, int first, int m,
+                           const int64_t *nb, const int64_t *cnt, float *qa, float *qb,
+                           int *ea, int *eb) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int E = m * kKmax;
+    if (e >= E) return;
+    const int j = e / kKmax, k = e % kKmax;
+    const int self = first + j;
+    const int64_t c = cnt[j] < (int64_t)kKmax ? cnt[j] : (int64_t)kKmax;
+    const int v = k < c ? (int)nb[(size_t)j * kKmax + k] : -1;
+    if (v < 0 || v >= self) {
+        qa[e] = 0.f;
+        qb[e] = nanf_();
+        ea[e] = -1;
+        eb[e] = -1;
+        return;
+    }
+    for (int d = 0; d < dof; ++d) {
+        qa[(size_t)d * E + e] = V[(size_t)d * rcap + self];
+        qb[(size_t)d * E + e] = V[(size_t)d * rcap + v];
+    }
+    ea[e] = self;
+    eb[e] = v;
+}
+
+__global__ void k_rm_link(const uint8_t *valid, const int *ea, const int *eb, int E, int *adj,
+                          int *deg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E || !valid[e] || ea[e] < 0) return;
+    const int a = ea[e], b = eb[e];
+    const int ka = atomicAdd(&deg[a], 1);
+    if (ka < kKmax) adj[(size_t)a * kKmax + ka] = b;
+    const int kb = atomicAdd(&deg[b], 1);
+    if (kb < kKmax) adj[(size_t)b * kKmax + kb] = a;
+}
+
+__global__ void k_tree_reset(const Slot *__restrict__ slots) {
+    const Slot &S = slots[blockIdx.x];
+    const int D = S.D;
+    for (int t = 0; t < 2; ++t) {
+        const float *root = t == 0 ? S.start : S.goal;
+        for (int d = threadIdx.x; d < D; d += blockDim.x) S.tq[t][(size_t)d * S.tcap] = root[d];
+        if (threadIdx.x == 0) {
+            S.tq[t][(size_t)D * S.tcap] = 0.f;
+            S.tpar[t][0] = -1;
+            for (int r = 0; r < S.K; ++r) S.trmv[t][(size_t)r * S.tcap] = t;  // roadmap vertex 0 / 1
+            S.tn[t] = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <class T>
+static cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(n, 1));
+}
+
+struct RobotRoadmap {
+    mrpop_problem *sub = nullptr;   // this robot alone with the obstacles
+    float *q = nullptr;             // [dof][rcap]
+    int *adj = nullptr, *deg = nullptr;
+    int n = 0;                      // host mirror of the vertex count
+    bool connected = false;
+    // scratch
+    float *cand = nullptr, *gq = nullptr, *ea_q = nullptr, *eb_q = nullptr;
+    uint8_t *cvalid = nullptr, *evalid = nullptr;
+    int64_t *nb = nullptr, *cnt = nullptr;
+    int *ea = nullptr, *eb = nullptr;
+};
+
+struct Planner {
+    mrpop_problem *p = nullptr;
+    mrpop_problem *fine = nullptr;  // same scene at resolution / 4
+    int K = 0, D = 0, rcap = 0, tcap = 0, n_per_round = 0;
+    std::vector<RobotRoadmap> rm;
+    int *rm_n = nullptr;
+    float *tq[2] = {nullptr, nullptr};
+    int *tpar[2] = {nullptr, nullptr}, *trmv[2] = {nullptr, nullptr}, *tn = nullptr;
+    float *buf = nullptr;  // step buffers
+    int64_t *near = nullptr, *conn = nullptr;
+    int *rmvnew = nullptr, *newidx = nullptr;
+    uint8_t *valid1 = nullptr, *valid2 = nullptr;
+    float *d_lo = nullptr, *d_hi = nullptr, *d_start = nullptr, *d_goal = nullptr,
+          *d_centre = nullptr, *d_axis = nullptr;
+    Ctrl *ctrl = nullptr;
+    Slot slot{};
+    VParams vp[2];
+    size_t vsmem = 0;
+    int vwarps = 1;
+    // incumbent
+    bool initialised = false, roadmap_ready = false, first_solved = false;
+    int mode = 0;  // 0 dRRT, 1 AO-X
+    long long iters_in_call = 0, total_iters = 0;
+    double c_best = INFINITY;
+    std::vector<float> best_path;  // [M][D]
+    std::vector<double> trace_t, trace_c;
+    unsigned long long seed = 0;
+    int step = 0;
+    int *d_path = nullptr;
+    float *d_pathq = nullptr;
+    int *d_len = nullptr;
+};
+
+static mrpop_status make_sub(mrpop_problem *p, int k, float res, mrpop_problem **out) {
+    const HostRobot &hr = p->robots[k];
+    mrpop_robot r{};
+    r.dof = hr.dof;
+    r.n_spheres = (int)hr.sphere_link.size();
+    r.dh = hr.dh.data();
+    r.q_lo = hr.q_lo.data();
+    r.q_hi = hr.q_hi.data();
+    r.sphere_link = hr.sphere_link.data();
+    r.sphere_xyzr = hr.sphere_xyzr.data();
+    std::memcpy(r.base, hr.base, sizeof(r.base));
+    mrpop_obstacles o{(int)(p->obs_spheres.size() / 4), p->obs_spheres.data(),
+                      (int)(p->obs_cuboids.size() / 15), p->obs_cuboids.data()};
+    mrpop_config c = p->cfg;
+    c.resolution = res;
+    return mrpop_create_problem(&r, 1, &o, nullptr, nullptr, &c, out);
+}
+
+static mrpop_status make_fine(mrpop_problem *p, mrpop_problem **out) {
+    std::vector<mrpop_robot> rs(p->robots.size());
+    for (size_t k = 0; k < rs.size(); ++k) {
+        const HostRobot &hr = p->robots[k];
+        rs[k].dof = hr.dof;
+        rs[k].n_spheres = (int)hr.sphere_link.size();
+        rs[k].dh = hr.dh.data();
+        rs[k].q_lo = hr.q_lo.data();
+        rs[k].q_hi = hr.q_hi.data();
+        rs[k].sphere_link = hr.sphere_link.data();
+        rs[k].sphere_xyzr = hr.sphere_xyzr.data();
+        std::memcpy(rs[k].base, hr.base, sizeof(rs[k].base));
+    }
+    mrpop_obstacles o{(int)(p->obs_spheres.size() / 4), p->obs_spheres.data(),
+                      (int)(p->obs_cuboids.size() / 15), p->obs_cuboids.data()};
+    mrpop_config c = p->cfg;
+    c.resolution = p->cfg.resolution * 0.25f;
+    return mrpop_create_problem(rs.data(), (int)rs.size(), &o, nullptr, nullptr, &c, out);
+}
+
+void destroy_planner(Planner *pl) {
+    if (!pl) return;
+    for (auto &r : pl->rm) {
+        mrpop_destroy_problem(r.sub);
+        cudaFree(r.q); cudaFree(r.adj); cudaFree(r.deg); cudaFree(r.cand); cudaFree(r.gq);
+        cudaFree(r.ea_q); cudaFree(r.eb_q); cudaFree(r.cvalid); cudaFree(r.evalid);
+        cudaFree(r.nb); cudaFree(r.cnt); cudaFree(r.ea); cudaFree(r.eb);
+    }
+    mrpop_destroy_problem(pl->fine);
+    cudaFree(pl->rm_n);
+    for (int t = 0; t < 2; ++t) {
+        cudaFree(pl->tq[t]); cudaFree(pl->tpar[t]); cudaFree(pl->trmv[t]);
+    }
+    cudaFree(pl->tn); cudaFree(pl->buf); cudaFree(pl->near); cudaFree(pl->conn);
+    cudaFree(pl->rmvnew); cudaFree(pl->newidx); cudaFree(pl->valid1); cudaFree(pl->valid2);
+    cudaFree(pl->d_lo); cudaFree(pl->d_hi); cudaFree(pl->d_start); cudaFree(pl->d_goal);
+    cudaFree(pl->d_centre); cudaFree(pl->d_axis); cudaFree(pl->ctrl); cudaFree(pl->d_path);
+    cudaFree(pl->d_pathq);
+    cudaFree(pl->d_len);
+    delete pl;
+}
+
+#define PL_TRY(expr)                                       \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return cuda_error(_e, #expr); \
+    } while (0)
+#define ST_TRY(expr)                       \
+    do {                                   \
+        mrpop_status _s = (expr);          \
+        if (_s != MRPOP_OK) return _s;     \
+    } while (0)
+
+static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
+    if (p->start.empty() || p->goal.empty())
+        return set_error(MRPOP_EINVAL, "mrpop_plan: the problem was created without start/goal");
+    Planner *pl = new (std::nothrow) Planner();
+    if (!pl) return set_error(MRPOP_ENOMEM, "host allocation failed");
+    *out = pl;
+    pl->p = p;
+    pl->K = p->dev.t.K;
+    pl->D = p->D;
+    pl->rcap = (int)std::max<int64_t>(64, std::min<int64_t>(p->cfg.roadmap_cap, 1 << 20));
+    pl->tcap = (int)std::max<int64_t>(1024, std::min<int64_t>(p->cfg.tree_cap, 1 << 22));
+    pl->n_per_round = std::max(1, std::min(p->cfg.n_per_round, 4096));
+    pl->seed = p->cfg.seed;
+    const int K = pl->K, D = pl->D, B = kStepIters, rcap = pl->rcap, tcap = pl->tcap;
+    ST_TRY(make_fine(p, &pl->fine));
+    pl->rm.resize(K);
+    int qoff = 0;
+    for (int k = 0; k < K; ++k) {
+        RobotRoadmap &r = pl->rm[k];
+        const int dof = p->robots[k].dof;
+        ST_TRY(make_sub(p, k, p->cfg.resolution, &r.sub));
+        const int nc = kOversample * pl->n_per_round;
+        const int E = pl->n_per_round * kKmax;
+        PL_TRY(dalloc(&r.q, (size_t)dof * rcap));
+        PL_TRY(dalloc(&r.adj, (size_t)rcap * kKmax));
+        PL_TRY(dalloc(&r.deg, (size_t)rcap));
+        PL_TRY(cudaMemset(r.deg, 0, sizeof(int) * rcap));
+        PL_TRY(dalloc(&r.cand, (size_t)dof * nc));
+        PL_TRY(dalloc(&r.cvalid, (size_t)nc));
+        PL_TRY(dalloc(&r.gq, (size_t)dof * pl->n_per_round + 2 * dof));
+        PL_TRY(dalloc(&r.nb, (size_t)(pl->n_per_round + 2) * kKmax));
+        PL_TRY(dalloc(&r.cnt, (size_t)pl->n_per_round + 2));
+        PL_TRY(dalloc(&r.ea_q, (size_t)dof * (E + 2 * kKmax)));
+        PL_TRY(dalloc(&r.eb_q, (size_t)dof * (E + 2 * kKmax)));
+        PL_TRY(dalloc(&r.evalid, (size_t)E + 2 * kKmax));
+        PL_TRY(dalloc(&r.ea, (size_t)E + 2 * kKmax));
+        PL_TRY(dalloc(&r.eb, (size_t)E + 2 * kKmax));
+        // vertices 0 and 1: the robot's start and goal
+        for (int d = 0; d < dof; ++d) {
+            PL_TRY(cudaMemcpy(r.q + (size_t)d * rcap, &p->start[qoff + d], sizeof(float),
+                              cudaMemcpyHostToDevice));
+            PL_TRY(cudaMemcpy(r.q + (size_t)d * rcap + 1, &p->goal[qoff + d], sizeof(float),
+                              cudaMemcpyHostToDevice));
+        }
+        r.n = 2;
+        pl->slot.dof[k] = dof;
+        pl->slot.qoff[k] = qoff;
+        pl->slot.rm_q[k] = r.q;
+        pl->slot.rm_adj[k] = r.adj;
+        pl->slot.rm_deg[k] = r.deg;
+        qoff += dof;
+    }
+    PL_TRY(dalloc(&pl->rm_n, K));
+    std::vector<int> twos(K, 2);
+    PL_TRY(cudaMemcpy(pl->rm_n, twos.data(), sizeof(int) * K, cudaMemcpyHostToDevice));
+    for (int t = 0; t < 2; ++t) {
+        PL_TRY(dalloc(&pl->tq[t], (size_t)(D + 1) * tcap));
+        PL_TRY(dalloc(&pl->tpar[t], (size_t)tcap));
+        PL_TRY(dalloc(&pl->trmv[t], (size_t)K * tcap));
+    }
+    PL_TRY(dalloc(&pl->tn, 2));
+    // step buffers: qrand, qnear, qnew, qconn [D][B]; crand, gnew, budget2 [B]
+    PL_TRY(dalloc(&pl->buf, (size_t)4 * D * B + 3 * B));
+    PL_TRY(dalloc(&pl->near, B));
+    PL_TRY(dalloc(&pl->conn, B));
+    PL_TRY(dalloc(&pl->rmvnew, (size_t)K * B));
+    PL_TRY(dalloc(&pl->newidx, B));
+    PL_TRY(dalloc(&pl->valid1, B));
+    PL_TRY(dalloc(&pl->valid2, B));
+    PL_TRY(dalloc(&pl->d_lo, D));
+    PL_TRY(dalloc(&pl->d_hi, D));
+    PL_TRY(dalloc(&pl->d_start, D));
+    PL_TRY(dalloc(&pl->d_goal, D));
+    PL_TRY(dalloc(&pl->d_centre, D));
+    PL_TRY(dalloc(&pl->d_axis, D));
+    PL_TRY(dalloc(&pl->ctrl, 1));
+    PL_TRY(dalloc(&pl->d_path, (size_t)2 * tcap + 2));
+    PL_TRY(dalloc(&pl->d_pathq, (size_t)(2 * tcap + 2) * D));
+    PL_TRY(dalloc(&pl->d_len, 1));
+    std::vector<float> centre(D), axis(D);
+    double cmin2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const double g = (double)p->goal[d] - p->start[d];
+        cmin2 += g * g;
+        centre[d] = (float)(0.5 * ((double)p->goal[d] + p->start[d]));
+    }
+    const double cmin = std::sqrt(cmin2);
+    for (int d = 0; d < D; ++d)
+        axis[d] = cmin > 0 ? (float)(((double)p->goal[d] - p->start[d]) / cmin) : (d == 0 ? 1.f : 0.f);
+    PL_TRY(cudaMemcpy(pl->d_lo, p->q_lo.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(pl->d_hi, p->q_hi.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(pl->d_start, p->start.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(pl->d_goal, p->goal.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(pl->d_centre, centre.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(pl->d_axis, axis.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+
+    Slot &S = pl->slot;
+    S.K = K; S.D = D; S.rcap = rcap; S.tcap = tcap;
+    S.q_lo = pl->d_lo; S.q_hi = pl->d_hi; S.start = pl->d_start; S.goal = pl->d_goal;
+    S.centre = pl->d_centre; S.axis = pl->d_axis; S.c_min = (float)cmin;
+    S.rm_n = pl->rm_n;
+    for (int t = 0; t < 2; ++t) {
+        S.tq[t] = pl->tq[t]; S.tpar[t] = pl->tpar[t]; S.trmv[t] = pl->trmv[t];
+    }
+    S.tn = pl->tn;
+    float *b = pl->buf;
+    S.qrand = b; b += (size_t)D * B;
+    S.qnear = b; b += (size_t)D * B;
+    S.qnew = b; b += (size_t)D * B;
+    S.qconn = b; b += (size_t)D * B;
+    S.crand = b; b += B;
+    S.gnew = b; b += B;
+    S.budget2 = b;
+    S.near = pl->near; S.conn = pl->conn; S.rmvnew = pl->rmvnew; S.newidx = pl->newidx;
+    S.valid1 = pl->valid1; S.valid2 = pl->valid2; S.ctrl = pl->ctrl;
+    ST_TRY(make_vparams(p, S.qnear, S.qnew, B, S.valid1, &pl->vp[0], &pl->vsmem, &pl->vwarps));
+    ST_TRY(make_vparams(p, S.qnew, S.qconn, B, S.valid2, &pl->vp[1], &pl->vsmem, &pl->vwarps));
+    pl->initialised = true;
+    return MRPOP_OK;
+}
+
+// One ROADMAP round for robot k (Alg. 2, lines on sampling, neighbours and
+// edge checks), followed by the start-goal connectivity test (BFS).
+static mrpop_status roadmap_round(Planner *pl, int k, cudaStream_t st) {
+    RobotRoadmap &r = pl->rm[k];
+    mrpop_problem *p = pl->p;
+    const int dof = p->robots[k].dof, rcap = pl->rcap;
+    if (r.n >= rcap) return MRPOP_OK;
+    const int want = std::min(pl->n_per_round, rcap - r.n);
+    const int nc = kOversample * pl->n_per_round;
+    const int off = pl->slot.qoff[k];
+    const unsigned long long key = mix64(pl->seed * 31ull + 7ull * (unsigned long long)k + 1ull);
+    const unsigned long long ctr = (unsigned long long)(pl->step + 1) * 0x100000ull +
+                                   (unsigned long long)r.n * 4096ull;
+    k_rm_sample<<<(nc + 127) / 128, 128, 0, st>>>(pl->d_lo + off, pl->d_hi + off, dof, nc, key, ctr,
+                                                   r.cand);
+    PL_TRY(cudaGetLastError());
+    ST_TRY(launch_validate(r.sub, r.cand, r.cand, nc, r.cvalid, nullptr, nullptr, nullptr, nullptr,
+                           st));
+    int *d_count = pl->rm_n + k;
+    k_rm_append<<<1, 32, 0, st>>>(r.cand, r.cvalid, nc, dof, want, r.q, rcap, d_count);
+    PL_TRY(cudaGetLastError());
+    int n_new = 0;
+    PL_TRY(cudaMemcpyAsync(&n_new, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    // neighbours of the new vertices (and of start/goal on the first round)
+    const int first = r.n == 2 && n_new > 2 ? 0 : r.n;
+    const int m = n_new - first;
+    if (m > 0) {
+        k_rm_gather<<<(m + 127) / 128, 128, 0, st>>>(r.q, rcap, dof, first, m, r.gq);
+        PL_TRY(cudaGetLastError());
+        ST_TRY(launch_neighbors(r.q, n_new, rcap, dof, r.gq, m, p->cfg.delta, kKmax, r.nb, r.cnt,
+                                st));
+        const int E = m * kKmax;
+        k_rm_edges<<<(E + 127) / 128, 128, 0, st>>>(r.q, rcap, dof, first, m, r.nb, r.cnt, r.ea_q,
+                                                     r.eb_q, r.ea, r.eb);
+        PL_TRY(cudaGetLastError());
+        ST_TRY(launch_validate(r.sub, r.ea_q, r.eb_q, E, r.evalid, nullptr, nullptr, nullptr,
+                               nullptr, st));
+        k_rm_link<<<(E + 127) / 128, 128, 0, st>>>(r.evalid, r.ea, r.eb, E, r.adj, r.deg);
+        PL_TRY(cudaGetLastError());
+    }
+    r.n = n_new;
+    // BFS from vertex 0 (start) to vertex 1 (goal)
+    std::vector<int> deg(n_new), adj((size_t)n_new * kKmax);
+    PL_TRY(cudaMemcpyAsync(deg.data(), r.deg, sizeof(int) * n_new, cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaMemcpyAsync(adj.data(), r.adj, sizeof(int) * (size_t)n_new * kKmax,
+                           cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    std::vector<char> seen(n_new, 0);
+    std::vector<int> q{0};
+    seen[0] = 1;
+    for (size_t h = 0; h < q.size(); ++h) {
+        const int u = q[h];
+        for (int j = 0; j < std::min(deg[u], kKmax); ++j) {
+            const int v = adj[(size_t)u * kKmax + j];
+            if (v >= 0 && v < n_new && !seen[v]) {
+                seen[v] = 1;
+                q.push_back(v);
+            }
+        }
+    }
+    r.connected = n_new > 1 && seen[1];
+    return MRPOP_OK;
+}
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// Accepts a candidate path if it is strictly cheaper (FP64 cost) and every
+// segment is valid at a quarter of the resolution.
+static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, cudaStream_t st,
+                                  double t_now, bool *accepted) {
+    *accepted = false;
+    const int cap = 2 * pl->tcap + 2, D = pl->D;
+    k_extract<<<1, 1, 0, st>>>(d_slot, it, pl->d_path, pl->d_pathq, cap, pl->d_len);
+    PL_TRY(cudaGetLastError());
+    int len = 0;
+    Ctrl c;
+    PL_TRY(cudaMemcpyAsync(&len, pl->d_len, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaMemcpyAsync(&c, pl->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    std::vector<float> path((size_t)len * D);
+    PL_TRY(cudaMemcpyAsync(path.data(), pl->d_pathq, sizeof(float) * path.size(),
+                           cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    const int a = c.tree_a;
+    if (a == 1) {  // expanded tree was the goal tree: reverse to start -> goal
+        for (int j = 0; j < len / 2; ++j)
+            for (int d = 0; d < D; ++d)
+                std::swap(path[(size_t)j * D + d], path[(size_t)(len - 1 - j) * D + d]);
+    }
+    double cost = 0.0;
+    for (int j = 0; j + 1 < len; ++j) {
+        double s = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double t = (double)path[(size_t)(j + 1) * D + d] - path[(size_t)j * D + d];
+            s += t * t;
+        }
+        cost += std::sqrt(s);
+    }
+    if (!(cost < pl->c_best) || len < 2) return MRPOP_OK;
+    // re-validate every segment at resolution / 4
+    const int M = len - 1;
+    std::vector<float> qa((size_t)D * M), qb((size_t)D * M);
+    for (int j = 0; j < M; ++j)
+        for (int d = 0; d < D; ++d) {
+            qa[(size_t)d * M + j] = path[(size_t)j * D + d];
+            qb[(size_t)d * M + j] = path[(size_t)(j + 1) * D + d];
+        }
+    float *dqa = nullptr, *dqb = nullptr;
+    uint8_t *dv = nullptr;
+    PL_TRY(cudaMalloc(&dqa, sizeof(float) * qa.size()));
+    PL_TRY(cudaMalloc(&dqb, sizeof(float) * qb.size()));
+    PL_TRY(cudaMalloc(&dv, M));
+    PL_TRY(cudaMemcpy(dqa, qa.data(), sizeof(float) * qa.size(), cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(dqb, qb.data(), sizeof(float) * qb.size(), cudaMemcpyHostToDevice));
+    mrpop_status s = launch_validate(pl->fine, dqa, dqb, M, dv, nullptr, nullptr, nullptr, nullptr, st);
+    std::vector<uint8_t> v(M);
+    if (s == MRPOP_OK) {
+        PL_TRY(cudaMemcpyAsync(v.data(), dv, M, cudaMemcpyDeviceToHost, st));
+        PL_TRY(cudaStreamSynchronize(st));
+    }
+    cudaFree(dqa); cudaFree(dqb); cudaFree(dv);
+    if (s != MRPOP_OK) return s;
+    for (int j = 0; j < M; ++j)
+        if (!v[j]) return MRPOP_OK;  // rejected at the finer resolution
+    pl->c_best = cost;
+    pl->best_path.swap(path);
+    pl->trace_t.push_back(t_now);
+    pl->trace_c.push_back(cost);
+    *accepted = true;
+    return MRPOP_OK;
+}
+
+static mrpop_status search_step(Planner *pl, Slot *d_slot, VParams *d_vp, cudaStream_t st) {
+    const dim3 g1((kStepIters + 127) / 128, 1), gq(kStepIters / kPQB, 1);
+    k_sample<<<g1, 128, 0, st>>>(d_slot);
+    k_nearest<0><<<gq, kPThreads, 0, st>>>(d_slot);
+    k_oracle<<<g1, 128, 0, st>>>(d_slot);
+    PL_TRY(cudaGetLastError());
+    const int spl = pl->p->dev.t.max_spheres_per_link;
+    const int bps = (kStepIters + pl->vwarps - 1) / pl->vwarps;
+    ST_TRY(launch_validate_batch(d_vp, 1, spl, pl->vwarps, bps, pl->vsmem, st));
+    k_insert<<<g1, 128, 0, st>>>(d_slot);
+    k_nearest<1><<<gq, kPThreads, 0, st>>>(d_slot);
+    k_conn_prep<<<g1, 128, 0, st>>>(d_slot);
+    PL_TRY(cudaGetLastError());
+    ST_TRY(launch_validate_batch(d_vp + 1, 1, spl, pl->vwarps, bps, pl->vsmem, st));
+    k_solution<<<g1, 128, 0, st>>>(d_slot);
+    PL_TRY(cudaGetLastError());
+    return MRPOP_OK;
+}
+
+static mrpop_status plan(mrpop_problem *p, double budget) {
+    const double t0 = now_s();
+    cudaStream_t st;
+    PL_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct Guard {
+        cudaStream_t s;
+        ~Guard() { cudaStreamDestroy(s); }
+    } guard{st};
+    if (!p->planner) ST_TRY(planner_init(p, &p->planner));
+    Planner *pl = p->planner;
+    // start and goal must be valid
+    {
+        uint8_t *dv = nullptr;
+        PL_TRY(cudaMalloc(&dv, 2));
+        ST_TRY(launch_validate(p, pl->d_start, pl->d_start, 1, dv, nullptr, nullptr, nullptr, nullptr, st));
+        ST_TRY(launch_validate(p, pl->d_goal, pl->d_goal, 1, dv + 1, nullptr, nullptr, nullptr, nullptr, st));
+        uint8_t v[2];
+        PL_TRY(cudaMemcpyAsync(v, dv, 2, cudaMemcpyDeviceToHost, st));
+        PL_TRY(cudaStreamSynchronize(st));
+        cudaFree(dv);
+        if (!v[0] || !v[1]) return set_error(MRPOP_EINVAL, "mrpop_plan: start or goal is in collision");
+    }
+    Slot *d_slot = nullptr;
+    VParams *d_vp = nullptr;
+    PL_TRY(cudaMalloc(&d_slot, sizeof(Slot)));
+    PL_TRY(cudaMalloc(&d_vp, sizeof(VParams) * 2));
+    struct Free2 {
+        void *a, *b;
+        ~Free2() { cudaFree(a); cudaFree(b); }
+    } fr{d_slot, d_vp};
+    PL_TRY(cudaMemcpy(d_slot, &pl->slot, sizeof(Slot), cudaMemcpyHostToDevice));
+    VParams vp[2] = {pl->vp[0], pl->vp[1]};
+    const int bps = (kStepIters + pl->vwarps - 1) / pl->vwarps;
+    for (auto &v : vp) v.total_warps = bps * pl->vwarps;
+    PL_TRY(cudaMemcpy(d_vp, vp, sizeof(vp), cudaMemcpyHostToDevice));
+
+    const long long max_iters = std::max<long long>(kStepIters, p->cfg.max_iters);
+    bool need_roadmap = true, reset_trees = !pl->roadmap_ready;
+    while (now_s() - t0 < budget) {
+        if (need_roadmap) {
+            // ROADMAP: grow every robot's roadmap by one round, then keep
+            // growing until every robot connects its start and goal
+            bool all = true;
+            do {
+                all = true;
+                for (int k = 0; k < pl->K; ++k) {
+                    ST_TRY(roadmap_round(pl, k, st));
+                    all = all && pl->rm[k].connected;
+                }
+                ++pl->step;
+            } while (!all && now_s() - t0 < budget);
+            if (!all) break;
+            pl->roadmap_ready = true;
+            need_roadmap = false;
+            pl->iters_in_call = 0;
+            if (pl->mode == 1 || reset_trees) {
+                k_tree_reset<<<1, 64, 0, st>>>(d_slot);
+                PL_TRY(cudaGetLastError());
+                reset_trees = false;
+            }
+        }
+        Ctrl c{};
+        c.c_best = pl->c_best < INFINITY ? (float)pl->c_best : INFINITY;
+        c.mode = pl->mode;
+        c.step = pl->step++;
+        c.seed = pl->seed;
+        c.best_key = ~0ull;
+        PL_TRY(cudaMemcpyAsync(pl->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+        ST_TRY(search_step(pl, d_slot, d_vp, st));
+        Ctrl r;
+        PL_TRY(cudaMemcpyAsync(&r, pl->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        PL_TRY(cudaStreamSynchronize(st));
+        pl->iters_in_call += kStepIters;
+        pl->total_iters += kStepIters;
+        bool accepted = false;
+        if (r.best_key != ~0ull)
+            ST_TRY(try_incumbent(pl, d_slot, (int)(r.best_key & 0xffffffffu), st, now_s() - t0,
+                                 &accepted));
+        if (accepted) {
+            pl->first_solved = true;
+            pl->mode = 1;            // from now on: AO-X
+            need_roadmap = true;     // Alg. 1: grow the roadmap, then optimise again
+        } else if (pl->iters_in_call >= max_iters || r.overflow) {
+            need_roadmap = true;     // iteration cap: grow the roadmap (c14)
+            if (r.overflow) reset_trees = true;
+        }
+    }
+    return MRPOP_OK;
+}
+
+}  // namespace mrpop
+
+using namespace mrpop;
+
+extern "C" mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path,
+                                   int64_t path_cap, int64_t *path_len, double *cost) {
+    if (!p) return set_error(MRPOP_EINVAL, "mrpop_plan: problem is NULL");
+    if (!(time_budget_s >= 0.0)) return set_error(MRPOP_EINVAL, "mrpop_plan: negative budget");
+    mrpop_status s = plan(p, time_budget_s);
+    if (s != MRPOP_OK) return s;
+    Planner *pl = p->planner;
+    const int64_t M = pl ? (int64_t)(pl->best_path.size() / std::max(1, pl->D)) : 0;
+    if (path_len) *path_len = M;
+    if (cost) *cost = pl && M > 0 ? pl->c_best : INFINITY;
+    if (M == 0) return set_error(MRPOP_ENOSOLUTION, "mrpop_plan: no path found within the budget");
+    if (path) {
+        if (path_cap < M)
+            return set_error(MRPOP_ECAPACITY, "mrpop_plan: path needs %lld vertices, cap %lld",
+                             (long long)M, (long long)path_cap);
+        std::memcpy(path, pl->best_path.data(), sizeof(float) * pl->best_path.size());
+    }
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_plan_trace(const mrpop_problem *p, double *times, double *costs,
+                                         int64_t cap, int64_t *n, int64_t *iterations) {
+    if (!p) return set_error(MRPOP_EINVAL, "mrpop_plan_trace: problem is NULL");
+    const Planner *pl = p->planner;
+    const int64_t m = pl ? (int64_t)pl->trace_c.size() : 0;
+    if (n) *n = m;
+    if (iterations) *iterations = pl ? pl->total_iters : 0;
+    for (int64_t i = 0; i < std::min(m, cap); ++i) {
+        if (times) times[i] = pl->trace_t[i];
+        if (costs) costs[i] = pl->trace_c[i];
+    }
+    return MRPOP_OK;
+}

@@ -51,25 +51,7 @@ constexpr float kQuantRange = 100.f;
 
 enum Mode { kVerdict = 0, kClearance = 1, kCount = 2 };
 
-struct VParams {
-    Tables t;
-    const float4 *blob;
-    const float *qa;
-    const float *qb;
-    int64_t E;
-    float res;
-    float margin;
-    uint8_t *valid;
-    float *length;
-    int32_t *npoints;
-    float *min_clear;
-    unsigned long long *counters;
-    int *work;  // [0] next edge, [1] finished warps; both return to 0 at exit
-    int total_warps;
-    int warp_floats;
-    int dpad;
-    int nstore;  // links of robots 0..K-2 (their frames and tile bounds are kept)
-};
+
 
 struct Frame {
     float r[9];  // row-major rotation
@@ -156,8 +138,7 @@ __device__ __forceinline__ int interval_count(const float *dq, int D, float res,
 }
 
 template <int MODE, int SPL>
-__global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams P) {
-    extern __shared__ float4 sm4[];
+__device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
     float4 *tab = sm4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *ws = reinterpret_cast<float *>(sm4 + P.t.n_f4) + (size_t)warp * P.warp_floats;
@@ -552,6 +533,23 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
 }
 
 template <int MODE, int SPL>
+__global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams P) {
+    extern __shared__ float4 sm4[];
+    validate_body<MODE, SPL>(P, sm4);
+}
+
+// Many problems in one launch: block row y serves problem y (its parameters
+// are staged in shared memory once per block).
+template <int SPL>
+__global__ void __launch_bounds__(kWarpsMax * 32) validate_batch_kernel(const VParams *Ps) {
+    extern __shared__ float4 sm4[];
+    __shared__ VParams sP;
+    if (threadIdx.x == 0) sP = Ps[blockIdx.y];
+    __syncthreads();
+    validate_body<kVerdict, SPL>(sP, sm4);
+}
+
+template <int MODE, int SPL>
 mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
                          cudaStream_t st) {
     auto kern = validate_kernel<MODE, SPL>;
@@ -648,6 +646,57 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
     if (min_clear) return launch_spl<kClearance>(p, V, warps, smem, st);
     if (counters) return launch_spl<kCount>(p, V, warps, smem, st);
     return launch_spl<kVerdict>(p, V, warps, smem, st);
+}
+
+mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
+                          uint8_t *valid, VParams *V, size_t *smem_out, int *warps_out) {
+    const Tables &t = p->dev.t;
+    *V = VParams{};
+    V->t = t;
+    V->blob = p->dev.blob;
+    V->qa = qa;
+    V->qb = qb;
+    V->E = n;
+    V->res = p->cfg.resolution;
+    V->margin = p->cfg.margin;
+    V->valid = valid;
+    V->work = p->dev.edge_counter;
+    V->dpad = (t.L + 3) & ~3;
+    V->nstore = t.link0[t.K - 1];
+    V->warp_floats = 2 * V->dpad + 4 * V->nstore + V->nstore * kXfFloats * 32;
+    const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
+    int warps = kWarpsMax;
+    size_t smem = 0;
+    for (; warps >= 1; warps >>= 1) {
+        smem = tab_bytes + (size_t)warps * V->warp_floats * sizeof(float);
+        if (smem + sizeof(VParams) + 1024 <= p->smem_optin) break;
+    }
+    if (warps < 1)
+        return set_error(MRPOP_EINVAL, "problem too large for the validation kernel's shared memory");
+    *smem_out = smem;
+    *warps_out = warps;
+    return MRPOP_OK;
+}
+
+template <int SPL>
+static mrpop_status batch_spl(const VParams *d_params, int nslots, int warps, int blocks_per_slot,
+                              size_t smem, cudaStream_t st) {
+    auto kern = validate_batch_kernel<SPL>;
+    MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    dim3 grid(blocks_per_slot, nslots);
+    kern<<<grid, warps * 32, smem, st>>>(d_params);
+    MRPOP_CUDA_TRY(cudaGetLastError());
+    return MRPOP_OK;
+}
+
+mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int spl, int warps,
+                                   int blocks_per_slot, size_t smem, cudaStream_t st) {
+    if (spl <= 4) return batch_spl<4>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    if (spl <= 8) return batch_spl<8>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    if (spl <= 9) return batch_spl<9>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    if (spl <= 12) return batch_spl<12>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    return batch_spl<16>(d_params, nslots, warps, blocks_per_slot, smem, st);
 }
 
 mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st) {

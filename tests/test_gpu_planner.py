@@ -1,0 +1,143 @@
+"""GPU planner (mrpop_plan): every returned path is re-validated by the FP64
+oracle at a quarter of the planning resolution, its reported cost equals the
+summed segment lengths C(sigma) (Sec. III-A), it runs from q_start to q_goal,
+and the incumbent costs decrease strictly over time (Alg. 1; Lem. C1: a
+connection is accepted only below c_best).  Trajectories themselves are not
+compared: the planner is randomised."""
+import numpy as np
+import pytest
+import torch
+from scipy.spatial import cKDTree
+
+from paper_2609_30644_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+RES = 0.02
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2609_30644_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return m
+
+
+def _robot_connected(orc, scene, k, qs, qg, n=1500, delta=0.8):
+    """Dense FP64 PRM of robot k alone (oracle checks): are its start and goal
+    in one free-space component?  Joint limits without wrap-around can split
+    free space, so a random start/goal pair may have no path at all."""
+    sub = synth.Scene([scene.robots[k]], scene.obs_spheres, scene.obs_cuboids)
+    o = orc.OracleScene(sub)
+    r = scene.robots[k]
+    off = sum(rr.dof for rr in scene.robots[:k])
+    rng = np.random.default_rng(k)
+    samp = rng.uniform(r.q_lo, r.q_hi, (n, r.dof)).astype(np.float32)
+    keep = [q for q in samp if o.config_valid(q, 2e-4)[0]]
+    V = np.array([qs[off:off + r.dof], qg[off:off + r.dof]] + keep, np.float32)
+    pairs = np.array(sorted(cKDTree(V).query_pairs(delta)))
+    res = o.validate_edges(np.ascontiguousarray(V[pairs[:, 0]].T),
+                           np.ascontiguousarray(V[pairs[:, 1]].T), RES, 2e-4, early_exit=True)
+    adj = [[] for _ in range(len(V))]
+    for (a, b), v in zip(pairs, res["valid"]):
+        if v:
+            adj[a].append(b)
+            adj[b].append(a)
+    seen, st = {0}, [0]
+    while st:
+        for w in adj[st.pop()]:
+            if w not in seen:
+                seen.add(w)
+                st.append(w)
+    return 1 in seen
+
+
+def _start_goal(orc, scene, seed, margin=1e-4, delta=0.8, check=True):
+    """Collision-free start/goal (oracle, with clearance above the margin)
+    whose robots each connect start and goal in a dense oracle PRM."""
+    o = orc.OracleScene(scene)
+    stream = synth.config_stream(scene, seed)
+    ok = lambda q: o.config_valid(q, margin + 1e-3)[0]
+    for _ in range(20):
+        qs, qg = synth.first_accepted(stream, ok), synth.first_accepted(stream, ok)
+        if not check or all(_robot_connected(orc, scene, k, qs, qg, delta=delta)
+                            for k in range(scene.K)):
+            return qs, qg, o
+    raise AssertionError("no feasible start/goal pair found")
+
+
+def _check_path(orc, o, path, cost, qs, qg):
+    assert path is not None and path.shape[0] >= 2
+    np.testing.assert_array_equal(path[0], qs)
+    np.testing.assert_array_equal(path[-1], qg)
+    ok, bad = o.path_valid(path, RES / 4, 0.0)
+    assert ok, f"segment {bad} invalid at res/4"
+    assert cost == pytest.approx(orc.path_cost(path), rel=1e-5)
+    assert cost >= np.linalg.norm(qg.astype(float) - qs.astype(float)) - 1e-6
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plan_planar_pair(mp, orc, seed):
+    scene = synth.planar_pair_scene(seed)
+    qs, qg, o = _start_goal(orc, scene, seed)
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=0.8, n_per_round=64,
+                    tree_cap=1 << 16, roadmap_cap=1 << 14, max_iters=4096, seed=seed,
+                    start=qs, goal=qg) as p:
+        path, cost = mp.plan(p, 2.0)
+        t, c, iters = mp.plan_trace(p)
+    _check_path(orc, o, path, cost, qs, qg)
+    assert len(c) >= 1 and c[-1] == pytest.approx(cost)
+    assert np.all(np.diff(c) < 0), "incumbents must decrease strictly"
+    assert np.all(np.diff(t) >= 0) and iters > 0
+
+
+def test_plan_table_pair(mp, orc):
+    scene = synth.table_pair_scene(0)
+    qs, qg, o = _start_goal(orc, scene, 5, delta=2.5)
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=2.5, n_per_round=64,
+                    tree_cap=1 << 16, roadmap_cap=1 << 14, max_iters=4096, seed=3,
+                    start=qs, goal=qg) as p:
+        path, cost = mp.plan(p, 4.0)
+        t, c, _ = mp.plan_trace(p)
+    _check_path(orc, o, path, cost, qs, qg)
+    assert np.all(np.diff(c) < 0)
+
+
+def test_plan_continues_and_improves(mp, orc):
+    """A second call continues from the device-resident state: the incumbent
+    never gets worse (Alg. 1 keeps c_best)."""
+    scene = synth.planar_pair_scene(4)
+    qs, qg, o = _start_goal(orc, scene, 4)
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=0.8, seed=9, start=qs, goal=qg) as p:
+        _, c1 = mp.plan(p, 1.0)
+        path, c2 = mp.plan(p, 1.0)
+    assert c2 <= c1
+    _check_path(orc, o, path, c2, qs, qg)
+
+
+def test_plan_rejects_colliding_start(mp, orc):
+    scene = synth.table_pair_scene(0)
+    o = orc.OracleScene(scene)
+    stream = synth.config_stream(scene, 77)
+    bad = synth.first_accepted(stream, lambda q: not o.config_valid(q, 0.0)[0])
+    good = synth.first_accepted(stream, lambda q: o.config_valid(q, 1e-3)[0])
+    with mp.Problem(scene, start=bad, goal=good) as p:
+        with pytest.raises(mp.MrpopError) as ei:
+            mp.plan(p, 0.5)
+    assert ei.value.status == 1
+
+
+def test_plan_obstacle_free_converges_to_straight_line(mp):
+    """Far-apart planar arms without obstacles: C* = |q_goal - q_start| (the
+    straight line is free).  The incumbent must approach it (Thm. 1)."""
+    scene = synth.planar_pair_scene(0)
+    scene.robots[0].base[3] = -2.0
+    scene.robots[1].base[3] = 2.0
+    scene = synth.Scene(scene.robots, np.zeros((0, 4), np.float32), np.zeros((0, 15), np.float32))
+    rng = np.random.default_rng(3)
+    qs = rng.uniform(-2.5, 2.5, 6).astype(np.float32)
+    qg = rng.uniform(-2.5, 2.5, 6).astype(np.float32)
+    cstar = float(np.linalg.norm(qg.astype(float) - qs.astype(float)))
+    with mp.Problem(scene, delta=0.8, seed=1, start=qs, goal=qg) as p:
+        path, cost = mp.plan(p, 3.0)
+    assert cost >= cstar - 1e-6
+    assert cost <= 1.5 * cstar, (cost, cstar)
