@@ -254,6 +254,27 @@ mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim, double *
 mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path, int64_t path_cap,
                         int64_t *path_len, double *cost);
 
+/* Plans n problems at once (the batched form of mrpop_plan): one search step
+ * advances every problem by 256 iterations in a single replay of a captured
+ * CUDA graph whose kernels take a problem dimension; problems that need a
+ * ROADMAP round skip the steps until it completes.  Runs until time_budget_s
+ * of wall time, or max_steps steps when max_steps > 0, or until every problem
+ * has reached target_costs[i] (host [n], or NULL for none).  A problem's
+ * planner evolves exactly as it would alone for the same number of steps
+ * (per-problem random streams, ordered inserts), so results do not depend on
+ * the mix.  statuses (host [n], may be NULL): MRPOP_OK, or MRPOP_EINVAL for a
+ * problem whose start or goal is in collision.  Results: mrpop_plan_result,
+ * mrpop_plan_trace.  Errors: EINVAL (NULL, repeated or start/goal-less
+ * problems), ENOMEM / ECUDA. */
+mrpop_status mrpop_plan_batch(mrpop_problem *const *ps, int32_t n, double time_budget_s,
+                              int64_t max_steps, const double *target_costs,
+                              mrpop_status *statuses);
+
+/* Best path and cost found so far for p (same outputs and errors as
+ * mrpop_plan, without planning). */
+mrpop_status mrpop_plan_result(mrpop_problem *p, float *path, int64_t path_cap, int64_t *path_len,
+                               double *cost);
+
 /* Incumbent history of the problem's planner: times[i] (seconds since the
  * start of the mrpop_plan call that found it) and costs[i], in order, at most
  * cap entries; *n receives the full count and *iterations the planner

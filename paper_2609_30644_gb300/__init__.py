@@ -11,7 +11,8 @@ generators) and ``build`` import without the library.
 from __future__ import annotations
 
 _OPS = ("MrpopError", "Problem", "edge_clearance", "fk", "lib", "library_path", "nearest",
-        "neighbors", "path_cost", "validate_edges", "validate_work", "EXPORTS", "plan", "plan_trace")
+        "neighbors", "path_cost", "validate_edges", "validate_work", "EXPORTS", "plan", "plan_trace",
+        "plan_batch", "plan_result")
 
 
 def __getattr__(name):

@@ -32,6 +32,8 @@ EXPORTS = (
     "mrpop_neighbors",
     "mrpop_path_cost",
     "mrpop_plan",
+    "mrpop_plan_batch",
+    "mrpop_plan_result",
     "mrpop_plan_trace",
 )
 
@@ -86,6 +88,8 @@ def _load() -> C.CDLL:
         "mrpop_path_cost": (i32, [vp, i64, i32, vp, vp]),
         "mrpop_plan": (i32, [vp, C.c_double, vp, i64, vp, vp]),
         "mrpop_plan_trace": (i32, [vp, vp, vp, i64, vp, vp]),
+        "mrpop_plan_batch": (i32, [vp, i32, C.c_double, i64, vp, vp]),
+        "mrpop_plan_result": (i32, [vp, vp, i64, vp, vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -307,3 +311,25 @@ def plan_trace(p: Problem) -> tuple:
     c = np.zeros(max(n.value, 1))
     _check(lib.mrpop_plan_trace(p.handle, t.ctypes.data, c.ctypes.data, n.value, None, None))
     return t[:n.value], c[:n.value], it.value
+
+
+def plan_batch(problems, time_budget_s: float, max_steps: int = 0, targets=None) -> np.ndarray:
+    """Plans all problems at once; returns their int32 statuses."""
+    n = len(problems)
+    hs = (C.c_void_p * n)(*[p.handle.value for p in problems])
+    st = np.zeros(n, dtype=np.int32)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.float64)
+    _check(lib.mrpop_plan_batch(hs, n, float(time_budget_s), int(max_steps),
+                                None if tg is None else tg.ctypes.data, st.ctypes.data))
+    return st
+
+
+def plan_result(p: Problem, path_cap: int = 1 << 16) -> tuple:
+    """(path float32 [M, D] or None, cost) of the best path found so far."""
+    buf = np.zeros((path_cap, p.D), dtype=np.float32)
+    n, cost = C.c_int64(), C.c_double()
+    st = lib.mrpop_plan_result(p.handle, buf.ctypes.data, path_cap, C.byref(n), C.byref(cost))
+    if st == 6:
+        return None, float("inf")
+    _check(st)
+    return buf[:n.value].copy(), cost.value

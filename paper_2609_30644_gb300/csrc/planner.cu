@@ -28,7 +28,7 @@
 namespace mrpop {
 
 constexpr int kStepIters = 256;     // iterations per step and problem
-constexpr int kKmax = 32;           // roadmap degree cap
+constexpr int kKmax = 64;           // roadmap degree cap
 constexpr int kOversample = 4;      // roadmap candidates per wanted sample
 constexpr int kInformedTries = 16;  // informed-sampling rejection limit
 
@@ -307,28 +307,43 @@ __global__ void k_oracle(const Slot *__restrict__ slots) {
 }
 
 // Insert z_new = (q_new, g_near + |q_new - q_near|) into the expanded tree and
-// prepare the connection budget c_best - g_new (AO-X) or +inf (dRRT).
-__global__ void k_insert(const Slot *__restrict__ slots) {
+// prepare the connection budget c_best - g_new (AO-X) or +inf (dRRT).  One
+// block per slot; new vertices get consecutive indices in iteration order (a
+// block-wide prefix sum), so a slot's trees do not depend on thread timing.
+__global__ void __launch_bounds__(kStepIters) k_insert(const Slot *__restrict__ slots) {
     const Slot &S = slots[blockIdx.y];
     Ctrl &C = *S.ctrl;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kStepIters) return;
+    __shared__ int wsum[kStepIters / 32];
+    const int i = threadIdx.x;
     const int B = kStepIters, D = S.D, a = C.tree_a;
+    const bool want = S.valid1[i] && S.gnew[i] < INFINITY;
+    const int lane = i & 31, warp = i >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kStepIters / 32; ++w) {
+        before += w < warp ? wsum[w] : 0;
+        total += wsum[w];
+    }
+    const int base = S.tn[a];
+    __syncthreads();
     int idx = -1;
-    if (S.valid1[i] && S.gnew[i] < INFINITY) {
-        idx = atomicAdd(&S.tn[a], 1);
-        if (idx >= S.tcap) {
-            C.overflow = 1;
-            idx = -1;
-        } else {
+    if (want) {
+        const int pos = base + before + __popc(bal & ((1u << lane) - 1u));
+        if (pos < S.tcap) {
+            idx = pos;
             for (int d = 0; d < D; ++d)
                 S.tq[a][(size_t)d * S.tcap + idx] = S.qnew[(size_t)d * B + i];
             S.tq[a][(size_t)D * S.tcap + idx] = S.gnew[i];
             S.tpar[a][idx] = (int)S.near[i];
             for (int r = 0; r < S.K; ++r)
                 S.trmv[a][(size_t)r * S.tcap + idx] = S.rmvnew[(size_t)r * B + i];
+        } else {
+            C.overflow = 1;
         }
     }
+    if (i == 0) S.tn[a] = min(base + total, S.tcap);
     S.newidx[i] = idx;
     S.budget2[i] = idx < 0 ? -INFINITY : (C.mode == 1 ? C.c_best - S.gnew[i] : INFINITY);
 }
@@ -442,15 +457,17 @@ __global__ void k_rm_edges(const float *V, int rcap, int dof, int first, int m,
     eb[e] = v;
 }
 
+// Roadmap edges in candidate order (one thread: the adjacency lists, capped
+// at kKmax, do not depend on thread timing).
 __global__ void k_rm_link(const uint8_t *valid, const int *ea, const int *eb, int E, int *adj,
                           int *deg) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E || !valid[e] || ea[e] < 0) return;
-    const int a = ea[e], b = eb[e];
-    const int ka = atomicAdd(&deg[a], 1);
-    if (ka < kKmax) adj[(size_t)a * kKmax + ka] = b;
-    const int kb = atomicAdd(&deg[b], 1);
-    if (kb < kKmax) adj[(size_t)b * kKmax + kb] = a;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int e = 0; e < E; ++e) {
+        if (!valid[e] || ea[e] < 0) continue;
+        const int a = ea[e], b = eb[e];
+        if (deg[a] < kKmax) adj[(size_t)a * kKmax + deg[a]++] = b;
+        if (deg[b] < kKmax) adj[(size_t)b * kKmax + deg[b]++] = a;
+    }
 }
 
 __global__ void k_tree_reset(const Slot *__restrict__ slots) {
@@ -515,6 +532,7 @@ struct Planner {
     double c_best = INFINITY;
     std::vector<float> best_path;  // [M][D]
     std::vector<double> trace_t, trace_c;
+    double trace_t0 = 0.0;
     unsigned long long seed = 0;
     int step = 0;
     int *d_path = nullptr;
@@ -752,7 +770,7 @@ static mrpop_status roadmap_round(Planner *pl, int k, cudaStream_t st) {
         PL_TRY(cudaGetLastError());
         ST_TRY(launch_validate(r.sub, r.ea_q, r.eb_q, E, r.evalid, nullptr, nullptr, nullptr,
                                nullptr, st));
-        k_rm_link<<<(E + 127) / 128, 128, 0, st>>>(r.evalid, r.ea, r.eb, E, r.adj, r.deg);
+        k_rm_link<<<1, 32, 0, st>>>(r.evalid, r.ea, r.eb, E, r.adj, r.deg);
         PL_TRY(cudaGetLastError());
     }
     r.n = n_new;
@@ -786,22 +804,20 @@ static double now_s() {
 
 // Accepts a candidate path if it is strictly cheaper (FP64 cost) and every
 // segment is valid at a quarter of the resolution.
-static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, cudaStream_t st,
-                                  double t_now, bool *accepted) {
+static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, int tree_a,
+                                  cudaStream_t st, double t_now, bool *accepted) {
     *accepted = false;
     const int cap = 2 * pl->tcap + 2, D = pl->D;
     k_extract<<<1, 1, 0, st>>>(d_slot, it, pl->d_path, pl->d_pathq, cap, pl->d_len);
     PL_TRY(cudaGetLastError());
     int len = 0;
-    Ctrl c;
     PL_TRY(cudaMemcpyAsync(&len, pl->d_len, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PL_TRY(cudaMemcpyAsync(&c, pl->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     PL_TRY(cudaStreamSynchronize(st));
     std::vector<float> path((size_t)len * D);
     PL_TRY(cudaMemcpyAsync(path.data(), pl->d_pathq, sizeof(float) * path.size(),
                            cudaMemcpyDeviceToHost, st));
     PL_TRY(cudaStreamSynchronize(st));
-    const int a = c.tree_a;
+    const int a = tree_a;
     if (a == 1) {  // expanded tree was the goal tree: reverse to start -> goal
         for (int j = 0; j < len / 2; ++j)
             for (int d = 0; d < D; ++d)
@@ -850,26 +866,111 @@ static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, cudaS
     return MRPOP_OK;
 }
 
-static mrpop_status search_step(Planner *pl, Slot *d_slot, VParams *d_vp, cudaStream_t st) {
-    const dim3 g1((kStepIters + 127) / 128, 1), gq(kStepIters / kPQB, 1);
-    k_sample<<<g1, 128, 0, st>>>(d_slot);
-    k_nearest<0><<<gq, kPThreads, 0, st>>>(d_slot);
-    k_oracle<<<g1, 128, 0, st>>>(d_slot);
+// One planning batch: slots (problems) that step together.  Every slot's
+// Ctrl lives in one device array so that a step needs one copy each way.
+struct Batch {
+    int n = 0;
+    std::vector<Planner *> pls;
+    Slot *d_slots = nullptr;
+    VParams *d_vp = nullptr;  // [2][n]: connection pass after the extension pass
+    Ctrl *d_ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;   // pinned
+    int spl = 4, warps = 1, bps = 1;
+    size_t smem = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    ~Batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(d_slots);
+        cudaFree(d_vp);
+        cudaFree(d_ctrl);
+        if (h_ctrl) cudaFreeHost(h_ctrl);
+    }
+};
+
+static mrpop_status enqueue_step(Batch &bt, cudaStream_t st) {
+    const int n = bt.n;
+    const dim3 g1((kStepIters + 127) / 128, n), gq(kStepIters / kPQB, n);
+    k_sample<<<g1, 128, 0, st>>>(bt.d_slots);
+    k_nearest<0><<<gq, kPThreads, 0, st>>>(bt.d_slots);
+    k_oracle<<<g1, 128, 0, st>>>(bt.d_slots);
     PL_TRY(cudaGetLastError());
-    const int spl = pl->p->dev.t.max_spheres_per_link;
-    const int bps = (kStepIters + pl->vwarps - 1) / pl->vwarps;
-    ST_TRY(launch_validate_batch(d_vp, 1, spl, pl->vwarps, bps, pl->vsmem, st));
-    k_insert<<<g1, 128, 0, st>>>(d_slot);
-    k_nearest<1><<<gq, kPThreads, 0, st>>>(d_slot);
-    k_conn_prep<<<g1, 128, 0, st>>>(d_slot);
+    ST_TRY(launch_validate_batch(bt.d_vp, n, bt.spl, bt.warps, bt.bps, bt.smem, st));
+    k_insert<<<dim3(1, n), kStepIters, 0, st>>>(bt.d_slots);
+    k_nearest<1><<<gq, kPThreads, 0, st>>>(bt.d_slots);
+    k_conn_prep<<<g1, 128, 0, st>>>(bt.d_slots);
     PL_TRY(cudaGetLastError());
-    ST_TRY(launch_validate_batch(d_vp + 1, 1, spl, pl->vwarps, bps, pl->vsmem, st));
-    k_solution<<<g1, 128, 0, st>>>(d_slot);
+    ST_TRY(launch_validate_batch(bt.d_vp + n, n, bt.spl, bt.warps, bt.bps, bt.smem, st));
+    k_solution<<<g1, 128, 0, st>>>(bt.d_slots);
     PL_TRY(cudaGetLastError());
     return MRPOP_OK;
 }
 
-static mrpop_status plan(mrpop_problem *p, double budget) {
+static mrpop_status build_batch(Batch &bt, cudaStream_t st) {
+    const int n = bt.n;
+    PL_TRY(cudaMalloc(&bt.d_slots, sizeof(Slot) * n));
+    PL_TRY(cudaMalloc(&bt.d_vp, sizeof(VParams) * 2 * n));
+    PL_TRY(cudaMalloc(&bt.d_ctrl, sizeof(Ctrl) * n));
+    PL_TRY(cudaMallocHost(&bt.h_ctrl, sizeof(Ctrl) * n));
+    // one launch configuration for every slot: the fewest warps any slot
+    // allows, the largest shared memory and sphere count any slot needs
+    int warps = 4;
+    for (Planner *pl : bt.pls) warps = std::min(warps, pl->vwarps);
+    size_t smem = 0;
+    int spl = 1;
+    for (Planner *pl : bt.pls) {
+        const size_t tab = (size_t)pl->p->dev.t.n_f4 * sizeof(float4);
+        smem = std::max(smem, tab + (size_t)warps * pl->vp[0].warp_floats * sizeof(float));
+        spl = std::max(spl, pl->p->dev.t.max_spheres_per_link);
+    }
+    bt.warps = warps;
+    bt.smem = smem;
+    bt.spl = spl;
+    bt.bps = (kStepIters + warps - 1) / warps;
+    std::vector<Slot> slots(n);
+    std::vector<VParams> vps(2 * n);
+    for (int i = 0; i < n; ++i) {
+        Planner *pl = bt.pls[i];
+        slots[i] = pl->slot;
+        slots[i].ctrl = bt.d_ctrl + i;
+        for (int k = 0; k < 2; ++k) {
+            vps[(size_t)k * n + i] = pl->vp[k];
+            vps[(size_t)k * n + i].total_warps = bt.bps * warps;
+        }
+    }
+    PL_TRY(cudaMemcpy(bt.d_slots, slots.data(), sizeof(Slot) * n, cudaMemcpyHostToDevice));
+    PL_TRY(cudaMemcpy(bt.d_vp, vps.data(), sizeof(VParams) * 2 * n, cudaMemcpyHostToDevice));
+    std::vector<Ctrl> idle(n);
+    for (auto &c : idle) {
+        c = Ctrl{};
+        c.mode = 2;
+        c.c_best = INFINITY;
+        c.best_key = ~0ull;
+    }
+    PL_TRY(cudaMemcpy(bt.d_ctrl, idle.data(), sizeof(Ctrl) * n, cudaMemcpyHostToDevice));
+    // one uncaptured step (sets kernel attributes), then capture the step
+    ST_TRY(enqueue_step(bt, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    PL_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    mrpop_status s = enqueue_step(bt, st);
+    cudaError_t e = cudaStreamEndCapture(st, &bt.graph);
+    if (s != MRPOP_OK) return s;
+    PL_TRY(e);
+    PL_TRY(cudaGraphInstantiate(&bt.exec, bt.graph, 0));
+    return MRPOP_OK;
+}
+
+struct SlotRun {
+    bool active = false, need_roadmap = true, reset_trees = true, reached = false;
+    double target = -INFINITY;
+    mrpop_status status = MRPOP_OK;
+};
+
+// Runs Alg. 1 on every problem of ps at once until the budget ends or every
+// problem reached its target cost.
+static mrpop_status plan_batch(mrpop_problem *const *ps, int n, double budget, int64_t max_steps,
+                               const double *targets, mrpop_status *statuses) {
     const double t0 = now_s();
     cudaStream_t st;
     PL_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -877,85 +978,106 @@ static mrpop_status plan(mrpop_problem *p, double budget) {
         cudaStream_t s;
         ~Guard() { cudaStreamDestroy(s); }
     } guard{st};
-    if (!p->planner) ST_TRY(planner_init(p, &p->planner));
-    Planner *pl = p->planner;
-    // start and goal must be valid
-    {
-        uint8_t *dv = nullptr;
-        PL_TRY(cudaMalloc(&dv, 2));
-        ST_TRY(launch_validate(p, pl->d_start, pl->d_start, 1, dv, nullptr, nullptr, nullptr, nullptr, st));
-        ST_TRY(launch_validate(p, pl->d_goal, pl->d_goal, 1, dv + 1, nullptr, nullptr, nullptr, nullptr, st));
-        uint8_t v[2];
-        PL_TRY(cudaMemcpyAsync(v, dv, 2, cudaMemcpyDeviceToHost, st));
-        PL_TRY(cudaStreamSynchronize(st));
-        cudaFree(dv);
-        if (!v[0] || !v[1]) return set_error(MRPOP_EINVAL, "mrpop_plan: start or goal is in collision");
+    Batch bt;
+    bt.n = n;
+    std::vector<SlotRun> run(n);
+    uint8_t *dv = nullptr;
+    PL_TRY(cudaMalloc(&dv, 2 * (size_t)n));
+    struct FreeV {
+        uint8_t *p;
+        ~FreeV() { cudaFree(p); }
+    } fv{dv};
+    for (int i = 0; i < n; ++i) {
+        mrpop_problem *p = ps[i];
+        if (!p->planner) ST_TRY(planner_init(p, &p->planner));
+        Planner *pl = p->planner;
+        bt.pls.push_back(pl);
+        ST_TRY(launch_validate(p, pl->d_start, pl->d_start, 1, dv + 2 * i, nullptr, nullptr, nullptr,
+                               nullptr, st));
+        ST_TRY(launch_validate(p, pl->d_goal, pl->d_goal, 1, dv + 2 * i + 1, nullptr, nullptr,
+                               nullptr, nullptr, st));
+        run[i].target = targets ? targets[i] : -INFINITY;
+        run[i].reset_trees = !pl->roadmap_ready;
+        pl->trace_t0 = t0;
     }
-    Slot *d_slot = nullptr;
-    VParams *d_vp = nullptr;
-    PL_TRY(cudaMalloc(&d_slot, sizeof(Slot)));
-    PL_TRY(cudaMalloc(&d_vp, sizeof(VParams) * 2));
-    struct Free2 {
-        void *a, *b;
-        ~Free2() { cudaFree(a); cudaFree(b); }
-    } fr{d_slot, d_vp};
-    PL_TRY(cudaMemcpy(d_slot, &pl->slot, sizeof(Slot), cudaMemcpyHostToDevice));
-    VParams vp[2] = {pl->vp[0], pl->vp[1]};
-    const int bps = (kStepIters + pl->vwarps - 1) / pl->vwarps;
-    for (auto &v : vp) v.total_warps = bps * pl->vwarps;
-    PL_TRY(cudaMemcpy(d_vp, vp, sizeof(vp), cudaMemcpyHostToDevice));
-
-    const long long max_iters = std::max<long long>(kStepIters, p->cfg.max_iters);
-    bool need_roadmap = true, reset_trees = !pl->roadmap_ready;
-    while (now_s() - t0 < budget) {
-        if (need_roadmap) {
-            // ROADMAP: grow every robot's roadmap by one round, then keep
-            // growing until every robot connects its start and goal
+    std::vector<uint8_t> sv(2 * (size_t)n);
+    PL_TRY(cudaMemcpyAsync(sv.data(), dv, 2 * (size_t)n, cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+        run[i].active = sv[2 * i] && sv[2 * i + 1];
+        if (!run[i].active) run[i].status = MRPOP_EINVAL;
+        if (bt.pls[i]->c_best <= run[i].target) {
+            run[i].active = false;
+            run[i].reached = true;
+        }
+    }
+    ST_TRY(build_batch(bt, st));
+    for (int64_t outer = 0; now_s() - t0 < budget && (max_steps <= 0 || outer < max_steps); ++outer) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            if (!run[i].active) continue;
+            any = true;
+            Planner *pl = bt.pls[i];
+            if (!run[i].need_roadmap) continue;
+            // ROADMAP round (Alg. 2); the slot rejoins the search steps once
+            // every robot connects its start and goal
             bool all = true;
-            do {
-                all = true;
-                for (int k = 0; k < pl->K; ++k) {
-                    ST_TRY(roadmap_round(pl, k, st));
-                    all = all && pl->rm[k].connected;
-                }
-                ++pl->step;
-            } while (!all && now_s() - t0 < budget);
-            if (!all) break;
+            for (int k = 0; k < pl->K; ++k) {
+                ST_TRY(roadmap_round(pl, k, st));
+                all = all && pl->rm[k].connected;
+            }
+            ++pl->step;
+            if (!all) continue;
             pl->roadmap_ready = true;
-            need_roadmap = false;
+            run[i].need_roadmap = false;
             pl->iters_in_call = 0;
-            if (pl->mode == 1 || reset_trees) {
-                k_tree_reset<<<1, 64, 0, st>>>(d_slot);
+            if (pl->mode == 1 || run[i].reset_trees) {
+                k_tree_reset<<<1, 64, 0, st>>>(bt.d_slots + i);
                 PL_TRY(cudaGetLastError());
-                reset_trees = false;
+                run[i].reset_trees = false;
             }
         }
-        Ctrl c{};
-        c.c_best = pl->c_best < INFINITY ? (float)pl->c_best : INFINITY;
-        c.mode = pl->mode;
-        c.step = pl->step++;
-        c.seed = pl->seed;
-        c.best_key = ~0ull;
-        PL_TRY(cudaMemcpyAsync(pl->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-        ST_TRY(search_step(pl, d_slot, d_vp, st));
-        Ctrl r;
-        PL_TRY(cudaMemcpyAsync(&r, pl->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        if (!any) break;
+        for (int i = 0; i < n; ++i) {
+            Planner *pl = bt.pls[i];
+            Ctrl &c = bt.h_ctrl[i];
+            c = Ctrl{};
+            c.c_best = pl->c_best < INFINITY ? (float)pl->c_best : INFINITY;
+            c.mode = run[i].active && !run[i].need_roadmap ? pl->mode : 2;
+            c.step = pl->step++;
+            c.seed = pl->seed;
+            c.best_key = ~0ull;
+        }
+        PL_TRY(cudaMemcpyAsync(bt.d_ctrl, bt.h_ctrl, sizeof(Ctrl) * n, cudaMemcpyHostToDevice, st));
+        PL_TRY(cudaGraphLaunch(bt.exec, st));
+        PL_TRY(cudaMemcpyAsync(bt.h_ctrl, bt.d_ctrl, sizeof(Ctrl) * n, cudaMemcpyDeviceToHost, st));
         PL_TRY(cudaStreamSynchronize(st));
-        pl->iters_in_call += kStepIters;
-        pl->total_iters += kStepIters;
-        bool accepted = false;
-        if (r.best_key != ~0ull)
-            ST_TRY(try_incumbent(pl, d_slot, (int)(r.best_key & 0xffffffffu), st, now_s() - t0,
-                                 &accepted));
-        if (accepted) {
-            pl->first_solved = true;
-            pl->mode = 1;            // from now on: AO-X
-            need_roadmap = true;     // Alg. 1: grow the roadmap, then optimise again
-        } else if (pl->iters_in_call >= max_iters || r.overflow) {
-            need_roadmap = true;     // iteration cap: grow the roadmap (c14)
-            if (r.overflow) reset_trees = true;
+        for (int i = 0; i < n; ++i) {
+            if (!run[i].active || run[i].need_roadmap) continue;
+            Planner *pl = bt.pls[i];
+            const Ctrl r = bt.h_ctrl[i];
+            pl->iters_in_call += kStepIters;
+            pl->total_iters += kStepIters;
+            bool accepted = false;
+            if (r.best_key != ~0ull)
+                ST_TRY(try_incumbent(pl, bt.d_slots + i, (int)(r.best_key & 0xffffffffu), r.tree_a,
+                                     st, now_s() - t0, &accepted));
+            const long long max_iters = std::max<long long>(kStepIters, pl->p->cfg.max_iters);
+            if (accepted) {
+                pl->mode = 1;                 // from now on: AO-X
+                run[i].need_roadmap = true;   // Alg. 1: grow the roadmap, optimise again
+                if (pl->c_best <= run[i].target) {
+                    run[i].active = false;
+                    run[i].reached = true;
+                }
+            } else if (pl->iters_in_call >= max_iters || r.overflow) {
+                run[i].need_roadmap = true;   // iteration cap: grow the roadmap (c14)
+                if (r.overflow) run[i].reset_trees = true;
+            }
         }
     }
+    if (statuses)
+        for (int i = 0; i < n; ++i) statuses[i] = run[i].status;
     return MRPOP_OK;
 }
 
@@ -963,24 +1085,54 @@ static mrpop_status plan(mrpop_problem *p, double budget) {
 
 using namespace mrpop;
 
-extern "C" mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path,
-                                   int64_t path_cap, int64_t *path_len, double *cost) {
-    if (!p) return set_error(MRPOP_EINVAL, "mrpop_plan: problem is NULL");
-    if (!(time_budget_s >= 0.0)) return set_error(MRPOP_EINVAL, "mrpop_plan: negative budget");
-    mrpop_status s = plan(p, time_budget_s);
-    if (s != MRPOP_OK) return s;
+static mrpop_status result(mrpop_problem *p, float *path, int64_t path_cap, int64_t *path_len,
+                           double *cost) {
     Planner *pl = p->planner;
     const int64_t M = pl ? (int64_t)(pl->best_path.size() / std::max(1, pl->D)) : 0;
     if (path_len) *path_len = M;
     if (cost) *cost = pl && M > 0 ? pl->c_best : INFINITY;
-    if (M == 0) return set_error(MRPOP_ENOSOLUTION, "mrpop_plan: no path found within the budget");
+    if (M == 0) return set_error(MRPOP_ENOSOLUTION, "no path found within the budget");
     if (path) {
         if (path_cap < M)
-            return set_error(MRPOP_ECAPACITY, "mrpop_plan: path needs %lld vertices, cap %lld",
-                             (long long)M, (long long)path_cap);
+            return set_error(MRPOP_ECAPACITY, "path needs %lld vertices, cap %lld", (long long)M,
+                             (long long)path_cap);
         std::memcpy(path, pl->best_path.data(), sizeof(float) * pl->best_path.size());
     }
     return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path,
+                                   int64_t path_cap, int64_t *path_len, double *cost) {
+    if (!p) return set_error(MRPOP_EINVAL, "mrpop_plan: problem is NULL");
+    if (!(time_budget_s >= 0.0)) return set_error(MRPOP_EINVAL, "mrpop_plan: negative budget");
+    if (p->start.empty() || p->goal.empty())
+        return set_error(MRPOP_EINVAL, "mrpop_plan: the problem was created without start/goal");
+    mrpop_status st = MRPOP_OK;
+    mrpop_status s = plan_batch(&p, 1, time_budget_s, 0, nullptr, &st);
+    if (s != MRPOP_OK) return s;
+    if (st != MRPOP_OK) return set_error(st, "mrpop_plan: start or goal is in collision");
+    return result(p, path, path_cap, path_len, cost);
+}
+
+extern "C" mrpop_status mrpop_plan_batch(mrpop_problem *const *ps, int32_t n, double time_budget_s,
+                                         int64_t max_steps, const double *target_costs,
+                                         mrpop_status *statuses) {
+    if (!ps || n < 1) return set_error(MRPOP_EINVAL, "mrpop_plan_batch: no problems");
+    if (!(time_budget_s >= 0.0)) return set_error(MRPOP_EINVAL, "mrpop_plan_batch: negative budget");
+    for (int i = 0; i < n; ++i) {
+        if (!ps[i]) return set_error(MRPOP_EINVAL, "mrpop_plan_batch: problem %d is NULL", i);
+        if (ps[i]->start.empty() || ps[i]->goal.empty())
+            return set_error(MRPOP_EINVAL, "mrpop_plan_batch: problem %d has no start/goal", i);
+        for (int j = 0; j < i; ++j)
+            if (ps[j] == ps[i]) return set_error(MRPOP_EINVAL, "mrpop_plan_batch: problem %d repeated", i);
+    }
+    return plan_batch(ps, n, time_budget_s, max_steps, target_costs, statuses);
+}
+
+extern "C" mrpop_status mrpop_plan_result(mrpop_problem *p, float *path, int64_t path_cap,
+                                          int64_t *path_len, double *cost) {
+    if (!p) return set_error(MRPOP_EINVAL, "mrpop_plan_result: problem is NULL");
+    return result(p, path, path_cap, path_len, cost);
 }
 
 extern "C" mrpop_status mrpop_plan_trace(const mrpop_problem *p, double *times, double *costs,

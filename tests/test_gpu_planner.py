@@ -141,3 +141,54 @@ def test_plan_obstacle_free_converges_to_straight_line(mp):
         path, cost = mp.plan(p, 3.0)
     assert cost >= cstar - 1e-6
     assert cost <= 1.5 * cstar, (cost, cstar)
+
+
+def _planar_problem(mp, orc, seed, **kw):
+    scene = synth.planar_pair_scene(seed)
+    qs, qg, o = _start_goal(orc, scene, seed)
+    p = mp.Problem(scene, resolution=RES, margin=1e-4, delta=0.8, n_per_round=64,
+                   tree_cap=1 << 15, roadmap_cap=1 << 13, max_iters=4096, seed=seed,
+                   start=qs, goal=qg, **kw)
+    return p, qs, qg, o
+
+
+def test_plan_batch_paths_valid(mp, orc):
+    """Four problems planned together: every result is oracle-valid."""
+    probs = [_planar_problem(mp, orc, s) for s in (0, 2, 3, 6)]
+    st = mp.plan_batch([p for p, *_ in probs], 3.0)
+    assert (st == 0).all()
+    for p, qs, qg, o in probs:
+        path, cost = mp.plan_result(p)
+        _check_path(orc, o, path, cost, qs, qg)
+        _, c, _ = mp.plan_trace(p)
+        assert np.all(np.diff(c) < 0)
+        p.close()
+
+
+def test_plan_batch_alone_equals_mix(mp, orc):
+    """The same problem, same seed and same number of steps gives exactly the
+    same path and cost alone and in a mix with other problems."""
+    steps = 40
+    a, *_ = _planar_problem(mp, orc, 2)
+    mp.plan_batch([a], 60.0, max_steps=steps)
+    alone = mp.plan_result(a)
+    a.close()
+    a2, *_ = _planar_problem(mp, orc, 2)
+    others = [_planar_problem(mp, orc, s)[0] for s in (0, 3)]
+    mp.plan_batch([others[0], a2, others[1]], 60.0, max_steps=steps)
+    mixed = mp.plan_result(a2)
+    assert alone[0] is not None
+    np.testing.assert_array_equal(alone[0], mixed[0])
+    assert alone[1] == mixed[1]
+    for p in [a2] + others:
+        p.close()
+
+
+def test_plan_batch_stops_at_target(mp, orc):
+    p, qs, qg, o = _planar_problem(mp, orc, 3)
+    st = mp.plan_batch([p], 5.0, targets=[1e9])   # any solution reaches the target
+    path, cost = mp.plan_result(p)
+    t, c, _ = mp.plan_trace(p)
+    assert len(c) == 1 and t[0] < 1.0
+    _check_path(orc, o, path, cost, qs, qg)
+    p.close()
