@@ -256,6 +256,89 @@ class ClockSampler:
         return out
 
 
+# ---------------------------------------------------------------------------
+# planner leg: problems solved per second to 1.1x best cost, plain vs batched
+# ---------------------------------------------------------------------------
+PLAN_PROBLEMS = 16
+PLAN_BUDGET_S = 1.5
+PLAN_DELTA = 2.5
+
+
+def plan_problems(mp, synth, n: int):
+    """Heterogeneous batched-workload problems (2..8 synthetic 7-DOF arms,
+    16..256 obstacles).  Start and goal are drawn uniformly and accepted when
+    the library's clearance is above 2 mm; scenes without such a pair in 10,240
+    draws are skipped."""
+    import numpy as np
+    import torch
+    out = []
+    idx = 0
+    while len(out) < n and idx < 4 * n:
+        sc = synth.batched_scene(idx)
+        stream = synth.config_stream(sc, idx)
+        found = []
+        with mp.Problem(sc) as tmp:
+            for _ in range(40):
+                qs = np.stack([next(stream) for _ in range(256)], axis=1)
+                qd = torch.from_numpy(qs).cuda()
+                c = mp.edge_clearance(tmp, qd, qd).cpu().numpy()
+                found += [qs[:, i].copy() for i in np.nonzero(c > 2e-3)[0]]
+                if len(found) >= 2:
+                    break
+        if len(found) >= 2:
+            out.append((idx, sc, found[0], found[1]))
+        idx += 1
+    return out
+
+
+def run_planner_leg(mp, synth):
+    import numpy as np
+
+    def make(entry):
+        idx, sc, qs, qg = entry
+        return mp.Problem(sc, resolution=RES, margin=MARGIN, delta=PLAN_DELTA, n_per_round=64,
+                          tree_cap=1 << 15, roadmap_cap=1 << 13, max_iters=4096, seed=idx,
+                          start=qs, goal=qg)
+
+    entries = plan_problems(mp, synth, PLAN_PROBLEMS)
+    traces = {"plain": [], "batched": []}
+    for e in entries:                                  # one problem at a time
+        p = make(e)
+        mp.plan(p, PLAN_BUDGET_S)
+        traces["plain"].append(mp.plan_trace(p)[:2])
+        p.close()
+    probs = [make(e) for e in entries]                 # all problems at once
+    t0 = time.perf_counter()
+    mp.plan_batch(probs, PLAN_BUDGET_S)
+    batched_wall = time.perf_counter() - t0
+    traces["batched"] = [mp.plan_trace(p)[:2] for p in probs]
+    for p in probs:
+        p.close()
+    finals = [[c[-1] if len(c) else np.inf for t, c in traces[k]] for k in ("plain", "batched")]
+    best = np.minimum(finals[0], finals[1])
+    res = {"problems": len(entries), "budget_s": PLAN_BUDGET_S,
+           "robots": [int(e[1].K) for e in entries], "batched_wall_s": batched_wall}
+    for k in ("plain", "batched"):
+        reach, ttfs = [], []
+        for (t, c), b in zip(traces[k], best):
+            hit = np.nonzero(c <= 1.1 * b)[0] if len(c) else []
+            reach.append(float(t[hit[0]]) if len(hit) else None)
+            if len(t):
+                ttfs.append(float(t[0]))
+        solved = sum(r is not None for r in reach)
+        spent = [r if r is not None else PLAN_BUDGET_S for r in reach]
+        # plain: problems run back to back; batched: all at once
+        wall = sum(spent) if k == "plain" else max(spent)
+        res[k] = {"solved_to_1.1x_best": solved, "wall_s": wall,
+                  "problems_per_s": solved / wall if wall > 0 else 0.0,
+                  "ttfs_p50_s": float(np.percentile(ttfs, 50)) if ttfs else None,
+                  "ttfs_p99_s": float(np.percentile(ttfs, 99)) if ttfs else None,
+                  "first_solutions": len(ttfs)}
+    if res["plain"]["problems_per_s"] > 0:
+        res["batched_over_plain"] = res["batched"]["problems_per_s"] / res["plain"]["problems_per_s"]
+    return res
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -407,6 +490,11 @@ def run_ours(args) -> None:
     # sanity: the e2e results equal the resident-input results
     assert torch.equal(h_valid, valid.cpu())
 
+    planner = None
+    if rank == 0 and not args.no_planner:
+        from paper_2609_30644_gb300 import synth as _synth
+        planner = run_planner_leg(mp, _synth)
+
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
         peaks = measured_peaks()
@@ -442,6 +530,7 @@ def run_ours(args) -> None:
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 5 * args.steps,   # validate, nearest, neighbors, path cost (2)
             "cpu_baseline": cpu,
+            "planner": planner,
         }
         print(json.dumps(line), flush=True)
     prob.close()
@@ -456,6 +545,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-planner", action="store_true",
+                    help="skip the plain-vs-batched planner leg (problems/s to 1.1x best)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

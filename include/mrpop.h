@@ -275,6 +275,48 @@ mrpop_status mrpop_plan_batch(mrpop_problem *const *ps, int32_t n, double time_b
 mrpop_status mrpop_plan_result(mrpop_problem *p, float *path, int64_t path_cap, int64_t *path_len,
                                double *cost);
 
+/* ---------------------------------------------------------------------------
+ * Serving (continuous batching).  A server owns one thread that keeps up to
+ * max_slots requests on the device and advances every running request by one
+ * planner iteration per loop, exactly as mrpop_plan_batch does; queued
+ * requests are admitted in arrival order whenever a slot is free and their
+ * estimated device memory fits in device_mem_budget bytes (<= 0: 80 % of the
+ * free memory at creation; a request is always admitted when nothing else
+ * runs).  A request's roadmaps and trees stay on the device until it
+ * finishes, then its device state is released (results stay readable with
+ * mrpop_plan_result / mrpop_plan_trace).  A problem handle belongs to the
+ * server from submission until its request is done: do not use or destroy it
+ * meanwhile.  The server uses the CUDA device current at creation.
+ * ------------------------------------------------------------------------- */
+typedef struct mrpop_server mrpop_server;
+
+mrpop_status mrpop_server_create(int32_t max_slots, int64_t device_mem_budget,
+                                 mrpop_server **out);
+
+/* Queues a planning request.  It finishes when its incumbent reaches
+ * target_cost (NaN: no target; +inf: the first solution), when budget_s
+ * seconds have passed since admission, or after max_steps iterations when
+ * max_steps > 0, whichever comes first.  *ticket identifies it.  Errors:
+ * EINVAL, EBUSY (the problem is already queued or running). */
+mrpop_status mrpop_server_submit(mrpop_server *s, mrpop_problem *p, double budget_s,
+                                 int64_t max_steps, double target_cost, int64_t *ticket);
+
+/* State of a request: *state 0 queued, 1 running, 2 done.  times (host
+ * double [4], may be NULL): admission, first solution, target reached, done,
+ * each in seconds since submission or -1 if not (yet) happened.  *cost: the
+ * final incumbent once done (+inf if none).  A request that failed returns its
+ * error status once done. */
+mrpop_status mrpop_server_poll(mrpop_server *s, int64_t ticket, int32_t *state, double *times,
+                               double *cost);
+
+/* Counters (host int64 [6]): requests admitted, completed, peak concurrent
+ * requests, peak admitted device memory (bytes), memory budget, queue length. */
+mrpop_status mrpop_server_stats(mrpop_server *s, int64_t *stats);
+
+/* Stops the server: running requests finish at once, queued ones are
+ * dropped, the thread is joined.  NULL is accepted. */
+mrpop_status mrpop_server_destroy(mrpop_server *s);
+
 /* Incumbent history of the problem's planner: times[i] (seconds since the
  * start of the mrpop_plan call that found it) and costs[i], in order, at most
  * cap entries; *n receives the full count and *iterations the planner

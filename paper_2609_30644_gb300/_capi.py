@@ -35,6 +35,11 @@ EXPORTS = (
     "mrpop_plan_batch",
     "mrpop_plan_result",
     "mrpop_plan_trace",
+    "mrpop_server_create",
+    "mrpop_server_submit",
+    "mrpop_server_poll",
+    "mrpop_server_stats",
+    "mrpop_server_destroy",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -90,6 +95,11 @@ def _load() -> C.CDLL:
         "mrpop_plan_trace": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_plan_batch": (i32, [vp, i32, C.c_double, i64, vp, vp]),
         "mrpop_plan_result": (i32, [vp, vp, i64, vp, vp]),
+        "mrpop_server_create": (i32, [i32, i64, vp]),
+        "mrpop_server_submit": (i32, [vp, vp, C.c_double, i64, C.c_double, vp]),
+        "mrpop_server_poll": (i32, [vp, i64, vp, vp, vp]),
+        "mrpop_server_stats": (i32, [vp, vp]),
+        "mrpop_server_destroy": (i32, [vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -333,3 +343,51 @@ def plan_result(p: Problem, path_cap: int = 1 << 16) -> tuple:
         return None, float("inf")
     _check(st)
     return buf[:n.value].copy(), cost.value
+
+
+class Server:
+    """Continuous-batching planning server (mrpop_server_*)."""
+
+    def __init__(self, max_slots: int = 64, device_mem_budget: int = 0):
+        h = C.c_void_p()
+        _check(lib.mrpop_server_create(int(max_slots), int(device_mem_budget), C.byref(h)))
+        self._h = h
+
+    def submit(self, p: Problem, budget_s: float, max_steps: int = 0,
+               target_cost: float = float("nan")) -> int:
+        t = C.c_int64()
+        _check(lib.mrpop_server_submit(self._h, p.handle, float(budget_s), int(max_steps),
+                                       float(target_cost), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> tuple:
+        """(state, times[4], cost); raises MrpopError for a failed request."""
+        st = C.c_int32()
+        times = np.zeros(4)
+        cost = C.c_double()
+        _check(lib.mrpop_server_poll(self._h, int(ticket), C.byref(st), times.ctypes.data,
+                                     C.byref(cost)))
+        return st.value, times, cost.value
+
+    def stats(self) -> dict:
+        v = np.zeros(6, dtype=np.int64)
+        _check(lib.mrpop_server_stats(self._h, v.ctypes.data))
+        return dict(zip(("admitted", "completed", "peak_active", "peak_mem", "mem_budget",
+                         "queued"), (int(x) for x in v)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            lib.mrpop_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

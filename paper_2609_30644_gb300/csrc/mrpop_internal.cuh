@@ -57,6 +57,7 @@ struct VParams {
     int warp_floats;
     int dpad;
     int nstore;  // links of robots 0..K-2 (their frames and tile bounds are kept)
+    int warps;   // warps of each block that take edges (the rest only stage tables)
 };
 
 struct DeviceProblem {

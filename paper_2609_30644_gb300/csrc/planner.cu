@@ -18,6 +18,12 @@
 // start and goal are connected (BFS on the host).
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -470,6 +476,35 @@ __global__ void k_rm_link(const uint8_t *valid, const int *ea, const int *eb, in
     }
 }
 
+// Start-goal connectivity of a roadmap: level-synchronous BFS from vertex 0
+// in one block (at most n levels), writes whether vertex 1 was reached.
+__global__ void __launch_bounds__(1024) k_rm_bfs(const int *adj, const int *deg, int n, int *level,
+                                                 int *connected) {
+    __shared__ int changed;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) level[v] = v == 0 ? 0 : -1;
+    __syncthreads();
+    for (int l = 0; l < n; ++l) {
+        if (threadIdx.x == 0) changed = 0;
+        __syncthreads();
+        for (int v = threadIdx.x; v < n; v += blockDim.x) {
+            if (level[v] != l) continue;
+            const int dg = min(deg[v], kKmax);
+            for (int k = 0; k < dg; ++k) {
+                const int w = adj[(size_t)v * kKmax + k];
+                if (w >= 0 && w < n && level[w] < 0) {
+                    level[w] = l + 1;
+                    changed = 1;
+                }
+            }
+        }
+        __syncthreads();
+        const int c = changed;
+        __syncthreads();
+        if (!c) break;
+    }
+    if (threadIdx.x == 0) *connected = n > 1 && level[1] >= 0;
+}
+
 __global__ void k_tree_reset(const Slot *__restrict__ slots) {
     const Slot &S = slots[blockIdx.x];
     const int D = S.D;
@@ -504,6 +539,8 @@ struct RobotRoadmap {
     uint8_t *cvalid = nullptr, *evalid = nullptr;
     int64_t *nb = nullptr, *cnt = nullptr;
     int *ea = nullptr, *eb = nullptr;
+    int *level = nullptr;  // BFS levels [rcap]
+    int *d_conn = nullptr;
 };
 
 struct Planner {
@@ -533,8 +570,13 @@ struct Planner {
     std::vector<float> best_path;  // [M][D]
     std::vector<double> trace_t, trace_c;
     double trace_t0 = 0.0;
+    bool released = false;  // device state freed (results kept on the host)
     unsigned long long seed = 0;
     int step = 0;
+    int *h_small = nullptr;  // pinned: per robot [new count, connected]
+    float *fine_qa = nullptr, *fine_qb = nullptr;  // path re-check buffers
+    uint8_t *fine_v = nullptr;
+    size_t fine_cap = 0;
     int *d_path = nullptr;
     float *d_pathq = nullptr;
     int *d_len = nullptr;
@@ -578,13 +620,23 @@ static mrpop_status make_fine(mrpop_problem *p, mrpop_problem **out) {
     return mrpop_create_problem(rs.data(), (int)rs.size(), &o, nullptr, nullptr, &c, out);
 }
 
+static void free_device(Planner *pl);
+static mrpop_status planner_init(mrpop_problem *p, Planner **out);
+
 void destroy_planner(Planner *pl) {
     if (!pl) return;
+    free_device(pl);
+    delete pl;
+}
+
+// Frees every device buffer of the planner; host-side results stay.
+static void free_device(Planner *pl) {
     for (auto &r : pl->rm) {
         mrpop_destroy_problem(r.sub);
         cudaFree(r.q); cudaFree(r.adj); cudaFree(r.deg); cudaFree(r.cand); cudaFree(r.gq);
         cudaFree(r.ea_q); cudaFree(r.eb_q); cudaFree(r.cvalid); cudaFree(r.evalid);
         cudaFree(r.nb); cudaFree(r.cnt); cudaFree(r.ea); cudaFree(r.eb);
+        cudaFree(r.level); cudaFree(r.d_conn);
     }
     mrpop_destroy_problem(pl->fine);
     cudaFree(pl->rm_n);
@@ -597,7 +649,50 @@ void destroy_planner(Planner *pl) {
     cudaFree(pl->d_centre); cudaFree(pl->d_axis); cudaFree(pl->ctrl); cudaFree(pl->d_path);
     cudaFree(pl->d_pathq);
     cudaFree(pl->d_len);
-    delete pl;
+    if (pl->h_small) cudaFreeHost(pl->h_small);
+    pl->h_small = nullptr;
+    cudaFree(pl->fine_qa);
+    cudaFree(pl->fine_qb);
+    cudaFree(pl->fine_v);
+    pl->fine_qa = pl->fine_qb = nullptr;
+    pl->fine_v = nullptr;
+    pl->fine_cap = 0;
+    for (auto &r : pl->rm) r = RobotRoadmap{};
+    pl->rm.clear();
+    pl->fine = nullptr;
+    pl->rm_n = nullptr;
+    for (int t = 0; t < 2; ++t) pl->tq[t] = nullptr, pl->tpar[t] = nullptr, pl->trmv[t] = nullptr;
+    pl->tn = nullptr; pl->buf = nullptr; pl->near = pl->conn = nullptr;
+    pl->rmvnew = pl->newidx = nullptr; pl->valid1 = pl->valid2 = nullptr;
+    pl->d_lo = pl->d_hi = pl->d_start = pl->d_goal = pl->d_centre = pl->d_axis = nullptr;
+    pl->ctrl = nullptr; pl->d_path = nullptr; pl->d_pathq = nullptr; pl->d_len = nullptr;
+    pl->released = true;
+}
+
+// (Re)creates the device state of p's planner; results of a released
+// planner (incumbent, path, trace) carry over.
+static mrpop_status ensure_planner(mrpop_problem *p) {
+    if (p->planner && !p->planner->released) return MRPOP_OK;
+    Planner *old = p->planner;
+    p->planner = nullptr;
+    Planner *pl = nullptr;
+    mrpop_status s = planner_init(p, &pl);
+    if (s != MRPOP_OK) {
+        destroy_planner(pl);
+        p->planner = old;
+        return s;
+    }
+    if (old) {
+        pl->c_best = old->c_best;
+        pl->best_path.swap(old->best_path);
+        pl->trace_t.swap(old->trace_t);
+        pl->trace_c.swap(old->trace_c);
+        pl->total_iters = old->total_iters;
+        pl->mode = old->c_best < INFINITY ? 1 : 0;
+        delete old;
+    }
+    p->planner = pl;
+    return MRPOP_OK;
 }
 
 #define PL_TRY(expr)                                       \
@@ -648,6 +743,8 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
         PL_TRY(dalloc(&r.evalid, (size_t)E + 2 * kKmax));
         PL_TRY(dalloc(&r.ea, (size_t)E + 2 * kKmax));
         PL_TRY(dalloc(&r.eb, (size_t)E + 2 * kKmax));
+        PL_TRY(dalloc(&r.level, (size_t)rcap));
+        PL_TRY(dalloc(&r.d_conn, 1));
         // vertices 0 and 1: the robot's start and goal
         for (int d = 0; d < dof; ++d) {
             PL_TRY(cudaMemcpy(r.q + (size_t)d * rcap, &p->start[qoff + d], sizeof(float),
@@ -664,6 +761,7 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
         qoff += dof;
     }
     PL_TRY(dalloc(&pl->rm_n, K));
+    PL_TRY(cudaMallocHost(&pl->h_small, sizeof(int) * 2 * K));
     std::vector<int> twos(K, 2);
     PL_TRY(cudaMemcpy(pl->rm_n, twos.data(), sizeof(int) * K, cudaMemcpyHostToDevice));
     for (int t = 0; t < 2; ++t) {
@@ -732,12 +830,16 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
     return MRPOP_OK;
 }
 
-// One ROADMAP round for robot k (Alg. 2, lines on sampling, neighbours and
-// edge checks), followed by the start-goal connectivity test (BFS).
-static mrpop_status roadmap_round(Planner *pl, int k, cudaStream_t st) {
+// One ROADMAP round for robot k (Alg. 2: sample free configurations, find
+// their neighbours within delta, check the edges, add them), in two phases so
+// that many robots of many problems share two host synchronisations.
+// Phase 1 enqueues sampling, validation and append; the new vertex count
+// lands in pinned memory.
+static mrpop_status rm_phase1(Planner *pl, int k, cudaStream_t st) {
     RobotRoadmap &r = pl->rm[k];
     mrpop_problem *p = pl->p;
     const int dof = p->robots[k].dof, rcap = pl->rcap;
+    pl->h_small[2 * k] = r.n;
     if (r.n >= rcap) return MRPOP_OK;
     const int want = std::min(pl->n_per_round, rcap - r.n);
     const int nc = kOversample * pl->n_per_round;
@@ -750,13 +852,20 @@ static mrpop_status roadmap_round(Planner *pl, int k, cudaStream_t st) {
     PL_TRY(cudaGetLastError());
     ST_TRY(launch_validate(r.sub, r.cand, r.cand, nc, r.cvalid, nullptr, nullptr, nullptr, nullptr,
                            st));
-    int *d_count = pl->rm_n + k;
-    k_rm_append<<<1, 32, 0, st>>>(r.cand, r.cvalid, nc, dof, want, r.q, rcap, d_count);
+    k_rm_append<<<1, 32, 0, st>>>(r.cand, r.cvalid, nc, dof, want, r.q, rcap, pl->rm_n + k);
     PL_TRY(cudaGetLastError());
-    int n_new = 0;
-    PL_TRY(cudaMemcpyAsync(&n_new, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PL_TRY(cudaStreamSynchronize(st));
-    // neighbours of the new vertices (and of start/goal on the first round)
+    PL_TRY(cudaMemcpyAsync(pl->h_small + 2 * k, pl->rm_n + k, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return MRPOP_OK;
+}
+
+// Phase 2 (the new count is known): neighbours of the new vertices (and of
+// start/goal on the first round), edge checks, links, and the start-goal BFS
+// on the device; the connected flag lands in pinned memory.
+static mrpop_status rm_phase2(Planner *pl, int k, cudaStream_t st) {
+    RobotRoadmap &r = pl->rm[k];
+    mrpop_problem *p = pl->p;
+    const int dof = p->robots[k].dof, rcap = pl->rcap;
+    const int n_new = pl->h_small[2 * k];
     const int first = r.n == 2 && n_new > 2 ? 0 : r.n;
     const int m = n_new - first;
     if (m > 0) {
@@ -774,26 +883,9 @@ static mrpop_status roadmap_round(Planner *pl, int k, cudaStream_t st) {
         PL_TRY(cudaGetLastError());
     }
     r.n = n_new;
-    // BFS from vertex 0 (start) to vertex 1 (goal)
-    std::vector<int> deg(n_new), adj((size_t)n_new * kKmax);
-    PL_TRY(cudaMemcpyAsync(deg.data(), r.deg, sizeof(int) * n_new, cudaMemcpyDeviceToHost, st));
-    PL_TRY(cudaMemcpyAsync(adj.data(), r.adj, sizeof(int) * (size_t)n_new * kKmax,
-                           cudaMemcpyDeviceToHost, st));
-    PL_TRY(cudaStreamSynchronize(st));
-    std::vector<char> seen(n_new, 0);
-    std::vector<int> q{0};
-    seen[0] = 1;
-    for (size_t h = 0; h < q.size(); ++h) {
-        const int u = q[h];
-        for (int j = 0; j < std::min(deg[u], kKmax); ++j) {
-            const int v = adj[(size_t)u * kKmax + j];
-            if (v >= 0 && v < n_new && !seen[v]) {
-                seen[v] = 1;
-                q.push_back(v);
-            }
-        }
-    }
-    r.connected = n_new > 1 && seen[1];
+    k_rm_bfs<<<1, 1024, 0, st>>>(r.adj, r.deg, n_new, r.level, r.d_conn);
+    PL_TRY(cudaGetLastError());
+    PL_TRY(cudaMemcpyAsync(pl->h_small + 2 * k + 1, r.d_conn, sizeof(int), cudaMemcpyDeviceToHost, st));
     return MRPOP_OK;
 }
 
@@ -841,21 +933,26 @@ static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, int t
             qa[(size_t)d * M + j] = path[(size_t)j * D + d];
             qb[(size_t)d * M + j] = path[(size_t)(j + 1) * D + d];
         }
-    float *dqa = nullptr, *dqb = nullptr;
-    uint8_t *dv = nullptr;
-    PL_TRY(cudaMalloc(&dqa, sizeof(float) * qa.size()));
-    PL_TRY(cudaMalloc(&dqb, sizeof(float) * qb.size()));
-    PL_TRY(cudaMalloc(&dv, M));
-    PL_TRY(cudaMemcpy(dqa, qa.data(), sizeof(float) * qa.size(), cudaMemcpyHostToDevice));
-    PL_TRY(cudaMemcpy(dqb, qb.data(), sizeof(float) * qb.size(), cudaMemcpyHostToDevice));
-    mrpop_status s = launch_validate(pl->fine, dqa, dqb, M, dv, nullptr, nullptr, nullptr, nullptr, st);
-    std::vector<uint8_t> v(M);
-    if (s == MRPOP_OK) {
-        PL_TRY(cudaMemcpyAsync(v.data(), dv, M, cudaMemcpyDeviceToHost, st));
-        PL_TRY(cudaStreamSynchronize(st));
+    if ((size_t)M > pl->fine_cap) {  // grow-only buffers for the fine re-check
+        cudaFree(pl->fine_qa);
+        cudaFree(pl->fine_qb);
+        cudaFree(pl->fine_v);
+        pl->fine_qa = pl->fine_qb = nullptr;
+        pl->fine_v = nullptr;
+        pl->fine_cap = 0;
+        const size_t cap = std::max<size_t>(256, 2 * (size_t)M);
+        PL_TRY(cudaMalloc(&pl->fine_qa, sizeof(float) * D * cap));
+        PL_TRY(cudaMalloc(&pl->fine_qb, sizeof(float) * D * cap));
+        PL_TRY(cudaMalloc(&pl->fine_v, cap));
+        pl->fine_cap = cap;
     }
-    cudaFree(dqa); cudaFree(dqb); cudaFree(dv);
-    if (s != MRPOP_OK) return s;
+    PL_TRY(cudaMemcpyAsync(pl->fine_qa, qa.data(), sizeof(float) * qa.size(), cudaMemcpyHostToDevice, st));
+    PL_TRY(cudaMemcpyAsync(pl->fine_qb, qb.data(), sizeof(float) * qb.size(), cudaMemcpyHostToDevice, st));
+    std::vector<uint8_t> v(M);
+    ST_TRY(launch_validate(pl->fine, pl->fine_qa, pl->fine_qb, M, pl->fine_v, nullptr, nullptr,
+                           nullptr, nullptr, st));
+    PL_TRY(cudaMemcpyAsync(v.data(), pl->fine_v, M, cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
     for (int j = 0; j < M; ++j)
         if (!v[j]) return MRPOP_OK;  // rejected at the finer resolution
     pl->c_best = cost;
@@ -877,17 +974,50 @@ struct Batch {
     Ctrl *h_ctrl = nullptr;   // pinned
     int spl = 4, warps = 1, bps = 1;
     size_t smem = 0;
+    std::vector<int> slot_warps;  // warps per block that take edges, per slot
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    bool owns = true;  // false: a view over arrays owned by a server
     ~Batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (!owns) return;
         cudaFree(d_slots);
         cudaFree(d_vp);
         cudaFree(d_ctrl);
         if (h_ctrl) cudaFreeHost(h_ctrl);
     }
 };
+
+// One launch configuration for all slots of a validation launch: blocks of
+// up to 4 warps and the shared memory of the most demanding slot; each slot
+// then uses as many of the 4 warps as its per-warp scratch fits into that
+// budget (at least the count it would use alone).
+static mrpop_status batch_config(Batch &bt) {
+    size_t smem = 0;
+    int spl = 1;
+    for (Planner *pl : bt.pls) {
+        const size_t tab = (size_t)pl->p->dev.t.n_f4 * sizeof(float4);
+        smem = std::max(smem, tab + (size_t)pl->vwarps * pl->vp[0].warp_floats * sizeof(float));
+        spl = std::max(spl, pl->p->dev.t.max_spheres_per_link);
+    }
+    bt.slot_warps.assign(bt.pls.size(), 1);
+    int wmax = 1;
+    for (size_t i = 0; i < bt.pls.size(); ++i) {
+        Planner *pl = bt.pls[i];
+        const size_t tab = (size_t)pl->p->dev.t.n_f4 * sizeof(float4);
+        const size_t per = (size_t)pl->vp[0].warp_floats * sizeof(float);
+        int w = (int)std::min<size_t>(4, (smem - tab) / per);
+        w = std::max(w, pl->vwarps);
+        bt.slot_warps[i] = w;
+        wmax = std::max(wmax, w);
+    }
+    bt.warps = wmax;
+    bt.smem = smem;
+    bt.spl = spl;
+    bt.bps = (kStepIters + wmax - 1) / wmax;
+    return MRPOP_OK;
+}
 
 static mrpop_status enqueue_step(Batch &bt, cudaStream_t st) {
     const int n = bt.n;
@@ -913,21 +1043,7 @@ static mrpop_status build_batch(Batch &bt, cudaStream_t st) {
     PL_TRY(cudaMalloc(&bt.d_vp, sizeof(VParams) * 2 * n));
     PL_TRY(cudaMalloc(&bt.d_ctrl, sizeof(Ctrl) * n));
     PL_TRY(cudaMallocHost(&bt.h_ctrl, sizeof(Ctrl) * n));
-    // one launch configuration for every slot: the fewest warps any slot
-    // allows, the largest shared memory and sphere count any slot needs
-    int warps = 4;
-    for (Planner *pl : bt.pls) warps = std::min(warps, pl->vwarps);
-    size_t smem = 0;
-    int spl = 1;
-    for (Planner *pl : bt.pls) {
-        const size_t tab = (size_t)pl->p->dev.t.n_f4 * sizeof(float4);
-        smem = std::max(smem, tab + (size_t)warps * pl->vp[0].warp_floats * sizeof(float));
-        spl = std::max(spl, pl->p->dev.t.max_spheres_per_link);
-    }
-    bt.warps = warps;
-    bt.smem = smem;
-    bt.spl = spl;
-    bt.bps = (kStepIters + warps - 1) / warps;
+    ST_TRY(batch_config(bt));
     std::vector<Slot> slots(n);
     std::vector<VParams> vps(2 * n);
     for (int i = 0; i < n; ++i) {
@@ -936,7 +1052,8 @@ static mrpop_status build_batch(Batch &bt, cudaStream_t st) {
         slots[i].ctrl = bt.d_ctrl + i;
         for (int k = 0; k < 2; ++k) {
             vps[(size_t)k * n + i] = pl->vp[k];
-            vps[(size_t)k * n + i].total_warps = bt.bps * warps;
+            vps[(size_t)k * n + i].warps = bt.slot_warps[i];
+            vps[(size_t)k * n + i].total_warps = bt.bps * bt.slot_warps[i];
         }
     }
     PL_TRY(cudaMemcpy(bt.d_slots, slots.data(), sizeof(Slot) * n, cudaMemcpyHostToDevice));
@@ -961,11 +1078,120 @@ static mrpop_status build_batch(Batch &bt, cudaStream_t st) {
     return MRPOP_OK;
 }
 
+// A target is reached by an actual solution only (a target of +inf means
+// "the first solution").
+static inline bool reached_target(double c_best, double target) {
+    return c_best < INFINITY && c_best <= target;
+}
+
 struct SlotRun {
     bool active = false, need_roadmap = true, reset_trees = true, reached = false;
     double target = -INFINITY;
     mrpop_status status = MRPOP_OK;
 };
+
+// Part of one outer iteration before the step: one ROADMAP round (Alg. 2) for
+// every listed slot that needs one, all robots of all those slots sharing two
+// host synchronisations; a slot whose robots all connect start and goal
+// rejoins the search, its trees restarted from the roots for AO-X.
+static mrpop_status roadmap_rounds(const std::vector<Planner *> &pls, std::vector<SlotRun *> &runs,
+                                   const Slot *d_slots, cudaStream_t st) {
+    std::vector<int> todo;
+    for (size_t i = 0; i < pls.size(); ++i)
+        if (runs[i]->active && runs[i]->need_roadmap) todo.push_back((int)i);
+    if (todo.empty()) return MRPOP_OK;
+    for (int i : todo)
+        for (int k = 0; k < pls[i]->K; ++k) ST_TRY(rm_phase1(pls[i], k, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    for (int i : todo)
+        for (int k = 0; k < pls[i]->K; ++k) ST_TRY(rm_phase2(pls[i], k, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    for (int i : todo) {
+        Planner *pl = pls[i];
+        SlotRun &run = *runs[i];
+        bool all = true;
+        for (int k = 0; k < pl->K; ++k) {
+            pl->rm[k].connected = pl->h_small[2 * k + 1] != 0;
+            all = all && pl->rm[k].connected;
+        }
+        ++pl->step;
+        if (!all) continue;
+        pl->roadmap_ready = true;
+        run.need_roadmap = false;
+        pl->iters_in_call = 0;
+        if (pl->mode == 1 || run.reset_trees) {
+            k_tree_reset<<<1, 64, 0, st>>>(d_slots + i);
+            PL_TRY(cudaGetLastError());
+            run.reset_trees = false;
+        }
+    }
+    return MRPOP_OK;
+}
+
+static void slot_ctrl(Planner *pl, const SlotRun &run, Ctrl &c) {
+    c = Ctrl{};
+    c.c_best = pl->c_best < INFINITY ? (float)pl->c_best : INFINITY;
+    c.mode = run.active && !run.need_roadmap ? pl->mode : 2;
+    c.step = pl->step++;
+    c.seed = pl->seed;
+    c.best_key = ~0ull;
+}
+
+// Per-slot part after the step: incumbent candidates and Alg. 1 transitions.
+static mrpop_status slot_after(Planner *pl, SlotRun &run, const Ctrl &r, const Slot *d_slot,
+                               cudaStream_t st, double t_rel) {
+    if (!run.active || run.need_roadmap) return MRPOP_OK;
+    pl->iters_in_call += kStepIters;
+    pl->total_iters += kStepIters;
+    bool accepted = false;
+    if (r.best_key != ~0ull)
+        ST_TRY(try_incumbent(pl, d_slot, (int)(r.best_key & 0xffffffffu), r.tree_a, st, t_rel,
+                             &accepted));
+    const long long max_iters = std::max<long long>(kStepIters, pl->p->cfg.max_iters);
+    if (accepted) {
+        pl->mode = 1;             // from now on: AO-X
+        run.need_roadmap = true;  // Alg. 1: grow the roadmap, optimise again
+        if (reached_target(pl->c_best, run.target)) {
+            run.active = false;
+            run.reached = true;
+        }
+    } else if (pl->iters_in_call >= max_iters || r.overflow) {
+        run.need_roadmap = true;  // iteration cap: grow the roadmap (c14)
+        if (r.overflow) run.reset_trees = true;
+    }
+    return MRPOP_OK;
+}
+
+static mrpop_status check_endpoints(const std::vector<Planner *> &pls, std::vector<SlotRun> &run,
+                                    cudaStream_t st) {
+    const int n = (int)pls.size();
+    uint8_t *dv = nullptr;
+    PL_TRY(cudaMalloc(&dv, 2 * (size_t)n));
+    std::vector<uint8_t> sv(2 * (size_t)n);
+    mrpop_status s = MRPOP_OK;
+    for (int i = 0; i < n && s == MRPOP_OK; ++i) {
+        Planner *pl = pls[i];
+        s = launch_validate(pl->p, pl->d_start, pl->d_start, 1, dv + 2 * i, nullptr, nullptr,
+                            nullptr, nullptr, st);
+        if (s == MRPOP_OK)
+            s = launch_validate(pl->p, pl->d_goal, pl->d_goal, 1, dv + 2 * i + 1, nullptr, nullptr,
+                                nullptr, nullptr, st);
+    }
+    cudaError_t e = cudaMemcpyAsync(sv.data(), dv, 2 * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dv);
+    if (s != MRPOP_OK) return s;
+    PL_TRY(e);
+    for (int i = 0; i < n; ++i) {
+        run[i].active = sv[2 * i] && sv[2 * i + 1];
+        if (!run[i].active) run[i].status = MRPOP_EINVAL;
+        if (reached_target(pls[i]->c_best, run[i].target)) {
+            run[i].active = false;
+            run[i].reached = true;
+        }
+    }
+    return MRPOP_OK;
+}
 
 // Runs Alg. 1 on every problem of ps at once until the budget ends or every
 // problem reached its target cost.
@@ -981,104 +1207,248 @@ static mrpop_status plan_batch(mrpop_problem *const *ps, int n, double budget, i
     Batch bt;
     bt.n = n;
     std::vector<SlotRun> run(n);
-    uint8_t *dv = nullptr;
-    PL_TRY(cudaMalloc(&dv, 2 * (size_t)n));
-    struct FreeV {
-        uint8_t *p;
-        ~FreeV() { cudaFree(p); }
-    } fv{dv};
     for (int i = 0; i < n; ++i) {
         mrpop_problem *p = ps[i];
-        if (!p->planner) ST_TRY(planner_init(p, &p->planner));
-        Planner *pl = p->planner;
-        bt.pls.push_back(pl);
-        ST_TRY(launch_validate(p, pl->d_start, pl->d_start, 1, dv + 2 * i, nullptr, nullptr, nullptr,
-                               nullptr, st));
-        ST_TRY(launch_validate(p, pl->d_goal, pl->d_goal, 1, dv + 2 * i + 1, nullptr, nullptr,
-                               nullptr, nullptr, st));
+        ST_TRY(ensure_planner(p));
+        bt.pls.push_back(p->planner);
         run[i].target = targets ? targets[i] : -INFINITY;
-        run[i].reset_trees = !pl->roadmap_ready;
-        pl->trace_t0 = t0;
+        run[i].reset_trees = !p->planner->roadmap_ready;
     }
-    std::vector<uint8_t> sv(2 * (size_t)n);
-    PL_TRY(cudaMemcpyAsync(sv.data(), dv, 2 * (size_t)n, cudaMemcpyDeviceToHost, st));
-    PL_TRY(cudaStreamSynchronize(st));
-    for (int i = 0; i < n; ++i) {
-        run[i].active = sv[2 * i] && sv[2 * i + 1];
-        if (!run[i].active) run[i].status = MRPOP_EINVAL;
-        if (bt.pls[i]->c_best <= run[i].target) {
-            run[i].active = false;
-            run[i].reached = true;
-        }
-    }
+    ST_TRY(check_endpoints(bt.pls, run, st));
     ST_TRY(build_batch(bt, st));
     for (int64_t outer = 0; now_s() - t0 < budget && (max_steps <= 0 || outer < max_steps); ++outer) {
         bool any = false;
+        std::vector<SlotRun *> rp;
         for (int i = 0; i < n; ++i) {
-            if (!run[i].active) continue;
-            any = true;
-            Planner *pl = bt.pls[i];
-            if (!run[i].need_roadmap) continue;
-            // ROADMAP round (Alg. 2); the slot rejoins the search steps once
-            // every robot connects its start and goal
-            bool all = true;
-            for (int k = 0; k < pl->K; ++k) {
-                ST_TRY(roadmap_round(pl, k, st));
-                all = all && pl->rm[k].connected;
-            }
-            ++pl->step;
-            if (!all) continue;
-            pl->roadmap_ready = true;
-            run[i].need_roadmap = false;
-            pl->iters_in_call = 0;
-            if (pl->mode == 1 || run[i].reset_trees) {
-                k_tree_reset<<<1, 64, 0, st>>>(bt.d_slots + i);
-                PL_TRY(cudaGetLastError());
-                run[i].reset_trees = false;
-            }
+            any = any || run[i].active;
+            rp.push_back(&run[i]);
         }
         if (!any) break;
-        for (int i = 0; i < n; ++i) {
-            Planner *pl = bt.pls[i];
-            Ctrl &c = bt.h_ctrl[i];
-            c = Ctrl{};
-            c.c_best = pl->c_best < INFINITY ? (float)pl->c_best : INFINITY;
-            c.mode = run[i].active && !run[i].need_roadmap ? pl->mode : 2;
-            c.step = pl->step++;
-            c.seed = pl->seed;
-            c.best_key = ~0ull;
-        }
+        ST_TRY(roadmap_rounds(bt.pls, rp, bt.d_slots, st));
+        for (int i = 0; i < n; ++i) slot_ctrl(bt.pls[i], run[i], bt.h_ctrl[i]);
         PL_TRY(cudaMemcpyAsync(bt.d_ctrl, bt.h_ctrl, sizeof(Ctrl) * n, cudaMemcpyHostToDevice, st));
         PL_TRY(cudaGraphLaunch(bt.exec, st));
         PL_TRY(cudaMemcpyAsync(bt.h_ctrl, bt.d_ctrl, sizeof(Ctrl) * n, cudaMemcpyDeviceToHost, st));
         PL_TRY(cudaStreamSynchronize(st));
-        for (int i = 0; i < n; ++i) {
-            if (!run[i].active || run[i].need_roadmap) continue;
-            Planner *pl = bt.pls[i];
-            const Ctrl r = bt.h_ctrl[i];
-            pl->iters_in_call += kStepIters;
-            pl->total_iters += kStepIters;
-            bool accepted = false;
-            if (r.best_key != ~0ull)
-                ST_TRY(try_incumbent(pl, bt.d_slots + i, (int)(r.best_key & 0xffffffffu), r.tree_a,
-                                     st, now_s() - t0, &accepted));
-            const long long max_iters = std::max<long long>(kStepIters, pl->p->cfg.max_iters);
-            if (accepted) {
-                pl->mode = 1;                 // from now on: AO-X
-                run[i].need_roadmap = true;   // Alg. 1: grow the roadmap, optimise again
-                if (pl->c_best <= run[i].target) {
-                    run[i].active = false;
-                    run[i].reached = true;
-                }
-            } else if (pl->iters_in_call >= max_iters || r.overflow) {
-                run[i].need_roadmap = true;   // iteration cap: grow the roadmap (c14)
-                if (r.overflow) run[i].reset_trees = true;
-            }
-        }
+        for (int i = 0; i < n; ++i)
+            ST_TRY(slot_after(bt.pls[i], run[i], bt.h_ctrl[i], bt.d_slots + i, st, now_s() - t0));
     }
     if (statuses)
         for (int i = 0; i < n; ++i) statuses[i] = run[i].status;
     return MRPOP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching.  A server thread keeps up to max_slots
+// requests on the device and advances all of them by one planner iteration
+// per loop (the same per-slot logic as mrpop_plan_batch, direct launches
+// instead of a graph because membership changes between iterations).  Queued
+// requests are admitted in arrival order when a slot and enough device memory
+// are free; a finished request releases its device state at once.
+// ---------------------------------------------------------------------------
+static size_t planner_bytes(const mrpop_problem *p) {
+    const int K = p->dev.t.K, D = p->D;
+    const size_t rcap = (size_t)std::max<int64_t>(64, std::min<int64_t>(p->cfg.roadmap_cap, 1 << 20));
+    const size_t tcap = (size_t)std::max<int64_t>(1024, std::min<int64_t>(p->cfg.tree_cap, 1 << 22));
+    const size_t npr = (size_t)std::max(1, std::min(p->cfg.n_per_round, 4096));
+    size_t b = 2 * ((size_t)D + 3 + K) * tcap * 4;            // trees
+    b += ((size_t)2 * tcap + 2) * ((size_t)D + 1) * 4;         // path extraction
+    b += ((size_t)4 * D + 8 + K) * kStepIters * 8;             // step buffers
+    for (const HostRobot &r : p->robots) {
+        b += rcap * ((size_t)r.dof + kKmax + 1) * 4;           // roadmap
+        b += npr * ((size_t)r.dof * (kOversample + 1) + (size_t)kKmax * (2 * r.dof + 12)) * 4;
+    }
+    b += (size_t)p->dev.t.n_f4 * 16 * (K + 2) + (1 << 16);     // sub-problem tables
+    return b;
+}
+
+struct Request {
+    int64_t ticket = 0;
+    mrpop_problem *p = nullptr;
+    double budget = 0.0, target = -INFINITY;
+    int64_t max_steps = 0, steps = 0;
+    double t_submit = 0.0, t_admit = -1.0, t_first = -1.0, t_target = -1.0, t_done = -1.0;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    mrpop_status status = MRPOP_OK;
+    SlotRun run;
+    size_t mem = 0;
+};
+
+}  // namespace mrpop
+
+struct mrpop_server {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<mrpop::Request *> queue;
+    std::vector<mrpop::Request *> active;  // server thread only
+    std::map<int64_t, std::unique_ptr<mrpop::Request>> all;
+    int max_slots = 64;
+    size_t mem_budget = 0, mem_used = 0;
+    int device = 0;
+    bool stop = false;
+    int64_t next_ticket = 1;
+    double t0 = 0.0;
+    mrpop_status fatal = MRPOP_OK;
+    int64_t admitted = 0, completed = 0, peak_active = 0;
+    size_t peak_mem = 0;
+    mrpop::Slot *d_slots = nullptr;
+    mrpop::VParams *d_vp = nullptr;
+    mrpop::Ctrl *d_ctrl = nullptr, *h_ctrl = nullptr;
+    std::thread th;
+};
+
+namespace mrpop {
+
+static mrpop_status server_rebuild(mrpop_server *sv, Batch &bt, cudaStream_t st) {
+    const int n = (int)sv->active.size();
+    bt.n = n;
+    bt.pls.clear();
+    if (n == 0) return MRPOP_OK;
+    for (Request *r : sv->active) bt.pls.push_back(r->p->planner);
+    ST_TRY(batch_config(bt));
+    std::vector<Slot> slots(n);
+    std::vector<VParams> vps(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        slots[i] = bt.pls[i]->slot;
+        slots[i].ctrl = sv->d_ctrl + i;
+        for (int k = 0; k < 2; ++k) {
+            vps[(size_t)k * n + i] = bt.pls[i]->vp[k];
+            vps[(size_t)k * n + i].warps = bt.slot_warps[i];
+            vps[(size_t)k * n + i].total_warps = bt.bps * bt.slot_warps[i];
+        }
+    }
+    // (the previous iteration's work on these arrays has completed: every
+    // iteration ends with a stream synchronisation)
+    PL_TRY(cudaMemcpyAsync(sv->d_slots, slots.data(), sizeof(Slot) * n, cudaMemcpyHostToDevice, st));
+    PL_TRY(cudaMemcpyAsync(sv->d_vp, vps.data(), sizeof(VParams) * 2 * n, cudaMemcpyHostToDevice, st));
+    bt.d_vp = sv->d_vp;
+    return MRPOP_OK;
+}
+
+static void server_finish(mrpop_server *sv, Request *r, double now) {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    r->state = 2;
+    r->t_done = now - r->t_submit;
+    if (r->p->planner) free_device(r->p->planner);
+    sv->mem_used -= r->mem;
+    ++sv->completed;
+}
+
+static void server_loop(mrpop_server *sv) {
+    cudaSetDevice(sv->device);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->fatal = MRPOP_ECUDA;
+        return;
+    }
+    Batch bt;
+    bt.owns = false;
+    bt.d_slots = sv->d_slots;
+    bt.d_ctrl = sv->d_ctrl;
+    bt.h_ctrl = sv->h_ctrl;
+    bool changed = true;
+    auto fail = [&](mrpop_status s) {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->fatal = s;
+    };
+    for (;;) {
+        std::vector<Request *> admit;
+        {
+            std::unique_lock<std::mutex> lock(sv->mu);
+            if (sv->stop) break;
+            while ((int)(sv->active.size() + admit.size()) < sv->max_slots && !sv->queue.empty()) {
+                Request *r = sv->queue.front();
+                const size_t need = planner_bytes(r->p);
+                // memory admission: wait for room unless nothing else runs
+                if (sv->mem_used + need > sv->mem_budget && !(sv->active.empty() && admit.empty()))
+                    break;
+                sv->queue.pop_front();
+                r->mem = need;
+                sv->mem_used += need;
+                sv->peak_mem = std::max(sv->peak_mem, sv->mem_used);
+                admit.push_back(r);
+            }
+            if (sv->active.empty() && admit.empty()) {
+                sv->cv.wait_for(lock, std::chrono::milliseconds(2));
+                continue;
+            }
+        }
+        for (Request *r : admit) {
+            mrpop_status s = ensure_planner(r->p);
+            std::vector<Planner *> one{r->p->planner};
+            std::vector<SlotRun> run(1);
+            run[0].target = r->target;
+            run[0].reset_trees = s == MRPOP_OK && !r->p->planner->roadmap_ready;
+            if (s == MRPOP_OK) s = check_endpoints(one, run, st);
+            if (s == MRPOP_OK) s = run[0].status;
+            const double now = now_s();
+            if (s != MRPOP_OK || !run[0].active) {
+                r->status = s;
+                server_finish(sv, r, now);
+                continue;
+            }
+            r->run = run[0];
+            r->t_admit = now - r->t_submit;
+            r->p->planner->trace_t0 = now;
+            {
+                std::lock_guard<std::mutex> lock(sv->mu);
+                r->state = 1;
+                ++sv->admitted;
+            }
+            sv->active.push_back(r);
+            changed = true;
+        }
+        sv->peak_active = std::max<int64_t>(sv->peak_active, (int64_t)sv->active.size());
+        if (sv->active.empty()) continue;
+        if (changed) {
+            mrpop_status s = server_rebuild(sv, bt, st);
+            if (s != MRPOP_OK) return fail(s);
+            changed = false;
+        }
+        const int n = bt.n;
+        std::vector<SlotRun *> rp;
+        for (Request *r : sv->active) rp.push_back(&r->run);
+        mrpop_status s = roadmap_rounds(bt.pls, rp, bt.d_slots, st);
+        for (int i = 0; i < n; ++i) slot_ctrl(bt.pls[i], sv->active[i]->run, bt.h_ctrl[i]);
+        cudaError_t e = cudaSuccess;
+        if (s == MRPOP_OK)
+            e = cudaMemcpyAsync(bt.d_ctrl, bt.h_ctrl, sizeof(Ctrl) * n, cudaMemcpyHostToDevice, st);
+        if (s == MRPOP_OK && e == cudaSuccess) s = enqueue_step(bt, st);
+        if (s == MRPOP_OK && e == cudaSuccess)
+            e = cudaMemcpyAsync(bt.h_ctrl, bt.d_ctrl, sizeof(Ctrl) * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(cuda_error(e, "server step"));
+        if (s != MRPOP_OK) return fail(s);
+        const double now = now_s();
+        std::vector<Request *> keep;
+        for (int i = 0; i < n; ++i) {
+            Request *r = sv->active[i];
+            Planner *pl = bt.pls[i];
+            s = slot_after(pl, r->run, bt.h_ctrl[i], bt.d_slots + i, st, now - pl->trace_t0);
+            if (s != MRPOP_OK) return fail(s);
+            ++r->steps;
+            const double t = now - r->t_submit;
+            if (r->t_first < 0 && !pl->trace_c.empty()) r->t_first = t;
+            if (r->t_target < 0 && reached_target(pl->c_best, r->target)) r->t_target = t;
+            const bool done = r->run.reached || !r->run.active ||
+                              now - (r->t_submit + r->t_admit) >= r->budget ||
+                              (r->max_steps > 0 && r->steps >= r->max_steps);
+            if (done) {
+                server_finish(sv, r, now);
+                changed = true;
+            } else {
+                keep.push_back(r);
+            }
+        }
+        sv->active.swap(keep);
+    }
+    // shutdown: running requests end now
+    const double now = now_s();
+    for (Request *r : sv->active) server_finish(sv, r, now);
+    sv->active.clear();
+    cudaStreamDestroy(st);
 }
 
 }  // namespace mrpop
@@ -1146,5 +1516,109 @@ extern "C" mrpop_status mrpop_plan_trace(const mrpop_problem *p, double *times, 
         if (times) times[i] = pl->trace_t[i];
         if (costs) costs[i] = pl->trace_c[i];
     }
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_create(int32_t max_slots, int64_t device_mem_budget,
+                                            mrpop_server **out) {
+    if (!out) return set_error(MRPOP_EINVAL, "mrpop_server_create: out is NULL");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 4096)
+        return set_error(MRPOP_EINVAL, "mrpop_server_create: max_slots=%d outside [1, 4096]", max_slots);
+    mrpop_server *sv = new (std::nothrow) mrpop_server();
+    if (!sv) return set_error(MRPOP_ENOMEM, "host allocation failed");
+    sv->max_slots = max_slots;
+    cudaError_t e = cudaGetDevice(&sv->device);
+    size_t fr = 0, tot = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_slots, sizeof(Slot) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_vp, sizeof(VParams) * 2 * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_ctrl, sizeof(Ctrl) * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&sv->h_ctrl, sizeof(Ctrl) * max_slots);
+    if (e != cudaSuccess) {
+        mrpop_status s = cuda_error(e, "mrpop_server_create");
+        cudaFree(sv->d_slots); cudaFree(sv->d_vp); cudaFree(sv->d_ctrl);
+        if (sv->h_ctrl) cudaFreeHost(sv->h_ctrl);
+        delete sv;
+        return s;
+    }
+    sv->mem_budget = device_mem_budget > 0 ? (size_t)device_mem_budget : (size_t)(0.8 * (double)fr);
+    sv->t0 = now_s();
+    sv->th = std::thread(server_loop, sv);
+    *out = sv;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_submit(mrpop_server *sv, mrpop_problem *p, double budget_s,
+                                            int64_t max_steps, double target_cost,
+                                            int64_t *ticket) {
+    if (!sv || !p) return set_error(MRPOP_EINVAL, "mrpop_server_submit: NULL argument");
+    if (!(budget_s >= 0.0)) return set_error(MRPOP_EINVAL, "mrpop_server_submit: negative budget");
+    if (p->start.empty() || p->goal.empty())
+        return set_error(MRPOP_EINVAL, "mrpop_server_submit: problem has no start/goal");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (sv->fatal != MRPOP_OK) return set_error(sv->fatal, "mrpop_server_submit: server stopped on an error");
+    for (auto &kv : sv->all)
+        if (kv.second->p == p && kv.second->state != 2)
+            return set_error(MRPOP_EBUSY, "mrpop_server_submit: problem already queued or running");
+    auto r = std::make_unique<Request>();
+    r->ticket = sv->next_ticket++;
+    r->p = p;
+    r->budget = budget_s;
+    r->max_steps = max_steps;
+    r->target = std::isnan(target_cost) ? -INFINITY : target_cost;
+    r->t_submit = now_s();
+    if (ticket) *ticket = r->ticket;
+    sv->queue.push_back(r.get());
+    sv->all[r->ticket] = std::move(r);
+    sv->cv.notify_one();
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_poll(mrpop_server *sv, int64_t ticket, int32_t *state,
+                                          double *times, double *cost) {
+    if (!sv) return set_error(MRPOP_EINVAL, "mrpop_server_poll: server is NULL");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return set_error(MRPOP_EINVAL, "mrpop_server_poll: unknown ticket");
+    const Request &r = *it->second;
+    if (state) *state = r.state;
+    if (times) {
+        times[0] = r.t_admit;
+        times[1] = r.t_first;
+        times[2] = r.t_target;
+        times[3] = r.t_done;
+    }
+    if (cost) *cost = (r.state == 2 && r.p->planner) ? r.p->planner->c_best : INFINITY;
+    if (r.state == 2 && r.status != MRPOP_OK) return set_error(r.status, "request failed");
+    if (sv->fatal != MRPOP_OK) return set_error(sv->fatal, "server stopped on an error");
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_stats(mrpop_server *sv, int64_t *stats) {
+    if (!sv || !stats) return set_error(MRPOP_EINVAL, "mrpop_server_stats: NULL argument");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    stats[0] = sv->admitted;
+    stats[1] = sv->completed;
+    stats[2] = sv->peak_active;
+    stats[3] = (int64_t)sv->peak_mem;
+    stats[4] = (int64_t)sv->mem_budget;
+    stats[5] = (int64_t)sv->queue.size();
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_destroy(mrpop_server *sv) {
+    if (!sv) return MRPOP_OK;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+        sv->cv.notify_all();
+    }
+    if (sv->th.joinable()) sv->th.join();
+    cudaFree(sv->d_slots);
+    cudaFree(sv->d_vp);
+    cudaFree(sv->d_ctrl);
+    if (sv->h_ctrl) cudaFreeHost(sv->h_ctrl);
+    delete sv;
     return MRPOP_OK;
 }

@@ -148,6 +148,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
 
     for (int i = threadIdx.x; i < P.t.n_f4; i += blockDim.x) tab[i] = P.blob[i];
     __syncthreads();
+    if (warp >= P.warps) return;  // spare warps of a shared multi-problem launch
 
     const Tables &t = P.t;
     const int K = t.K, D = t.L, NS = t.NS, NC = t.NC;
@@ -561,6 +562,7 @@ mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
     const int64_t want = (V.E + warps - 1) / warps;
     const int grid = (int)std::min<int64_t>((int64_t)p->num_sms * bps, want);
     V.total_warps = grid * warps;
+    V.warps = warps;
     kern<<<grid, warps * 32, smem, st>>>(V);
     MRPOP_CUDA_TRY(cudaGetLastError());
     return MRPOP_OK;
@@ -675,6 +677,7 @@ mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, in
         return set_error(MRPOP_EINVAL, "problem too large for the validation kernel's shared memory");
     *smem_out = smem;
     *warps_out = warps;
+    V->warps = warps;
     return MRPOP_OK;
 }
 

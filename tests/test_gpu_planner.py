@@ -174,7 +174,12 @@ def test_plan_batch_alone_equals_mix(mp, orc):
     alone = mp.plan_result(a)
     a.close()
     a2, *_ = _planar_problem(mp, orc, 2)
-    others = [_planar_problem(mp, orc, s)[0] for s in (0, 3)]
+    # partners of another size (14-DOF, other tables) change the shared launch
+    # configuration of the batch, not the result
+    table = synth.table_pair_scene(0)
+    tqs, tqg, _ = _start_goal(orc, table, 5, check=False)
+    big = mp.Problem(table, resolution=RES, margin=1e-4, delta=2.5, seed=1, start=tqs, goal=tqg)
+    others = [_planar_problem(mp, orc, 0)[0], big]
     mp.plan_batch([others[0], a2, others[1]], 60.0, max_steps=steps)
     mixed = mp.plan_result(a2)
     assert alone[0] is not None
