@@ -336,7 +336,71 @@ def run_planner_leg(mp, synth):
                   "first_solutions": len(ttfs)}
     if res["plain"]["problems_per_s"] > 0:
         res["batched_over_plain"] = res["batched"]["problems_per_s"] / res["plain"]["problems_per_s"]
-    return res
+    return res, entries, best
+
+
+SERVE_RATE = 100.0
+SERVE_REQUESTS = 48
+
+
+def run_serving_leg(mp, synth, entries, best):
+    """Poisson stream of planning requests (the planner leg's problems, cycled)
+    into the continuous-batching server.  Each request ends at 1.1x its
+    problem's best known cost or after the planner budget.  Reports p50/p99
+    time to first solution and to the target, and completed requests/s."""
+    import numpy as np
+    arrivals = synth.poisson_arrivals(SERVE_RATE, SERVE_REQUESTS, seed=7)
+    reqs = []
+    with mp.Server(max_slots=64) as srv:
+        t0 = time.perf_counter()
+        for k, ta in enumerate(arrivals):
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.0005)
+            j = k % len(entries)
+            idx, sc, qs, qg = entries[j]
+            p = mp.Problem(sc, resolution=RES, margin=MARGIN, delta=PLAN_DELTA, n_per_round=64,
+                           tree_cap=1 << 15, roadmap_cap=1 << 13, max_iters=4096, seed=idx,
+                           start=qs, goal=qg)
+            tgt = 1.1 * best[j] if np.isfinite(best[j]) else float("inf")
+            reqs.append((p, srv.submit(p, PLAN_BUDGET_S, target_cost=tgt)))
+        done = {}
+        while len(done) < len(reqs):
+            for p, t in reqs:
+                if t not in done:
+                    st, times, _ = srv.poll(t)
+                    if st == 2:
+                        done[t] = times
+            time.sleep(0.002)
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+    for p, _ in reqs:
+        p.close()
+    tt = np.array([done[t] for _, t in reqs])
+    first = tt[:, 1][tt[:, 1] >= 0]
+    target = tt[:, 2][tt[:, 2] >= 0]
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    return {"rate_per_s": SERVE_RATE, "requests": len(reqs), "wall_s": wall,
+            "completed_per_s": len(reqs) / wall, "ttfs_p50_s": pct(first, 50),
+            "ttfs_p99_s": pct(first, 99), "to_1.1x_best_p50_s": pct(target, 50),
+            "to_1.1x_best_p99_s": pct(target, 99), "reached_1.1x_best": int(len(target)),
+            "first_solutions": int(len(first)), "peak_concurrent": stats["peak_active"]}
+
+
+def profiled_traffic(kernel_file: str, name: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    profiles/<name>.txt, when that summary was taken on the current source of
+    kernel_file (its sha256 is recorded there); None otherwise."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name + ".txt")
+    try:
+        rec = dict(l.split(":", 1) for l in open(path) if ":" in l and not l.startswith("#"))
+        src = os.path.join(ROOT, "paper_2609_30644_gb300", "csrc", kernel_file)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256", "").strip() != sha:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def measured_peaks():
@@ -373,10 +437,8 @@ def run_ours(args) -> None:
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    from paper_2609_30644_gb300 import replicas
+    dist = replicas.init("nccl", dev)   # replicas: no collective on the data path
 
     scene, x = make_inputs(rank)
     prob = mp.Problem(scene, resolution=RES, margin=MARGIN)
@@ -404,7 +466,9 @@ def run_ours(args) -> None:
             ev[4].record(stream)
         return idx, cnt
 
-    # algorithmic work of the validation launch on this batch (untimed)
+    # launch shape from the autotuner, then the algorithmic work of the
+    # validation launch on this batch (both untimed)
+    tuned = mp.autotune(prob, g["qa"], g["qb"])
     counters = mp.validate_work(prob, g["qa"], g["qb"]).cpu().numpy()
     flops_per_launch = algorithmic_flops(counters)
 
@@ -418,8 +482,7 @@ def run_ours(args) -> None:
     except Exception:
         pass
     clocks = ClockSampler(uuid)
-    if dist is not None:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     clocks.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -429,8 +492,7 @@ def run_ours(args) -> None:
         step(g, evs[i])
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
-    if dist is not None:
-        dist.barrier()
+    replicas.barrier(dist)
     clk = clocks.stop()
 
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
@@ -438,11 +500,7 @@ def run_ours(args) -> None:
     nn_ms = [e[1].elapsed_time(e[2]) for e in evs]
     rm_ms = [e[2].elapsed_time(e[3]) for e in evs]
     pc_ms = [e[3].elapsed_time(e[4]) for e in evs]
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(dist, float(sum(step_ms)), dev)
     ms_per_step = total_ms / args.steps
     value = world * E_EDGES / (ms_per_step / 1000.0)
 
@@ -480,20 +538,17 @@ def run_ours(args) -> None:
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_total = float(sum(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = replicas.max_over_ranks(dist, float(sum(e2e_ms)), dev)
     e2e_value = world * E_EDGES / (e2e_total / args.steps / 1000.0)
 
     # sanity: the e2e results equal the resident-input results
     assert torch.equal(h_valid, valid.cpu())
 
-    planner = None
+    planner = serving = None
     if rank == 0 and not args.no_planner:
         from paper_2609_30644_gb300 import synth as _synth
-        planner = run_planner_leg(mp, _synth)
+        planner, entries, best = run_planner_leg(mp, _synth)
+        serving = run_serving_leg(mp, _synth, entries, best)
 
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
@@ -502,6 +557,10 @@ def run_ours(args) -> None:
         peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
         val_avg_s = statistics.mean(val_ms) / 1000.0
         achieved = flops_per_launch / val_avg_s / 1e12
+        # NEAREST by definition: D subtractions and D fused multiply-adds per
+        # (query, vertex) pair (3 D flops); the filter of the candidates is extra
+        nn_flops = float(NN_QUERIES) * NN_TREE * 3 * scene.D
+        nn_achieved = nn_flops / (statistics.mean(nn_ms) / 1000.0) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -512,13 +571,24 @@ def run_ours(args) -> None:
                        "margin_m": MARGIN, "nearest": f"{NN_QUERIES} queries x {NN_TREE} vertices",
                        "neighbors": f"{RM_QUERIES} queries x {RM_VERTS} vertices, 7-DOF",
                        "path_vertices": PATH_M, "l2": "flushed between steps (256 MB write)",
+                       "validate_launch": {"warps_per_block": tuned[0],
+                                           "order": ["strided", "contiguous"][tuned[1]],
+                                           "autotune_ms": tuned[2]},
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "alu", "kernel": "validate_kernel",
-                         "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "traffic": None,
+            "roofline": {"bound": "alu", "kernel": "nearest_qpt_kernel<14>",
+                         "achieved": nn_achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": nn_achieved / peak_tflops,
+                         "traffic": profiled_traffic("nearest.cu", "nearest_qpt_kernel_table_pair"),
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x "
-                                        f"2 flop x {sm_max:.0f} MHz",
-                         "flops_per_launch": flops_per_launch},
+                                        f"2 flop x {sm_max:.0f} MHz (of derived peak)",
+                         "flops_per_launch": nn_flops,
+                         "share_of_step": statistics.mean(nn_ms) / ms_per_step},
+            "roofline_validate": {"bound": "alu", "kernel": "validate_kernel",
+                                  "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                                  "frac": achieved / peak_tflops,
+                                  "traffic": profiled_traffic("validate.cu", "validate_kernel_table_pair"),
+                                  "flops_per_launch": flops_per_launch,
+                                  "share_of_step": statistics.mean(val_ms) / ms_per_step},
             "kernel_ms": {"validate": statistics.mean(val_ms), "nearest": statistics.mean(nn_ms),
                           "neighbors": statistics.mean(rm_ms), "path_cost": statistics.mean(pc_ms)},
             "valid_fraction": float(valid.float().mean().item()),
@@ -531,6 +601,7 @@ def run_ours(args) -> None:
             "gpu_launches": 5 * args.steps,   # validate, nearest, neighbors, path cost (2)
             "cpu_baseline": cpu,
             "planner": planner,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     prob.close()

@@ -183,6 +183,25 @@ mrpop_status mrpop_edge_clearance(mrpop_problem *p, const float *qa, const float
 mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, const float *qb,
                                  int64_t n_edges, int64_t *counters, void *cuda_stream);
 
+/* Autotuner of the validation launch (the batching pattern's tuned launch
+ * shape; the paper fixes its own launch for its GPU).  Times
+ * mrpop_validate_edges on the caller's edges (device SoA [D][n_edges], n_edges
+ * > 0; verdicts written to valid) for every candidate that fits: warps per
+ * block 1, 2 or 4, checkpoints strided across the edge (order 0: every tile
+ * samples the whole edge, so collisions end an edge early) or contiguous
+ * (order 1: tighter tile bounds, better culling on free edges).  The fastest
+ * becomes the problem's launch for later validation calls and planner steps.
+ * config (host int32 [2], may be NULL): warps, order; ms_per_launch (host,
+ * may be NULL): its mean time.  Synchronises the stream.  Verdicts do not
+ * depend on the launch. */
+mrpop_status mrpop_autotune(mrpop_problem *p, const float *qa, const float *qb, int64_t n_edges,
+                            uint8_t *valid, int32_t *config, float *ms_per_launch,
+                            void *cuda_stream);
+
+/* Sets the validation launch directly: warps_per_block 0 (largest that fits),
+ * 1, 2 or 4; order 0 (strided) or 1 (contiguous). */
+mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_block, int32_t order);
+
 /* NEAREST(V, q, c) of Alg. 2 for n_queries queries: among tree vertices with
  * g_v + |q - q_v| < c, the one closest to q; ties go to the lowest g, then the
  * lowest index (Sec. III-D); -1 when no vertex qualifies.

@@ -27,6 +27,8 @@ EXPORTS = (
     "mrpop_validate_edges_ex",
     "mrpop_edge_clearance",
     "mrpop_validate_work",
+    "mrpop_autotune",
+    "mrpop_set_launch",
     "mrpop_nearest",
     "mrpop_nearest_noalloc",
     "mrpop_neighbors",
@@ -87,6 +89,8 @@ def _load() -> C.CDLL:
         "mrpop_validate_edges_ex": (i32, [vp, vp, vp, i64, vp, vp, vp, vp]),
         "mrpop_edge_clearance": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_validate_work": (i32, [vp, vp, vp, i64, vp, vp]),
+        "mrpop_autotune": (i32, [vp, vp, vp, i64, vp, vp, vp, vp]),
+        "mrpop_set_launch": (i32, [vp, i32, i32]),
         "mrpop_nearest": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_nearest_noalloc": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
@@ -252,6 +256,22 @@ def validate_work(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -
                                    _dptr(qb, torch.float32, "qb"), n,
                                    _dptr(out, torch.int64, "counters"), _stream(stream)))
     return out
+
+
+def autotune(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -> tuple:
+    """Tunes p's validation launch on these edges: (warps, order, ms)."""
+    n = _edges(p, qa, qb)
+    valid = torch.empty(n, dtype=torch.uint8, device=qa.device)
+    cfg = np.zeros(2, dtype=np.int32)
+    ms = C.c_float()
+    _check(lib.mrpop_autotune(p.handle, _dptr(qa, torch.float32, "qa"),
+                              _dptr(qb, torch.float32, "qb"), n, valid.data_ptr(),
+                              cfg.ctypes.data, C.byref(ms), _stream(stream)))
+    return int(cfg[0]), int(cfg[1]), ms.value
+
+
+def set_launch(p: Problem, warps_per_block: int, order: int) -> None:
+    _check(lib.mrpop_set_launch(p.handle, int(warps_per_block), int(order)))
 
 
 def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,

@@ -378,3 +378,25 @@ extern "C" mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t di
     if (!cost_out || (M > 0 && !path)) return set_error(MRPOP_EINVAL, "mrpop_path_cost: NULL buffer");
     return launch_path_cost(path, M, dim, cost_out, (cudaStream_t)stream);
 }
+
+extern "C" mrpop_status mrpop_autotune(mrpop_problem *p, const float *qa, const float *qb,
+                                      int64_t n_edges, uint8_t *valid, int32_t *config,
+                                      float *ms_per_launch, void *stream) {
+    mrpop_status st = check_edges(p, qa, qb, n_edges, valid, "mrpop_autotune");
+    if (st != MRPOP_OK) return st;
+    if (n_edges == 0) return set_error(MRPOP_EINVAL, "mrpop_autotune: no edges to time");
+    return autotune_validate(p, qa, qb, n_edges, valid, 3, config, ms_per_launch,
+                             (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_block,
+                                        int32_t order) {
+    if (!p) return set_error(MRPOP_EINVAL, "mrpop_set_launch: problem is NULL");
+    if (warps_per_block != 0 && warps_per_block != 1 && warps_per_block != 2 &&
+        warps_per_block != 4)
+        return set_error(MRPOP_EINVAL, "mrpop_set_launch: warps_per_block must be 0, 1, 2 or 4");
+    if (order != 0 && order != 1) return set_error(MRPOP_EINVAL, "mrpop_set_launch: order must be 0 or 1");
+    p->tuned_warps = warps_per_block;
+    p->tuned_order = order;
+    return MRPOP_OK;
+}

@@ -58,6 +58,7 @@ struct VParams {
     int dpad;
     int nstore;  // links of robots 0..K-2 (their frames and tile bounds are kept)
     int warps;   // warps of each block that take edges (the rest only stage tables)
+    int order;   // checkpoints to lanes: 0 strided across the edge, 1 contiguous
 };
 
 struct DeviceProblem {
@@ -93,6 +94,8 @@ struct mrpop_problem {
     std::vector<float> start, goal, q_lo, q_hi;
     int num_sms = 0;
     size_t smem_optin = 0;
+    int tuned_warps = 0;  // autotuned warps per block (0: largest that fits)
+    int tuned_order = 0;  // autotuned checkpoint order
 };
 
 namespace mrpop {
@@ -112,6 +115,9 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
                              uint8_t *valid, float *length, int32_t *npoints,
                              float *min_clear, unsigned long long *counters,
                              cudaStream_t st);
+mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
+                               uint8_t *valid, int reps, int32_t *out, float *ms_out,
+                               cudaStream_t st);
 // Fills V for validating n edges of problem p (warps per block and dynamic
 // shared memory of the launch go to *warps_out / *smem_out).
 mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, int64_t n,

@@ -29,6 +29,8 @@
 //    frames of robots 0..K-2 go to a per-warp shared scratch [link][15][lane]
 //    (lane-contiguous, conflict-free) for the robot-robot tests.
 #include <cfloat>
+#include <cmath>
+#include <algorithm>
 
 #include "mrpop_internal.cuh"
 
@@ -180,7 +182,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
         float minc = too_long ? -FLT_MAX : FLT_MAX;
 
         for (int tile = 0; tile < T; ++tile) {
-            int k = tile + T * lane;
+            int k = P.order ? tile * 32 + lane : tile + T * lane;
             const bool active = k <= n;
             if (!active) k = n;
             const float tk = __fdiv_rn((float)k, (float)n);
@@ -634,12 +636,13 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
     V.nstore = nstore;
     V.warp_floats = 2 * V.dpad + 4 * nstore + nstore * kXfFloats * 32;
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
-    int warps = kWarpsMax;
+    int warps = p->tuned_warps > 0 ? p->tuned_warps : kWarpsMax;
     size_t smem = 0;
     for (; warps >= 1; warps >>= 1) {
         smem = tab_bytes + (size_t)warps * V.warp_floats * sizeof(float);
         if (smem <= p->smem_optin) break;
     }
+    V.order = p->tuned_order;
     if (warps < 1)
         return set_error(MRPOP_EINVAL,
                          "problem too large for the validation kernel's shared memory "
@@ -667,12 +670,13 @@ mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, in
     V->nstore = t.link0[t.K - 1];
     V->warp_floats = 2 * V->dpad + 4 * V->nstore + V->nstore * kXfFloats * 32;
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
-    int warps = kWarpsMax;
+    int warps = p->tuned_warps > 0 ? p->tuned_warps : kWarpsMax;
     size_t smem = 0;
     for (; warps >= 1; warps >>= 1) {
         smem = tab_bytes + (size_t)warps * V->warp_floats * sizeof(float);
         if (smem + sizeof(VParams) + 1024 <= p->smem_optin) break;
     }
+    V->order = p->tuned_order;
     if (warps < 1)
         return set_error(MRPOP_EINVAL, "problem too large for the validation kernel's shared memory");
     *smem_out = smem;
@@ -700,6 +704,62 @@ mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int spl,
     if (spl <= 9) return batch_spl<9>(d_params, nslots, warps, blocks_per_slot, smem, st);
     if (spl <= 12) return batch_spl<12>(d_params, nslots, warps, blocks_per_slot, smem, st);
     return batch_spl<16>(d_params, nslots, warps, blocks_per_slot, smem, st);
+}
+
+// Times the validation kernel on the caller's edges for every candidate
+// launch (warps per block 1, 2, 4 that fit; strided or contiguous checkpoint
+// order), keeps the fastest in the problem and reports it.
+mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
+                               uint8_t *valid, int reps, int32_t *out, float *ms_out,
+                               cudaStream_t st) {
+    cudaEvent_t a, b;
+    MRPOP_CUDA_TRY(cudaEventCreate(&a));
+    MRPOP_CUDA_TRY(cudaEventCreate(&b));
+    float best = INFINITY;
+    int bw = 0, bo = 0;
+    const int save_w = p->tuned_warps, save_o = p->tuned_order;
+    mrpop_status s = MRPOP_OK;
+    for (int w = 1; w <= kWarpsMax && s == MRPOP_OK; w *= 2)
+        for (int o = 0; o < 2 && s == MRPOP_OK; ++o) {
+            const size_t need = (size_t)p->dev.t.n_f4 * sizeof(float4) +
+                                (size_t)w * (2 * ((p->dev.t.L + 3) & ~3) +
+                                             (4 + kXfFloats * 32) * p->dev.t.link0[p->dev.t.K - 1]) *
+                                    sizeof(float);
+            if (need + sizeof(VParams) + 1024 > p->smem_optin) continue;
+            p->tuned_warps = w;
+            p->tuned_order = o;
+            s = launch_validate(p, qa, qb, n, valid, nullptr, nullptr, nullptr, nullptr, st);  // warm
+            float tot = 0.f;
+            for (int r = 0; r < reps && s == MRPOP_OK; ++r) {
+                cudaEventRecord(a, st);
+                s = launch_validate(p, qa, qb, n, valid, nullptr, nullptr, nullptr, nullptr, st);
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                tot += ms;
+            }
+            if (s == MRPOP_OK && tot < best) {
+                best = tot;
+                bw = w;
+                bo = o;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != MRPOP_OK || bw == 0) {
+        p->tuned_warps = save_w;
+        p->tuned_order = save_o;
+        return s != MRPOP_OK ? s : set_error(MRPOP_EINVAL, "no launch configuration fits");
+    }
+    p->tuned_warps = bw;
+    p->tuned_order = bo;
+    if (out) {
+        out[0] = bw;
+        out[1] = bo;
+    }
+    if (ms_out) *ms_out = best / std::max(1, reps);
+    return MRPOP_OK;
 }
 
 mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st) {

@@ -234,3 +234,23 @@ def test_robot_robot_contact_spatial(mp, orc):
     _check_verdicts(v, ref, 1e-4)
     assert np.all(np.abs(c - ref["min_clear"]) <= REL * (1 + np.abs(ref["min_clear"])))
     assert cnt[6] > 0        # sphere-level robot-robot tests did run
+
+
+def test_launch_configs_and_autotune_same_verdicts(mp, orc):
+    """Every launch the autotuner may pick (warps per block, checkpoint order)
+    gives the same verdicts, also on edges long enough for many tiles."""
+    scene = synth.table_pair_scene(0)
+    qa, qb = synth.candidate_edges(scene, 4096, seed=41, step_hi=2.5)
+    with mp.Problem(scene, margin=1e-4) as p:
+        ref = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+        for w in (1, 2, 4):
+            for order in (0, 1):
+                mp.set_launch(p, w, order)
+                got = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+                np.testing.assert_array_equal(got, ref)
+        w, order, ms = mp.autotune(p, _dev(qa), _dev(qb))
+        assert w in (1, 2, 4) and order in (0, 1) and ms > 0
+        np.testing.assert_array_equal(mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy(), ref)
+    o = orc.OracleScene(scene)
+    idx = np.arange(0, 4096, 97)
+    _check_verdicts(ref[idx], o.validate_edges(qa[:, idx], qb[:, idx], 0.02, 1e-4), 1e-4)
