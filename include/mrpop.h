@@ -267,7 +267,9 @@ mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim, double *
  *             (Sec. III-A) in FP64 from the returned FP32 vertices, +inf when
  *             none.
  * Every returned path has been re-checked at resolution / 4 with the
- * problem's margin; incumbents only ever decrease strictly.
+ * problem's margin; incumbents only ever decrease strictly.  A single-robot
+ * problem (K = 1) skips roadmap construction and extends its trees directly
+ * in configuration space by at most cfg.delta per step (Sec. V-C ablation).
  * Errors: EINVAL (no start/goal, or either in collision), ENOSOLUTION (no path
  * within the budget), ECAPACITY (path_cap too small; path_len is set). */
 mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path, int64_t path_cap,
@@ -335,6 +337,14 @@ mrpop_status mrpop_server_stats(mrpop_server *s, int64_t *stats);
 /* Stops the server: running requests finish at once, queued ones are
  * dropped, the thread is joined.  NULL is accepted. */
 mrpop_status mrpop_server_destroy(mrpop_server *s);
+
+/* The index-th accepted incumbent path (0 = first solution; costs decrease
+ * with the index), for use as seeds of a downstream optimiser (Sec. III-F
+ * records every path of the optimisation for that).  Same outputs as
+ * mrpop_plan_result; cost is that incumbent's cost.  Errors: EINVAL (index
+ * outside [0, n) with n from mrpop_plan_trace), ECAPACITY. */
+mrpop_status mrpop_plan_history(const mrpop_problem *p, int64_t index, float *path,
+                                int64_t path_cap, int64_t *path_len, double *cost);
 
 /* Incumbent history of the problem's planner: times[i] (seconds since the
  * start of the mrpop_plan call that found it) and costs[i], in order, at most

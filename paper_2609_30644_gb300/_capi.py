@@ -37,6 +37,7 @@ EXPORTS = (
     "mrpop_plan_batch",
     "mrpop_plan_result",
     "mrpop_plan_trace",
+    "mrpop_plan_history",
     "mrpop_server_create",
     "mrpop_server_submit",
     "mrpop_server_poll",
@@ -99,6 +100,7 @@ def _load() -> C.CDLL:
         "mrpop_plan_trace": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_plan_batch": (i32, [vp, i32, C.c_double, i64, vp, vp]),
         "mrpop_plan_result": (i32, [vp, vp, i64, vp, vp]),
+        "mrpop_plan_history": (i32, [vp, i64, vp, i64, vp, vp]),
         "mrpop_server_create": (i32, [i32, i64, vp]),
         "mrpop_server_submit": (i32, [vp, vp, C.c_double, i64, C.c_double, vp]),
         "mrpop_server_poll": (i32, [vp, i64, vp, vp, vp]),
@@ -330,6 +332,15 @@ def plan(p: Problem, time_budget_s: float, path_cap: int = 1 << 16) -> tuple:
     if st == 6:  # MRPOP_ENOSOLUTION
         return None, float("inf")
     _check(st)
+    return buf[:n.value].copy(), cost.value
+
+
+def plan_history(p: Problem, index: int, path_cap: int = 1 << 16) -> tuple:
+    """(path float32 [M, D], cost) of the index-th accepted incumbent."""
+    buf = np.zeros((path_cap, p.D), dtype=np.float32)
+    n, cost = C.c_int64(), C.c_double()
+    _check(lib.mrpop_plan_history(p.handle, int(index), buf.ctypes.data, path_cap, C.byref(n),
+                                  C.byref(cost)))
     return buf[:n.value].copy(), cost.value
 
 

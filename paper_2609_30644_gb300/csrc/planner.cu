@@ -51,6 +51,8 @@ struct Ctrl {
 
 struct Slot {
     int K, D, rcap, tcap;
+    int direct;    // single robot: no roadmap, steer in configuration space
+    float step;    // direct mode: extension length (rad)
     int dof[MRPOP_MAX_ROBOTS];
     int qoff[MRPOP_MAX_ROBOTS];
     const float *q_lo, *q_hi, *start, *goal, *centre, *axis;
@@ -258,7 +260,27 @@ __global__ void k_oracle(const Slot *__restrict__ slots) {
     bool active = C.mode != 2 && nr >= 0;
     bool moved = false;
     float len2 = 0.f;
-    if (active) {
+    if (active && S.direct) {
+        // single-robot mode (Sec. V-C): extend from q_near toward q_rand by at
+        // most `step` (the robot plans in its configuration space directly)
+        float d2 = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const float t = S.qrand[(size_t)d * B + i] - S.tq[a][(size_t)d * S.tcap + nr];
+            d2 = fmaf(t, t, d2);
+        }
+        const float dist = sqrtf(d2);
+        const float f = dist > S.step ? S.step / dist : 1.f;
+        for (int d = 0; d < D; ++d) {
+            const float qa = S.tq[a][(size_t)d * S.tcap + nr];
+            const float qb = fmaf(f, S.qrand[(size_t)d * B + i] - qa, qa);
+            S.qnear[(size_t)d * B + i] = qa;
+            S.qnew[(size_t)d * B + i] = qb;
+            const float t = qb - qa;
+            len2 = fmaf(t, t, len2);
+        }
+        S.rmvnew[i] = 0;
+        moved = len2 > 0.f;
+    } else if (active) {
         for (int r = 0; r < S.K; ++r) {
             const int u = S.trmv[a][(size_t)r * S.tcap + nr];
             const int dof = S.dof[r], off = S.qoff[r];
@@ -569,8 +591,10 @@ struct Planner {
     double c_best = INFINITY;
     std::vector<float> best_path;  // [M][D]
     std::vector<double> trace_t, trace_c;
+    std::vector<std::vector<float>> history;  // every accepted incumbent path
     double trace_t0 = 0.0;
     bool released = false;  // device state freed (results kept on the host)
+    bool direct = false;    // single robot: no roadmap (Sec. V-C)
     unsigned long long seed = 0;
     int step = 0;
     int *h_small = nullptr;  // pinned: per robot [new count, connected]
@@ -687,6 +711,7 @@ static mrpop_status ensure_planner(mrpop_problem *p) {
         pl->best_path.swap(old->best_path);
         pl->trace_t.swap(old->trace_t);
         pl->trace_c.swap(old->trace_c);
+        pl->history.swap(old->history);
         pl->total_iters = old->total_iters;
         pl->mode = old->c_best < INFINITY ? 1 : 0;
         delete old;
@@ -807,6 +832,9 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
 
     Slot &S = pl->slot;
     S.K = K; S.D = D; S.rcap = rcap; S.tcap = tcap;
+    S.direct = K == 1 ? 1 : 0;
+    S.step = p->cfg.delta > 0.f ? p->cfg.delta : 0.5f;
+    pl->direct = S.direct != 0;
     S.q_lo = pl->d_lo; S.q_hi = pl->d_hi; S.start = pl->d_start; S.goal = pl->d_goal;
     S.centre = pl->d_centre; S.axis = pl->d_axis; S.c_min = (float)cmin;
     S.rm_n = pl->rm_n;
@@ -956,6 +984,7 @@ static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, int t
     for (int j = 0; j < M; ++j)
         if (!v[j]) return MRPOP_OK;  // rejected at the finer resolution
     pl->c_best = cost;
+    pl->history.push_back(path);
     pl->best_path.swap(path);
     pl->trace_t.push_back(t_now);
     pl->trace_c.push_back(cost);
@@ -1097,8 +1126,22 @@ struct SlotRun {
 static mrpop_status roadmap_rounds(const std::vector<Planner *> &pls, std::vector<SlotRun *> &runs,
                                    const Slot *d_slots, cudaStream_t st) {
     std::vector<int> todo;
-    for (size_t i = 0; i < pls.size(); ++i)
-        if (runs[i]->active && runs[i]->need_roadmap) todo.push_back((int)i);
+    for (size_t i = 0; i < pls.size(); ++i) {
+        if (!runs[i]->active || !runs[i]->need_roadmap) continue;
+        if (pls[i]->direct) {  // single robot: no roadmap, start from the roots
+            SlotRun &run = *runs[i];
+            run.need_roadmap = false;
+            pls[i]->roadmap_ready = true;
+            pls[i]->iters_in_call = 0;
+            if (pls[i]->mode == 1 || run.reset_trees) {
+                k_tree_reset<<<1, 64, 0, st>>>(d_slots + i);
+                PL_TRY(cudaGetLastError());
+                run.reset_trees = false;
+            }
+            continue;
+        }
+        todo.push_back((int)i);
+    }
     if (todo.empty()) return MRPOP_OK;
     for (int i : todo)
         for (int k = 0; k < pls[i]->K; ++k) ST_TRY(rm_phase1(pls[i], k, st));
@@ -1151,13 +1194,28 @@ static mrpop_status slot_after(Planner *pl, SlotRun &run, const Ctrl &r, const S
     if (accepted) {
         pl->mode = 1;             // from now on: AO-X
         run.need_roadmap = true;  // Alg. 1: grow the roadmap, optimise again
+        if (pl->direct) {         // single robot: no roadmap; AO-X restarts from the roots
+            run.need_roadmap = false;
+            pl->iters_in_call = 0;
+            k_tree_reset<<<1, 64, 0, st>>>(d_slot);
+            PL_TRY(cudaGetLastError());
+        }
         if (reached_target(pl->c_best, run.target)) {
             run.active = false;
             run.reached = true;
         }
     } else if (pl->iters_in_call >= max_iters || r.overflow) {
-        run.need_roadmap = true;  // iteration cap: grow the roadmap (c14)
-        if (r.overflow) run.reset_trees = true;
+        if (pl->direct) {
+            // single robot: the search continues; AO-X and full trees restart
+            if (pl->mode == 1 || r.overflow) {
+                k_tree_reset<<<1, 64, 0, st>>>(d_slot);
+                PL_TRY(cudaGetLastError());
+            }
+            pl->iters_in_call = 0;
+        } else {
+            run.need_roadmap = true;  // iteration cap: grow the roadmap (c14)
+            if (r.overflow) run.reset_trees = true;
+        }
     }
     return MRPOP_OK;
 }
@@ -1620,5 +1678,26 @@ extern "C" mrpop_status mrpop_server_destroy(mrpop_server *sv) {
     cudaFree(sv->d_ctrl);
     if (sv->h_ctrl) cudaFreeHost(sv->h_ctrl);
     delete sv;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_plan_history(const mrpop_problem *p, int64_t index, float *path,
+                                           int64_t path_cap, int64_t *path_len, double *cost) {
+    if (!p) return set_error(MRPOP_EINVAL, "mrpop_plan_history: problem is NULL");
+    const Planner *pl = p->planner;
+    const int64_t n = pl ? (int64_t)pl->history.size() : 0;
+    if (index < 0 || index >= n)
+        return set_error(MRPOP_EINVAL, "mrpop_plan_history: index %lld outside [0, %lld)",
+                         (long long)index, (long long)n);
+    const std::vector<float> &h = pl->history[(size_t)index];
+    const int64_t M = (int64_t)(h.size() / std::max(1, pl->D));
+    if (path_len) *path_len = M;
+    if (cost) *cost = pl->trace_c[(size_t)index];
+    if (path) {
+        if (path_cap < M)
+            return set_error(MRPOP_ECAPACITY, "mrpop_plan_history: path needs %lld vertices",
+                             (long long)M);
+        std::memcpy(path, h.data(), sizeof(float) * h.size());
+    }
     return MRPOP_OK;
 }

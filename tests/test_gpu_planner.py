@@ -197,3 +197,28 @@ def test_plan_batch_stops_at_target(mp, orc):
     assert len(c) == 1 and t[0] < 1.0
     _check_path(orc, o, path, cost, qs, qg)
     p.close()
+
+
+@pytest.mark.parametrize("kind", ["planar", "spatial"])
+def test_plan_single_robot_direct(mp, orc, kind):
+    """K = 1 skips the roadmap and plans directly in configuration space
+    (Sec. V-C); the result obeys the same checks."""
+    if kind == "planar":
+        base = synth.planar_pair_scene(2)
+        delta = 0.8
+    else:
+        base = synth.table_pair_scene(0)
+        delta = 1.0
+    scene = synth.Scene([base.robots[0]], base.obs_spheres, base.obs_cuboids)
+    qs, qg, o = _start_goal(orc, scene, 3, delta=max(delta, 0.8 if kind == "planar" else 2.5))
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=delta, seed=2, start=qs, goal=qg) as p:
+        path, cost = mp.plan(p, 2.0)
+        t, c, it = mp.plan_trace(p)
+        hist = [mp.plan_history(p, k) for k in range(len(c))]
+    _check_path(orc, o, path, cost, qs, qg)
+    assert np.all(np.diff(c) < 0)
+    # every recorded incumbent is itself a valid path with its recorded cost
+    for (hp, hc), ck in zip(hist, c):
+        assert hc == ck
+        _check_path(orc, o, hp, hc, qs, qg)
+    np.testing.assert_array_equal(hist[-1][0], path)
