@@ -257,6 +257,34 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
             tile[(DIM + 1) * kTile + j] = n2 * (1.f - kC3);
         }
         __syncthreads();
+        if (v0 == vs) {
+            // Seed each query's best with an exact check of the slice's first
+            // 32 vertices, so that the filter below starts from a finite
+            // bound instead of re-checking the whole first tile.
+            const int np = min(nv, 32);
+            for (int u = 0; u < np; ++u) {
+#pragma unroll
+                for (int j = 0; j < kQPT; ++j) {
+                    const float g = tile[DIM * kTile + u];
+                    if (!(g < cq[j])) continue;
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        float lo, hi;
+                        f2_unpack(m2q[j][d], lo, hi);
+                        const float a = -0.5f * lo - tile[d * kTile + u];
+                        d2 = fmaf(a, a, d2);
+                    }
+                    if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
+                        (d2 < best[j].d2 || g < best[j].g)) {
+                        best[j].d2 = d2;
+                        best[j].g = g;
+                        best[j].idx = v0 + u;
+                        lim[j] = fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU);
+                    }
+                }
+            }
+        }
         const int ng = (nv + 7) >> 3;   // groups of 8 vertices
         for (int gq = 0; gq < ng; ++gq) {
             const float4 wa = tile4[(DIM + 1) * (kTile / 4) + 2 * gq];
@@ -298,6 +326,9 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
                     cm &= cm - 1;
                     {
                         const int vl = 8 * gq + u;
+                        // a vertex with g >= c is never admissible (distances
+                        // are >= 0): no exact check needed
+                        if (!(tile[DIM * kTile + vl] < cq[j])) continue;
                         float d2 = 0.f;
 #pragma unroll
                         for (int d = 0; d < DIM; ++d) {
