@@ -52,6 +52,8 @@ class _Scene(C.Structure):
         ("obs_spheres", C.c_void_p),
         ("n_obs_cuboids", C.c_int32),
         ("obs_cuboids", C.c_void_p),
+        ("self_collision", C.c_int32),
+        ("self_mask", C.c_void_p),
     ]
 
 
@@ -93,7 +95,7 @@ def _load():
 class OracleScene:
     """Holds contiguous float32/int32 copies of a synth.Scene for the C oracle."""
 
-    def __init__(self, scene):
+    def __init__(self, scene, self_collision: bool = False):
         rs = scene.robots
         self.K = len(rs)
         self.D = int(sum(r.dof for r in rs))
@@ -118,9 +120,21 @@ class OracleScene:
         else:
             n_oc = self.obs_cuboids.shape[0]
         self.n_sph_per = [r.n_spheres for r in rs]
+        # adjacency masks (bit i of row j pairs links i < j); robots without
+        # one take every pair two or more links apart
+        masks = [getattr(r, "self_mask", None) for r in rs]
+        self.self_mask = None
+        if any(m is not None for m in masks):
+            rows = []
+            for r, m in zip(rs, masks):
+                rows.append(np.asarray(m, dtype=np.uint16) if m is not None else np.array(
+                    [(1 << (j - 1)) - 1 if j >= 2 else 0 for j in range(r.dof)], dtype=np.uint16))
+            self.self_mask = np.ascontiguousarray(np.concatenate(rows), dtype=np.uint16)
         self._s = _Scene(self.K, _p(self.dof), _p(self.dh), _p(self.n_spheres),
                          _p(self.sphere_link), _p(self.sphere_xyzr), _p(self.base),
-                         n_os, _p(self.obs_spheres), n_oc, _p(self.obs_cuboids))
+                         n_os, _p(self.obs_spheres), n_oc, _p(self.obs_cuboids),
+                         int(bool(self_collision)),
+                         _p(self.self_mask) if self.self_mask is not None else None)
 
     @property
     def ptr(self):

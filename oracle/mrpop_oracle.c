@@ -158,6 +158,7 @@ int32_t orc_config_valid(const orc_scene *s, const double *q, double margin, dou
         orc_fk_robot(s, k, q + joint_offset(s, k), w + 4 * s0);
         for (int32_t i = 0; i < s->n_spheres[k]; ++i) owner[s0 + i] = k;
     }
+    const int32_t *link = s->sphere_link;  /* link of each sphere within its robot */
     double mc = DBL_MAX;
     int32_t valid = 1;
     for (int32_t i = 0; i < total_s; ++i) {
@@ -174,9 +175,18 @@ int32_t orc_config_valid(const orc_scene *s, const double *q, double margin, dou
             if (cl < mc) mc = cl;
             if (cl < margin) valid = 0;
         }
-        /* robot-robot: spheres of two different robots (no self-collision) */
+        /* robot-robot: spheres of two different robots; with self-collision
+         * also spheres of one robot on a link pair of its adjacency mask */
         for (int32_t j = i + 1; j < total_s; ++j) {
-            if (owner[j] == owner[i]) continue;
+            if (owner[j] == owner[i]) {
+                if (!s->self_collision) continue;
+                const int32_t hi = link[j] > link[i] ? link[j] : link[i];
+                const int32_t lo = link[j] > link[i] ? link[i] : link[j];
+                const int32_t paired = s->self_mask
+                    ? (s->self_mask[joint_offset(s, owner[i]) + hi] >> lo) & 1
+                    : hi - lo >= 2;
+                if (hi == lo || !paired) continue;
+            }
             const double *cj = w + 4 * j;
             const double cl = orc_sphere_sphere_clearance(ci, ci[3], cj, cj[3]);
             if (cl < mc) mc = cl;

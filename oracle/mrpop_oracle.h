@@ -40,6 +40,10 @@ typedef struct {
     const float *obs_spheres;
     int32_t n_obs_cuboids;
     const float *obs_cuboids;
+    int32_t self_collision;  /* 1: also test link pairs of one robot (below)  */
+    const uint16_t *self_mask; /* [sum dof] or NULL: bit i of row j (i < j) of a
+                                * robot pairs its links i and j; NULL pairs
+                                * every i, j with j >= i + 2                */
 } orc_scene;
 
 /* Forward kinematics of robot k at its joint vector q (length dof[k]):
@@ -56,8 +60,9 @@ double orc_sphere_cuboid_clearance(const double *c, double r, const float *cuboi
 
 /* Validity of one composite configuration q [D].  Returns 1 when no robot
  * sphere is in contact with an obstacle and no two spheres of different robots
- * are in contact; contact means clearance < margin.  *min_clear receives the
- * smallest clearance of any tested pair (may be NULL). */
+ * are in contact (and, with self_collision, no two spheres of one robot on
+ * a link pair of its adjacency mask); contact means clearance < margin.
+ * *min_clear receives the smallest clearance of any tested pair (may be NULL). */
 int32_t orc_config_valid(const orc_scene *s, const double *q, double margin, double *min_clear);
 
 /* Number of interpolation intervals n = max(1, ceil(||qb - qa||_2 / res)),

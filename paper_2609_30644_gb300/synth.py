@@ -56,6 +56,9 @@ class Robot:
     sphere_link: np.ndarray  # int32 [S], non-decreasing link index
     sphere_xyzr: np.ndarray  # float32 [S, 4] in the link's frame F_j'
     base: np.ndarray         # float32 [12] row-major 3x4
+    # uint16 [dof] or None: bit i of row j (i < j) pairs links i and j for
+    # self-collision tests; None pairs every link two or more apart
+    self_mask: Optional[np.ndarray] = None
 
     @property
     def n_spheres(self) -> int:

@@ -6,6 +6,7 @@ edge sampling, and library routines (scipy cKDTree) for special cases.
 No GPU needed.  Chosen so that a dropped term, a wrong sign or index, or a
 transposed operand anywhere in the oracle fails at least one of them.
 """
+import dataclasses
 import math
 import os
 
@@ -221,7 +222,8 @@ def test_sphere_sphere_symmetric_and_scaled(orc):
 
 def _planar_min_clearance(scene, q):
     """All-pairs clearance with closed-form planar FK and scipy-free numpy."""
-    w = [planar_closed_form(rb, q[3 * k:3 * k + 3]) for k, rb in enumerate(scene.robots)]
+    offs = np.cumsum([0] + [rb.dof for rb in scene.robots])
+    w = [planar_closed_form(rb, q[offs[k]:offs[k + 1]]) for k, rb in enumerate(scene.robots)]
     mc = np.inf
     for k, wk in enumerate(w):
         oc = scene.obs_spheres.astype(float)
@@ -457,3 +459,73 @@ def test_path_cost(orc):
     ref = sum(np.linalg.norm(path[j + 1].astype(float) - path[j].astype(float)) for j in range(6))
     assert orc.path_cost(path) == pytest.approx(ref, rel=1e-14)
     assert orc.path_cost(path[:1]) == 0.0
+
+
+# ----------------------------------------------------------------------------
+# optional self-collision (links at least two apart on one robot)
+# ----------------------------------------------------------------------------
+
+def test_self_collision_folded_planar_arm(orc):
+    """Hand-derived: the planar arm of the golden file folded as (0, pi, 0)
+    puts link 2's first sphere at (-0.4, -0.0375) and link 0's first sphere at
+    (-0.4, 0.0375): 0.075 m apart, radii 0.04 + 0.04 -> clearance -0.005.
+    Links 0-1 and 1-2 are adjacent and never tested against each other."""
+    scene = synth.planar_pair_scene(0)
+    one = synth.Scene([scene.robots[0]], np.zeros((0, 4), np.float32),
+                      np.zeros((0, 15), np.float32))
+    q = [0.0, math.pi, 0.0]
+    ok, mc = orc.OracleScene(one, self_collision=True).config_valid(q, 0.0)
+    assert not ok and mc == pytest.approx(-0.005, abs=1e-6)
+    ok, _ = orc.OracleScene(one, self_collision=False).config_valid(q, 0.0)
+    assert ok
+    # straight arm: the closest tested pair is link 0's last circle (y = 0.2625)
+    # and link 2's first (y = 0.6375), 0.375 apart -> clearance 0.295
+    ok, mc = orc.OracleScene(one, self_collision=True).config_valid([0.0, 0.0, 0.0], 0.0)
+    assert ok and mc == pytest.approx(0.295, abs=1e-6)
+    # an adjacency mask without the (0, 2) pair accepts the folded arm
+    rb = dataclasses.replace(scene.robots[0], self_mask=np.zeros(3, np.uint16))
+    masked = synth.Scene([rb], one.obs_spheres, one.obs_cuboids)
+    ok, mc = orc.OracleScene(masked, self_collision=True).config_valid(q, 0.0)
+    assert ok and mc > 1e300  # no pair is tested: the minimum stays at DBL_MAX
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_self_collision_allpairs_planar(orc, masked):
+    """All-pairs numpy (closed-form planar FK) including the same-robot pairs
+    of the adjacency mask agrees with the oracle's minimum and verdict: the
+    default mask (links two or more apart) and a 5-link arm's explicit mask
+    that pairs links (0, 2), (0, 4), (1, 3) and (2, 4) only."""
+    scene = synth.planar_pair_scene(1)
+    if masked:
+        rng = np.random.default_rng(3)
+        arms = []
+        for rb in scene.robots:
+            arm = synth.planar_arm(rb.base, n_links=5, link_len=0.2)
+            arms.append(dataclasses.replace(
+                arm, self_mask=np.array([0, 0, 1, 2, 1 | 4], np.uint16)))
+        scene = synth.Scene(arms, scene.obs_spheres, scene.obs_cuboids)
+        pairs = {(0, 2), (0, 4), (1, 3), (2, 4)}
+    o = orc.OracleScene(scene, self_collision=True)
+    rng = np.random.default_rng(21)
+    n_bad = n_self = 0
+    for _ in range(200):
+        q = rng.uniform(-math.pi, math.pi, scene.D)
+        ref = _planar_min_clearance(scene, q)
+        ref_other = ref
+        off = 0
+        for rb in scene.robots:
+            w = planar_closed_form(rb, q[off:off + rb.dof])
+            off += rb.dof
+            lk = rb.sphere_link
+            for a in range(len(w)):
+                for b in range(a + 1, len(w)):
+                    la, lb = sorted((int(lk[a]), int(lk[b])))
+                    if ((la, lb) in pairs) if masked else lb - la >= 2:
+                        d = np.linalg.norm(w[a, :3] - w[b, :3]) - w[a, 3] - w[b, 3]
+                        ref = min(ref, d)
+        ok, mc = o.config_valid(q, 0.0)
+        assert mc == pytest.approx(ref, abs=1e-12)
+        assert ok == (ref >= 0.0)
+        n_bad += not ok
+        n_self += ref < 0.0 <= ref_other
+    assert n_bad > 0 and n_self > 0
