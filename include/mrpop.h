@@ -65,7 +65,13 @@ typedef struct mrpop_problem mrpop_problem; /* opaque, library-owned */
  *               non-decreasing; at most MRPOP_MAX_SPHERES_PER_LINK per link
  *   sphere_xyzr host [n_spheres][4] centre in frame F_j' (joint j's frame
  *               after its rotation Rz(q_j + theta_offset_j)) and radius
- *   base        row-major 3x4 [R | t] pose of the first joint's frame.
+ *   base        row-major 3x4 [R | t] pose of the first joint's frame
+ *   self_mask   host [dof] or NULL: the adjacency mask used when the
+ *               config's self_collision is 1.  Bit i of self_mask[j] (i < j)
+ *               set means links i and j of this robot are tested against
+ *               each other; bits i >= j must be zero (EINVAL otherwise).
+ *               NULL selects every pair with j >= i + 2.  Ignored when
+ *               self_collision is 0.
  * The frame after joint j is F_j' * Tz(d_j) * Tx(a_j) * Rx(alpha_j). */
 typedef struct {
     int32_t dof;
@@ -76,6 +82,7 @@ typedef struct {
     const int32_t *sphere_link;
     const float *sphere_xyzr;
     float base[12];
+    const uint16_t *self_mask;
 } mrpop_robot;
 
 /* Obstacles (host arrays): spheres [n][4] = cx, cy, cz, r; cuboids [n][15] =
@@ -98,7 +105,12 @@ typedef struct {
  *   n_per_round  roadmap samples per robot per ROADMAP call (Alg. 2)
  *   tree_cap, roadmap_cap   vertex capacities of planner trees / roadmaps
  *   max_iters    planner iteration cap per search call
- *   seed         planner random seed */
+ *   seed         planner random seed
+ *   self_collision  0: a robot's spheres are never tested against its own
+ *                (the default; free space per robot counts obstacles only);
+ *                1: spheres of the link pairs that each robot's self_mask
+ *                selects are tested too (by default links i and j >= i + 2;
+ *                adjacent links may overlap at their joint) */
 typedef struct {
     float resolution;
     float margin;
@@ -108,6 +120,7 @@ typedef struct {
     int64_t roadmap_cap;
     int64_t max_iters;
     uint64_t seed;
+    int32_t self_collision;
 } mrpop_config;
 
 /* Message of the last failed call on this thread ("" when none). */

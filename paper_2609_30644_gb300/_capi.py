@@ -58,7 +58,8 @@ class MrpopError(RuntimeError):
 class _Robot(C.Structure):
     _fields_ = [("dof", C.c_int32), ("n_spheres", C.c_int32), ("dh", C.c_void_p),
                 ("q_lo", C.c_void_p), ("q_hi", C.c_void_p), ("sphere_link", C.c_void_p),
-                ("sphere_xyzr", C.c_void_p), ("base", C.c_float * 12)]
+                ("sphere_xyzr", C.c_void_p), ("base", C.c_float * 12),
+                ("self_mask", C.c_void_p)]
 
 
 class _Obstacles(C.Structure):
@@ -69,7 +70,8 @@ class _Obstacles(C.Structure):
 class _Config(C.Structure):
     _fields_ = [("resolution", C.c_float), ("margin", C.c_float), ("delta", C.c_float),
                 ("n_per_round", C.c_int32), ("tree_cap", C.c_int64),
-                ("roadmap_cap", C.c_int64), ("max_iters", C.c_int64), ("seed", C.c_uint64)]
+                ("roadmap_cap", C.c_int64), ("max_iters", C.c_int64), ("seed", C.c_uint64),
+                ("self_collision", C.c_int32)]
 
 
 def _load() -> C.CDLL:
@@ -151,7 +153,7 @@ class Problem:
                  delta: float = 1.0, n_per_round: int = 64, tree_cap: int = 1 << 16,
                  roadmap_cap: int = 1 << 14, max_iters: int = 4096, seed: int = 0,
                  start: Optional[Sequence[float]] = None,
-                 goal: Optional[Sequence[float]] = None):
+                 goal: Optional[Sequence[float]] = None, self_collision: bool = False):
         keep = []
         robots = (_Robot * len(scene.robots))()
         for i, r in enumerate(scene.robots):
@@ -165,13 +167,18 @@ class Problem:
             robots[i].sphere_link, robots[i].sphere_xyzr = arrs[3].ctypes.data, arrs[4].ctypes.data
             for j, v in enumerate(np.asarray(r.base, dtype=np.float32).reshape(12)):
                 robots[i].base[j] = float(v)
+            sm = getattr(r, "self_mask", None)
+            if sm is not None:
+                sm = _host(sm, np.uint16)
+                keep.append(sm)
+                robots[i].self_mask = sm.ctypes.data
         osph = _host(np.asarray(scene.obs_spheres).reshape(-1, 4), np.float32)
         ocub = _host(np.asarray(scene.obs_cuboids).reshape(-1, 15), np.float32)
         keep += [osph, ocub]
         obs = _Obstacles(osph.shape[0], osph.ctypes.data if osph.size else None,
                          ocub.shape[0], ocub.ctypes.data if ocub.size else None)
         cfg = _Config(resolution, margin, delta, n_per_round, tree_cap, roadmap_cap,
-                      max_iters, seed)
+                      max_iters, seed, int(bool(self_collision)))
         st = _host(start, np.float32) if start is not None else None
         gl = _host(goal, np.float32) if goal is not None else None
         keep += [a for a in (st, gl) if a is not None]

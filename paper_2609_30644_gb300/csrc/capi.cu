@@ -90,8 +90,11 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
     if (!(cfg->margin >= 0.f) || !std::isfinite(cfg->margin))
         return set_error(MRPOP_EINVAL, "margin must be >= 0 and finite");
 
+    if (cfg->self_collision != 0 && cfg->self_collision != 1)
+        return set_error(MRPOP_EINVAL, "self_collision must be 0 or 1");
     Tables t;
     t.K = K;
+    t.selfcol = cfg->self_collision;
     int L = 0, S = 0;
     for (int k = 0; k < K; ++k) {
         const mrpop_robot &r = robots[k];
@@ -179,7 +182,14 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
             A[4] = dh[3];
             A[5] = f_of_i(s_glob + first);
             A[6] = f_of_i(cnt);
-            A[7] = f_of_i(k);
+            // same-robot partner links of link j (bit i: link i < j), or 0
+            // when self-collision is off
+            uint32_t sm = 0;
+            if (t.selfcol) sm = r.self_mask ? r.self_mask[j] : (j >= 2 ? (1u << (j - 1)) - 1u : 0u);
+            if (sm >> j)
+                return set_error(MRPOP_EINVAL, "robot %d: self_mask[%d] has bits at or above %d", k,
+                                 j, j);
+            A[7] = f_of_i((int)sm);
             coarse_sphere(r.sphere_xyzr + 4 * first, cnt, A + 8);
         }
         std::memcpy(f4(t.off_sph + s_glob), r.sphere_xyzr, 4 * sizeof(float) * r.n_spheres);

@@ -31,6 +31,7 @@ struct Tables {
     int K = 0, L = 0, S = 0, NS = 0, NC = 0;
     int link0[MRPOP_MAX_ROBOTS + 1] = {0};  // first link of robot k; link0[K] = L
     int max_spheres_per_link = 0;
+    int selfcol = 0;  // 1: also test links i, j >= i + 2 of one robot
     int off_base = 0, off_link = 0, off_sph = 0, off_os = 0, off_oc = 0, n_f4 = 0;
 };
 

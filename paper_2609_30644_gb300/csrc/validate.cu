@@ -201,7 +201,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
 
             for (int b = 0; b < K; ++b) {
                 const int l0 = t.link0[b], l1 = t.link0[b + 1];
-                const bool store = b < K - 1;
+                const bool store = b < K - 1 || t.selfcol;
                 Frame Tm = load_base(tab, t, b);
                 for (int l = l0; l < l1; ++l) {
                     const float4 LA = tab[t.off_link + kLinkF4 * l];
@@ -394,22 +394,28 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                             }
                         }
 
-                        // ---- robot vs earlier robots (links 0 .. l0-1)
-                        if (l0 > 0) {
+                        // ---- robot vs earlier robots (links 0 .. l0-1) and, with
+                        // self-collision, vs the links of this robot that its
+                        // adjacency mask pairs with link l (bit i: link l0 + i)
+                        const unsigned long long pm =
+                            (l0 > 0 ? ~0ull >> (64 - l0) : 0ull) |
+                            ((unsigned long long)(unsigned)__float_as_int(LB.w) << l0);
+                        const unsigned pm0 = (unsigned)pm, pm1 = (unsigned)(pm >> 32);
+                        if (pm) {
                             unsigned own0 = 0, own1 = 0;
                             if (MODE == kClearance) {
-                                own0 = low_mask(l0);
-                                own1 = l0 > 32 ? low_mask(l0 - 32) : 0u;
+                                own0 = pm0;
+                                own1 = pm1;
                             } else {
                                 // tile-level candidates: lane i tests link i (and i + 32)
                                 bool h0 = false, h1 = false;
-                                if (lane < l0) {
+                                if ((pm0 >> lane) & 1u) {
                                     const float4 o = tb[lane];
                                     const float d2 = dist2(bnd.x, bnd.y, bnd.z, o.x, o.y, o.z);
                                     const float th2 = bnd.w + o.w + m;
                                     h0 = d2 < th2 * th2;
                                 }
-                                if (lane + 32 < l0) {
+                                if ((pm1 >> lane) & 1u) {
                                     const float4 o = tb[lane + 32];
                                     const float d2 = dist2(bnd.x, bnd.y, bnd.z, o.x, o.y, o.z);
                                     const float th2 = bnd.w + o.w + m;
@@ -443,7 +449,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                         own1 = own;
                                 }
                                 if (MODE == kCount) {
-                                    if (lane == 0) cnt[8] += l0;
+                                    if (lane == 0) cnt[8] += __popcll(pm);
                                     if (active) cnt[3] += __popc(cand0) + __popc(cand1);
                                 }
                             }
@@ -642,7 +648,7 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
     V.counters = counters;
     V.work = p->dev.edge_counter;
     V.dpad = (t.L + 3) & ~3;
-    const int nstore = t.link0[t.K - 1];
+    const int nstore = t.selfcol ? t.L : t.link0[t.K - 1];
     V.nstore = nstore;
     V.warp_floats = 2 * V.dpad + 4 * nstore + nstore * kXfFloats * 32;
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
@@ -677,7 +683,7 @@ mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, in
     V->valid = valid;
     V->work = p->dev.edge_counter;
     V->dpad = (t.L + 3) & ~3;
-    V->nstore = t.link0[t.K - 1];
+    V->nstore = t.selfcol ? t.L : t.link0[t.K - 1];
     V->warp_floats = 2 * V->dpad + 4 * V->nstore + V->nstore * kXfFloats * 32;
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
     int warps = p->tuned_warps > 0 ? p->tuned_warps : kWarpsMax;
@@ -733,7 +739,9 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
         for (int o = 0; o < 2 && s == MRPOP_OK; ++o) {
             const size_t need = (size_t)p->dev.t.n_f4 * sizeof(float4) +
                                 (size_t)w * (2 * ((p->dev.t.L + 3) & ~3) +
-                                             (4 + kXfFloats * 32) * p->dev.t.link0[p->dev.t.K - 1]) *
+                                             (4 + kXfFloats * 32) *
+                                                 (p->dev.t.selfcol ? p->dev.t.L
+                                                                   : p->dev.t.link0[p->dev.t.K - 1])) *
                                     sizeof(float);
             if (need + sizeof(VParams) + 1024 > p->smem_optin) continue;
             p->tuned_warps = w;

@@ -82,6 +82,20 @@ def test_create_rejects_bad_config(capi):
         capi.Problem(_scene(), margin=-1.0)
 
 
+def test_create_rejects_bad_self_mask(capi):
+    """A self-collision mask bit at or above its own link is malformed; with
+    self-collision off the mask is ignored."""
+    import dataclasses
+    s = _scene()
+    s.robots[0] = dataclasses.replace(s.robots[0], self_mask=np.array([0, 2, 1], np.uint16))
+    with pytest.raises(capi.MrpopError) as ei:
+        capi.Problem(s, self_collision=True)
+    assert ei.value.status == 1 and "self_mask" in str(ei.value)
+    with pytest.raises(capi.MrpopError) as ei:   # valid tables: fails only at the device
+        capi.Problem(s, self_collision=False)
+    assert "self_mask" not in str(ei.value)
+
+
 def test_nearest_rejects_bad_dim(capi):
     lib = capi.lib
     st = lib.mrpop_nearest(None, 0, 0, 0, None, None, 1, None, None)

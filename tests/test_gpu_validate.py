@@ -254,3 +254,65 @@ def test_launch_configs_and_autotune_same_verdicts(mp, orc):
     o = orc.OracleScene(scene)
     idx = np.arange(0, 4096, 97)
     _check_verdicts(ref[idx], o.validate_edges(qa[:, idx], qb[:, idx], 0.02, 1e-4), 1e-4)
+
+
+# ----------------------------------------------------------------------------
+# optional self-collision with an adjacency mask
+# ----------------------------------------------------------------------------
+
+def _zero_pose_mask_scene(orc, scene, slack=0.01):
+    """Adjacency masks in the usual allowed-collision style: pair links i and
+    j >= i + 2 of each arm unless their spheres come within ``slack`` of each
+    other at the zero configuration (oracle FK)."""
+    import dataclasses
+    w = orc.OracleScene(scene).fk(np.zeros(scene.D))
+    arms, s0 = [], 0
+    for rb in scene.robots:
+        ww = w[s0:s0 + rb.n_spheres]
+        s0 += rb.n_spheres
+        lk = rb.sphere_link
+        m = np.zeros(rb.dof, np.uint16)
+        for j in range(rb.dof):
+            for i in range(j - 1):
+                a, b = ww[lk == i], ww[lk == j]
+                d = (np.linalg.norm(a[:, None, :3] - b[None, :, :3], axis=2)
+                     - a[:, None, 3] - b[None, :, 3])
+                if d.min() >= slack:
+                    m[j] |= 1 << i
+        arms.append(dataclasses.replace(rb, self_mask=m))
+    return synth.Scene(arms, scene.obs_spheres, scene.obs_cuboids, scene.name)
+
+
+@pytest.mark.parametrize("name,n_edges,masked", [("planar_pair", 600, False),
+                                                  ("table_pair", 300, True),
+                                                  ("grid4", 60, True)])
+def test_self_collision_parity(mp, orc, name, n_edges, masked):
+    """Verdicts, clearances and interval counts with self-collision on: the
+    default mask (links two or more apart) on the planar arms and zero-pose
+    adjacency masks on the 7-DOF arms.  Self-collision must change verdicts
+    (the test is not vacuous) and the kernel must follow the oracle."""
+    scene = SCENES[name]()
+    if masked:
+        scene = _zero_pose_mask_scene(orc, scene)
+    qa, qb = synth.candidate_edges(scene, n_edges, seed=11, step_hi=3.0)
+    ref0 = orc.OracleScene(scene).validate_edges(qa, qb, 0.02, 0.0, early_exit=False)
+    ref = orc.OracleScene(scene, self_collision=True).validate_edges(qa, qb, 0.02, 0.0,
+                                                                     early_exit=False)
+    assert (ref["valid"] != ref0["valid"]).sum() > 0
+    assert ref["valid"].sum() > 0
+    with mp.Problem(scene, resolution=0.02, self_collision=True) as p:
+        n = qa.shape[1]
+        valid = torch.empty(n, dtype=torch.uint8, device="cuda")
+        length = torch.empty(n, dtype=torch.float32, device="cuda")
+        npts = torch.empty(n, dtype=torch.int32, device="cuda")
+        mp.validate_edges(p, _dev(qa), _dev(qb), valid, length, npts)
+        np.testing.assert_array_equal(npts.cpu().numpy(), ref["npoints"])
+        c = mp.edge_clearance(p, _dev(qa), _dev(qb)).cpu().numpy().astype(np.float64)
+        v = valid.cpu().numpy()
+    err = np.abs(c - ref["min_clear"])
+    assert (err <= REL * (1 + np.abs(ref["min_clear"]))).all(), err.max()
+    _check_verdicts(v, ref, 0.0)
+    # self-collision off ignores the masks: the plain verdicts come back
+    with mp.Problem(scene, resolution=0.02) as p:
+        v0 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+    _check_verdicts(v0, ref0, 0.0)
