@@ -359,6 +359,16 @@ mrpop_status mrpop_server_destroy(mrpop_server *s);
 mrpop_status mrpop_plan_history(const mrpop_problem *p, int64_t index, float *path,
                                 int64_t path_cap, int64_t *path_len, double *cost);
 
+/* Measured FP32 FMA throughput of the current device in TFLOP/s, the
+ * roofline denominator of this library's kernels (all FP32 SIMT).  The paper
+ * has no counterpart: this is a calibration utility.  It launches 8
+ * independent FMA chains per thread of iters steps each on 2,048 threads per
+ * SM, once to warm up and then 5 times timed with CUDA events on cuda_stream
+ * (synchronises it).  packed 0 times scalar FFMA, 1 the packed two-lane
+ * fma.rn.f32x2 form.  Errors: EINVAL (NULL tflops, packed not 0/1, iters
+ * outside 1 .. 2^24), ECUDA. */
+mrpop_status mrpop_fp32_peak(int32_t packed, int32_t iters, double *tflops, void *cuda_stream);
+
 /* Incumbent history of the problem's planner: times[i] (seconds since the
  * start of the mrpop_plan call that found it) and costs[i], in order, at most
  * cap entries; *n receives the full count and *iterations the planner

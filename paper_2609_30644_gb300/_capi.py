@@ -43,6 +43,7 @@ EXPORTS = (
     "mrpop_server_poll",
     "mrpop_server_stats",
     "mrpop_server_destroy",
+    "mrpop_fp32_peak",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -108,6 +109,7 @@ def _load() -> C.CDLL:
         "mrpop_server_poll": (i32, [vp, i64, vp, vp, vp]),
         "mrpop_server_stats": (i32, [vp, vp]),
         "mrpop_server_destroy": (i32, [vp]),
+        "mrpop_fp32_peak": (i32, [i32, i32, vp, vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -327,6 +329,13 @@ def path_cost(path: torch.Tensor, out: Optional[torch.Tensor] = None, stream=Non
     _check(lib.mrpop_path_cost(_dptr(path, torch.float32, "path"), M, dim,
                                _dptr(out, torch.float64, "cost"), _stream(stream)))
     return out
+
+
+def fp32_peak(packed: bool = False, iters: int = 32768, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s)."""
+    out = C.c_double()
+    _check(lib.mrpop_fp32_peak(int(bool(packed)), int(iters), C.byref(out), _stream(stream)))
+    return out.value
 
 
 def plan(p: Problem, time_budget_s: float, path_cap: int = 1 << 16) -> tuple:
