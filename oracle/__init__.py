@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrpop_oracle.c")
+_SRC_PLANNER = os.path.join(_HERE, "mrpop_ref_planner.c")
 _HDR = os.path.join(_HERE, "mrpop_oracle.h")
 _LIB = os.path.join(_HERE, f"liboracle.{platform.machine()}.so")
 _lock = threading.Lock()
@@ -29,12 +30,12 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, -O2, no fp contraction)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_PLANNER, _HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call([
             "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-            "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"])
+            "-Wall", "-Wextra", "-o", tmp, _SRC, _SRC_PLANNER, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -83,6 +84,7 @@ def _load():
             "orc_neighbors": (i64, [vp, i64, i64, i32, vp, f32, i64, vp, pd]),
             "orc_path_cost": (f64, [vp, i64, i32]),
             "orc_path_valid": (i32, [vp, vp, i64, f32, f64, vp]),
+            "orc_plan": (i32, [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -250,3 +252,41 @@ def neighbors(tree, q, delta, k_max: int, n_vertices: Optional[int] = None,
 def path_cost(path) -> float:
     path = np.ascontiguousarray(path, dtype=np.float32)
     return float(_load().orc_path_cost(_p(path), path.shape[0], path.shape[1]))
+
+
+class _PlanParams(C.Structure):
+    _fields_ = [("resolution", C.c_double), ("margin", C.c_double), ("delta", C.c_double),
+                ("n_per_round", C.c_int32), ("max_iters", C.c_int64),
+                ("iter_budget", C.c_int64), ("time_budget_s", C.c_double),
+                ("round_budget", C.c_int64), ("target_cost", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+def plan_reference(scene, start, goal, *, resolution: float = 0.02, margin: float = 1e-4,
+                   delta: float = 1.0, n_per_round: int = 64, max_iters: int = 4096,
+                   iter_budget: int = 0, time_budget_s: float = 0.0,
+                   round_budget: int = 0, target_cost: float = -1.0, seed: int = 0, self_collision: bool = False,
+                   path_cap: int = 1 << 16, trace_cap: int = 1024) -> dict:
+    """The FP64 reference planner (Alg. 1/2, sequential) on a synth.Scene.
+    Returns {status, path [M, D] float64 or None, cost, times, costs,
+    trace_iters, iterations}; status 0 = solved, 1 = no solution, -1 = error."""
+    o = OracleScene(scene, self_collision=self_collision)
+    lo = np.ascontiguousarray(np.concatenate([r.q_lo for r in scene.robots]), dtype=np.float32)
+    hi = np.ascontiguousarray(np.concatenate([r.q_hi for r in scene.robots]), dtype=np.float32)
+    st = np.ascontiguousarray(start, dtype=np.float64)
+    gl = np.ascontiguousarray(goal, dtype=np.float64)
+    pp = _PlanParams(resolution, margin, delta, n_per_round, max_iters, iter_budget,
+                     time_budget_s, round_budget, target_cost, seed)
+    path = np.zeros((path_cap, o.D), dtype=np.float64)
+    tt = np.zeros(trace_cap, dtype=np.float64)
+    tc = np.zeros(trace_cap, dtype=np.float64)
+    ti = np.zeros(trace_cap, dtype=np.int64)
+    plen, cost, ntr, its = C.c_int64(), C.c_double(), C.c_int64(), C.c_int64()
+    status = _load().orc_plan(o.ptr, _p(lo), _p(hi), _p(st), _p(gl), C.byref(pp), _p(path),
+                              path_cap, C.byref(plen), C.byref(cost), _p(tt), _p(tc), _p(ti),
+                              trace_cap, C.byref(ntr), C.byref(its))
+    n = min(ntr.value, trace_cap)
+    return {"status": int(status),
+            "path": path[:plen.value].copy() if status == 0 and plen.value <= path_cap else None,
+            "cost": cost.value, "times": tt[:n].copy(), "costs": tc[:n].copy(),
+            "trace_iters": ti[:n].copy(), "iterations": its.value}

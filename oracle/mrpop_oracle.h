@@ -104,6 +104,37 @@ double orc_path_cost(const float *path, int64_t M, int32_t D);
 int32_t orc_path_valid(const orc_scene *s, const float *path, int64_t M, float res,
                        double margin, int64_t *bad_segment);
 
+/* ------------------------------------------------------------------------- */
+/* FP64 reference planner (mrpop_ref_planner.c): Alg. 1 and Alg. 2 run one    */
+/* iteration at a time on one host thread.                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double resolution;    /* edge discretisation step (rad)                    */
+    double margin;        /* contact inflation (m)                             */
+    double delta;         /* per-robot roadmap connection radius (rad)         */
+    int32_t n_per_round;  /* roadmap samples per robot per ROADMAP call        */
+    int64_t max_iters;    /* iterations per dRRT / AO-X search call            */
+    int64_t iter_budget;  /* total search iterations (<= 0: no limit)          */
+    double time_budget_s; /* wall-clock budget (<= 0: no limit); a time or an
+                           * iteration budget must be set                      */
+    int64_t round_budget; /* total ROADMAP rounds (<= 0: no limit)            */
+    double target_cost;   /* stop once the incumbent costs <= this (-1: never) */
+    uint64_t seed;        /* SplitMix64 seed                                   */
+} orc_plan_params;
+
+/* Plans from start to goal (composite, double [D]) within the joint limits
+ * q_lo, q_hi [D].  Returns 0 with a path (path [path_len][D] when path_len <=
+ * path_cap; *cost = C(sigma) in FP64), 1 when no path was found within the
+ * budget, -1 on invalid input, allocation failure, a start or goal in
+ * collision, or a robot without free samples.  Every accepted incumbent is
+ * recorded: trace_t (seconds since the call began), trace_c (its cost),
+ * trace_it (iterations so far), at most trace_cap entries; *n_trace receives
+ * the full count and *iterations the search iterations run. */
+int32_t orc_plan(const orc_scene *s, const float *q_lo, const float *q_hi, const double *start,
+                 const double *goal, const orc_plan_params *pp, double *path, int64_t path_cap,
+                 int64_t *path_len, double *cost, double *trace_t, double *trace_c,
+                 int64_t *trace_it, int64_t trace_cap, int64_t *n_trace, int64_t *iterations);
+
 #ifdef __cplusplus
 }
 #endif
