@@ -664,7 +664,8 @@ def run_ours(args) -> None:
                        "path_vertices": PATH_M, "l2": "flushed between steps (256 MB write)",
                        "validate_launch": {"warps_per_block": tuned[0],
                                            "order": ["strided", "contiguous"][tuned[1]],
-                                           "autotune_ms": tuned[2]},
+                                           "fine_stage": ["union", "reassigned"][tuned[2]],
+                                           "autotune_ms": tuned[3]},
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "kernel": "nearest_qpt_kernel<14>",
                          "achieved": nn_achieved, "peak": peak_tflops, "unit": "TFLOP/s",

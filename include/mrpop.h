@@ -202,18 +202,25 @@ mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, const float 
  * > 0; verdicts written to valid) for every candidate that fits: warps per
  * block 1, 2 or 4, checkpoints strided across the edge (order 0: every tile
  * samples the whole edge, so collisions end an edge early) or contiguous
- * (order 1: tighter tile bounds, better culling on free edges).  The fastest
- * becomes the problem's launch for later validation calls and planner steps.
- * config (host int32 [2], may be NULL): warps, order; ms_per_launch (host,
- * may be NULL): its mean time.  Synchronises the stream.  Verdicts do not
- * depend on the launch. */
+ * (order 1: tighter tile bounds, better culling on free edges), and the fine
+ * obstacle tests as one warp-wide pass over every obstacle any checkpoint's
+ * coarse sphere hit (fine stage 0) or as work items dealt out to the lanes in
+ * proportion to each checkpoint's coarse hits (fine stage 1, the paper's
+ * load-proportional thread reassignment of Sec. III-E).  The fastest becomes
+ * the problem's launch for later validation calls and planner steps.  config
+ * (host int32 [3], may be NULL): warps, order, fine stage; ms_per_launch
+ * (host, may be NULL): its mean time.  Synchronises the stream.  Verdicts do
+ * not depend on the launch. */
 mrpop_status mrpop_autotune(mrpop_problem *p, const float *qa, const float *qb, int64_t n_edges,
                             uint8_t *valid, int32_t *config, float *ms_per_launch,
                             void *cuda_stream);
 
 /* Sets the validation launch directly: warps_per_block 0 (largest that fits),
- * 1, 2 or 4; order 0 (strided) or 1 (contiguous). */
-mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_block, int32_t order);
+ * 1, 2 or 4; order 0 (strided) or 1 (contiguous); fine_stage 0 (warp-wide
+ * union) or 1 (reassigned work items), as described for mrpop_autotune.
+ * Errors: EINVAL for any other value. */
+mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_block, int32_t order,
+                              int32_t fine_stage);
 
 /* NEAREST(V, q, c) of Alg. 2 for n_queries queries: among tree vertices with
  * g_v + |q - q_v| < c, the one closest to q; ties go to the lowest g, then the

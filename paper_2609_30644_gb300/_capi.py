@@ -94,7 +94,7 @@ def _load() -> C.CDLL:
         "mrpop_edge_clearance": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_validate_work": (i32, [vp, vp, vp, i64, vp, vp]),
         "mrpop_autotune": (i32, [vp, vp, vp, i64, vp, vp, vp, vp]),
-        "mrpop_set_launch": (i32, [vp, i32, i32]),
+        "mrpop_set_launch": (i32, [vp, i32, i32, i32]),
         "mrpop_nearest": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_nearest_noalloc": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
@@ -270,19 +270,19 @@ def validate_work(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -
 
 
 def autotune(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -> tuple:
-    """Tunes p's validation launch on these edges: (warps, order, ms)."""
+    """Tunes p's validation launch on these edges: (warps, order, fine_stage, ms)."""
     n = _edges(p, qa, qb)
     valid = torch.empty(n, dtype=torch.uint8, device=qa.device)
-    cfg = np.zeros(2, dtype=np.int32)
+    cfg = np.zeros(3, dtype=np.int32)
     ms = C.c_float()
     _check(lib.mrpop_autotune(p.handle, _dptr(qa, torch.float32, "qa"),
                               _dptr(qb, torch.float32, "qb"), n, valid.data_ptr(),
                               cfg.ctypes.data, C.byref(ms), _stream(stream)))
-    return int(cfg[0]), int(cfg[1]), ms.value
+    return int(cfg[0]), int(cfg[1]), int(cfg[2]), ms.value
 
 
-def set_launch(p: Problem, warps_per_block: int, order: int) -> None:
-    _check(lib.mrpop_set_launch(p.handle, int(warps_per_block), int(order)))
+def set_launch(p: Problem, warps_per_block: int, order: int, fine_stage: int = 0) -> None:
+    _check(lib.mrpop_set_launch(p.handle, int(warps_per_block), int(order), int(fine_stage)))
 
 
 def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,

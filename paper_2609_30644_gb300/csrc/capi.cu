@@ -400,13 +400,16 @@ extern "C" mrpop_status mrpop_autotune(mrpop_problem *p, const float *qa, const 
 }
 
 extern "C" mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_block,
-                                        int32_t order) {
+                                        int32_t order, int32_t fine_stage) {
     if (!p) return set_error(MRPOP_EINVAL, "mrpop_set_launch: problem is NULL");
     if (warps_per_block != 0 && warps_per_block != 1 && warps_per_block != 2 &&
         warps_per_block != 4)
         return set_error(MRPOP_EINVAL, "mrpop_set_launch: warps_per_block must be 0, 1, 2 or 4");
     if (order != 0 && order != 1) return set_error(MRPOP_EINVAL, "mrpop_set_launch: order must be 0 or 1");
+    if (fine_stage != 0 && fine_stage != 1)
+        return set_error(MRPOP_EINVAL, "mrpop_set_launch: fine_stage must be 0 or 1");
     p->tuned_warps = warps_per_block;
     p->tuned_order = order;
+    p->tuned_fine = fine_stage;
     return MRPOP_OK;
 }

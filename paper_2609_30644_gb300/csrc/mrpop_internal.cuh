@@ -60,7 +60,17 @@ struct VParams {
     int nstore;  // links of robots 0..K-2 (their frames and tile bounds are kept)
     int warps;   // warps of each block that take edges (the rest only stage tables)
     int order;   // checkpoints to lanes: 0 strided across the edge, 1 contiguous
+    int fine;    // fine obstacle tests: 0 warp-union mask, 1 reassigned work items
 };
+
+// Per-warp shared scratch of the validation kernel (floats): q_a, q_b - q_a,
+// tile bounds and frames of the stored links, and with reassigned fine tests
+// one more link frame [12][32] plus 32 hit masks and 32 prefix sums.
+inline int validate_warp_floats(const Tables &t, int fine) {
+    const int dpad = (t.L + 3) & ~3;
+    const int nstore = t.selfcol ? t.L : t.link0[t.K - 1];
+    return 2 * dpad + 4 * nstore + nstore * kXfFloats * 32 + (fine ? kXfFloats * 32 + 64 : 0);
+}
 
 struct DeviceProblem {
     Tables t;
@@ -97,6 +107,7 @@ struct mrpop_problem {
     size_t smem_optin = 0;
     int tuned_warps = 0;  // autotuned warps per block (0: largest that fits)
     int tuned_order = 0;  // autotuned checkpoint order
+    int tuned_fine = 0;   // autotuned fine-test mode (0 union, 1 reassigned)
 };
 
 namespace mrpop {
@@ -124,9 +135,11 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
 mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
                           uint8_t *valid, VParams *V, size_t *smem_out, int *warps_out);
 // Validates every problem's batch in one launch: d_params is a device array
-// of nslots VParams whose total_warps equal blocks_per_slot * warps.
+// of nslots VParams whose total_warps equal blocks_per_slot * warps; fine
+// selects the reassigned fine stage (every slot's scratch must provide it).
 mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int spl, int warps,
-                                   int blocks_per_slot, size_t smem, cudaStream_t st);
+                                   int blocks_per_slot, size_t smem, bool fine,
+                                   cudaStream_t st);
 mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st);
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,

@@ -208,8 +208,11 @@ constexpr int kQThreads = 128;
 constexpr int kQPT = 2;
 constexpr int kTile = 256;
 
+// Up to 14 coordinates the registers are capped so that 7 blocks (28 warps)
+// stay resident per SM; the compiler fits the loop without spilling and the
+// extra warps hide the shared-memory latency of the vertex tiles.
 template <int DIM>
-__global__ void __launch_bounds__(kQThreads)
+__global__ void __launch_bounds__(kQThreads, DIM <= 14 ? 7 : 1)
 nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
                    const float *__restrict__ queries, const float *__restrict__ budgets, int Q,
                    int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial) {

@@ -1002,6 +1002,7 @@ struct Batch {
     Ctrl *d_ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;   // pinned
     int spl = 4, warps = 1, bps = 1;
+    bool fine = false;  // reassigned fine stage (only when every slot asks for it)
     size_t smem = 0;
     std::vector<int> slot_warps;  // warps per block that take edges, per slot
     cudaGraphExec_t exec = nullptr;
@@ -1044,6 +1045,8 @@ static mrpop_status batch_config(Batch &bt) {
     bt.warps = wmax;
     bt.smem = smem;
     bt.spl = spl;
+    bt.fine = !bt.pls.empty();
+    for (Planner *pl : bt.pls) bt.fine = bt.fine && pl->vp[0].fine != 0;
     bt.bps = (kStepIters + wmax - 1) / wmax;
     return MRPOP_OK;
 }
@@ -1055,12 +1058,13 @@ static mrpop_status enqueue_step(Batch &bt, cudaStream_t st) {
     k_nearest<0><<<gq, kPThreads, 0, st>>>(bt.d_slots);
     k_oracle<<<g1, 128, 0, st>>>(bt.d_slots);
     PL_TRY(cudaGetLastError());
-    ST_TRY(launch_validate_batch(bt.d_vp, n, bt.spl, bt.warps, bt.bps, bt.smem, st));
+    ST_TRY(launch_validate_batch(bt.d_vp, n, bt.spl, bt.warps, bt.bps, bt.smem, bt.fine, st));
     k_insert<<<dim3(1, n), kStepIters, 0, st>>>(bt.d_slots);
     k_nearest<1><<<gq, kPThreads, 0, st>>>(bt.d_slots);
     k_conn_prep<<<g1, 128, 0, st>>>(bt.d_slots);
     PL_TRY(cudaGetLastError());
-    ST_TRY(launch_validate_batch(bt.d_vp + n, n, bt.spl, bt.warps, bt.bps, bt.smem, st));
+    ST_TRY(launch_validate_batch(bt.d_vp + n, n, bt.spl, bt.warps, bt.bps, bt.smem, bt.fine,
+                                 st));
     k_solution<<<g1, 128, 0, st>>>(bt.d_slots);
     PL_TRY(cudaGetLastError());
     return MRPOP_OK;

@@ -137,6 +137,82 @@ __device__ __forceinline__ void joint_sincos(float th, float *s, float *c) {
 
 __device__ __forceinline__ unsigned low_mask(int n) { return n >= 32 ? kFull : ((1u << n) - 1u); }
 
+// Second stage with load-proportional reassignment (Sec. III-E): the fine
+// tests that the lanes' own coarse hits call for -- (checkpoint k, obstacle o
+// hit by k's link sphere, fine sphere s of the link) -- are numbered by a warp
+// prefix sum of the per-lane counts and dealt out to all 32 lanes in turn, so
+// the warp spends ceil(total / 32) passes on them instead of one pass of
+// every lane over every obstacle that any lane hit.  A lane rebuilds its
+// item's fine sphere from the owning checkpoint's link frame, which every lane
+// puts in the warp's shared scratch fr ([12][32] floats, then 32 hit masks and
+// 32 prefix sums).  A fine hit implies a coarse hit (the coarse sphere encloses
+// the fine ones with slack), so the verdict equals the union form's.
+template <bool CUBOID>
+__device__ __forceinline__ bool fine_reassigned(unsigned own, int c0, int ns, int sf,
+                                                const Frame &F, float m, const float4 *tab,
+                                                const Tables &t, float *fr, int lane) {
+    if (!__any_sync(kFull, own != 0u)) return false;  // the common case: no fine work
+    const int mine = __popc(own) * ns;
+    int incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return false;
+    unsigned *own_s = reinterpret_cast<unsigned *>(fr + kXfFloats * 32);
+    int *pre_s = reinterpret_cast<int *>(own_s + 32);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) fr[c * 32 + lane] = F.r[c];
+    fr[9 * 32 + lane] = F.t[0];
+    fr[10 * 32 + lane] = F.t[1];
+    fr[11 * 32 + lane] = F.t[2];
+    own_s[lane] = own;
+    pre_s[lane] = incl - mine;
+    __syncwarp();
+    const float inv_ns = 1.f / (float)ns;
+    bool hit = false;
+    for (int b = 0; b < total; b += 32) {
+        const int item = b + lane;
+        if (item < total) {
+            int k = 0;  // owner: the last lane whose first item is <= item
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (pre_s[k + step] <= item) k += step;
+            const int r = item - pre_s[k];
+            int jo = (int)((float)r * inv_ns);  // r / ns, corrected below
+            if (jo * ns > r) --jo;
+            if ((jo + 1) * ns <= r) ++jo;
+            const int s = r - jo * ns;
+            unsigned mm = own_s[k];
+            for (int q = 0; q < jo; ++q) mm &= mm - 1;  // jo-th set bit of k's mask
+            const int o = __ffs(mm) - 1;
+            Frame Fk;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) Fk.r[c] = fr[c * 32 + k];
+            Fk.t[0] = fr[9 * 32 + k];
+            Fk.t[1] = fr[10 * 32 + k];
+            Fk.t[2] = fr[11 * 32 + k];
+            const float4 sp = tab[t.off_sph + sf + s];
+            const float3 p = apply(Fk, sp.x, sp.y, sp.z);
+            if (CUBOID) {
+                const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + o);
+                const float d2 = box_dist2(p.x, p.y, p.z, cbp[0], cbp[1], cbp[2], cbp[3], cbp[4]);
+                const float th2 = sp.w + m;
+                hit |= d2 < th2 * th2;
+            } else {
+                const float4 ob = tab[t.off_os + c0 + o];
+                const float d2 = dist2(p.x, p.y, p.z, ob.x, ob.y, ob.z);
+                const float th2 = sp.w + ob.w + m;
+                hit |= d2 < th2 * th2;
+            }
+        }
+    }
+    __syncwarp();  // the scratch is rewritten by the next call
+    return hit;
+}
+
 // Interval count n = max(1, ceil(|dq|_2 / res)) in FP32 with a sequential
 // fused multiply-add sum (the oracle takes the same integer decision in FP32).
 __device__ __forceinline__ int interval_count(const float *dq, int D, float res, float *len_out) {
@@ -149,14 +225,16 @@ __device__ __forceinline__ int interval_count(const float *dq, int D, float res,
     return nf > 1073741824.f ? 1073741824 : (int)nf;
 }
 
-template <int MODE, int SPL>
+template <int MODE, int SPL, bool RA>
 __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
     float4 *tab = sm4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *ws = reinterpret_cast<float *>(sm4 + P.t.n_f4) + (size_t)warp * P.warp_floats;
     float *qa_s = ws, *dq_s = ws + P.dpad;
     float4 *tb = reinterpret_cast<float4 *>(ws + 2 * P.dpad);      // tile bounds [nstore]
-    float *xf = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][15][32]
+    float *xf = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][12][32]
+    float *fr = xf + P.nstore * kXfFloats * 32;                     // reassignment scratch
+    constexpr bool ra = MODE == kVerdict && RA;  // reassigned fine obstacle tests
 
     for (int i = threadIdx.x; i < P.t.n_f4; i += blockDim.x) tab[i] = P.blob[i];
     __syncthreads();
@@ -301,6 +379,11 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     if (active) cnt[2] += __popc(cand);
                                 }
                             }
+                            if (ra) {
+                                hit |= fine_reassigned<false>(own, c0, ns, sf, F, m, tab, t, fr,
+                                                              lane);
+                                continue;
+                            }
                             const unsigned wm =
                                 MODE == kClearance ? own : __reduce_or_sync(kFull, own);
                             if (MODE == kCount && active) {
@@ -362,6 +445,11 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     if (lane == 0) cnt[11] += cn;
                                     if (active) cnt[10] += __popc(cand);
                                 }
+                            }
+                            if (ra) {
+                                hit |= fine_reassigned<true>(own, c0, ns, sf, F, m, tab, t, fr,
+                                                             lane);
+                                continue;
                             }
                             const unsigned wm =
                                 MODE == kClearance ? own : __reduce_or_sync(kFull, own);
@@ -551,27 +639,27 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
     }
 }
 
-template <int MODE, int SPL>
+template <int MODE, int SPL, bool RA>
 __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams P) {
     extern __shared__ float4 sm4[];
-    validate_body<MODE, SPL>(P, sm4);
+    validate_body<MODE, SPL, RA>(P, sm4);
 }
 
 // Many problems in one launch: block row y serves problem y (its parameters
 // are staged in shared memory once per block).
-template <int SPL>
+template <int SPL, bool RA>
 __global__ void __launch_bounds__(kWarpsMax * 32) validate_batch_kernel(const VParams *Ps) {
     extern __shared__ float4 sm4[];
     __shared__ VParams sP;
     if (threadIdx.x == 0) sP = Ps[blockIdx.y];
     __syncthreads();
-    validate_body<kVerdict, SPL>(sP, sm4);
+    validate_body<kVerdict, SPL, RA>(sP, sm4);
 }
 
-template <int MODE, int SPL>
+template <int MODE, int SPL, bool RA>
 mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
                          cudaStream_t st) {
-    auto kern = validate_kernel<MODE, SPL>;
+    auto kern = validate_kernel<MODE, SPL, RA>;
     MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     int bps = 0;
@@ -586,15 +674,24 @@ mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
     return MRPOP_OK;
 }
 
+template <int MODE, bool RA>
+mrpop_status launch_spl_ra(mrpop_problem *p, VParams &V, int warps, size_t smem,
+                           cudaStream_t st) {
+    const int spl = p->dev.t.max_spheres_per_link;
+    if (spl <= 4) return launch_mode<MODE, 4, RA>(p, V, warps, smem, st);
+    if (spl <= 8) return launch_mode<MODE, 8, RA>(p, V, warps, smem, st);
+    if (spl <= 9) return launch_mode<MODE, 9, RA>(p, V, warps, smem, st);
+    if (spl <= 12) return launch_mode<MODE, 12, RA>(p, V, warps, smem, st);
+    return launch_mode<MODE, 16, RA>(p, V, warps, smem, st);
+}
+
+// The reassigned fine stage exists for verdicts only; the clearance and
+// work-count modes always take the union form.
 template <int MODE>
 mrpop_status launch_spl(mrpop_problem *p, VParams &V, int warps, size_t smem,
                         cudaStream_t st) {
-    const int spl = p->dev.t.max_spheres_per_link;
-    if (spl <= 4) return launch_mode<MODE, 4>(p, V, warps, smem, st);
-    if (spl <= 8) return launch_mode<MODE, 8>(p, V, warps, smem, st);
-    if (spl <= 9) return launch_mode<MODE, 9>(p, V, warps, smem, st);
-    if (spl <= 12) return launch_mode<MODE, 12>(p, V, warps, smem, st);
-    return launch_mode<MODE, 16>(p, V, warps, smem, st);
+    if (MODE == kVerdict && V.fine) return launch_spl_ra<MODE, true>(p, V, warps, smem, st);
+    return launch_spl_ra<MODE, false>(p, V, warps, smem, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,9 +745,9 @@ mrpop_status launch_validate(mrpop_problem *p, const float *qa, const float *qb,
     V.counters = counters;
     V.work = p->dev.edge_counter;
     V.dpad = (t.L + 3) & ~3;
-    const int nstore = t.selfcol ? t.L : t.link0[t.K - 1];
-    V.nstore = nstore;
-    V.warp_floats = 2 * V.dpad + 4 * nstore + nstore * kXfFloats * 32;
+    V.nstore = t.selfcol ? t.L : t.link0[t.K - 1];
+    V.fine = p->tuned_fine;
+    V.warp_floats = validate_warp_floats(t, V.fine);
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
     int warps = p->tuned_warps > 0 ? p->tuned_warps : kWarpsMax;
     size_t smem = 0;
@@ -684,7 +781,8 @@ mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, in
     V->work = p->dev.edge_counter;
     V->dpad = (t.L + 3) & ~3;
     V->nstore = t.selfcol ? t.L : t.link0[t.K - 1];
-    V->warp_floats = 2 * V->dpad + 4 * V->nstore + V->nstore * kXfFloats * 32;
+    V->fine = p->tuned_fine;
+    V->warp_floats = validate_warp_floats(t, V->fine);
     const size_t tab_bytes = (size_t)t.n_f4 * sizeof(float4);
     int warps = p->tuned_warps > 0 ? p->tuned_warps : kWarpsMax;
     size_t smem = 0;
@@ -701,10 +799,10 @@ mrpop_status make_vparams(mrpop_problem *p, const float *qa, const float *qb, in
     return MRPOP_OK;
 }
 
-template <int SPL>
+template <int SPL, bool RA>
 static mrpop_status batch_spl(const VParams *d_params, int nslots, int warps, int blocks_per_slot,
                               size_t smem, cudaStream_t st) {
-    auto kern = validate_batch_kernel<SPL>;
+    auto kern = validate_batch_kernel<SPL, RA>;
     MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     dim3 grid(blocks_per_slot, nslots);
@@ -713,18 +811,27 @@ static mrpop_status batch_spl(const VParams *d_params, int nslots, int warps, in
     return MRPOP_OK;
 }
 
+template <bool RA>
+static mrpop_status batch_spl_ra(const VParams *d_params, int nslots, int spl, int warps,
+                                 int blocks_per_slot, size_t smem, cudaStream_t st) {
+    if (spl <= 4) return batch_spl<4, RA>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    if (spl <= 8) return batch_spl<8, RA>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    if (spl <= 9) return batch_spl<9, RA>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    if (spl <= 12) return batch_spl<12, RA>(d_params, nslots, warps, blocks_per_slot, smem, st);
+    return batch_spl<16, RA>(d_params, nslots, warps, blocks_per_slot, smem, st);
+}
+
 mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int spl, int warps,
-                                   int blocks_per_slot, size_t smem, cudaStream_t st) {
-    if (spl <= 4) return batch_spl<4>(d_params, nslots, warps, blocks_per_slot, smem, st);
-    if (spl <= 8) return batch_spl<8>(d_params, nslots, warps, blocks_per_slot, smem, st);
-    if (spl <= 9) return batch_spl<9>(d_params, nslots, warps, blocks_per_slot, smem, st);
-    if (spl <= 12) return batch_spl<12>(d_params, nslots, warps, blocks_per_slot, smem, st);
-    return batch_spl<16>(d_params, nslots, warps, blocks_per_slot, smem, st);
+                                   int blocks_per_slot, size_t smem, bool fine,
+                                   cudaStream_t st) {
+    if (fine) return batch_spl_ra<true>(d_params, nslots, spl, warps, blocks_per_slot, smem, st);
+    return batch_spl_ra<false>(d_params, nslots, spl, warps, blocks_per_slot, smem, st);
 }
 
 // Times the validation kernel on the caller's edges for every candidate
 // launch (warps per block 1, 2, 4 that fit; strided or contiguous checkpoint
-// order), keeps the fastest in the problem and reports it.
+// order; union or reassigned fine tests), keeps the fastest in the problem
+// and reports it.
 mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
                                uint8_t *valid, int reps, int32_t *out, float *ms_out,
                                cudaStream_t st) {
@@ -732,20 +839,18 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
     MRPOP_CUDA_TRY(cudaEventCreate(&a));
     MRPOP_CUDA_TRY(cudaEventCreate(&b));
     float best = INFINITY;
-    int bw = 0, bo = 0;
-    const int save_w = p->tuned_warps, save_o = p->tuned_order;
+    int bw = 0, bo = 0, bf = 0;
+    const int save_w = p->tuned_warps, save_o = p->tuned_order, save_f = p->tuned_fine;
     mrpop_status s = MRPOP_OK;
     for (int w = 1; w <= kWarpsMax && s == MRPOP_OK; w *= 2)
-        for (int o = 0; o < 2 && s == MRPOP_OK; ++o) {
+        for (int o = 0; o < 2 && s == MRPOP_OK; ++o)
+        for (int f = 0; f < 2 && s == MRPOP_OK; ++f) {
             const size_t need = (size_t)p->dev.t.n_f4 * sizeof(float4) +
-                                (size_t)w * (2 * ((p->dev.t.L + 3) & ~3) +
-                                             (4 + kXfFloats * 32) *
-                                                 (p->dev.t.selfcol ? p->dev.t.L
-                                                                   : p->dev.t.link0[p->dev.t.K - 1])) *
-                                    sizeof(float);
+                                (size_t)w * validate_warp_floats(p->dev.t, f) * sizeof(float);
             if (need + sizeof(VParams) + 1024 > p->smem_optin) continue;
             p->tuned_warps = w;
             p->tuned_order = o;
+            p->tuned_fine = f;
             s = launch_validate(p, qa, qb, n, valid, nullptr, nullptr, nullptr, nullptr, st);  // warm
             float tot = 0.f;
             for (int r = 0; r < reps && s == MRPOP_OK; ++r) {
@@ -761,6 +866,7 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
                 best = tot;
                 bw = w;
                 bo = o;
+                bf = f;
             }
         }
     cudaEventDestroy(a);
@@ -768,13 +874,16 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
     if (s != MRPOP_OK || bw == 0) {
         p->tuned_warps = save_w;
         p->tuned_order = save_o;
+        p->tuned_fine = save_f;
         return s != MRPOP_OK ? s : set_error(MRPOP_EINVAL, "no launch configuration fits");
     }
     p->tuned_warps = bw;
     p->tuned_order = bo;
+    p->tuned_fine = bf;
     if (out) {
         out[0] = bw;
         out[1] = bo;
+        out[2] = bf;
     }
     if (ms_out) *ms_out = best / std::max(1, reps);
     return MRPOP_OK;

@@ -90,6 +90,19 @@ def test_plan_planar_pair(mp, orc, seed):
     assert np.all(np.diff(t) >= 0) and iters > 0
 
 
+def test_plan_reassigned_fine_stage(mp, orc):
+    """The planner's batched validation launches with the reassigned fine
+    stage: the returned path is oracle-valid at res/4."""
+    scene = synth.planar_pair_scene(0)
+    qs, qg, o = _start_goal(orc, scene, 0)
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=0.8, n_per_round=64,
+                    tree_cap=1 << 16, roadmap_cap=1 << 14, max_iters=4096, seed=5,
+                    start=qs, goal=qg) as p:
+        mp.set_launch(p, 0, 0, 1)
+        path, cost = mp.plan(p, 1.5)
+    _check_path(orc, o, path, cost, qs, qg)
+
+
 def test_plan_table_pair(mp, orc):
     scene = synth.table_pair_scene(0)
     qs, qg, o = _start_goal(orc, scene, 5, delta=2.5)

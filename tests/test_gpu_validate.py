@@ -97,7 +97,11 @@ def test_verdict_parity(mp, orc, name, n_edges, margin):
         # repeated launches reuse the self-resetting work counter
         v2 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
         np.testing.assert_array_equal(v, v2)
+        # the reassigned fine stage (load-proportional work items)
+        mp.set_launch(p, 0, 0, 1)
+        v3 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
     _check_verdicts(v, ref, margin)
+    _check_verdicts(v3, ref, margin)
 
 
 def test_verdict_matches_gpu_clearance(mp):
@@ -237,19 +241,23 @@ def test_robot_robot_contact_spatial(mp, orc):
 
 
 def test_launch_configs_and_autotune_same_verdicts(mp, orc):
-    """Every launch the autotuner may pick (warps per block, checkpoint order)
-    gives the same verdicts, also on edges long enough for many tiles."""
+    """Every launch the autotuner may pick (warps per block, checkpoint order,
+    union or reassigned fine tests) gives the same verdicts, also on edges
+    long enough for many tiles."""
     scene = synth.table_pair_scene(0)
     qa, qb = synth.candidate_edges(scene, 4096, seed=41, step_hi=2.5)
     with mp.Problem(scene, margin=1e-4) as p:
         ref = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
         for w in (1, 2, 4):
             for order in (0, 1):
-                mp.set_launch(p, w, order)
-                got = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
-                np.testing.assert_array_equal(got, ref)
-        w, order, ms = mp.autotune(p, _dev(qa), _dev(qb))
-        assert w in (1, 2, 4) and order in (0, 1) and ms > 0
+                for fine in (0, 1):
+                    mp.set_launch(p, w, order, fine)
+                    got = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+                    np.testing.assert_array_equal(got, ref)
+        with pytest.raises(mp.MrpopError):
+            mp.set_launch(p, 4, 0, 2)
+        w, order, fine, ms = mp.autotune(p, _dev(qa), _dev(qb))
+        assert w in (1, 2, 4) and order in (0, 1) and fine in (0, 1) and ms > 0
         np.testing.assert_array_equal(mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy(), ref)
     o = orc.OracleScene(scene)
     idx = np.arange(0, 4096, 97)
