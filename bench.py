@@ -319,7 +319,12 @@ def run_reference_planner(entries, budget: float):
     return out, workers, time.perf_counter() - t0
 
 
-def run_planner_leg(mp, synth):
+def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: int = PLAN_PROBLEMS,
+                    batched_budget: float = PLAN_BUDGET_S):
+    """Plain (one problem at a time, on the first plain_sample problems: its
+    throughput does not depend on how many follow) against batched (all
+    n_problems at once, batched_budget of wall time); the FP64 reference and a
+    long batched run on the same sample supply best-cost candidates."""
     import numpy as np
 
     def make(entry):
@@ -328,22 +333,23 @@ def run_planner_leg(mp, synth):
                           tree_cap=1 << 15, roadmap_cap=1 << 13, max_iters=4096, seed=idx,
                           start=qs, goal=qg)
 
-    entries = plan_problems(mp, synth, PLAN_PROBLEMS)
+    entries = plan_problems(mp, synth, n_problems)
+    sample = entries[:plain_sample]
     traces = {"plain": [], "batched": []}
-    for e in entries:                                  # one problem at a time
+    for e in sample:                                   # one problem at a time
         p = make(e)
         mp.plan(p, PLAN_BUDGET_S)
         traces["plain"].append(mp.plan_trace(p)[:2])
         p.close()
     probs = [make(e) for e in entries]                 # all problems at once
     t0 = time.perf_counter()
-    mp.plan_batch(probs, PLAN_BUDGET_S)
+    mp.plan_batch(probs, batched_budget)
     batched_wall = time.perf_counter() - t0
     traces["batched"] = [mp.plan_trace(p)[:2] for p in probs]
     for p in probs:
         p.close()
     # a long batched run that only supplies best-cost candidates
-    probs = [make(e) for e in entries]
+    probs = [make(e) for e in sample]
     mp.plan_batch(probs, LONG_FACTOR * PLAN_BUDGET_S)
     long_final = [mp.plan_trace(p)[1] for p in probs]
     long_final = [c[-1] if len(c) else np.inf for c in long_final]
@@ -351,15 +357,21 @@ def run_planner_leg(mp, synth):
         p.close()
     # CPU baseline: the FP64 reference planner on the same problems (it cannot
     # finish a first roadmap on most of them within the GPU's budget)
-    ref_out, ref_workers, ref_wall = run_reference_planner(entries, LONG_FACTOR * PLAN_BUDGET_S)
+    ref_out, ref_workers, ref_wall = run_reference_planner(sample, LONG_FACTOR * PLAN_BUDGET_S)
     traces["cpu_reference"] = [(np.asarray(t), np.asarray(c)) for t, c, _, _ in ref_out]
     kinds = ("plain", "batched", "cpu_reference")
-    finals = [[c[-1] if len(c) else np.inf for t, c in traces[k]] for k in kinds]
-    best = np.min(np.asarray(finals + [long_final]), axis=0)
-    res = {"problems": len(entries), "budget_s": PLAN_BUDGET_S,
+    final = lambda c: c[-1] if len(c) else np.inf
+    best = np.array([final(c) for t, c in traces["batched"]])
+    m = len(sample)
+    for cand in ([final(c) for t, c in traces["plain"]], [final(c) for t, c in traces["cpu_reference"]],
+                 long_final):
+        best[:m] = np.minimum(best[:m], cand)
+    res = {"problems": len(entries), "plain_sample": m, "budget_s": PLAN_BUDGET_S,
+           "batched_budget_s": batched_budget,
            "robots": [int(e[1].K) for e in entries], "batched_wall_s": batched_wall,
            "best_cost_from": (f"minimum final cost over the plain and batched runs, a "
-                              f"{LONG_FACTOR}x-budget batched run and the FP64 reference")}
+                              f"{LONG_FACTOR}x-budget batched run and the FP64 reference "
+                              f"(the last three on the first {m} problems)")}
     for k in kinds:
         reach, ttfs = [], []
         for (t, c), b in zip(traces[k], best):
@@ -368,13 +380,14 @@ def run_planner_leg(mp, synth):
             if len(t):
                 ttfs.append(float(t[0]))
         solved = sum(r is not None for r in reach)
-        budget = PLAN_BUDGET_S * (LONG_FACTOR if k == "cpu_reference" else 1)
+        budget = {"plain": PLAN_BUDGET_S, "batched": batched_budget,
+                  "cpu_reference": LONG_FACTOR * PLAN_BUDGET_S}[k]
         spent = [r if r is not None else budget for r in reach]
         # plain: problems run back to back; batched: all at once; the CPU
         # reference: back to back on each of its cores (sum / cores)
         wall = (sum(spent) if k == "plain" else max(spent) if k == "batched"
                 else sum(spent) / ref_workers)
-        res[k] = {"solved_to_1.1x_best": solved, "wall_s": wall,
+        res[k] = {"problems": len(reach), "solved_to_1.1x_best": solved, "wall_s": wall,
                   "problems_per_s": solved / wall if wall > 0 else 0.0,
                   "ttfs_p50_s": float(np.percentile(ttfs, 50)) if ttfs else None,
                   "ttfs_p99_s": float(np.percentile(ttfs, 99)) if ttfs else None,
@@ -393,13 +406,14 @@ SERVE_RATE = 100.0
 SERVE_REQUESTS = 48
 
 
-def run_serving_leg(mp, synth, entries, best):
+def run_serving_leg(mp, synth, entries, best, rate: float = SERVE_RATE,
+                    n_requests: int = SERVE_REQUESTS):
     """Poisson stream of planning requests (the planner leg's problems, cycled)
     into the continuous-batching server.  Each request ends at 1.1x its
     problem's best known cost or after the planner budget.  Reports p50/p99
     time to first solution and to the target, and completed requests/s."""
     import numpy as np
-    arrivals = synth.poisson_arrivals(SERVE_RATE, SERVE_REQUESTS, seed=7)
+    arrivals = synth.poisson_arrivals(rate, n_requests, seed=7)
     reqs = []
     with mp.Server(max_slots=64) as srv:
         t0 = time.perf_counter()
@@ -429,7 +443,7 @@ def run_serving_leg(mp, synth, entries, best):
     first = tt[:, 1][tt[:, 1] >= 0]
     target = tt[:, 2][tt[:, 2] >= 0]
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
-    return {"rate_per_s": SERVE_RATE, "requests": len(reqs), "wall_s": wall,
+    return {"rate_per_s": rate, "requests": len(reqs), "wall_s": wall,
             "completed_per_s": len(reqs) / wall, "ttfs_p50_s": pct(first, 50),
             "ttfs_p99_s": pct(first, 99), "to_1.1x_best_p50_s": pct(target, 50),
             "to_1.1x_best_p99_s": pct(target, 99), "reached_1.1x_best": int(len(target)),
@@ -632,8 +646,12 @@ def run_ours(args) -> None:
     planner = serving = None
     if rank == 0 and not args.no_planner:
         from paper_2609_30644_gb300 import synth as _synth
-        planner, entries, best = run_planner_leg(mp, _synth)
-        serving = run_serving_leg(mp, _synth, entries, best)
+        planner, entries, best = run_planner_leg(
+            mp, _synth, args.planner_problems,
+            min(args.planner_problems, args.plain_sample), args.batched_budget)
+        serving = [run_serving_leg(mp, _synth, entries, best, float(r), args.serving_requests)
+                   for r in args.serving_rates.split(",")]
+        serving = serving[0] if len(serving) == 1 else serving
 
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
@@ -719,6 +737,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-planner", action="store_true",
                     help="skip the plain-vs-batched planner leg (problems/s to 1.1x best)")
+    ap.add_argument("--planner-problems", type=int, default=PLAN_PROBLEMS,
+                    help="problems planned at once in the batched planner leg (256: the "
+                         "batched workload of 2-8 arms)")
+    ap.add_argument("--plain-sample", type=int, default=PLAN_PROBLEMS,
+                    help="problems the plain planner and the CPU reference run, one at a time")
+    ap.add_argument("--batched-budget", type=float, default=PLAN_BUDGET_S,
+                    help="wall-clock budget of the batched planner run (s)")
+    ap.add_argument("--serving-rates", default=str(SERVE_RATE),
+                    help="comma-separated Poisson arrival rates of the serving leg (1/s)")
+    ap.add_argument("--serving-requests", type=int, default=SERVE_REQUESTS,
+                    help="requests per serving rate")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
