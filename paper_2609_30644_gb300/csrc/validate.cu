@@ -11,10 +11,11 @@
 //  * Per link, forward kinematics in registers (Rz, then the d/a/alpha
 //    offsets), then three levels of culling:
 //      1. tile level: the warp bounds the link's coarse spheres at its 32
-//         checkpoints by one sphere (around the box of the centres, from
-//         integer min/max warp reductions); lane i
-//         tests obstacle i (and the tile bound of earlier robots' link i)
-//         against it, and a ballot gives the candidate set;
+//         checkpoints by one sphere (around the exact box of the centres, from
+//         order-preserving integer min/max warp reductions); lane i tests
+//         obstacle i (and the tile bound of earlier links i) against it, and a
+//         ballot gives the candidate set -- when it is empty, nothing below
+//         runs for that obstacle group;
 //      2. checkpoint level ("coarse" stage of the paper): each lane tests its
 //         own link sphere against the candidates only;
 //      3. sphere level ("fine" stage): the warp-wide OR of the lanes' hit
@@ -40,16 +41,18 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsMax = 4;
 constexpr int kCounters = MRPOP_WORK_COUNTERS;
-// Absolute slack (m) added to tile bounds: covers the quantisation step and
-// FP32 rounding of the box centre and radius, so the tile test never drops a
-// candidate that a checkpoint's own link-level test would keep.
+// Absolute slack (m) added to tile bounds: covers FP32 rounding of the box
+// centre and half extents (a few ulps of workspace coordinates), so the tile
+// test never drops a candidate that a checkpoint's own link-level test keeps.
 constexpr float kTileSlack = 4e-4f;
-// Tile bounds quantise coarse centres to 0.1 mm integers so that min/max are
-// single warp reductions; within +-100 m the integers stay below 2^24 and
-// convert back to float exactly.  A tile with a centre beyond that range gets
-// an unbounded sphere (every obstacle becomes a candidate).
-constexpr float kQuant = 1e4f;
-constexpr float kQuantRange = 100.f;
+
+// Order-preserving map of floats to signed integers (and back): for finite
+// values a < b exactly when ord(a) < ord(b).
+__device__ __forceinline__ int ord(float v) {
+    const int k = __float_as_int(v);
+    return k ^ ((k >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float unord(int o) { return __int_as_float(o ^ ((o >> 31) & 0x7fffffff)); }
 
 enum Mode { kVerdict = 0, kClearance = 1, kCount = 2 };
 
@@ -295,30 +298,24 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
 
                     // Tile bound: one sphere around this link's coarse spheres at
                     // all 32 checkpoints of the tile (warp-uniform), built from the
-                    // axis-aligned box of the coarse centres quantised to 0.1 mm
-                    // (rounded outward) with single-instruction integer reductions.
+                    // exact axis-aligned box of the coarse centres: each float is
+                    // mapped to an order-preserving integer so that min and max are
+                    // single-instruction warp reductions.
                     float4 bnd = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (MODE != kClearance) {
-                        const float qx = fminf(fmaxf(cc.x, -kQuantRange), kQuantRange) * kQuant;
-                        const float qy = fminf(fmaxf(cc.y, -kQuantRange), kQuantRange) * kQuant;
-                        const float qz = fminf(fmaxf(cc.z, -kQuantRange), kQuantRange) * kQuant;
-                        const int x0 = __reduce_min_sync(kFull, __float2int_rd(qx));
-                        const int x1 = __reduce_max_sync(kFull, __float2int_ru(qx));
-                        const int y0 = __reduce_min_sync(kFull, __float2int_rd(qy));
-                        const int y1 = __reduce_max_sync(kFull, __float2int_ru(qy));
-                        const int z0 = __reduce_min_sync(kFull, __float2int_rd(qz));
-                        const int z1 = __reduce_max_sync(kFull, __float2int_ru(qz));
-                        const float ex = (float)(x1 - x0) * (0.5f / kQuant);
-                        const float ey = (float)(y1 - y0) * (0.5f / kQuant);
-                        const float ez = (float)(z1 - z0) * (0.5f / kQuant);
-                        bnd.x = (float)(x0 + x1) * (0.5f / kQuant);
-                        bnd.y = (float)(y0 + y1) * (0.5f / kQuant);
-                        bnd.z = (float)(z0 + z1) * (0.5f / kQuant);
-                        bnd.w = __fsqrt_rn(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + LC.w + kTileSlack;
-                        // outside the quantisation range the bound admits everything
-                        const bool far = !(fmaxf(fabsf(cc.x), fmaxf(fabsf(cc.y), fabsf(cc.z))) <
-                                           kQuantRange);
-                        if (__any_sync(kFull, far)) bnd.w = FLT_MAX * 2.f;
+                        const float x0 = unord(__reduce_min_sync(kFull, ord(cc.x)));
+                        const float x1 = unord(__reduce_max_sync(kFull, ord(cc.x)));
+                        const float y0 = unord(__reduce_min_sync(kFull, ord(cc.y)));
+                        const float y1 = unord(__reduce_max_sync(kFull, ord(cc.y)));
+                        const float z0 = unord(__reduce_min_sync(kFull, ord(cc.z)));
+                        const float z1 = unord(__reduce_max_sync(kFull, ord(cc.z)));
+                        const float ex = 0.5f * (x1 - x0), ey = 0.5f * (y1 - y0),
+                                    ez = 0.5f * (z1 - z0);
+                        bnd.x = 0.5f * (x0 + x1);
+                        bnd.y = 0.5f * (y0 + y1);
+                        bnd.z = 0.5f * (z0 + z1);
+                        bnd.w = __fsqrt_ru(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + LC.w + kTileSlack;
+                        if (!(bnd.w < FLT_MAX)) bnd.w = FLT_MAX * 2.f;  // never for finite inputs
                         if (MODE == kCount && lane == 0) cnt[9] += 1;
                     }
                     if (store) {
@@ -331,6 +328,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                         if (lane == 0) tb[l] = bnd;
                         __syncwarp();
                     }
+                    bool vote = false;  // a fine stage ran: the early-exit vote is due
                     if (ns > 0) {
                         float4 pw[SPL];
                         bool have = false;
@@ -353,7 +351,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                         // ---- robot vs obstacle spheres
                         for (int c0 = 0; c0 < NS; c0 += 32) {
                             const int cn = min(32, NS - c0);
-                            unsigned own = 0;
+                            unsigned own = 0, cand = 0;
                             if (MODE == kClearance) {
                                 own = low_mask(cn);
                             } else {
@@ -364,7 +362,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     const float th2 = bnd.w + ob.w + m;
                                     h = d2 < th2 * th2;
                                 }
-                                const unsigned cand = __ballot_sync(kFull, h);
+                                cand = __ballot_sync(kFull, h);
                                 unsigned cm = cand;
                                 while (cm) {
                                     const int o = __ffs(cm) - 1;
@@ -379,6 +377,8 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     if (active) cnt[2] += __popc(cand);
                                 }
                             }
+                            if (MODE != kClearance && cand == 0u) continue;  // nothing near
+                            vote = true;
                             if (ra) {
                                 hit |= fine_reassigned<false>(own, c0, ns, sf, F, m, tab, t, fr,
                                                               lane);
@@ -419,7 +419,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                         // that encloses the fine spheres stays conservative)
                         for (int c0 = 0; c0 < NC; c0 += 32) {
                             const int cn = min(32, NC - c0);
-                            unsigned own = 0;
+                            unsigned own = 0, cand = 0;
                             if (MODE == kClearance) {
                                 own = low_mask(cn);
                             } else {
@@ -431,7 +431,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     const float th2 = bnd.w + m;
                                     h = d2 < th2 * th2;
                                 }
-                                const unsigned cand = __ballot_sync(kFull, h);
+                                cand = __ballot_sync(kFull, h);
                                 unsigned cm = cand;
                                 while (cm) {
                                     const int o = __ffs(cm) - 1;
@@ -446,6 +446,8 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     if (active) cnt[10] += __popc(cand);
                                 }
                             }
+                            if (MODE != kClearance && cand == 0u) continue;  // nothing near
+                            vote = true;
                             if (ra) {
                                 hit |= fine_reassigned<true>(own, c0, ns, sf, F, m, tab, t, fr,
                                                              lane);
@@ -490,7 +492,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                             ((unsigned long long)(unsigned)__float_as_int(LB.w) << l0);
                         const unsigned pm0 = (unsigned)pm, pm1 = (unsigned)(pm >> 32);
                         if (pm) {
-                            unsigned own0 = 0, own1 = 0;
+                            unsigned own0 = 0, own1 = 0, candp = 0;
                             if (MODE == kClearance) {
                                 own0 = pm0;
                                 own1 = pm1;
@@ -540,7 +542,10 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     if (lane == 0) cnt[8] += __popcll(pm);
                                     if (active) cnt[3] += __popc(cand0) + __popc(cand1);
                                 }
+                                candp = cand0 | cand1;
                             }
+                            if (MODE == kClearance || candp != 0u) {
+                            vote = true;
                             const unsigned w0 = MODE == kClearance ? own0 : __reduce_or_sync(kFull, own0);
                             const unsigned w1 = MODE == kClearance ? own1 : __reduce_or_sync(kFull, own1);
                             if (MODE == kCount && active) {
@@ -591,11 +596,13 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                     }
                                 }
                             }
+                            }  // candidates near link l
                         }
                         if (MODE == kCount && active && own_any) cnt[7] += ns;
                     }
                     Tm = advance(F, LA.x, LA.y, LA.z, LA.w);
-                    if (MODE != kClearance && __any_sync(kFull, hit)) goto tile_done;
+                    // a hit can only come from a fine stage of this link
+                    if (MODE != kClearance && vote && __any_sync(kFull, hit)) goto tile_done;
                 }
             }
         tile_done:
