@@ -489,10 +489,14 @@ def run_ours(args) -> None:
         workers = os.cpu_count() or 1
         n = 256 * workers
         v, wall = oracle_sample(n, workers)
+        v1, wall1 = oracle_sample(256, 1)
         cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
                "sample": f"{n} edges (every {E_EDGES // n}th of the batch) with {n} nearest "
                          f"queries over {NN_TREE} vertices, {n // 64} radius queries and a "
-                         f"{n + 1}-vertex path cost; {wall:.1f} s wall on {workers} processes"}
+                         f"{n + 1}-vertex path cost; {wall:.1f} s wall on {workers} processes",
+               "single_core_value": v1,
+               "single_core_sample": f"256 edges of the same composition on one process, "
+                                     f"{wall1:.1f} s"}
 
     import numpy as np
     import torch
@@ -670,6 +674,17 @@ def run_ours(args) -> None:
         # (query, vertex) pair (3 D flops); the filter of the candidates is extra
         nn_flops = float(NN_QUERIES) * NN_TREE * 3 * scene.D
         nn_achieved = nn_flops / (statistics.mean(nn_ms) / 1000.0) / 1e12
+        # HBM side of the same launches: each input is read once, each output
+        # written once (algorithmic bytes)
+        hbm_peak = float(peaks.get("hbm_gbs") or 6658.3)
+        nn_bytes = 4.0 * (scene.D + 1) * NN_TREE + 4.0 * (scene.D + 1) * NN_QUERIES + 8.0 * NN_QUERIES
+        val_bytes = 2 * 4.0 * scene.D * E_EDGES + E_EDGES
+        hbm = {}
+        for k, b, ms_ in (("nearest", nn_bytes, statistics.mean(nn_ms)),
+                          ("validate_mixed", val_bytes, statistics.mean(val_ms))):
+            gbs = b / (ms_ / 1000.0) / 1e9
+            hbm[k] = {"bytes_per_launch": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": gbs / hbm_peak}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -707,6 +722,7 @@ def run_ours(args) -> None:
                                                                     "validate_kernel_table_pair"),
                                         "flops_per_launch": flops_per_launch,
                                         "share_of_step": statistics.mean(val_ms) / ms_per_step},
+            "roofline_hbm": hbm,
             "kernel_ms": {"validate": statistics.mean(val_ms), "nearest": statistics.mean(nn_ms),
                           "neighbors": statistics.mean(rm_ms), "path_cost": statistics.mean(pc_ms)},
             "valid_fraction": float(valid.float().mean().item()),
