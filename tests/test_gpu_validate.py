@@ -324,3 +324,40 @@ def test_self_collision_parity(mp, orc, name, n_edges, masked):
     with mp.Problem(scene, resolution=0.02) as p:
         v0 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
     _check_verdicts(v0, ref0, 0.0)
+
+
+def _max_size_scene():
+    """At the ABI limits: 4 planar arms of 16 links (64 links, the maximum
+    composite dimension) with 16 spheres on every link (1,024 robot spheres),
+    and 512 sphere + 512 cuboid obstacles (the obstacle maximum)."""
+    bases = [synth._yaw_base(x, y, 0.0, a) for x, y, a in   # arms point outward
+             ((-0.45, -0.45, -2.3), (0.45, -0.45, -0.8), (-0.45, 0.45, 2.3), (0.45, 0.45, 0.8))]
+    arms = [synth.planar_arm(b, n_links=16, link_len=0.05, spheres_per_link=16, radius=0.008)
+            for b in bases]
+    for a in arms:   # joint limits +-0.5 rad: a 16-link chain folds onto itself less often
+        a.q_lo[:] = -0.5
+        a.q_hi[:] = 0.5
+    rng = np.random.default_rng(77)
+    sph, cub = synth._clutter(rng, 512, 512, (-1.6, -1.6, -0.3), (1.6, 1.6, 0.3),
+                              [a.base for a in arms], keep_out=0.1)
+    sph[:, 3] *= 0.12
+    cub[:, 3:6] *= 0.12
+    return synth.Scene(arms, sph, cub, "max_size")
+
+
+@pytest.mark.parametrize("self_collision", [False, True])
+def test_max_size_scene(mp, orc, self_collision):
+    """64 links, 16 spheres per link, 1,024 obstacles (one warp per block fits
+    the tables and scratch): verdicts and clearances against the oracle."""
+    scene = _max_size_scene()
+    assert scene.D == 64 and sum(r.n_spheres for r in scene.robots) == 1024
+    o = orc.OracleScene(scene, self_collision=self_collision)
+    qa, qb = synth.candidate_edges(scene, 24, seed=3, step_lo=0.05, step_hi=0.4)
+    ref = o.validate_edges(qa, qb, 0.02, 0.0)
+    assert 0 < ref["valid"].sum() < 24
+    with mp.Problem(scene, resolution=0.02, self_collision=self_collision) as p:
+        v = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+        c = mp.edge_clearance(p, _dev(qa[:, :6]), _dev(qb[:, :6])).cpu().numpy().astype(np.float64)
+    _check_verdicts(v, ref, 0.0)
+    err = np.abs(c - ref["min_clear"][:6])
+    assert (err <= REL * (1 + np.abs(ref["min_clear"][:6]))).all(), err.max()
