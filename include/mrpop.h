@@ -65,7 +65,9 @@ typedef struct mrpop_problem mrpop_problem; /* opaque, library-owned */
  *               non-decreasing; at most MRPOP_MAX_SPHERES_PER_LINK per link
  *   sphere_xyzr host [n_spheres][4] centre in frame F_j' (joint j's frame
  *               after its rotation Rz(q_j + theta_offset_j)) and radius
- *   base        row-major 3x4 [R | t] pose of the first joint's frame
+ *   base        row-major 3x4 [R | t] pose of the first joint's frame; R a
+ *               proper rotation (R^T R = I within 1e-3, det R > 0; EINVAL
+ *               otherwise)
  *   self_mask   host [dof] or NULL: the adjacency mask used when the
  *               config's self_collision is 1.  Bit i of self_mask[j] (i < j)
  *               set means links i and j of this robot are tested against

@@ -1,6 +1,7 @@
 // C ABI entry points: problem creation (geometry tables), argument checking
 // and dispatch to the kernel launchers.  Every entry point returns a status
 // and records a message for mrpop_last_error(); nothing here aborts.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -111,6 +112,21 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
         for (int j = 0; j < r.dof; ++j)
             if (!(r.q_lo[j] <= r.q_hi[j]))
                 return set_error(MRPOP_EINVAL, "robot %d joint %d: q_lo > q_hi", k, j);
+        {   // the base rotation must be proper: R^T R = I within 1e-3, det R > 0
+            const float *b = r.base;
+            double worst = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double dot = 0.0;
+                    for (int m = 0; m < 3; ++m) dot += (double)b[4 * m + i] * b[4 * m + j];
+                    worst = std::max(worst, std::fabs(dot - (i == j ? 1.0 : 0.0)));
+                }
+            const double det = (double)b[0] * ((double)b[5] * b[10] - (double)b[6] * b[9]) -
+                               (double)b[1] * ((double)b[4] * b[10] - (double)b[6] * b[8]) +
+                               (double)b[2] * ((double)b[4] * b[9] - (double)b[5] * b[8]);
+            if (!(worst <= 1e-3) || !(det > 0.0))
+                return set_error(MRPOP_EINVAL, "robot %d: base is not a proper rotation", k);
+        }
         int prev = 0;
         for (int s = 0; s < r.n_spheres; ++s) {
             const int l = r.sphere_link[s];

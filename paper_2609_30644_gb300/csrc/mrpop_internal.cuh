@@ -37,7 +37,10 @@ struct Tables {
 
 constexpr int kLinkF4 = 3;
 constexpr int kCuboidF4 = 5;
-constexpr int kXfFloats = 12;  // stored link frame: R (9), t (3)
+// Stored link frame: the first two columns of R and t (the third column of a
+// proper rotation is their cross product).
+constexpr int kXfFloats = 9;
+constexpr int kFrFloats = 12;  // a full frame, R (9) and t (3)
 
 // Parameters of one validation launch (one problem, one batch of edges).
 struct VParams {
@@ -69,7 +72,7 @@ struct VParams {
 inline int validate_warp_floats(const Tables &t, int fine) {
     const int dpad = (t.L + 3) & ~3;
     const int nstore = t.selfcol ? t.L : t.link0[t.K - 1];
-    return 2 * dpad + 4 * nstore + nstore * kXfFloats * 32 + (fine ? kXfFloats * 32 + 64 : 0);
+    return 2 * dpad + 4 * nstore + nstore * kXfFloats * 32 + (fine ? kFrFloats * 32 + 64 : 0);
 }
 
 struct DeviceProblem {

@@ -27,8 +27,9 @@
 //    proportion to the fine-test load) balances work across motions; here the
 //    warp-uniform union mask keeps all 32 lanes busy on the same tests instead.
 //  * Geometry tables are staged once per block into shared memory; link
-//    frames of robots 0..K-2 go to a per-warp shared scratch [link][15][lane]
-//    (lane-contiguous, conflict-free) for the robot-robot tests.
+//    frames of robots 0..K-2 go to a per-warp shared scratch [link][9][lane]
+//    (two rotation columns and the translation; lane-contiguous,
+//    conflict-free) for the robot-robot tests.
 #include <cfloat>
 #include <cmath>
 #include <algorithm>
@@ -118,6 +119,26 @@ __device__ __forceinline__ float box_dist2(float px, float py, float pz, const f
     return fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
 }
 
+// Link frames kept for later links' robot-robot tests, lane-contiguous
+// ([component][32]): columns 0 and 1 of R, then t; column 2 is rebuilt as
+// their cross product (every frame is a proper rotation: the base is checked
+// at create time and each joint multiplies by rotations).
+__device__ __forceinline__ void store_frame(float *x, const Frame &F) {
+    x[0] = F.r[0]; x[32] = F.r[3]; x[64] = F.r[6];
+    x[96] = F.r[1]; x[128] = F.r[4]; x[160] = F.r[7];
+    x[192] = F.t[0]; x[224] = F.t[1]; x[256] = F.t[2];
+}
+__device__ __forceinline__ Frame load_frame(const float *x) {
+    Frame F;
+    F.r[0] = x[0]; F.r[3] = x[32]; F.r[6] = x[64];
+    F.r[1] = x[96]; F.r[4] = x[128]; F.r[7] = x[160];
+    F.t[0] = x[192]; F.t[1] = x[224]; F.t[2] = x[256];
+    F.r[2] = F.r[3] * F.r[7] - F.r[6] * F.r[4];
+    F.r[5] = F.r[6] * F.r[1] - F.r[0] * F.r[7];
+    F.r[8] = F.r[0] * F.r[4] - F.r[3] * F.r[1];
+    return F;
+}
+
 __device__ __forceinline__ Frame load_base(const float4 *tab, const Tables &t, int b) {
     const float4 r0 = tab[t.off_base + 3 * b], r1 = tab[t.off_base + 3 * b + 1],
                  r2 = tab[t.off_base + 3 * b + 2];
@@ -164,7 +185,7 @@ __device__ __forceinline__ bool fine_reassigned(unsigned own, int c0, int ns, in
     }
     const int total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return false;
-    unsigned *own_s = reinterpret_cast<unsigned *>(fr + kXfFloats * 32);
+    unsigned *own_s = reinterpret_cast<unsigned *>(fr + kFrFloats * 32);
     int *pre_s = reinterpret_cast<int *>(own_s + 32);
 #pragma unroll
     for (int c = 0; c < 9; ++c) fr[c * 32 + lane] = F.r[c];
@@ -235,7 +256,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
     float *ws = reinterpret_cast<float *>(sm4 + P.t.n_f4) + (size_t)warp * P.warp_floats;
     float *qa_s = ws, *dq_s = ws + P.dpad;
     float4 *tb = reinterpret_cast<float4 *>(ws + 2 * P.dpad);      // tile bounds [nstore]
-    float *xf = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][12][32]
+    float *xf = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][9][32]
     float *fr = xf + P.nstore * kXfFloats * 32;                     // reassignment scratch
     constexpr bool ra = MODE == kVerdict && RA;  // reassigned fine obstacle tests
 
@@ -319,12 +340,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                         if (MODE == kCount && lane == 0) cnt[9] += 1;
                     }
                     if (store) {
-                        float *x = xf + (size_t)l * kXfFloats * 32 + lane;
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) x[c * 32] = F.r[c];
-                        x[9 * 32] = F.t[0];
-                        x[10 * 32] = F.t[1];
-                        x[11 * 32] = F.t[2];
+                        store_frame(xf + (size_t)l * kXfFloats * 32 + lane, F);
                         if (lane == 0) tb[l] = bnd;
                         __syncwarp();
                     }
@@ -520,14 +536,9 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                         const int bit = __ffs(cm) - 1;
                                         cm &= cm - 1;
                                         const int i = bit + 32 * w;
-                                        const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
                                         const float4 LCi = tab[t.off_link + kLinkF4 * i + 2];
-                                        Frame Fi;
-#pragma unroll
-                                        for (int c = 0; c < 9; ++c) Fi.r[c] = x[c * 32];
-                                        Fi.t[0] = x[9 * 32];
-                                        Fi.t[1] = x[10 * 32];
-                                        Fi.t[2] = x[11 * 32];
+                                        const Frame Fi =
+                                            load_frame(xf + (size_t)i * kXfFloats * 32 + lane);
                                         const float3 ci = apply(Fi, LCi.x, LCi.y, LCi.z);
                                         const float d2 = dist2(cc.x, cc.y, cc.z, ci.x, ci.y, ci.z);
                                         const float th2 = LC.w + LCi.w + m;
@@ -568,13 +579,8 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                 while (mm) {
                                     const int i = __ffs(mm) - 1 + 32 * w;
                                     mm &= mm - 1;
-                                    const float *x = xf + (size_t)i * kXfFloats * 32 + lane;
-                                    Frame Fi;
-#pragma unroll
-                                    for (int c = 0; c < 9; ++c) Fi.r[c] = x[c * 32];
-                                    Fi.t[0] = x[9 * 32];
-                                    Fi.t[1] = x[10 * 32];
-                                    Fi.t[2] = x[11 * 32];
+                                    const Frame Fi =
+                                        load_frame(xf + (size_t)i * kXfFloats * 32 + lane);
                                     const float4 LBi = tab[t.off_link + kLinkF4 * i + 1];
                                     const int sfi = __float_as_int(LBi.y), nsi = __float_as_int(LBi.z);
                                     for (int s2 = 0; s2 < nsi; ++s2) {

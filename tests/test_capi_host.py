@@ -55,6 +55,8 @@ def _scene():
     (lambda s: s.robots[0].sphere_xyzr.__setitem__((0, 3), -1.0), "radius"),
     (lambda s: s.obs_spheres.__setitem__((0, 3), np.nan), "non-finite"),
     (lambda s: s.robots[1].base.__setitem__(3, np.inf), "non-finite"),
+    (lambda s: s.robots[0].base.__setitem__(slice(8, 11), [0.0, 0.0, -1.0]), "proper rotation"),
+    (lambda s: s.robots[0].base.__setitem__(0, 1.5), "proper rotation"),
 ])
 def test_create_rejects_malformed(capi, mutate, msg):
     s = _scene()
