@@ -37,9 +37,10 @@ struct Tables {
 
 constexpr int kLinkF4 = 3;
 constexpr int kCuboidF4 = 5;
-// Stored link frame: the first two columns of R and t (the third column of a
-// proper rotation is their cross product).
-constexpr int kXfFloats = 9;
+// Kept per stored link and checkpoint for later links' robot-robot tests: the
+// link's coarse sphere centre (3 floats); the rare fine tests rebuild the
+// link's frame along its chain instead of keeping it.
+constexpr int kXcFloats = 3;
 constexpr int kFrFloats = 12;  // a full frame, R (9) and t (3)
 
 // Parameters of one validation launch (one problem, one batch of edges).
@@ -72,7 +73,7 @@ struct VParams {
 inline int validate_warp_floats(const Tables &t, int fine) {
     const int dpad = (t.L + 3) & ~3;
     const int nstore = t.selfcol ? t.L : t.link0[t.K - 1];
-    return 2 * dpad + 4 * nstore + nstore * kXfFloats * 32 + (fine ? kFrFloats * 32 + 64 : 0);
+    return 2 * dpad + 4 * nstore + nstore * kXcFloats * 32 + (fine ? kFrFloats * 32 + 64 : 0);
 }
 
 struct DeviceProblem {

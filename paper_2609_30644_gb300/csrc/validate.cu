@@ -26,10 +26,10 @@
 //  * The paper's own design (4 threads per motion, then threads reassigned in
 //    proportion to the fine-test load) balances work across motions; here the
 //    warp-uniform union mask keeps all 32 lanes busy on the same tests instead.
-//  * Geometry tables are staged once per block into shared memory; link
-//    frames of robots 0..K-2 go to a per-warp shared scratch [link][9][lane]
-//    (two rotation columns and the translation; lane-contiguous,
-//    conflict-free) for the robot-robot tests.
+//  * Geometry tables are staged once per block into shared memory; the
+//    coarse centres of robots 0..K-2 go to a per-warp shared scratch
+//    [link][3][lane] (lane-contiguous, conflict-free) for the robot-robot
+//    tests, whose rare fine stage rebuilds the other link's frame.
 #include <cfloat>
 #include <cmath>
 #include <algorithm>
@@ -119,26 +119,6 @@ __device__ __forceinline__ float box_dist2(float px, float py, float pz, const f
     return fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
 }
 
-// Link frames kept for later links' robot-robot tests, lane-contiguous
-// ([component][32]): columns 0 and 1 of R, then t; column 2 is rebuilt as
-// their cross product (every frame is a proper rotation: the base is checked
-// at create time and each joint multiplies by rotations).
-__device__ __forceinline__ void store_frame(float *x, const Frame &F) {
-    x[0] = F.r[0]; x[32] = F.r[3]; x[64] = F.r[6];
-    x[96] = F.r[1]; x[128] = F.r[4]; x[160] = F.r[7];
-    x[192] = F.t[0]; x[224] = F.t[1]; x[256] = F.t[2];
-}
-__device__ __forceinline__ Frame load_frame(const float *x) {
-    Frame F;
-    F.r[0] = x[0]; F.r[3] = x[32]; F.r[6] = x[64];
-    F.r[1] = x[96]; F.r[4] = x[128]; F.r[7] = x[160];
-    F.t[0] = x[192]; F.t[1] = x[224]; F.t[2] = x[256];
-    F.r[2] = F.r[3] * F.r[7] - F.r[6] * F.r[4];
-    F.r[5] = F.r[6] * F.r[1] - F.r[0] * F.r[7];
-    F.r[8] = F.r[0] * F.r[4] - F.r[3] * F.r[1];
-    return F;
-}
-
 __device__ __forceinline__ Frame load_base(const float4 *tab, const Tables &t, int b) {
     const float4 r0 = tab[t.off_base + 3 * b], r1 = tab[t.off_base + 3 * b + 1],
                  r2 = tab[t.off_base + 3 * b + 2];
@@ -148,6 +128,13 @@ __device__ __forceinline__ Frame load_base(const float4 *tab, const Tables &t, i
     T.r[6] = r2.x; T.r[7] = r2.y; T.r[8] = r2.z; T.t[2] = r2.w;
     return T;
 }
+
+// Frame F_i' of link i at the lane's checkpoint (parameter tk), rebuilt along
+// its robot's chain from the base with the same operations, in the same order,
+// as the main forward-kinematics loop.  Used only by fine robot-robot tests,
+// which are rare; the coarse tests read the stored coarse centres.
+__device__ __forceinline__ Frame link_frame(const float4 *tab, const Tables &t, const float *qa_s,
+                                            const float *dq_s, int i, float tk);
 
 // Joint-angle sine and cosine: reduce the angle to [-pi, pi] with one fused
 // multiply-add, then the hardware approximation __sincosf (absolute error
@@ -237,6 +224,23 @@ __device__ __forceinline__ bool fine_reassigned(unsigned own, int c0, int ns, in
     return hit;
 }
 
+__device__ __forceinline__ Frame link_frame(const float4 *tab, const Tables &t, const float *qa_s,
+                                            const float *dq_s, int i, float tk) {
+    int b = 0;
+    while (t.link0[b + 1] <= i) ++b;
+    Frame Tm = load_base(tab, t, b);
+    for (int l = t.link0[b];; ++l) {
+        const float4 LA = tab[t.off_link + kLinkF4 * l];
+        const float4 LB = tab[t.off_link + kLinkF4 * l + 1];
+        const float th = __fmaf_rn(tk, dq_s[l], qa_s[l]) + LB.x;
+        float sn, cs;
+        joint_sincos(th, &sn, &cs);
+        const Frame F = rotz(Tm, cs, sn);
+        if (l == i) return F;
+        Tm = advance(F, LA.x, LA.y, LA.z, LA.w);
+    }
+}
+
 // Interval count n = max(1, ceil(|dq|_2 / res)) in FP32 with a sequential
 // fused multiply-add sum (the oracle takes the same integer decision in FP32).
 __device__ __forceinline__ int interval_count(const float *dq, int D, float res, float *len_out) {
@@ -256,8 +260,8 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
     float *ws = reinterpret_cast<float *>(sm4 + P.t.n_f4) + (size_t)warp * P.warp_floats;
     float *qa_s = ws, *dq_s = ws + P.dpad;
     float4 *tb = reinterpret_cast<float4 *>(ws + 2 * P.dpad);      // tile bounds [nstore]
-    float *xf = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][9][32]
-    float *fr = xf + P.nstore * kXfFloats * 32;                     // reassignment scratch
+    float *xc = ws + 2 * P.dpad + 4 * P.nstore;                     // [nstore][3][32]
+    float *fr = xc + P.nstore * kXcFloats * 32;                     // reassignment scratch
     constexpr bool ra = MODE == kVerdict && RA;  // reassigned fine obstacle tests
 
     for (int i = threadIdx.x; i < P.t.n_f4; i += blockDim.x) tab[i] = P.blob[i];
@@ -340,7 +344,10 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                         if (MODE == kCount && lane == 0) cnt[9] += 1;
                     }
                     if (store) {
-                        store_frame(xf + (size_t)l * kXfFloats * 32 + lane, F);
+                        float *x = xc + (size_t)l * kXcFloats * 32 + lane;
+                        x[0] = cc.x;
+                        x[32] = cc.y;
+                        x[64] = cc.z;
                         if (lane == 0) tb[l] = bnd;
                         __syncwarp();
                     }
@@ -537,10 +544,8 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                         cm &= cm - 1;
                                         const int i = bit + 32 * w;
                                         const float4 LCi = tab[t.off_link + kLinkF4 * i + 2];
-                                        const Frame Fi =
-                                            load_frame(xf + (size_t)i * kXfFloats * 32 + lane);
-                                        const float3 ci = apply(Fi, LCi.x, LCi.y, LCi.z);
-                                        const float d2 = dist2(cc.x, cc.y, cc.z, ci.x, ci.y, ci.z);
+                                        const float *x = xc + (size_t)i * kXcFloats * 32 + lane;
+                                        const float d2 = dist2(cc.x, cc.y, cc.z, x[0], x[32], x[64]);
                                         const float th2 = LC.w + LCi.w + m;
                                         own |= (d2 < th2 * th2) ? (1u << bit) : 0u;
                                     }
@@ -579,8 +584,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                 while (mm) {
                                     const int i = __ffs(mm) - 1 + 32 * w;
                                     mm &= mm - 1;
-                                    const Frame Fi =
-                                        load_frame(xf + (size_t)i * kXfFloats * 32 + lane);
+                                    const Frame Fi = link_frame(tab, t, qa_s, dq_s, i, tk);
                                     const float4 LBi = tab[t.off_link + kLinkF4 * i + 1];
                                     const int sfi = __float_as_int(LBi.y), nsi = __float_as_int(LBi.z);
                                     for (int s2 = 0; s2 < nsi; ++s2) {
