@@ -439,18 +439,38 @@ __global__ void k_rm_sample(const float *lo, const float *hi, int dof, int n,
     for (int d = 0; d < dof; ++d) out[(size_t)d * n + i] = lo[d] + rng.uniform() * (hi[d] - lo[d]);
 }
 
-// Append up to `want` valid candidates (in candidate order) to V_r.
-__global__ void k_rm_append(const float *cand, const uint8_t *valid, int n, int dof, int want,
-                            float *V, int rcap, int *count) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int c = *count, added = 0;
-    for (int i = 0; i < n && added < want && c < rcap; ++i) {
-        if (!valid[i]) continue;
-        for (int d = 0; d < dof; ++d) V[(size_t)d * rcap + c] = cand[(size_t)d * n + i];
-        ++c;
-        ++added;
+// Append up to `want` valid candidates (in candidate order) to V_r: one
+// block; a block-wide prefix count of the valid flags gives every candidate
+// its slot, chunk after chunk.
+constexpr int kAppendThreads = 256;
+__global__ void __launch_bounds__(kAppendThreads)
+k_rm_append(const float *cand, const uint8_t *valid, int n, int dof, int want, float *V, int rcap,
+            int *count) {
+    __shared__ int warp_sum[kAppendThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c0 = *count;
+    const int room = max(0, min(want, rcap - c0));
+    __syncthreads();  // every thread has read *count before thread 0 rewrites it
+    int base = 0;     // valid candidates before the current chunk
+    for (int i0 = 0; i0 < n && base < room; i0 += kAppendThreads) {
+        const int i = i0 + threadIdx.x;
+        const bool v = i < n && valid[i];
+        const unsigned bal = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) warp_sum[w] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < kAppendThreads / 32; ++k) {
+            before += k < w ? warp_sum[k] : 0;
+            total += warp_sum[k];
+        }
+        const int pos = base + before + __popc(bal & ((1u << lane) - 1u));
+        if (v && pos < room)
+            for (int d = 0; d < dof; ++d) V[(size_t)d * rcap + c0 + pos] = cand[(size_t)d * n + i];
+        base += total;
+        __syncthreads();  // warp_sum is rewritten by the next chunk
     }
-    *count = c;
+    if (threadIdx.x == 0) *count = c0 + min(base, room);
 }
 
 __global__ void k_rm_gather(const float *V, int rcap, int dof, int first, int m, float *out) {
@@ -485,16 +505,31 @@ __global__ void k_rm_edges(const float *V, int rcap, int dof, int first, int m,
     eb[e] = v;
 }
 
-// Roadmap edges in candidate order (one thread: the adjacency lists, capped
-// at kKmax, do not depend on thread timing).
+// Roadmap edges in candidate order, one warp: edges go in chunks of 32; in a
+// chunk the new-vertex ends are appended first, then the neighbour ends, and
+// lanes with the same target vertex take consecutive slots in lane order
+// (match + rank), so the adjacency lists (capped at kKmax) do not depend on
+// thread timing.  The direction oracle's choice does not depend on the order
+// within a list (ties go to the lowest vertex index).
 __global__ void k_rm_link(const uint8_t *valid, const int *ea, const int *eb, int E, int *adj,
                           int *deg) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int e = 0; e < E; ++e) {
-        if (!valid[e] || ea[e] < 0) continue;
-        const int a = ea[e], b = eb[e];
-        if (deg[a] < kKmax) adj[(size_t)a * kKmax + deg[a]++] = b;
-        if (deg[b] < kKmax) adj[(size_t)b * kKmax + deg[b]++] = a;
+    const int lane = threadIdx.x;
+    for (int e0 = 0; e0 < E; e0 += 32) {
+        const int e = e0 + lane;
+        const bool ok = e < E && valid[e] && ea[e] >= 0;
+        const int a = ok ? ea[e] : -1, b = ok ? eb[e] : -1;
+        for (int side = 0; side < 2; ++side) {
+            const int x = side == 0 ? a : b, y = side == 0 ? b : a;
+            const unsigned grp = __match_any_sync(0xffffffffu, x);
+            const int d0 = x >= 0 ? deg[x] : 0;
+            __syncwarp();  // the whole group has read deg[x]
+            if (x >= 0) {
+                const int slot = d0 + __popc(grp & ((1u << lane) - 1u));
+                if (slot < kKmax) adj[(size_t)x * kKmax + slot] = y;
+                if (lane == __ffs(grp) - 1) deg[x] = min(d0 + __popc(grp), kKmax);
+            }
+            __syncwarp();  // deg[] is read again by the other side
+        }
     }
 }
 
@@ -880,7 +915,8 @@ static mrpop_status rm_phase1(Planner *pl, int k, cudaStream_t st) {
     PL_TRY(cudaGetLastError());
     ST_TRY(launch_validate(r.sub, r.cand, r.cand, nc, r.cvalid, nullptr, nullptr, nullptr, nullptr,
                            st));
-    k_rm_append<<<1, 32, 0, st>>>(r.cand, r.cvalid, nc, dof, want, r.q, rcap, pl->rm_n + k);
+    k_rm_append<<<1, kAppendThreads, 0, st>>>(r.cand, r.cvalid, nc, dof, want, r.q, rcap,
+                                              pl->rm_n + k);
     PL_TRY(cudaGetLastError());
     PL_TRY(cudaMemcpyAsync(pl->h_small + 2 * k, pl->rm_n + k, sizeof(int), cudaMemcpyDeviceToHost, st));
     return MRPOP_OK;

@@ -33,6 +33,10 @@
 #include <cfloat>
 #include <cmath>
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
 
 #include "mrpop_internal.cuh"
 
@@ -673,14 +677,44 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_batch_kernel(const VP
     validate_body<kVerdict, SPL, RA>(sP, sm4);
 }
 
+// Resident blocks per SM of a validation kernel for a launch shape.  The
+// kernel's dynamic shared-memory limit is raised to the device maximum once,
+// and occupancies are cached per (kernel, device, threads, bytes): the
+// planner issues thousands of small validation launches, and these host
+// queries would otherwise cost more than the launches themselves.
+static mrpop_status cached_occupancy(const void *kern, int device, int smem_optin, int threads,
+                                     size_t smem, int *bps) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> occ;
+    static std::set<std::pair<const void *, int>> raised;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!raised.count({kern, device})) {
+        cudaFuncAttributes fa{};
+        MRPOP_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        const int limit = smem_optin - (int)fa.sharedSizeBytes;  // static shared memory counts too
+        MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            limit));
+        raised.insert({kern, device});
+    }
+    const auto key = std::make_tuple(kern, device, threads, smem);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+        int b = 0;
+        MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem));
+        it = occ.emplace(key, b).first;
+    }
+    *bps = it->second;
+    return MRPOP_OK;
+}
+
 template <int MODE, int SPL, bool RA>
 mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
                          cudaStream_t st) {
     auto kern = validate_kernel<MODE, SPL, RA>;
-    MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
     int bps = 0;
-    MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, warps * 32, smem));
+    const mrpop_status os = cached_occupancy((const void *)kern, p->device, (int)p->smem_optin,
+                                             warps * 32, smem, &bps);
+    if (os != MRPOP_OK) return os;
     if (bps < 1) return set_error(MRPOP_EINVAL, "validation kernel does not fit on an SM");
     const int64_t want = (V.E + warps - 1) / warps;
     const int grid = (int)std::min<int64_t>((int64_t)p->num_sms * bps, want);
@@ -820,8 +854,11 @@ template <int SPL, bool RA>
 static mrpop_status batch_spl(const VParams *d_params, int nslots, int warps, int blocks_per_slot,
                               size_t smem, cudaStream_t st) {
     auto kern = validate_batch_kernel<SPL, RA>;
-    MRPOP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+    int dev = 0, optin = 0, bps = 0;
+    MRPOP_CUDA_TRY(cudaGetDevice(&dev));
+    MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const mrpop_status os = cached_occupancy((const void *)kern, dev, optin, warps * 32, smem, &bps);
+    if (os != MRPOP_OK) return os;
     dim3 grid(blocks_per_slot, nslots);
     kern<<<grid, warps * 32, smem, st>>>(d_params);
     MRPOP_CUDA_TRY(cudaGetLastError());

@@ -52,7 +52,7 @@ def _wait(server, tickets, timeout=60.0):
 
 
 def test_serving_result_same_alone_and_in_mix(mp, orc, cases):
-    steps = 30
+    steps = 400   # long enough that every later arrival joins a running batch
     alone = []
     for c in cases:
         p = _make(mp, c)
@@ -64,7 +64,7 @@ def test_serving_result_same_alone_and_in_mix(mp, orc, cases):
         tickets = []
         for p in probs:
             tickets.append(srv.submit(p, 60.0, max_steps=steps))
-            time.sleep(0.01)       # staggered arrivals: later ones join a running batch
+            time.sleep(0.002)      # staggered arrivals: later ones join a running batch
         _wait(srv, tickets)
         st = srv.stats()
     assert st["completed"] == len(cases) and st["peak_active"] >= 2
