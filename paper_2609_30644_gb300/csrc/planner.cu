@@ -429,23 +429,14 @@ __global__ void k_extract(const Slot *__restrict__ slots, int it, int *scratch, 
 }
 
 // ---------------------------------------------------------------------------
-// roadmap kernels (one robot of one slot)
+// roadmap building blocks (one robot of one slot)
 // ---------------------------------------------------------------------------
-__global__ void k_rm_sample(const float *lo, const float *hi, int dof, int n,
-                            unsigned long long key, unsigned long long ctr0, float *out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Rng rng{key, ctr0 + (unsigned long long)i * 64ull};
-    for (int d = 0; d < dof; ++d) out[(size_t)d * n + i] = lo[d] + rng.uniform() * (hi[d] - lo[d]);
-}
-
 // Append up to `want` valid candidates (in candidate order) to V_r: one
 // block; a block-wide prefix count of the valid flags gives every candidate
 // its slot, chunk after chunk.
 constexpr int kAppendThreads = 256;
-__global__ void __launch_bounds__(kAppendThreads)
-k_rm_append(const float *cand, const uint8_t *valid, int n, int dof, int want, float *V, int rcap,
-            int *count) {
+__device__ __forceinline__ void append_valid(const float *cand, const uint8_t *valid, int n,
+                                             int dof, int want, float *V, int rcap, int *count) {
     __shared__ int warp_sum[kAppendThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c0 = *count;
@@ -473,46 +464,14 @@ k_rm_append(const float *cand, const uint8_t *valid, int n, int dof, int want, f
     if (threadIdx.x == 0) *count = c0 + min(base, room);
 }
 
-__global__ void k_rm_gather(const float *V, int rcap, int dof, int first, int m, float *out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    for (int d = 0; d < dof; ++d) out[(size_t)d * m + i] = V[(size_t)d * rcap + first + i];
-}
-
-// Candidate roadmap edges (new vertex, earlier neighbour within delta).
-__global__ void k_rm_edges(const float *V, int rcap, int dof, int first, int m,
-                           const int64_t *nb, const int64_t *cnt, float *qa, float *qb,
-                           int *ea, int *eb) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int E = m * kKmax;
-    if (e >= E) return;
-    const int j = e / kKmax, k = e % kKmax;
-    const int self = first + j;
-    const int64_t c = cnt[j] < (int64_t)kKmax ? cnt[j] : (int64_t)kKmax;
-    const int v = k < c ? (int)nb[(size_t)j * kKmax + k] : -1;
-    if (v < 0 || v >= self) {
-        qa[e] = 0.f;
-        qb[e] = nanf_();
-        ea[e] = -1;
-        eb[e] = -1;
-        return;
-    }
-    for (int d = 0; d < dof; ++d) {
-        qa[(size_t)d * E + e] = V[(size_t)d * rcap + self];
-        qb[(size_t)d * E + e] = V[(size_t)d * rcap + v];
-    }
-    ea[e] = self;
-    eb[e] = v;
-}
-
 // Roadmap edges in candidate order, one warp: edges go in chunks of 32; in a
 // chunk the new-vertex ends are appended first, then the neighbour ends, and
 // lanes with the same target vertex take consecutive slots in lane order
 // (match + rank), so the adjacency lists (capped at kKmax) do not depend on
 // thread timing.  The direction oracle's choice does not depend on the order
 // within a list (ties go to the lowest vertex index).
-__global__ void k_rm_link(const uint8_t *valid, const int *ea, const int *eb, int E, int *adj,
-                          int *deg) {
+__device__ __forceinline__ void link_edges(const uint8_t *valid, const int *ea, const int *eb,
+                                           int E, int *adj, int *deg) {
     const int lane = threadIdx.x;
     for (int e0 = 0; e0 < E; e0 += 32) {
         const int e = e0 + lane;
@@ -535,8 +494,8 @@ __global__ void k_rm_link(const uint8_t *valid, const int *ea, const int *eb, in
 
 // Start-goal connectivity of a roadmap: level-synchronous BFS from vertex 0
 // in one block (at most n levels), writes whether vertex 1 was reached.
-__global__ void __launch_bounds__(1024) k_rm_bfs(const int *adj, const int *deg, int n, int *level,
-                                                 int *connected) {
+__device__ __forceinline__ void bfs_connected(const int *adj, const int *deg, int n, int *level,
+                                              int *connected) {
     __shared__ int changed;
     for (int v = threadIdx.x; v < n; v += blockDim.x) level[v] = v == 0 ? 0 : -1;
     __syncthreads();
@@ -560,6 +519,146 @@ __global__ void __launch_bounds__(1024) k_rm_bfs(const int *adj, const int *deg,
         if (!c) break;
     }
     if (threadIdx.x == 0) *connected = n > 1 && level[1] >= 0;
+}
+
+// ---------------------------------------------------------------------------
+// batched ROADMAP rounds: one job per robot of every problem that needs a
+// round; every kernel takes a job dimension (blockIdx.y), so a round costs a
+// fixed number of launches however many robots and problems take part.
+// ---------------------------------------------------------------------------
+struct RmJob {
+    float *q;               // V_r, SoA [dof][rcap]
+    int *adj, *deg, *count;  // adjacency [rcap][kKmax], degrees, vertex count (device)
+    int rcap, dof;
+    float *cand;            // candidate samples [dof][nc]
+    uint8_t *cvalid;
+    float *gq;              // vertices whose neighbours are searched [dof][m]
+    int64_t *nb, *cnt;      // neighbour lists [m][kKmax] and counts
+    float *ea_q, *eb_q;     // candidate edges [dof][emax]
+    uint8_t *evalid;
+    int *ea, *eb;
+    int *level, *conn;      // BFS levels [rcap], start-goal connected flag
+    const float *lo, *hi;   // joint limits of this robot
+    unsigned long long key, ctr;  // sampling stream
+    int nc, want, n_old, emax;
+    float delta;
+    int m, first;           // written by k_rmb_gather
+};
+
+__global__ void k_rmb_sample(const RmJob *__restrict__ jobs) {
+    const RmJob &J = jobs[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= J.nc) return;
+    Rng rng{J.key, J.ctr + (unsigned long long)i * 64ull};
+    for (int d = 0; d < J.dof; ++d)
+        J.cand[(size_t)d * J.nc + i] = J.lo[d] + rng.uniform() * (J.hi[d] - J.lo[d]);
+}
+
+__global__ void __launch_bounds__(kAppendThreads) k_rmb_append(const RmJob *__restrict__ jobs) {
+    const RmJob &J = jobs[blockIdx.y];
+    append_valid(J.cand, J.cvalid, J.nc, J.dof, J.want, J.q, J.rcap, J.count);
+}
+
+// The vertices whose neighbours are searched: the new ones, and on the first
+// round also start and goal (vertices 0 and 1).
+__global__ void k_rmb_gather(RmJob *__restrict__ jobs) {
+    RmJob &J = jobs[blockIdx.y];
+    const int n_new = *J.count;
+    const int first = J.n_old == 2 && n_new > 2 ? 0 : J.n_old;
+    const int m = n_new - first;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        J.m = m;
+        J.first = first;
+    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    for (int d = 0; d < J.dof; ++d) J.gq[(size_t)d * m + i] = J.q[(size_t)d * J.rcap + first + i];
+}
+
+// NEIGHBORS(V_r, c, delta) of Alg. 2 for the gathered vertices: one warp per
+// query scans V_r in index order (ballot + prefix count), keeping the first
+// kKmax indices within delta; the same test as the NEIGHBORS primitive.
+constexpr int kRmNbWarps = 8;
+__global__ void __launch_bounds__(kRmNbWarps * 32) k_rmb_neighbors(const RmJob *__restrict__ jobs) {
+    const RmJob &J = jobs[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kRmNbWarps + (threadIdx.x >> 5);
+    const int m = J.m, n = *J.count, dof = J.dof;
+    if (i >= m) return;
+    float qv[MRPOP_MAX_DOF];
+#pragma unroll
+    for (int d = 0; d < MRPOP_MAX_DOF; ++d) qv[d] = d < dof ? J.gq[(size_t)d * m + i] : 0.f;
+    int count = 0;
+    for (int c = 0; c < n; c += 32) {
+        const int v = c + lane;
+        bool in = false;
+        if (v < n) {
+            float d2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < MRPOP_MAX_DOF; ++d)
+                if (d < dof) {
+                    const float a = qv[d] - J.q[(size_t)d * J.rcap + v];
+                    d2 = fmaf(a, a, d2);
+                }
+            in = __fsqrt_rn(d2) <= J.delta;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int pos = count + __popc(bal & ((1u << lane) - 1u));
+            if (pos < kKmax) J.nb[(size_t)i * kKmax + pos] = v;
+        }
+        count += __popc(bal);
+    }
+    for (int pos = count + lane; pos < kKmax; pos += 32) J.nb[(size_t)i * kKmax + pos] = -1;
+    if (lane == 0) J.cnt[i] = count;
+}
+
+// Candidate roadmap edges (gathered vertex, earlier neighbour within delta);
+// unused slots up to emax get a NaN edge, which validation rejects unchecked.
+__global__ void k_rmb_edges(const RmJob *__restrict__ jobs) {
+    const RmJob &J = jobs[blockIdx.y];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= J.emax) return;
+    const int E = J.m * kKmax, j = e / kKmax, k = e % kKmax;
+    int v = -1, self = -1;
+    if (e < E) {
+        self = J.first + j;
+        const int64_t c = J.cnt[j] < (int64_t)kKmax ? J.cnt[j] : (int64_t)kKmax;
+        v = k < c ? (int)J.nb[(size_t)j * kKmax + k] : -1;
+    }
+    if (v < 0 || v >= self) {
+        for (int d = 0; d < J.dof; ++d) {
+            J.ea_q[(size_t)d * J.emax + e] = 0.f;
+            J.eb_q[(size_t)d * J.emax + e] = nanf_();
+        }
+        J.ea[e] = -1;
+        J.eb[e] = -1;
+        return;
+    }
+    for (int d = 0; d < J.dof; ++d) {
+        J.ea_q[(size_t)d * J.emax + e] = J.q[(size_t)d * J.rcap + self];
+        J.eb_q[(size_t)d * J.emax + e] = J.q[(size_t)d * J.rcap + v];
+    }
+    J.ea[e] = self;
+    J.eb[e] = v;
+}
+
+__global__ void k_rmb_link(const RmJob *__restrict__ jobs) {
+    const RmJob &J = jobs[blockIdx.y];
+    link_edges(J.evalid, J.ea, J.eb, J.m * kKmax, J.adj, J.deg);
+}
+
+__global__ void __launch_bounds__(1024) k_rmb_bfs(const RmJob *__restrict__ jobs) {
+    const RmJob &J = jobs[blockIdx.y];
+    bfs_connected(J.adj, J.deg, *J.count, J.level, J.conn);
+}
+
+// (vertex count, connected) of every job, for one copy to the host.
+__global__ void k_rmb_collect(const RmJob *__restrict__ jobs, int nj, int *out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nj) return;
+    out[2 * j] = *jobs[j].count;
+    out[2 * j + 1] = *jobs[j].conn;
 }
 
 __global__ void k_tree_reset(const Slot *__restrict__ slots) {
@@ -598,6 +697,9 @@ struct RobotRoadmap {
     int *ea = nullptr, *eb = nullptr;
     int *level = nullptr;  // BFS levels [rcap]
     int *d_conn = nullptr;
+    VParams vp_c, vp_e;    // validation of the candidates and of the candidate edges
+    int vw_c = 1, vw_e = 1;
+    size_t vs_c = 0, vs_e = 0;
 };
 
 struct Planner {
@@ -632,7 +734,6 @@ struct Planner {
     bool direct = false;    // single robot: no roadmap (Sec. V-C)
     unsigned long long seed = 0;
     int step = 0;
-    int *h_small = nullptr;  // pinned: per robot [new count, connected]
     float *fine_qa = nullptr, *fine_qb = nullptr;  // path re-check buffers
     uint8_t *fine_v = nullptr;
     size_t fine_cap = 0;
@@ -708,8 +809,6 @@ static void free_device(Planner *pl) {
     cudaFree(pl->d_centre); cudaFree(pl->d_axis); cudaFree(pl->ctrl); cudaFree(pl->d_path);
     cudaFree(pl->d_pathq);
     cudaFree(pl->d_len);
-    if (pl->h_small) cudaFreeHost(pl->h_small);
-    pl->h_small = nullptr;
     cudaFree(pl->fine_qa);
     cudaFree(pl->fine_qb);
     cudaFree(pl->fine_v);
@@ -813,6 +912,9 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
                               cudaMemcpyHostToDevice));
         }
         r.n = 2;
+        ST_TRY(make_vparams(r.sub, r.cand, r.cand, nc, r.cvalid, &r.vp_c, &r.vs_c, &r.vw_c));
+        ST_TRY(make_vparams(r.sub, r.ea_q, r.eb_q, E + 2 * kKmax, r.evalid, &r.vp_e, &r.vs_e,
+                            &r.vw_e));
         pl->slot.dof[k] = dof;
         pl->slot.qoff[k] = qoff;
         pl->slot.rm_q[k] = r.q;
@@ -821,7 +923,6 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
         qoff += dof;
     }
     PL_TRY(dalloc(&pl->rm_n, K));
-    PL_TRY(cudaMallocHost(&pl->h_small, sizeof(int) * 2 * K));
     std::vector<int> twos(K, 2);
     PL_TRY(cudaMemcpy(pl->rm_n, twos.data(), sizeof(int) * K, cudaMemcpyHostToDevice));
     for (int t = 0; t < 2; ++t) {
@@ -893,63 +994,145 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
     return MRPOP_OK;
 }
 
-// One ROADMAP round for robot k (Alg. 2: sample free configurations, find
-// their neighbours within delta, check the edges, add them), in two phases so
-// that many robots of many problems share two host synchronisations.
-// Phase 1 enqueues sampling, validation and append; the new vertex count
-// lands in pinned memory.
-static mrpop_status rm_phase1(Planner *pl, int k, cudaStream_t st) {
-    RobotRoadmap &r = pl->rm[k];
-    mrpop_problem *p = pl->p;
-    const int dof = p->robots[k].dof, rcap = pl->rcap;
-    pl->h_small[2 * k] = r.n;
-    if (r.n >= rcap) return MRPOP_OK;
-    const int want = std::min(pl->n_per_round, rcap - r.n);
-    const int nc = kOversample * pl->n_per_round;
-    const int off = pl->slot.qoff[k];
-    const unsigned long long key = mix64(pl->seed * 31ull + 7ull * (unsigned long long)k + 1ull);
-    const unsigned long long ctr = (unsigned long long)(pl->step + 1) * 0x100000ull +
-                                   (unsigned long long)r.n * 4096ull;
-    k_rm_sample<<<(nc + 127) / 128, 128, 0, st>>>(pl->d_lo + off, pl->d_hi + off, dof, nc, key, ctr,
-                                                   r.cand);
-    PL_TRY(cudaGetLastError());
-    ST_TRY(launch_validate(r.sub, r.cand, r.cand, nc, r.cvalid, nullptr, nullptr, nullptr, nullptr,
-                           st));
-    k_rm_append<<<1, kAppendThreads, 0, st>>>(r.cand, r.cvalid, nc, dof, want, r.q, rcap,
-                                              pl->rm_n + k);
-    PL_TRY(cudaGetLastError());
-    PL_TRY(cudaMemcpyAsync(pl->h_small + 2 * k, pl->rm_n + k, sizeof(int), cudaMemcpyDeviceToHost, st));
-    return MRPOP_OK;
+// One common launch shape for a batched validation over several problems
+// (blocks of up to 4 warps, the shared memory of the most demanding one;
+// each then uses as many warps as its per-warp scratch fits, at least as many
+// as it would alone) and the per-problem parameters that go with it.
+static void common_validation(std::vector<VParams> &vps, const std::vector<int> &own_warps,
+                              const std::vector<const mrpop_problem *> &probs, int64_t max_edges,
+                              int *warps, int *bps, size_t *smem, int *spl) {
+    size_t sm = 0;
+    int sp = 1;
+    for (size_t j = 0; j < vps.size(); ++j) {
+        const size_t tab = (size_t)probs[j]->dev.t.n_f4 * sizeof(float4);
+        sm = std::max(sm, tab + (size_t)own_warps[j] * vps[j].warp_floats * sizeof(float));
+        sp = std::max(sp, probs[j]->dev.t.max_spheres_per_link);
+    }
+    int wmax = 1;
+    std::vector<int> w(vps.size());
+    for (size_t j = 0; j < vps.size(); ++j) {
+        const size_t tab = (size_t)probs[j]->dev.t.n_f4 * sizeof(float4);
+        const size_t per = (size_t)vps[j].warp_floats * sizeof(float);
+        w[j] = std::max(own_warps[j], (int)std::min<size_t>(4, (sm - tab) / per));
+        wmax = std::max(wmax, w[j]);
+    }
+    const int b = (int)std::max<int64_t>(1, (max_edges + wmax - 1) / wmax);
+    for (size_t j = 0; j < vps.size(); ++j) {
+        vps[j].warps = w[j];
+        vps[j].total_warps = b * w[j];
+    }
+    *warps = wmax;
+    *bps = b;
+    *smem = sm;
+    *spl = sp;
 }
 
-// Phase 2 (the new count is known): neighbours of the new vertices (and of
-// start/goal on the first round), edge checks, links, and the start-goal BFS
-// on the device; the connected flag lands in pinned memory.
-static mrpop_status rm_phase2(Planner *pl, int k, cudaStream_t st) {
-    RobotRoadmap &r = pl->rm[k];
-    mrpop_problem *p = pl->p;
-    const int dof = p->robots[k].dof, rcap = pl->rcap;
-    const int n_new = pl->h_small[2 * k];
-    const int first = r.n == 2 && n_new > 2 ? 0 : r.n;
-    const int m = n_new - first;
-    if (m > 0) {
-        k_rm_gather<<<(m + 127) / 128, 128, 0, st>>>(r.q, rcap, dof, first, m, r.gq);
-        PL_TRY(cudaGetLastError());
-        ST_TRY(launch_neighbors(r.q, n_new, rcap, dof, r.gq, m, p->cfg.delta, kKmax, r.nb, r.cnt,
-                                st));
-        const int E = m * kKmax;
-        k_rm_edges<<<(E + 127) / 128, 128, 0, st>>>(r.q, rcap, dof, first, m, r.nb, r.cnt, r.ea_q,
-                                                     r.eb_q, r.ea, r.eb);
-        PL_TRY(cudaGetLastError());
-        ST_TRY(launch_validate(r.sub, r.ea_q, r.eb_q, E, r.evalid, nullptr, nullptr, nullptr,
-                               nullptr, st));
-        k_rm_link<<<1, 32, 0, st>>>(r.evalid, r.ea, r.eb, E, r.adj, r.deg);
-        PL_TRY(cudaGetLastError());
+// One ROADMAP round (Alg. 2) for every robot of every listed problem: each
+// robot samples n free configurations, links them to the vertices of V_r
+// within delta whose edges are free for that robot, and a BFS decides
+// whether its start and goal are connected.  All robots of all problems share
+// every launch (a job dimension) and one host synchronisation; the vertex
+// counts stay on the device between the phases.
+static mrpop_status roadmap_round_jobs(const std::vector<Planner *> &pls, cudaStream_t st) {
+    std::vector<RmJob> jobs;
+    std::vector<VParams> vc, ve;
+    std::vector<int> wc, we;
+    std::vector<const mrpop_problem *> subs;
+    int nc_max = 1, m_max = 1, e_max = 1;
+    for (Planner *pl : pls) {
+        mrpop_problem *p = pl->p;
+        for (int k = 0; k < pl->K; ++k) {
+            RobotRoadmap &r = pl->rm[k];
+            const int dof = p->robots[k].dof, off = pl->slot.qoff[k];
+            RmJob J{};
+            J.q = r.q;
+            J.adj = r.adj;
+            J.deg = r.deg;
+            J.count = pl->rm_n + k;
+            J.rcap = pl->rcap;
+            J.dof = dof;
+            J.cand = r.cand;
+            J.cvalid = r.cvalid;
+            J.gq = r.gq;
+            J.nb = r.nb;
+            J.cnt = r.cnt;
+            J.ea_q = r.ea_q;
+            J.eb_q = r.eb_q;
+            J.evalid = r.evalid;
+            J.ea = r.ea;
+            J.eb = r.eb;
+            J.level = r.level;
+            J.conn = r.d_conn;
+            J.lo = pl->d_lo + off;
+            J.hi = pl->d_hi + off;
+            J.key = mix64(pl->seed * 31ull + 7ull * (unsigned long long)k + 1ull);
+            J.ctr = (unsigned long long)(pl->step + 1) * 0x100000ull +
+                    (unsigned long long)r.n * 4096ull;
+            J.want = r.n >= pl->rcap ? 0 : std::min(pl->n_per_round, pl->rcap - r.n);
+            J.nc = kOversample * pl->n_per_round;
+            J.n_old = r.n;
+            J.emax = (pl->n_per_round + 2) * kKmax;
+            J.delta = p->cfg.delta;
+            nc_max = std::max(nc_max, J.nc);
+            m_max = std::max(m_max, pl->n_per_round + 2);
+            e_max = std::max(e_max, J.emax);
+            jobs.push_back(J);
+            vc.push_back(r.vp_c);
+            ve.push_back(r.vp_e);
+            wc.push_back(r.vw_c);
+            we.push_back(r.vw_e);
+            subs.push_back(r.sub);
+        }
     }
-    r.n = n_new;
-    k_rm_bfs<<<1, 1024, 0, st>>>(r.adj, r.deg, n_new, r.level, r.d_conn);
+    const int nj = (int)jobs.size();
+    if (nj == 0) return MRPOP_OK;
+    int w_c, b_c, spl_c, w_e, b_e, spl_e;
+    size_t s_c, s_e;
+    common_validation(vc, wc, subs, nc_max, &w_c, &b_c, &s_c, &spl_c);
+    common_validation(ve, we, subs, e_max, &w_e, &b_e, &s_e, &spl_e);
+
+    RmJob *d_jobs = nullptr;
+    VParams *d_vp = nullptr;
+    int *d_out = nullptr;
+    PL_TRY(cudaMallocAsync(&d_jobs, sizeof(RmJob) * nj, st));
+    PL_TRY(cudaMallocAsync(&d_vp, sizeof(VParams) * 2 * nj, st));
+    PL_TRY(cudaMallocAsync(&d_out, sizeof(int) * 2 * nj, st));
+    struct Release {
+        void *a, *b, *c;
+        cudaStream_t s;
+        ~Release() {
+            cudaFreeAsync(a, s);
+            cudaFreeAsync(b, s);
+            cudaFreeAsync(c, s);
+        }
+    } release{d_jobs, d_vp, d_out, st};
+    PL_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(RmJob) * nj, cudaMemcpyHostToDevice, st));
+    PL_TRY(cudaMemcpyAsync(d_vp, vc.data(), sizeof(VParams) * nj, cudaMemcpyHostToDevice, st));
+    PL_TRY(cudaMemcpyAsync(d_vp + nj, ve.data(), sizeof(VParams) * nj, cudaMemcpyHostToDevice, st));
+
+    k_rmb_sample<<<dim3((nc_max + 127) / 128, nj), 128, 0, st>>>(d_jobs);
     PL_TRY(cudaGetLastError());
-    PL_TRY(cudaMemcpyAsync(pl->h_small + 2 * k + 1, r.d_conn, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ST_TRY(launch_validate_batch(d_vp, nj, spl_c, w_c, b_c, s_c, false, st));
+    k_rmb_append<<<dim3(1, nj), kAppendThreads, 0, st>>>(d_jobs);
+    k_rmb_gather<<<dim3((m_max + 127) / 128, nj), 128, 0, st>>>(d_jobs);
+    k_rmb_neighbors<<<dim3((m_max + kRmNbWarps - 1) / kRmNbWarps, nj), kRmNbWarps * 32, 0, st>>>(
+        d_jobs);
+    k_rmb_edges<<<dim3((e_max + 127) / 128, nj), 128, 0, st>>>(d_jobs);
+    PL_TRY(cudaGetLastError());
+    ST_TRY(launch_validate_batch(d_vp + nj, nj, spl_e, w_e, b_e, s_e, false, st));
+    k_rmb_link<<<dim3(1, nj), 32, 0, st>>>(d_jobs);
+    k_rmb_bfs<<<dim3(1, nj), 1024, 0, st>>>(d_jobs);
+    k_rmb_collect<<<(nj + 127) / 128, 128, 0, st>>>(d_jobs, nj, d_out);
+    PL_TRY(cudaGetLastError());
+    std::vector<int> out(2 * (size_t)nj);
+    PL_TRY(cudaMemcpyAsync(out.data(), d_out, sizeof(int) * 2 * nj, cudaMemcpyDeviceToHost, st));
+    PL_TRY(cudaStreamSynchronize(st));
+    int j = 0;
+    for (Planner *pl : pls)
+        for (int k = 0; k < pl->K; ++k, ++j) {
+            pl->rm[k].n = out[2 * (size_t)j];
+            pl->rm[k].connected = out[2 * (size_t)j + 1] != 0;
+        }
     return MRPOP_OK;
 }
 
@@ -1183,20 +1366,14 @@ static mrpop_status roadmap_rounds(const std::vector<Planner *> &pls, std::vecto
         todo.push_back((int)i);
     }
     if (todo.empty()) return MRPOP_OK;
-    for (int i : todo)
-        for (int k = 0; k < pls[i]->K; ++k) ST_TRY(rm_phase1(pls[i], k, st));
-    PL_TRY(cudaStreamSynchronize(st));
-    for (int i : todo)
-        for (int k = 0; k < pls[i]->K; ++k) ST_TRY(rm_phase2(pls[i], k, st));
-    PL_TRY(cudaStreamSynchronize(st));
+    std::vector<Planner *> round;
+    for (int i : todo) round.push_back(pls[i]);
+    ST_TRY(roadmap_round_jobs(round, st));
     for (int i : todo) {
         Planner *pl = pls[i];
         SlotRun &run = *runs[i];
         bool all = true;
-        for (int k = 0; k < pl->K; ++k) {
-            pl->rm[k].connected = pl->h_small[2 * k + 1] != 0;
-            all = all && pl->rm[k].connected;
-        }
+        for (int k = 0; k < pl->K; ++k) all = all && pl->rm[k].connected;
         ++pl->step;
         if (!all) continue;
         pl->roadmap_ready = true;
