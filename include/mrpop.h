@@ -236,6 +236,19 @@ mrpop_status mrpop_nearest(const float *tree, int64_t n_vertices, int64_t ld, in
                            const float *queries, const float *budgets, int64_t n_queries,
                            int64_t *out_idx, void *cuda_stream);
 
+/* How many (query, vertex) pairs mrpop_nearest evaluates for these inputs
+ * (a diagnostic for roofline accounting; no paper counterpart).  A vertex
+ * with g_v >= c is never admissible, so for batches of >= 2048 queries in
+ * dimensions 3, 6, 7, 14, 21 or 28 mrpop_nearest orders the tree by g and the
+ * queries by budget and lets each block of 256 consecutive queries scan only
+ * the vertices whose g bucket lies at or below its largest budget; other
+ * batches scan all n_queries x n_vertices pairs.  Same arguments as
+ * mrpop_nearest, with *pairs (host) receiving the count.  Synchronises the
+ * stream.  Errors: as mrpop_nearest. */
+mrpop_status mrpop_nearest_work(const float *tree, int64_t n_vertices, int64_t ld, int32_t dim,
+                                const float *queries, const float *budgets, int64_t n_queries,
+                                int64_t *pairs, void *cuda_stream);
+
 /* Largest n_queries accepted by mrpop_nearest_noalloc. */
 #define MRPOP_NEAREST_NOALLOC_MAX_QUERIES 65536
 

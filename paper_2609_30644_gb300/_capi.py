@@ -31,6 +31,7 @@ EXPORTS = (
     "mrpop_set_launch",
     "mrpop_nearest",
     "mrpop_nearest_noalloc",
+    "mrpop_nearest_work",
     "mrpop_neighbors",
     "mrpop_path_cost",
     "mrpop_plan",
@@ -97,6 +98,7 @@ def _load() -> C.CDLL:
         "mrpop_set_launch": (i32, [vp, i32, i32, i32]),
         "mrpop_nearest": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_nearest_noalloc": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
+        "mrpop_nearest_work": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
         "mrpop_path_cost": (i32, [vp, i64, i32, vp, vp]),
         "mrpop_plan": (i32, [vp, C.c_double, vp, i64, vp, vp]),
@@ -302,6 +304,20 @@ def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
                              _dptr(budgets, torch.float32, "budgets"), Q,
                              _dptr(out, torch.int64, "out_idx"), _stream(stream)))
     return out
+
+
+def nearest_work(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
+                 n_vertices: Optional[int] = None, stream=None) -> int:
+    """(query, vertex) pairs nearest() evaluates for these inputs."""
+    dim, ld = int(tree.shape[0]) - 1, int(tree.shape[1])
+    N = ld if n_vertices is None else int(n_vertices)
+    Q = int(queries.shape[1])
+    out = C.c_int64()
+    _check(lib.mrpop_nearest_work(_dptr(tree, torch.float32, "tree"), N, ld, dim,
+                                  _dptr(queries, torch.float32, "queries"),
+                                  _dptr(budgets, torch.float32, "budgets"), Q, C.byref(out),
+                                  _stream(stream)))
+    return out.value
 
 
 def neighbors(tree: torch.Tensor, queries: torch.Tensor, delta: float, k_max: int,

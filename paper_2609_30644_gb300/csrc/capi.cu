@@ -380,6 +380,21 @@ extern "C" mrpop_status mrpop_nearest(const float *tree, int64_t N, int64_t ld, 
     return launch_nearest(tree, N, ld, dim, queries, budgets, Q, out_idx, (cudaStream_t)stream);
 }
 
+extern "C" mrpop_status mrpop_nearest_work(const float *tree, int64_t N, int64_t ld, int32_t dim,
+                                           const float *queries, const float *budgets, int64_t Q,
+                                           int64_t *pairs, void *stream) {
+    if (!pairs) return set_error(MRPOP_EINVAL, "mrpop_nearest_work: pairs is NULL");
+    *pairs = 0;
+    if (dim < 1 || dim > MRPOP_MAX_LINKS)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_work: dim=%d outside [1, %d]", dim,
+                         MRPOP_MAX_LINKS);
+    if (N < 0 || Q < 0 || ld < N || N > (int64_t)INT32_MAX || Q > (int64_t)INT32_MAX)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_work: bad sizes");
+    if (Q == 0 || N == 0) return MRPOP_OK;
+    if (!queries || !budgets || !tree) return set_error(MRPOP_EINVAL, "mrpop_nearest_work: NULL buffer");
+    return nearest_pairs(tree, N, ld, dim, queries, budgets, Q, pairs, (cudaStream_t)stream);
+}
+
 extern "C" mrpop_status mrpop_neighbors(const float *tree, int64_t N, int64_t ld, int32_t dim,
                                         const float *queries, int64_t Q, float delta,
                                         int64_t k_max, int64_t *out_idx, int64_t *out_cnt,

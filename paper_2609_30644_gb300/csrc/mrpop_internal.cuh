@@ -148,6 +148,9 @@ mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, 
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,
                             int64_t *out_idx, cudaStream_t st);
+// Number of (query, vertex) pairs launch_nearest scans for these inputs.
+mrpop_status nearest_pairs(const float *tree, int64_t N, int64_t ld, int dim, const float *queries,
+                           const float *budgets, int64_t Q, int64_t *pairs, cudaStream_t st);
 mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
                               const float *queries, int64_t Q, float delta, int64_t k_max,
                               int64_t *out_idx, int64_t *out_cnt, cudaStream_t st);

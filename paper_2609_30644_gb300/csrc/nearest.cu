@@ -192,6 +192,8 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
 // registers and the block streams its slice of the tree through shared memory
 // in tiles of kTile vertices, kept as SoA rows [dim][kTile] (coalesced,
 // conflict-free stores) plus two rows per vertex: g and a scaled squared norm.
+// It runs on the budget-ordered tree and queries prepared below (perm, cut
+// and seed given); with those null it is a plain scan of the whole slice.
 //
 // Filter, then exact decision.  For each (query, vertex) the inner loop only
 // accumulates the dot product with -2q (one packed FP32x2 FMA per coordinate
@@ -215,7 +217,9 @@ template <int DIM>
 __global__ void __launch_bounds__(kQThreads, DIM <= 14 ? 7 : 1)
 nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
                    const float *__restrict__ queries, const float *__restrict__ budgets, int Q,
-                   int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial) {
+                   int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial,
+                   const int *__restrict__ perm, const int *__restrict__ cut,
+                   const float *__restrict__ seed) {
     // rows 0..DIM-1 coordinates, row DIM g, row DIM+1 |x|^2 (1 - c3)
     __shared__ __align__(16) float tile[(DIM + 2) * kTile];
     constexpr float kU = 5.9604645e-8f;                   // 2^-24
@@ -241,8 +245,49 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
         best[j] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
         lim[j] = FLT_MAX * 2.f;
     }
+    // Budget-ordered mode (perm, cut given): the tree is sorted by g and this
+    // query block only scans the first cut[block] vertices (no vertex beyond
+    // has g below the block's largest budget); results carry original indices
+    // (perm), which also break exact (d^2, g) ties.
     const int vs = blockIdx.y * chunk;
-    const int ve = min(N, vs + chunk);
+    const int ve = min(cut ? min(N, cut[blockIdx.x]) : N, vs + chunk);
+    if (cut && vs >= ve) return;  // no partial record: the reduce skips this slice
+    auto orig = [&](int v) { return perm ? __ldg(perm + v) : v; };
+    if (seed) {
+        // the exact squared distance of an admissible vertex found by the
+        // seeding pass bounds the answer for every slice
+#pragma unroll
+        for (int j = 0; j < kQPT; ++j) {
+            const int q = qb + j * kQThreads + threadIdx.x;
+            const float sd = q < Q ? seed[q] : FLT_MAX * 2.f;
+            if (sd <= FLT_MAX) lim[j] = fmaf(sd, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU);
+        }
+    }
+    if (cut) {
+        // An admissible vertex of this slice has |q - x| < c - g_min(slice):
+        // the filter starts from that bound (rounded up, with the same
+        // inflation as below), or admits nothing when c <= g_min.
+        __shared__ float red_g[kQThreads / 32];
+        float gm = FLT_MAX;
+        for (int v = vs + threadIdx.x; v < ve; v += kQThreads)
+            gm = fminf(gm, __ldg(tree + (size_t)DIM * ld + v));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
+        if ((threadIdx.x & 31) == 0) red_g[threadIdx.x >> 5] = gm;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kQThreads / 32; ++k) gm = fminf(gm, red_g[k]);
+#pragma unroll
+        for (int j = 0; j < kQPT; ++j) {
+            if (!(cq[j] > gm)) {
+                lim[j] = -FLT_MAX * 2.f;
+            } else {
+                const float t = __fsub_ru(cq[j], gm);
+                const float b2 = __fmul_ru(t, t);
+                lim[j] = fminf(lim[j], fmaf(b2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU));
+            }
+        }
+    }
     const float4 *tile4 = reinterpret_cast<const float4 *>(tile);
     for (int v0 = vs; v0 < ve; v0 += kTile) {
         const int nv = min(kTile, ve - v0);
@@ -260,7 +305,7 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
             tile[(DIM + 1) * kTile + j] = n2 * (1.f - kC3);
         }
         __syncthreads();
-        if (v0 == vs) {
+        if (v0 == vs && !seed) {
             // Seed each query's best with an exact check of the slice's first
             // 32 vertices, so that the filter below starts from a finite
             // bound instead of re-checking the whole first tile.
@@ -279,11 +324,12 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
                         d2 = fmaf(a, a, d2);
                     }
                     if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
-                        (d2 < best[j].d2 || g < best[j].g)) {
+                        (d2 < best[j].d2 || g < best[j].g ||
+                         (g == best[j].g && orig(v0 + u) < best[j].idx))) {
                         best[j].d2 = d2;
                         best[j].g = g;
-                        best[j].idx = v0 + u;
-                        lim[j] = fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU);
+                        best[j].idx = orig(v0 + u);
+                        lim[j] = fminf(lim[j], fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU));
                     }
                 }
             }
@@ -343,11 +389,12 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
                         const float g = tile[DIM * kTile + vl];
                         // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index)
                         if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
-                            (d2 < best[j].d2 || g < best[j].g)) {
+                            (d2 < best[j].d2 || g < best[j].g ||
+                             (g == best[j].g && orig(v0 + vl) < best[j].idx))) {
                             best[j].d2 = d2;
                             best[j].g = g;
-                            best[j].idx = v0 + vl;
-                            lim[j] = fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU);
+                            best[j].idx = orig(v0 + vl);
+                            lim[j] = fminf(lim[j], fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU));
                         }
                     }
                 }
@@ -365,37 +412,319 @@ nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Budget-ordered NEAREST for large batches.  A vertex with g_v >= c is never
+// admissible (distances are >= 0), so once the tree is ordered by g and the
+// queries by budget, a block of queries only needs the prefix of the tree
+// whose g lies below its largest budget.  Both orders come from counting
+// sorts into kSortBuckets buckets over the finite range of g (budgets are
+// bucketed on the same scale); the order inside a bucket does not matter,
+// because exact ties are broken by original vertex index.
+// ---------------------------------------------------------------------------
+constexpr int kSortBuckets = 1024;
+
+struct SortState {
+    int gmin, gmax;                      // order-preserving keys of the finite g range
+    int tree_off[kSortBuckets + 1];      // bucket starts of the g-ordered tree
+    int tree_cur[kSortBuckets];
+    int query_off[kSortBuckets + 1];
+    int query_cur[kSortBuckets];
+};
+
+__device__ __forceinline__ int fkey(float v) {
+    const int k = __float_as_int(v);
+    return k ^ ((k >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float unkey(int o) { return __int_as_float(o ^ ((o >> 31) & 0x7fffffff)); }
+
+// Bucket of a value on the g scale; monotonic in v (a subtraction and a
+// product by a positive constant), non-finite values go to the last bucket.
+__device__ __forceinline__ int sort_bucket(float v, float lo, float scale) {
+    if (!(fabsf(v) <= FLT_MAX)) return kSortBuckets - 1;
+    const float b = floorf((v - lo) * scale);
+    if (!(b > 0.f)) return 0;
+    return b >= (float)(kSortBuckets - 1) ? kSortBuckets - 1 : (int)b;
+}
+
+__device__ __forceinline__ void g_scale(const SortState &S, float *lo, float *scale) {
+    const float a = unkey(S.gmin), b = unkey(S.gmax);
+    *lo = a;
+    *scale = b > a ? (float)kSortBuckets / (b - a) : 0.f;
+}
+
+__global__ void sort_init(SortState *S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        S->gmin = 0x7fffffff;
+        S->gmax = (int)0x80000000;
+    }
+    if (i <= kSortBuckets) S->tree_off[i] = S->query_off[i] = 0;
+}
+
+__global__ void sort_range(const float *__restrict__ g, int N, SortState *S) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    if (v < N) {
+        const float x = g[v];
+        if (fabsf(x) <= FLT_MAX) lo = hi = fkey(x);
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if ((threadIdx.x & 31) == 0 && lo <= hi) {
+        atomicMin(&S->gmin, lo);
+        atomicMax(&S->gmax, hi);
+    }
+}
+
+// Warp-aggregated counter update: lanes of a warp with the same bucket b
+// (b < 0: no item) add their count once, through the group's first lane, and
+// each receives the counter's old value plus its rank in the group (many
+// budgets can share one bucket, e.g. every budget above the largest g).
+__device__ __forceinline__ int grouped_add(int *counters, int b) {
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(kFull, b);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (b >= 0 && lane == leader) base = atomicAdd(&counters[b], __popc(grp));
+    base = __shfl_sync(kFull, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+__global__ void sort_histogram(const float *__restrict__ g, int N, const float *__restrict__ c,
+                               int Q, SortState *S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo, scale;
+    g_scale(*S, &lo, &scale);
+    grouped_add(S->tree_off + 1, i < N ? sort_bucket(g[i], lo, scale) : -1);
+    grouped_add(S->query_off + 1, i < Q ? sort_bucket(c[i], lo, scale) : -1);
+}
+
+// Inclusive scan of the shifted counts (one block of kSortBuckets threads):
+// off[b] becomes the start of bucket b; the cursors start there.
+__global__ void __launch_bounds__(kSortBuckets) sort_scan(SortState *S) {
+    __shared__ int part[kSortBuckets / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int which = 0; which < 2; ++which) {
+        int *off = which ? S->query_off : S->tree_off;
+        int *cur = which ? S->query_cur : S->tree_cur;
+        int x = off[t + 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) part[w] = x;
+        __syncthreads();
+        int before = 0;
+        for (int k = 0; k < w; ++k) before += part[k];
+        __syncthreads();
+        off[t + 1] = x + before;
+        __syncthreads();
+        cur[t] = off[t];
+        __syncthreads();
+    }
+}
+
+// Scatter the tree (all D+1 rows) and the queries into bucket order.
+__global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, int dim,
+                             const float *__restrict__ queries, const float *__restrict__ budgets,
+                             int Q, SortState *S, float *__restrict__ tree_s,
+                             int *__restrict__ perm, float *__restrict__ q_s,
+                             float *__restrict__ c_s, int *__restrict__ qperm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo, scale;
+    g_scale(*S, &lo, &scale);
+    const int bt = i < N ? sort_bucket(tree[(size_t)dim * ld + i], lo, scale) : -1;
+    const int pt = grouped_add(S->tree_cur, bt);
+    if (i < N) {
+        for (int d = 0; d <= dim; ++d) tree_s[(size_t)d * N + pt] = tree[(size_t)d * ld + i];
+        perm[pt] = i;
+    }
+    const float c = i < Q ? budgets[i] : 0.f;
+    const int bq = i < Q ? sort_bucket(c, lo, scale) : -1;
+    const int pq = grouped_add(S->query_cur, bq);
+    if (i < Q) {
+        for (int d = 0; d < dim; ++d) q_s[(size_t)d * Q + pq] = queries[(size_t)d * Q + i];
+        c_s[pq] = c;
+        qperm[pq] = i;
+    }
+}
+
+// Vertices a block of bq consecutive (ordered) queries must scan: up to the
+// end of the bucket that holds the largest budget of the block (0 when no
+// finite vertex has g below it).
+__global__ void __launch_bounds__(256) sort_cut(const float *__restrict__ c_s, int Q, int bq,
+                                                const SortState *S, int N, int *__restrict__ cut) {
+    __shared__ float red[8];
+    const int b = blockIdx.x;
+    float m = -FLT_MAX;
+    for (int i = b * bq + threadIdx.x; i < min(Q, (b + 1) * bq); i += blockDim.x)
+        m = fmaxf(m, c_s[i]);  // NaN budgets admit nothing and are ignored here
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+        m = fmaxf(m, red[0]);
+        float lo, scale;
+        g_scale(*S, &lo, &scale);
+        int n;
+        if (S->gmin > S->gmax)
+            n = 0;                                 // no finite g at all
+        else if (!(m > unkey(S->gmin)))
+            n = 0;                                 // no vertex has g < m
+        else if (m > unkey(S->gmax))
+            n = N;
+        else
+            n = S->tree_off[sort_bucket(m, lo, scale) + 1];
+        cut[b] = n;
+    }
+}
+
+// Seeding pass: for each (ordered) query, the smallest exact squared
+// distance (the kernel's own formula) among kSeedSamples evenly spaced vertices
+// of the g-ordered tree that are admissible for it; +inf when none is.
+constexpr int kSeedSamples = 64;
 template <int DIM>
-mrpop_status nearest_qpt(const float *tree, int N, int64_t ld, const float *queries,
-                         const float *budgets, int Q, int64_t *out_idx, cudaStream_t st) {
+__global__ void __launch_bounds__(128) nearest_seed(const float *__restrict__ tree_s, int N,
+                                                    const float *__restrict__ q_s,
+                                                    const float *__restrict__ c_s, int Q,
+                                                    float *__restrict__ seed) {
+    __shared__ float xs[DIM + 1][kSeedSamples];  // the sample vertices, g in the last row
+    const int n = min(N, kSeedSamples);
+    for (int t = threadIdx.x; t < (DIM + 1) * kSeedSamples; t += blockDim.x) {
+        const int d = t / kSeedSamples, k = t % kSeedSamples;
+        xs[d][k] = k < n ? tree_s[(size_t)d * N + (int)(((int64_t)k * N) / n)] : 0.f;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q) return;
+    float q[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) q[d] = q_s[(size_t)d * Q + i];
+    const float c = c_s[i];
+    float best = FLT_MAX * 2.f;
+    for (int k = 0; k < n; ++k) {
+        const float g = xs[DIM][k];
+        if (!(g < c)) continue;
+        float d2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const float a = q[d] - xs[d][k];
+            d2 = fmaf(a, a, d2);
+        }
+        if (g + __fsqrt_rn(d2) < c) best = fminf(best, d2);
+    }
+    seed[i] = best;
+}
+
+__global__ void nearest_sorted_reduce(const Best *__restrict__ partial, const int *__restrict__ cut,
+                                      int chunk, int Q, int bq, const int *__restrict__ qperm,
+                                      int64_t *__restrict__ out_idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q) return;
+    const int ns = (cut[i / bq] + chunk - 1) / chunk;
+    Best b{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+    for (int s = 0; s < ns; ++s) {
+        const Best o = partial[(size_t)s * Q + i];
+        if (better(o, b)) b = o;
+    }
+    out_idx[qperm[i]] = b.idx;
+}
+
+// Pairs the budget-ordered pass scans: sum over query blocks of (queries in
+// the block) x cut.
+__global__ void sort_count_pairs(const int *__restrict__ cut, int qblocks, int Q, int bq,
+                                 unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (int b = threadIdx.x; b < qblocks; b += blockDim.x)
+        acc += (unsigned long long)min(bq, Q - b * bq) * (unsigned long long)cut[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// out_idx null: only count the scanned pairs into *pairs (synchronises).
+template <int DIM>
+mrpop_status nearest_qpt_sorted(const float *tree, int N, int64_t ld, const float *queries,
+                                const float *budgets, int Q, int64_t *out_idx, cudaStream_t st,
+                                int64_t *pairs = nullptr) {
     int dev = 0, sms = 1, bps = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_qpt_kernel<DIM>, kQThreads, 0);
+    MRPOP_CUDA_TRY(cudaGetDevice(&dev));
+    MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MRPOP_CUDA_TRY(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_qpt_kernel<DIM>, kQThreads, 0));
     bps = std::max(bps, 1);
-    const int qblocks = (Q + kQThreads * kQPT - 1) / (kQThreads * kQPT);
-    const int target = sms * bps;
-    // as many tree slices as fit in one wave of resident blocks (a partial
-    // second wave would idle most SMs at the end)
-    int splits = std::max(1, target / qblocks);
-    splits = std::min(splits, std::max(1, (N + kTile - 1) / kTile));
-    splits = std::min(splits, 65535);
+    const int bq = kQThreads * kQPT;
+    const int qblocks = (Q + bq - 1) / bq;
+    // about four waves of (query block, tree slice) pieces before the cut
+    // removes some: the dynamic block scheduler then evens out the blocks
+    // that stop early
+    int splits = std::max(1, (4 * sms * bps + qblocks - 1) / qblocks);
     int chunk = (N + splits - 1) / splits;
     chunk = std::max(kTile, ((chunk + kTile - 1) / kTile) * kTile);
     splits = std::max(1, (N + chunk - 1) / chunk);
-    Best *partial = nullptr;
-    if (splits > 1)
-        MRPOP_CUDA_TRY(cudaMallocAsync((void **)&partial, sizeof(Best) * (size_t)splits * Q, st));
-    dim3 grid(qblocks, splits);
-    nearest_qpt_kernel<DIM><<<grid, kQThreads, 0, st>>>(tree, N, ld, queries, budgets, Q, chunk,
-                                                        out_idx, partial);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && splits > 1) {
-        nearest_reduce_kernel<<<(Q + 255) / 256, 256, 0, st>>>(partial, splits, Q, out_idx);
-        e = cudaGetLastError();
+    if (splits > 65535) return set_error(MRPOP_EINVAL, "nearest: tree too large");
+    // one stream-ordered arena: sort state, ordered tree and queries,
+    // permutations, cuts, partial bests
+    auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_state = align(sizeof(SortState));
+    const size_t b_tree = align(sizeof(float) * (size_t)(DIM + 1) * N);
+    const size_t b_perm = align(sizeof(int) * (size_t)N);
+    const size_t b_q = align(sizeof(float) * (size_t)DIM * Q);
+    const size_t b_c = align(sizeof(float) * (size_t)Q);
+    const size_t b_qp = align(sizeof(int) * (size_t)Q);
+    const size_t b_cut = align(sizeof(int) * (size_t)qblocks);
+    const size_t b_part = align(sizeof(Best) * (size_t)splits * Q);
+    const size_t b_seed = align(sizeof(float) * (size_t)Q);
+    char *arena = nullptr;
+    MRPOP_CUDA_TRY(cudaMallocAsync((void **)&arena,
+                                   b_state + b_tree + b_perm + b_q + b_c + b_qp + b_cut + b_part +
+                                       b_seed,
+                                   st));
+    char *at = arena;
+    auto take = [&](size_t b) { char *r = at; at += b; return r; };
+    SortState *S = (SortState *)take(b_state);
+    float *tree_s = (float *)take(b_tree);
+    int *perm = (int *)take(b_perm);
+    float *q_s = (float *)take(b_q);
+    float *c_s = (float *)take(b_c);
+    int *qperm = (int *)take(b_qp);
+    int *cut = (int *)take(b_cut);
+    Best *partial = (Best *)take(b_part);
+    float *seed = (float *)take(b_seed);
+    const int n_max = std::max(N, Q);
+    const float *g = tree + (size_t)DIM * ld;
+    sort_init<<<(kSortBuckets + 256) / 256, 256, 0, st>>>(S);
+    sort_range<<<(N + 255) / 256, 256, 0, st>>>(g, N, S);
+    sort_histogram<<<(n_max + 255) / 256, 256, 0, st>>>(g, N, budgets, Q, S);
+    sort_scan<<<1, kSortBuckets, 0, st>>>(S);
+    sort_scatter<<<(n_max + 255) / 256, 256, 0, st>>>(tree, N, ld, DIM, queries, budgets, Q, S,
+                                                       tree_s, perm, q_s, c_s, qperm);
+    sort_cut<<<qblocks, 256, 0, st>>>(c_s, Q, bq, S, N, cut);
+    if (!out_idx) {
+        unsigned long long *d_pairs = (unsigned long long *)seed;  // 8 bytes of the arena
+        unsigned long long h = 0;
+        cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st);
+        sort_count_pairs<<<1, 256, 0, st>>>(cut, qblocks, Q, bq, d_pairs);
+        cudaMemcpyAsync(&h, d_pairs, sizeof(h), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        cudaFreeAsync(arena, st);
+        if (e != cudaSuccess) return cuda_error(e, "nearest pair count");
+        *pairs = (int64_t)h;
+        return MRPOP_OK;
     }
-    if (partial) cudaFreeAsync(partial, st);
-    if (e != cudaSuccess) return cuda_error(e, "nearest (query-blocked) kernel launch");
+    nearest_seed<DIM><<<(Q + 127) / 128, 128, 0, st>>>(tree_s, N, q_s, c_s, Q, seed);
+    dim3 grid(qblocks, splits);
+    nearest_qpt_kernel<DIM><<<grid, kQThreads, 0, st>>>(tree_s, N, N, q_s, c_s, Q, chunk, nullptr,
+                                                        partial, perm, cut, seed);
+    nearest_sorted_reduce<<<(Q + 255) / 256, 256, 0, st>>>(partial, cut, chunk, Q, bq, qperm,
+                                                           out_idx);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(arena, st);
+    if (e != cudaSuccess) return cuda_error(e, "nearest (budget-ordered) launch");
     return MRPOP_OK;
 }
 
@@ -506,12 +835,12 @@ mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
     // Large batches: queries in registers against shared-memory tree tiles.
     if (Q >= 2048 && N > 0) {
         switch (dim) {
-            case 3: return nearest_qpt<3>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 6: return nearest_qpt<6>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 7: return nearest_qpt<7>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 14: return nearest_qpt<14>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 21: return nearest_qpt<21>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 28: return nearest_qpt<28>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 3: return nearest_qpt_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 6: return nearest_qpt_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 7: return nearest_qpt_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 14: return nearest_qpt_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 21: return nearest_qpt_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 28: return nearest_qpt_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st);
             default: break;
         }
     }
@@ -531,6 +860,24 @@ mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
     }
     if (dp <= 48) return nearest_dp<48>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
     return nearest_dp<64>(tree, n, ld, dim, queries, budgets, q, out_idx, st);
+}
+
+mrpop_status nearest_pairs(const float *tree, int64_t N, int64_t ld, int dim, const float *queries,
+                           const float *budgets, int64_t Q, int64_t *pairs, cudaStream_t st) {
+    const int n = (int)N, q = (int)Q;
+    *pairs = N * Q;  // the small-batch kernels scan every vertex
+    if (Q >= 2048 && N > 0) {
+        switch (dim) {
+            case 3: return nearest_qpt_sorted<3>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 6: return nearest_qpt_sorted<6>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 7: return nearest_qpt_sorted<7>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 14: return nearest_qpt_sorted<14>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 21: return nearest_qpt_sorted<21>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 28: return nearest_qpt_sorted<28>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            default: break;
+        }
+    }
+    return MRPOP_OK;
 }
 
 mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,

@@ -168,3 +168,26 @@ def test_nearest_query_blocked_parity(mp, orc, D, N, Q):
     np.testing.assert_array_equal(big, small)
     sample = np.concatenate([np.arange(64), np.random.default_rng(D).choice(Q, 200, replace=False)])
     _check_nearest(orc, tree, qs, cs, big, sample=sample)
+
+
+def test_nearest_work_counts(mp, orc):
+    """Pairs the budget-ordered pass evaluates: all of them for unbounded
+    budgets or small batches, none when every budget is below every cost
+    (and then nothing is admissible), and in between for mixed budgets; the
+    results of the mixed case still match the oracle on a sample."""
+    D, N, Q = 7, 3000, 4096
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, N, lo, hi, seed=9, dup_frac=0.05)
+    qs, _ = synth.nn_queries(D, Q, lo, hi, seed=10)
+    t, q = _dev(tree), _dev(qs)
+    big = torch.full((Q,), 1e30, dtype=torch.float32, device="cuda")
+    assert mp.nearest_work(t, q, big) == Q * N
+    assert mp.nearest_work(t, q[:, :100].contiguous(), big[:100]) == 100 * N
+    low = torch.full((Q,), float(tree[D].min()) * 0.5 - 1.0, dtype=torch.float32, device="cuda")
+    assert mp.nearest_work(t, q, low) == 0
+    assert (mp.nearest(t, q, low).cpu().numpy() == -1).all()
+    cs = np.random.default_rng(11).uniform(0.0, float(tree[D].max()), Q).astype(np.float32)
+    pairs = mp.nearest_work(t, q, _dev(cs))
+    assert 0 < pairs < Q * N
+    got = mp.nearest(t, q, _dev(cs)).cpu().numpy()
+    _check_nearest(orc, tree, qs, cs, got, sample=np.arange(0, Q, 37))
