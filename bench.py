@@ -741,8 +741,9 @@ def run_ours(args) -> None:
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             # per step: validate; NEAREST = 6 ordering kernels + seeding + the
-            # query-blocked kernel + its reduce; neighbors; path cost + its sum
-            "gpu_launches": 13 * args.steps,
+            # query-blocked kernel + its reduce; neighbors over vertex ranges +
+            # the ordered merge; path cost + its sum
+            "gpu_launches": 14 * args.steps,
             "cpu_baseline": cpu,
             "planner": planner,
             "serving": serving,

@@ -738,16 +738,21 @@ constexpr int kNbTile = 256;
 __global__ void __launch_bounds__(kNbWarps * 32)
 neighbors_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
                  const float *__restrict__ queries, int Q, float delta, int64_t k_max,
-                 int64_t *__restrict__ out_idx, int64_t *__restrict__ out_cnt) {
+                 int64_t *__restrict__ out_idx, int64_t *__restrict__ out_cnt, int chunk) {
+    // blockIdx.y takes vertices [y * chunk, (y + 1) * chunk); with several
+    // ranges (gridDim.y > 1) the lists go to per-range slots of out_idx /
+    // out_cnt ([q][range]) and neighbors_merge concatenates them in order
     __shared__ float qs[kNbWarps][MRPOP_MAX_LINKS];
     extern __shared__ float tile[];  // [dim][kNbTile]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = blockIdx.x * kNbWarps + warp;
     const bool qok = q < Q;
     for (int d = lane; d < dim; d += 32) qs[warp][d] = qok ? queries[(size_t)d * Q + q] : 0.f;
+    const int64_t slot = (int64_t)q * gridDim.y + blockIdx.y;  // this query's range slot
+    const int vs = blockIdx.y * chunk, ve = min(N, vs + chunk);
     int64_t count = 0;
-    for (int v0 = 0; v0 < N; v0 += kNbTile) {
-        const int nv = min(kNbTile, N - v0);
+    for (int v0 = vs; v0 < ve; v0 += kNbTile) {
+        const int nv = min(kNbTile, ve - v0);
         __syncthreads();
         for (int i = threadIdx.x; i < dim * kNbTile; i += blockDim.x) {
             const int d = i / kNbTile, j = i - d * kNbTile;
@@ -769,14 +774,34 @@ neighbors_kernel(const float *__restrict__ tree, int N, int64_t ld, int dim,
             const unsigned bal = __ballot_sync(kFull, in);
             if (in) {
                 const int64_t pos = count + __popc(bal & ((1u << lane) - 1u));
-                if (pos < k_max) out_idx[(size_t)q * k_max + pos] = v0 + v;
+                if (pos < k_max) out_idx[(size_t)slot * k_max + pos] = v0 + v;
             }
             count += __popc(bal);
         }
     }
     if (!qok) return;
-    for (int64_t pos = count + lane; pos < k_max; pos += 32) out_idx[(size_t)q * k_max + pos] = -1;
-    if (lane == 0) out_cnt[q] = count;
+    for (int64_t pos = count + lane; pos < k_max; pos += 32) out_idx[(size_t)slot * k_max + pos] = -1;
+    if (lane == 0) out_cnt[slot] = count;
+}
+
+// Concatenates each query's per-range lists in range order (ascending vertex
+// index), keeping the first k_max, and adds up the counts.
+__global__ void neighbors_merge(const int64_t *__restrict__ part_idx,
+                                const int64_t *__restrict__ part_cnt, int ranges, int Q,
+                                int64_t k_max, int64_t *__restrict__ out_idx,
+                                int64_t *__restrict__ out_cnt) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    int64_t total = 0;
+    for (int r = 0; r < ranges; ++r) {
+        const int64_t slot = (int64_t)q * ranges + r;
+        const int64_t c = part_cnt[slot];
+        for (int64_t i = 0; i < c && total + i < k_max; ++i)
+            out_idx[(size_t)q * k_max + total + i] = part_idx[(size_t)slot * k_max + i];
+        total += c;
+    }
+    for (int64_t pos = total; pos < k_max; ++pos) out_idx[(size_t)q * k_max + pos] = -1;
+    out_cnt[q] = total;
 }
 
 // C(sigma): segment lengths in FP32, sums in FP64 with a fixed reduction order
@@ -888,9 +913,33 @@ mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
     if (smem > 48 * 1024)
         MRPOP_CUDA_TRY(cudaFuncSetAttribute(neighbors_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    neighbors_kernel<<<blocks, kNbWarps * 32, smem, st>>>(tree, (int)N, ld, dim, queries, (int)Q,
-                                                          delta, k_max, out_idx, out_cnt);
-    MRPOP_CUDA_TRY(cudaGetLastError());
+    // Few queries leave most SMs idle with one warp per query: split the
+    // vertices into ranges (at least one tile each) until about 8,192 warps run.
+    int sms = 1, dev = 0;
+    MRPOP_CUDA_TRY(cudaGetDevice(&dev));
+    MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t want = std::max<int64_t>(1, (int64_t)sms * 54 / std::max<int64_t>(Q, 1));
+    const int ranges = (int)std::min<int64_t>(std::min<int64_t>(want, (N + kNbTile - 1) / kNbTile),
+                                              std::max<int64_t>(1, 65535));
+    if (ranges <= 1 || k_max > 4096) {
+        neighbors_kernel<<<blocks, kNbWarps * 32, smem, st>>>(tree, (int)N, ld, dim, queries,
+                                                              (int)Q, delta, k_max, out_idx,
+                                                              out_cnt, (int)std::max<int64_t>(N, 1));
+        MRPOP_CUDA_TRY(cudaGetLastError());
+        return MRPOP_OK;
+    }
+    const int chunk = (int)(((N + ranges - 1) / ranges + kNbTile - 1) / kNbTile * kNbTile);
+    const int nr = (int)((N + chunk - 1) / chunk);
+    int64_t *part = nullptr;
+    const size_t kidx = (size_t)Q * nr * (size_t)std::max<int64_t>(k_max, 1);
+    MRPOP_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(int64_t) * (kidx + (size_t)Q * nr), st));
+    neighbors_kernel<<<dim3(blocks, nr), kNbWarps * 32, smem, st>>>(
+        tree, (int)N, ld, dim, queries, (int)Q, delta, k_max, part, part + kidx, chunk);
+    neighbors_merge<<<(int)((Q + 127) / 128), 128, 0, st>>>(part, part + kidx, nr, (int)Q, k_max,
+                                                           out_idx, out_cnt);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess) return cuda_error(e, "neighbors launch");
     return MRPOP_OK;
 }
 
