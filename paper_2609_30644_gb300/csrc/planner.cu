@@ -1172,13 +1172,32 @@ static mrpop_status try_incumbent(Planner *pl, const Slot *d_slot, int it, int t
         cost += std::sqrt(s);
     }
     if (!(cost < pl->c_best) || len < 2) return MRPOP_OK;
-    // re-validate every segment at resolution / 4
-    const int M = len - 1;
-    std::vector<float> qa((size_t)D * M), qb((size_t)D * M);
-    for (int j = 0; j < M; ++j)
+    // Re-validate every segment at resolution / 4.  A segment is cut into
+    // equal sub-edges of at most 31 intervals at that resolution, so that the
+    // check spreads over many warps (one warp per sub-edge) instead of a few
+    // long edges walked tile after tile; the checkpoint density is the same.
+    const double res4 = 0.25 * (double)pl->p->cfg.resolution;
+    std::vector<int> parts(len > 1 ? len - 1 : 0);
+    int M = 0;
+    for (int j = 0; j + 1 < len; ++j) {
+        double s2 = 0.0;
         for (int d = 0; d < D; ++d) {
-            qa[(size_t)d * M + j] = path[(size_t)j * D + d];
-            qb[(size_t)d * M + j] = path[(size_t)(j + 1) * D + d];
+            const double t = (double)path[(size_t)(j + 1) * D + d] - path[(size_t)j * D + d];
+            s2 += t * t;
+        }
+        const double n = std::ceil(std::sqrt(s2) / res4);
+        parts[j] = (int)std::min(4096.0, std::max(1.0, std::ceil(n / 31.0)));
+        M += parts[j];
+    }
+    std::vector<float> qa((size_t)D * M), qb((size_t)D * M);
+    for (int j = 0, e = 0; j + 1 < len; ++j)
+        for (int i = 0; i < parts[j]; ++i, ++e) {
+            const double t0 = (double)i / parts[j], t1 = (double)(i + 1) / parts[j];
+            for (int d = 0; d < D; ++d) {
+                const double a = path[(size_t)j * D + d], b = path[(size_t)(j + 1) * D + d];
+                qa[(size_t)d * M + e] = i == 0 ? (float)a : (float)(a + t0 * (b - a));
+                qb[(size_t)d * M + e] = i + 1 == parts[j] ? (float)b : (float)(a + t1 * (b - a));
+            }
         }
     if ((size_t)M > pl->fine_cap) {  // grow-only buffers for the fine re-check
         cudaFree(pl->fine_qa);
