@@ -36,6 +36,7 @@ namespace mrpop {
 constexpr int kStepIters = 256;     // iterations per step and problem
 constexpr int kKmax = 64;           // roadmap degree cap
 constexpr int kOversample = 4;      // roadmap candidates per wanted sample
+constexpr int kRoadmapEdgesPerWarp = 16;  // roadmap validation: edges per warp on average
 constexpr int kInformedTries = 16;  // informed-sampling rejection limit
 
 struct Ctrl {
@@ -998,9 +999,12 @@ static mrpop_status planner_init(mrpop_problem *p, Planner **out) {
 // (blocks of up to 4 warps, the shared memory of the most demanding one;
 // each then uses as many warps as its per-warp scratch fits, at least as many
 // as it would alone) and the per-problem parameters that go with it.
+// edges_per_warp sets the blocks per problem: each block first stages the
+// problem's tables, so large batches share that cost among several edges per
+// warp (the per-problem work counter still hands out edges one at a time).
 static void common_validation(std::vector<VParams> &vps, const std::vector<int> &own_warps,
                               const std::vector<const mrpop_problem *> &probs, int64_t max_edges,
-                              int *warps, int *bps, size_t *smem, int *spl) {
+                              int edges_per_warp, int *warps, int *bps, size_t *smem, int *spl) {
     size_t sm = 0;
     int sp = 1;
     for (size_t j = 0; j < vps.size(); ++j) {
@@ -1016,7 +1020,8 @@ static void common_validation(std::vector<VParams> &vps, const std::vector<int> 
         w[j] = std::max(own_warps[j], (int)std::min<size_t>(4, (sm - tab) / per));
         wmax = std::max(wmax, w[j]);
     }
-    const int b = (int)std::max<int64_t>(1, (max_edges + wmax - 1) / wmax);
+    const int64_t per_block = (int64_t)wmax * std::max(1, edges_per_warp);
+    const int b = (int)std::max<int64_t>(1, (max_edges + per_block - 1) / per_block);
     for (size_t j = 0; j < vps.size(); ++j) {
         vps[j].warps = w[j];
         vps[j].total_warps = b * w[j];
@@ -1088,8 +1093,8 @@ static mrpop_status roadmap_round_jobs(const std::vector<Planner *> &pls, cudaSt
     if (nj == 0) return MRPOP_OK;
     int w_c, b_c, spl_c, w_e, b_e, spl_e;
     size_t s_c, s_e;
-    common_validation(vc, wc, subs, nc_max, &w_c, &b_c, &s_c, &spl_c);
-    common_validation(ve, we, subs, e_max, &w_e, &b_e, &s_e, &spl_e);
+    common_validation(vc, wc, subs, nc_max, kRoadmapEdgesPerWarp, &w_c, &b_c, &s_c, &spl_c);
+    common_validation(ve, we, subs, e_max, kRoadmapEdgesPerWarp, &w_e, &b_e, &s_e, &spl_e);
 
     RmJob *d_jobs = nullptr;
     VParams *d_vp = nullptr;
