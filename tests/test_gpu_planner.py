@@ -22,12 +22,12 @@ def mp():
     return m
 
 
-def _robot_connected(orc, scene, k, qs, qg, n=1500, delta=0.8):
+def _robot_connected(orc, scene, k, qs, qg, n=1500, delta=0.8, self_collision=False):
     """Dense FP64 PRM of robot k alone (oracle checks): are its start and goal
     in one free-space component?  Joint limits without wrap-around can split
     free space, so a random start/goal pair may have no path at all."""
     sub = synth.Scene([scene.robots[k]], scene.obs_spheres, scene.obs_cuboids)
-    o = orc.OracleScene(sub)
+    o = orc.OracleScene(sub, self_collision=self_collision)
     r = scene.robots[k]
     off = sum(rr.dof for rr in scene.robots[:k])
     rng = np.random.default_rng(k)
@@ -100,6 +100,25 @@ def test_plan_reassigned_fine_stage(mp, orc):
                     start=qs, goal=qg) as p:
         mp.set_launch(p, 0, 0, 1)
         path, cost = mp.plan(p, 1.5)
+    _check_path(orc, o, path, cost, qs, qg)
+
+
+def test_plan_with_self_collision(mp, orc):
+    """Planning with self-collision on (default adjacency mask): the returned
+    path is valid for the self-colliding oracle at res/4."""
+    scene = synth.planar_pair_scene(0)
+    o = orc.OracleScene(scene, self_collision=True)
+    stream = synth.config_stream(scene, 0)
+    ok = lambda q: o.config_valid(q, 1e-4 + 1e-3)[0]
+    for _ in range(20):
+        qs, qg = synth.first_accepted(stream, ok), synth.first_accepted(stream, ok)
+        if all(_robot_connected(orc, scene, k, qs, qg, delta=0.8, self_collision=True)
+               for k in range(scene.K)):
+            break
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=0.8, n_per_round=64,
+                    tree_cap=1 << 16, roadmap_cap=1 << 14, max_iters=4096, seed=3,
+                    start=qs, goal=qg, self_collision=True) as p:
+        path, cost = mp.plan(p, 2.0)
     _check_path(orc, o, path, cost, qs, qg)
 
 
