@@ -254,3 +254,39 @@ def test_plan_single_robot_direct(mp, orc, kind):
         assert hc == ck
         _check_path(orc, o, hp, hc, qs, qg)
     np.testing.assert_array_equal(hist[-1][0], path)
+
+
+def test_plan_planar_within_2000_iterations(mp, orc):
+    """The planar pair's iteration budget: a solution within 2,000 search
+    iterations (steps that only grow roadmaps do not count), oracle-valid at
+    res/4.  Runs are deterministic for a seed."""
+    scene = synth.planar_pair_scene(1)
+    qs, qg, o = _start_goal(orc, scene, 1)
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=0.8, n_per_round=64,
+                    tree_cap=1 << 16, roadmap_cap=1 << 14, max_iters=4096, seed=1,
+                    start=qs, goal=qg) as p:
+        for _ in range(200):
+            mp.plan_batch([p], 60.0, max_steps=1)
+            if mp.plan_trace(p)[2] >= 2000:
+                break
+        t, c, iters = mp.plan_trace(p)
+        path, cost = mp.plan_result(p)
+    assert iters <= 2048 and len(c) >= 1
+    _check_path(orc, o, path, cost, qs, qg)
+
+
+def test_plan_grid4(mp, orc):
+    """Four 7-DOF arms over a shared cube (28-DOF) with 128 obstacles: a path
+    within a 2 s budget (the workload allows 10 s), oracle-valid at res/4."""
+    scene = synth.grid4_scene(0)
+    o = orc.OracleScene(scene)
+    stream = synth.config_stream(scene, 0)
+    ok = lambda q: o.config_valid(q, 2e-3)[0]
+    qs, qg = synth.first_accepted(stream, ok), synth.first_accepted(stream, ok)
+    with mp.Problem(scene, resolution=RES, margin=1e-4, delta=2.5, n_per_round=64,
+                    tree_cap=1 << 16, roadmap_cap=1 << 13, max_iters=4096, seed=1,
+                    start=qs, goal=qg) as p:
+        path, cost = mp.plan(p, 2.0)
+        t, c, iters = mp.plan_trace(p)
+    assert np.all(np.diff(c) < 0)
+    _check_path(orc, o, path, cost, qs, qg)
