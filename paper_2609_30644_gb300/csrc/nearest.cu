@@ -1,14 +1,15 @@
 // Cost-filtered nearest neighbour (Alg. 2 NEAREST), radius query (Alg. 2
 // NEIGHBORS) and path cost (Sec. III-A) over SoA state-cost trees.
 //
-// NEAREST: a block owns QB queries (staged in shared memory) and a slice of
-// the tree.  Each thread streams vertices of the slice through registers
-// (coalesced SoA rows), evaluates all QB queries against the vertex with
-// float4 broadcast reads of the queries, and keeps a running best per query
-// under the key (d^2, g, index).  A warp-shuffle argmin and a cross-warp pass
-// finish the block; when the tree is split across blocks (few queries, large
-// tree), partial bests go to stream-ordered scratch and a second kernel
-// reduces them.
+// NEAREST, small batches: a block owns QB queries (staged in shared memory)
+// and a slice of the tree.  Each thread streams vertices of the slice through
+// registers (coalesced SoA rows), evaluates all QB queries against the vertex
+// with float4 broadcast reads of the queries, and keeps a running best per
+// query under the key (d^2, g, index).  A warp-shuffle argmin and a
+// cross-warp pass finish the block; when the tree is split across blocks (few
+// queries, large tree), partial bests go to stream-ordered scratch and a
+// second kernel reduces them.  Large batches take the budget-ordered,
+// query-blocked path further down.
 #include <algorithm>
 #include <cfloat>
 #include <mutex>

@@ -15,7 +15,9 @@
 // Roadmaps (Alg. 2 ROADMAP): per robot, batches of uniform samples are
 // checked against the obstacles (a single-robot sub-problem), connected to
 // their neighbours within delta (NEIGHBORS) by checked edges, and grown until
-// start and goal are connected (BFS on the host).
+// start and goal are connected (a BFS on the device).  A round runs for every
+// robot of every problem that needs one at once: each phase is one launch
+// with a job dimension, and the round ends with one host synchronisation.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
