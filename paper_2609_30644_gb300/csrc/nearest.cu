@@ -8,8 +8,8 @@
 // query under the key (d^2, g, index).  A warp-shuffle argmin and a
 // cross-warp pass finish the block; when the tree is split across blocks (few
 // queries, large tree), partial bests go to stream-ordered scratch and a
-// second kernel reduces them.  Large batches take the budget-ordered,
-// query-blocked path further down.
+// second kernel reduces them.  Large batches take the budget-ordered path
+// further down, whose filter runs on the tensor cores.
 #include <algorithm>
 #include <cfloat>
 #include <mutex>
@@ -168,248 +168,344 @@ mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const flo
     return MRPOP_OK;
 }
 
-typedef unsigned long long f2;  // two FP32 lanes in one 64-bit register pair
-
-__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-// NEAREST for large query batches: every thread owns QPT queries in
-// registers and the block streams its slice of the tree through shared memory
-// in tiles of kTile vertices, kept as SoA rows [dim][kTile] (coalesced,
-// conflict-free stores) plus two rows per vertex: g and a scaled squared norm.
-// It runs on the budget-ordered tree and queries prepared below (perm, cut
-// and seed given); with those null it is a plain scan of the whole slice.
+// ---------------------------------------------------------------------------
+// NEAREST filter on the tensor cores.  The expansion
+//   e(q, x) = |q|^2 + |x|^2 - 2 q.x
+// is one contraction over K = D + 2 (padded to a multiple of 8) once the norms
+// ride along as two extra coordinates: A[q] = (-2 q, 1, |q|^2) and
+// B[x] = (x, |x|^2 (1 - kTc), 1).  A warp owns 32 queries (two 16-row
+// m-tiles, A fragments in registers for the whole kernel) and walks the block's
+// shared-memory vertex tile 8 vertices at a time (one ldmatrix per two k-steps,
+// one TF32 mma.sync per m-tile and k-step); the accumulators are the filter
+// values, compared in registers against the running bound of their query.
 //
-// Filter, then exact decision.  For each (query, vertex) the inner loop only
-// accumulates the dot product with -2q (one packed FP32x2 FMA per coordinate
-// for two vertices), which gives the expansion |q|^2 + |x|^2 - 2 q.x of the
-// squared distance.  Its FP32 error is at most (12 D + 24) u (|q|^2 + |x|^2)
-// (u = 2^-24: the dot product and both norms are D-term FMA sums, bounded by
-// Cauchy-Schwarz), and the exact FP32 distance below differs from the true one
-// by at most 4 (D + 2) u d^2.  A vertex whose expansion, lowered by that bound,
-// still exceeds the running best cannot become the best; every other vertex
-// is re-evaluated with the same exact formula as the other NEAREST kernels
-// (sum of fmaf((q_d - x_d)^2)), which alone decides.  Results are therefore
-// identical to the plain scan.
-constexpr int kQThreads = 128;
-constexpr int kQPT = 2;
-constexpr int kTile = 256;
+// Error bound.  TF32 keeps 10 of the 23 stored mantissa bits (truncation, or
+// rounding, of each operand: relative error <= 2^-10), products are exact and
+// the accumulation error stays below 2^-14 of sum |a_k b_k| for K <= 32.  With
+// sum |a_k b_k| <= 2 (|q|^2 + |x|^2), the computed value is within
+// 1.04 * 2^-8 (|q|^2 + |x|^2) of e.  The vertex half of that error is taken
+// out of B (|x|^2 scaled by 1 - kTc), the query half goes into the bound
+// (kTq |q|^2).  The exact FP32 squared distance (sum of fmaf((q_d - x_d)^2))
+// is within 4 (D + 2) u d^2 of the true one (u = 2^-24), so a bound built
+// from the exact distance d2 of any admissible vertex as
+//   lim = (d2 (1 + 4 (D + 2) u) + kTq |q|^2) (1 + 4 u)
+// is never below the computed filter value of the true nearest vertex.  Every
+// vertex that passes is re-evaluated with the exact formula, which alone
+// decides: the results equal the plain scan's.  The bound holds while every
+// nonzero coordinate has a magnitude in [2^-60, 2^60] (normal products, no
+// overflow); the ordering pass flags any other input and the kernel then sends
+// every pair to the exact check.
+constexpr int kTcWarps = 8;
+constexpr int kSliceAlign = 256;           // tree slices are whole tiles
+constexpr int kTcThreads = kTcWarps * 32;
+constexpr int kTcQueries = kTcWarps * 32;  // queries per block
+constexpr float kTc = 1.125f / 256.f;      // folded into |x|^2
+constexpr float kTq = 1.25f / 256.f;       // widening by |q|^2
 
-// Up to 14 coordinates the registers are capped so that 7 blocks (28 warps)
-// stay resident per SM; the compiler fits the loop without spilling and the
-// extra warps hide the shared-memory latency of the vertex tiles.
 template <int DIM>
-__global__ void __launch_bounds__(kQThreads, DIM <= 14 ? 7 : 1)
-nearest_qpt_kernel(const float *__restrict__ tree, int N, int64_t ld,
-                   const float *__restrict__ queries, const float *__restrict__ budgets, int Q,
-                   int chunk, int64_t *__restrict__ out_idx, Best *__restrict__ partial,
-                   const int *__restrict__ perm, const int *__restrict__ cut,
-                   const float *__restrict__ seed) {
-    // rows 0..DIM-1 coordinates, row DIM g, row DIM+1 |x|^2 (1 - c3)
-    __shared__ __align__(16) float tile[(DIM + 2) * kTile];
-    constexpr float kU = 5.9604645e-8f;                   // 2^-24
-    constexpr float kC3 = (12.f * DIM + 24.f) * kU;       // expansion error / (|q|^2 + |x|^2)
-    constexpr float kC1 = 4.f * (DIM + 2.f) * kU;         // exact-distance relative error
-    f2 m2q[kQPT][DIM];   // (-2 q_d, -2 q_d) packed; q_d = -0.5 * (-2 q_d) exactly
-    float cq[kQPT], qn[kQPT], lim[kQPT];
-    Best best[kQPT];
-    const int qb = blockIdx.x * kQThreads * kQPT;
+struct TcShape {
+    static constexpr int K = ((DIM + 2 + 7) / 8) * 8;  // contraction length
+    static constexpr int KS = K / 8;                   // m16n8k8 steps
+    static constexpr int CH = K / 4;                   // 16-byte chunks per vertex row
+    static constexpr int VT = K <= 16 ? 256 : 128;     // vertices per tile (16 KB)
+};
+
+// Chunk swizzle of a vertex row: the 8 rows one ldmatrix reads (8 consecutive
+// vertices, one chunk each) land in 8 distinct 16-byte bank groups.
+template <int CH>
+__device__ __forceinline__ int tc_swz(int v) {
+    if (CH == 8) return v & 7;
+    if (CH == 4) return (v >> 1) & 3;
+    return (v >> 2) & 1;  // CH = 2 or 6
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2,
+                                        unsigned &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned &r0, unsigned &r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr)
+                 : "memory");
+}
+
+// Inputs: the g-ordered tree (SoA rows, ld = N) with perm (ordered -> original
+// index), the budget-ordered queries, cut (vertices each query block scans),
+// the shared bound seed (see below); *exhaustive != 0 turns the filter off.
+// Block (x, y) takes queries [256 x, 256 x + 256) and the tree slice
+// [y chunk, (y + 1) chunk) cut at cut[x]; its partial bests go to
+// partial[y][q] for the reduce.
+template <int DIM>
+__global__ void __launch_bounds__(kTcThreads)
+nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
+                  const float *__restrict__ budgets, int Q, int chunk,
+                  Best *__restrict__ partial, const int *__restrict__ perm,
+                  const int *__restrict__ cut, float *__restrict__ seed,
+                  const int *__restrict__ exhaustive) {
+    using S = TcShape<DIM>;
+    constexpr int K = S::K, KS = S::KS, CH = S::CH, VT = S::VT;
+    __shared__ __align__(16) float xt[VT * K];  // vertex rows, swizzled chunks
+    __shared__ float gt[VT];
+    __shared__ float qsm[DIM][kTcQueries];      // the block's queries (exact checks)
+    __shared__ float red_g[kTcWarps];
+    constexpr float kU = 5.9604645e-8f;            // 2^-24
+    constexpr float kC1 = 4.f * (DIM + 2.f) * kU;  // exact-distance relative error
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int qb = blockIdx.x * kTcQueries;
+    const int vs = blockIdx.y * chunk;
+    const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
+    if (vs >= ve) return;  // no partial record: the reduce skips this slice
+    const bool exact_only = *exhaustive != 0;
+
+    {
+        // kTcThreads == kTcQueries: thread t stages query qb + t (independent loads)
+        const int j = threadIdx.x;
+        const bool ok = qb + j < Q;
 #pragma unroll
-    for (int j = 0; j < kQPT; ++j) {
-        const int q = qb + j * kQThreads + threadIdx.x;
+        for (int d = 0; d < DIM; ++d) qsm[d][j] = ok ? __ldg(queries + (size_t)d * Q + qb + j) : 0.f;
+    }
+    __syncthreads();
+    // rows of this thread: slot r = 2 * mt + h is query qb + 32 warp + 16 mt + grp + 8 h
+    auto row_l = [&](int r) { return warp * 32 + (r >> 1) * 16 + grp + (r & 1) * 8; };
+    auto row_q = [&](int r) { return qb + row_l(r); };
+    float cq[4], qn[4], lim[4];
+    Best best[4];
+    unsigned a[2][KS][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = row_q(r);
         const bool ok = q < Q;
         float n2 = 0.f;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            const float v = ok ? queries[(size_t)d * Q + q] : 0.f;
-            m2q[j][d] = f2_pack(-2.f * v, -2.f * v);
+            const float v = qsm[d][row_l(r)];
             n2 = fmaf(v, v, n2);
         }
-        qn[j] = n2;
-        cq[j] = ok ? budgets[q] : -FLT_MAX;   // nothing is admissible for padding
-        best[j] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
-        lim[j] = FLT_MAX * 2.f;
+        qn[r] = n2;
+        cq[r] = ok ? budgets[q] : -FLT_MAX;  // nothing is admissible for padding
+        best[r] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+        lim[r] = FLT_MAX * 2.f;
     }
-    // Budget-ordered mode (perm, cut given): the tree is sorted by g and this
-    // query block only scans the first cut[block] vertices (no vertex beyond
-    // has g below the block's largest budget); results carry original indices
-    // (perm), which also break exact (d^2, g) ties.
-    const int vs = blockIdx.y * chunk;
-    const int ve = min(cut ? min(N, cut[blockIdx.x]) : N, vs + chunk);
-    if (cut && vs >= ve) return;  // no partial record: the reduce skips this slice
-    auto orig = [&](int v) { return perm ? __ldg(perm + v) : v; };
-    if (seed) {
-        // the exact squared distance of an admissible vertex found by the
-        // seeding pass bounds the answer for every slice
+    // A fragments: a0 (row grp, k tig), a1 (row grp + 8, k tig), a2/a3 the same rows at k + 4
 #pragma unroll
-        for (int j = 0; j < kQPT; ++j) {
-            const int q = qb + j * kQThreads + threadIdx.x;
-            const float sd = q < Q ? seed[q] : FLT_MAX * 2.f;
-            if (sd <= FLT_MAX) lim[j] = fmaf(sd, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU);
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 2 * mt + (i & 1);
+                const int q = row_q(r);
+                const int k = 8 * ks + tig + 4 * (i >> 1);
+                float v = 0.f;
+                if (k < DIM)
+                    v = q < Q ? -2.f * qsm[k][row_l(r)] : 0.f;
+                else if (k == DIM)
+                    v = 1.f;
+                else if (k == DIM + 1)
+                    v = qn[r];
+                a[mt][ks][i] = __float_as_uint(v);
+            }
         }
     }
-    if (cut) {
-        // An admissible vertex of this slice has |q - x| < c - g_min(slice):
-        // the filter starts from that bound (rounded up, with the same
-        // inflation as below), or admits nothing when c <= g_min.
-        __shared__ float red_g[kQThreads / 32];
+    unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
+    auto widen = [&](int r, float sd) {
+        if (sd <= FLT_MAX) lim[r] = fminf(lim[r], fmaf(sd, 1.f + kC1, kTq * qn[r]) * (1.f + 4.f * kU));
+    };
+    unsigned pend[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = row_q(r);
+        pend[r] = q < Q ? __ldcg(shared_lim + q) : 0x7f800000u;
+        widen(r, __uint_as_float(pend[r]));
+    }
+    {
+        // an admissible vertex of this slice has |q - x| < c - g_min(slice)
         float gm = FLT_MAX;
-        for (int v = vs + threadIdx.x; v < ve; v += kQThreads)
-            gm = fminf(gm, __ldg(tree + (size_t)DIM * ld + v));
+#pragma unroll 4
+        for (int v = vs + threadIdx.x; v < ve; v += kTcThreads)
+            gm = fminf(gm, __ldg(tree + (size_t)DIM * N + v));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
-        if ((threadIdx.x & 31) == 0) red_g[threadIdx.x >> 5] = gm;
+        if (lane == 0) red_g[warp] = gm;
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kQThreads / 32; ++k) gm = fminf(gm, red_g[k]);
+        for (int k = 0; k < kTcWarps; ++k) gm = fminf(gm, red_g[k]);
 #pragma unroll
-        for (int j = 0; j < kQPT; ++j) {
-            if (!(cq[j] > gm)) {
-                lim[j] = -FLT_MAX * 2.f;
+        for (int r = 0; r < 4; ++r) {
+            if (!(cq[r] > gm)) {
+                lim[r] = -FLT_MAX * 2.f;
+            } else if (exact_only) {
+                lim[r] = FLT_MAX * 2.f;
             } else {
-                const float t = __fsub_ru(cq[j], gm);
+                const float t = __fsub_ru(cq[r], gm);
                 const float b2 = __fmul_ru(t, t);
-                lim[j] = fminf(lim[j], fmaf(b2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU));
+                lim[r] = fminf(lim[r], fmaf(b2, 1.f + kC1, kTq * qn[r]) * (1.f + 4.f * kU));
             }
         }
     }
-    const float4 *tile4 = reinterpret_cast<const float4 *>(tile);
-    for (int v0 = vs; v0 < ve; v0 += kTile) {
-        const int nv = min(kTile, ve - v0);
+    const unsigned xt_s = (unsigned)__cvta_generic_to_shared(xt);
+    // ldmatrix row addresses of this lane: matrix (lane >> 3) of a pair of
+    // k-steps, vertex row (lane & 7) of the 8-vertex n-tile
+    const int lrow = lane & 7, lmat = lane >> 3;
+    // The next tile's vertex (coordinates and g) is loaded into registers
+    // while the current tile is being scanned, so that the load latency
+    // overlaps the tensor-core work; 32-bit element indices keep the per-row
+    // offsets cheap (N (D + 1) < 2^31).
+    const int t_ld = threadIdx.x & (VT - 1);  // VT < kTcThreads: two threads per row store the same values
+    float px[DIM + 1];
+    auto prefetch = [&](int v0n) {
+        const bool ok = t_ld < min(VT, ve - v0n);
+        const unsigned base = (unsigned)(v0n + t_ld);
+#pragma unroll
+        for (int d = 0; d <= DIM; ++d) px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)N)) : 0.f;
+        if (!ok) px[DIM] = FLT_MAX * 2.f;  // padding vertex: g = +inf
+    };
+    prefetch(vs);
+    for (int v0 = vs; v0 < ve; v0 += VT) {
+        const int nv = min(VT, ve - v0);
         __syncthreads();
-        for (int i = threadIdx.x; i < (DIM + 1) * kTile; i += kQThreads) {
-            const int d = i / kTile, j = i - d * kTile;
-            // padding vertices get g = +inf: never admissible
-            tile[i] = j < nv ? __ldg(tree + (size_t)d * ld + v0 + j) : (d == DIM ? FLT_MAX * 2.f : 0.f);
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < kTile; j += kQThreads) {
+        {
+            // one vertex row per thread: coordinates, folded norm, 1, zero pad
+            float *row = xt + t_ld * K;
+            const int sw = tc_swz<CH>(t_ld);
+            const bool ok = t_ld < nv;
+            float x[K];
             float n2 = 0.f;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) n2 = fmaf(tile[d * kTile + j], tile[d * kTile + j], n2);
-            tile[(DIM + 1) * kTile + j] = n2 * (1.f - kC3);
+            for (int d = 0; d < DIM; ++d) {
+                x[d] = px[d];
+                n2 = fmaf(x[d], x[d], n2);
+            }
+            x[DIM] = ok ? n2 * (1.f - kTc) : FLT_MAX * 2.f;  // padding: never passes
+            x[DIM + 1] = 1.f;
+#pragma unroll
+            for (int d = DIM + 2; d < K; ++d) x[d] = 0.f;
+            gt[t_ld] = px[DIM];
+            float4 *row4 = reinterpret_cast<float4 *>(row);
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                row4[c ^ sw] = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
         }
         __syncthreads();
-        if (v0 == vs && !seed) {
-            // Seed each query's best with an exact check of the slice's first
-            // 32 vertices, so that the filter below starts from a finite
-            // bound instead of re-checking the whole first tile.
-            const int np = min(nv, 32);
-            for (int u = 0; u < np; ++u) {
+        if (v0 + VT < ve) prefetch(v0 + VT);
+        // refresh the bounds from the shared one (loaded a tile ago)
+        if (!exact_only) {
 #pragma unroll
-                for (int j = 0; j < kQPT; ++j) {
-                    const float g = tile[DIM * kTile + u];
-                    if (!(g < cq[j])) continue;
-                    float d2 = 0.f;
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        float lo, hi;
-                        f2_unpack(m2q[j][d], lo, hi);
-                        const float a = -0.5f * lo - tile[d * kTile + u];
-                        d2 = fmaf(a, a, d2);
-                    }
-                    if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
-                        (d2 < best[j].d2 || g < best[j].g ||
-                         (g == best[j].g && orig(v0 + u) < best[j].idx))) {
-                        best[j].d2 = d2;
-                        best[j].g = g;
-                        best[j].idx = orig(v0 + u);
-                        lim[j] = fminf(lim[j], fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU));
-                    }
-                }
+            for (int r = 0; r < 4; ++r) {
+                const int q = row_q(r);
+                widen(r, __uint_as_float(pend[r]));
+                if (q < Q) pend[r] = __ldcg(shared_lim + q);
             }
         }
-        const int ng = (nv + 7) >> 3;   // groups of 8 vertices
-        for (int gq = 0; gq < ng; ++gq) {
-            const float4 wa = tile4[(DIM + 1) * (kTile / 4) + 2 * gq];
-            const float4 wb = tile4[(DIM + 1) * (kTile / 4) + 2 * gq + 1];
-            f2 acc[kQPT][4];
+        const int ng = (nv + 7) >> 3;
+        for (int nt = 0; nt < ng; ++nt) {
+            const int vrow = nt * 8 + lrow;
+            unsigned b[KS][2];
 #pragma unroll
-            for (int j = 0; j < kQPT; ++j) {
-                const f2 qq = f2_pack(qn[j], qn[j]);
-                acc[j][0] = f2_add(f2_pack(wa.x, wa.y), qq);
-                acc[j][1] = f2_add(f2_pack(wa.z, wa.w), qq);
-                acc[j][2] = f2_add(f2_pack(wb.x, wb.y), qq);
-                acc[j][3] = f2_add(f2_pack(wb.z, wb.w), qq);
+            for (int kp = 0; kp + 1 < KS; kp += 2) {
+                const int c = 2 * kp + lmat;  // chunk of k-step kp (lmat 0, 1) or kp + 1 (2, 3)
+                const unsigned addr = xt_s + (unsigned)((vrow * K + 4 * (c ^ tc_swz<CH>(vrow))) * 4);
+                ldsm_x4(addr, b[kp][0], b[kp][1], b[kp + 1][0], b[kp + 1][1]);
             }
+            if (KS & 1) {
+                const int c = 2 * (KS - 1) + (lmat & 1);
+                const unsigned addr = xt_s + (unsigned)((vrow * K + 4 * (c ^ tc_swz<CH>(vrow))) * 4);
+                ldsm_x2(addr, b[KS - 1][0], b[KS - 1][1]);
+            }
+            float acc[2][4];
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                const float4 xa = tile4[d * (kTile / 4) + 2 * gq];
-                const float4 xb = tile4[d * (kTile / 4) + 2 * gq + 1];
-                const f2 x0 = f2_pack(xa.x, xa.y), x1 = f2_pack(xa.z, xa.w);
-                const f2 x2 = f2_pack(xb.x, xb.y), x3 = f2_pack(xb.z, xb.w);
+            for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
-                for (int j = 0; j < kQPT; ++j) {
-                    acc[j][0] = f2_fma(m2q[j][d], x0, acc[j][0]);
-                    acc[j][1] = f2_fma(m2q[j][d], x1, acc[j][1]);
-                    acc[j][2] = f2_fma(m2q[j][d], x2, acc[j][2]);
-                    acc[j][3] = f2_fma(m2q[j][d], x3, acc[j][3]);
+                for (int i = 0; i < 4; ++i) acc[mt][i] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) mma_tf32(acc[mt], a[mt][ks], b[ks][0], b[ks][1]);
+            }
+            // c0, c1: row grp, vertices 2 tig, 2 tig + 1; c2, c3: row grp + 8.
+            // Without the bound (exact_only) every pair goes to the exact check.
+            bool any = exact_only;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) any |= acc[mt][i] <= lim[2 * mt + (i >> 1)];
+            if (!__any_sync(kFull, any)) continue;
+            unsigned pass = 0;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    pass |= (exact_only || acc[mt][i] <= lim[2 * mt + (i >> 1)]) ? 1u << (4 * mt + i) : 0u;
+            // survivors are rare: one copy of the exact check, with the row's
+            // state selected and written back by value
+            while (pass) {
+                const int e = __ffs(pass) - 1;
+                pass &= pass - 1;
+                const int r = 2 * (e >> 2) + ((e >> 1) & 1);
+                const int q = row_q(r);
+                const int vl = nt * 8 + 2 * tig + (e & 1);
+                if (q >= Q || vl >= nv) continue;
+                float c_r = cq[0], q_r = qn[0], l_r = lim[0];
+                Best b_r = best[0];
+#pragma unroll
+                for (int k = 1; k < 4; ++k)
+                    if (r == k) { c_r = cq[k]; q_r = qn[k]; l_r = lim[k]; b_r = best[k]; }
+                const float g = gt[vl];
+                // a vertex with g >= c is never admissible
+                if (!(g < c_r)) continue;
+                const float *xr = xt + vl * K;
+                const int sw = tc_swz<CH>(vl);
+                float d2 = 0.f;
+                const float *qp = &qsm[0][q - qb];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const float dq = qp[d * kTcQueries] - xr[4 * ((d >> 2) ^ sw) + (d & 3)];
+                    d2 = fmaf(dq, dq, d2);
                 }
-            }
-#pragma unroll
-            for (int j = 0; j < kQPT; ++j) {
-                float e[8];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) f2_unpack(acc[j][h], e[2 * h], e[2 * h + 1]);
-                unsigned cm = 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) cm |= (e[u] <= lim[j]) ? (1u << u) : 0u;
-                // survivors of the filter (a superset once lim shrinks below)
-                while (cm) {
-                    const int u = __ffs(cm) - 1;
-                    cm &= cm - 1;
-                    {
-                        const int vl = 8 * gq + u;
-                        // a vertex with g >= c is never admissible (distances
-                        // are >= 0): no exact check needed
-                        if (!(tile[DIM * kTile + vl] < cq[j])) continue;
-                        float d2 = 0.f;
-#pragma unroll
-                        for (int d = 0; d < DIM; ++d) {
-                            float lo, hi;
-                            f2_unpack(m2q[j][d], lo, hi);
-                            const float a = -0.5f * lo - tile[d * kTile + vl];
-                            d2 = fmaf(a, a, d2);
-                        }
-                        const float g = tile[DIM * kTile + vl];
-                        // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index)
-                        if (d2 <= best[j].d2 && g + __fsqrt_rn(d2) < cq[j] &&
-                            (d2 < best[j].d2 || g < best[j].g ||
-                             (g == best[j].g && orig(v0 + vl) < best[j].idx))) {
-                            best[j].d2 = d2;
-                            best[j].g = g;
-                            best[j].idx = orig(v0 + vl);
-                            lim[j] = fminf(lim[j], fmaf(d2, 1.f + kC1, kC3 * qn[j]) * (1.f + 4.f * kU));
-                        }
+                // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index)
+                const int id = __ldg(perm + v0 + vl);
+                if (d2 <= b_r.d2 && g + __fsqrt_rn(d2) < c_r &&
+                    (d2 < b_r.d2 || g < b_r.g || (g == b_r.g && id < b_r.idx))) {
+                    b_r = Best{d2, g, id};
+                    if (!exact_only) {
+                        l_r = fminf(l_r, fmaf(d2, 1.f + kC1, kTq * q_r) * (1.f + 4.f * kU));
+                        atomicMin(shared_lim + q, __float_as_uint(d2));
                     }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (r == k) { lim[k] = l_r; best[k] = b_r; }
                 }
+            }
+            // the quad's lanes scan different vertex columns of the same
+            // rows: a record of one tightens the bound of all four
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 1));
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 2));
             }
         }
     }
+    // the four lanes of a quad hold the same rows: combine, lane tig == 0 writes
 #pragma unroll
-    for (int j = 0; j < kQPT; ++j) {
-        const int q = qb + j * kQThreads + threadIdx.x;
-        if (q >= Q) continue;
-        if (partial)
-            partial[(size_t)blockIdx.y * Q + q] = best[j];
-        else
-            out_idx[q] = best[j].idx;
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            const Best other = shfl_best(best[r], o);
+            if (better(other, best[r])) best[r] = other;
+        }
+        const int q = row_q(r);
+        if (tig == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
     }
 }
 
@@ -426,6 +522,7 @@ constexpr int kSortBuckets = 1024;
 
 struct SortState {
     int gmin, gmax;                      // order-preserving keys of the finite g range
+    int exact_only;                      // a coordinate lies outside the filter's range
     int tree_off[kSortBuckets + 1];      // bucket starts of the g-ordered tree
     int tree_cur[kSortBuckets];
     int query_off[kSortBuckets + 1];
@@ -458,6 +555,7 @@ __global__ void sort_init(SortState *S) {
     if (i == 0) {
         S->gmin = 0x7fffffff;
         S->gmax = (int)0x80000000;
+        S->exact_only = 0;
     }
     if (i <= kSortBuckets) S->tree_off[i] = S->query_off[i] = 0;
 }
@@ -537,18 +635,33 @@ __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, 
     g_scale(*S, &lo, &scale);
     const int bt = i < N ? sort_bucket(tree[(size_t)dim * ld + i], lo, scale) : -1;
     const int pt = grouped_add(S->tree_cur, bt);
+    // the tensor-core filter's error bound needs every nonzero coordinate in
+    // [2^-60, 2^60]; anything else (NaN and infinities included) turns it off
+    bool out_of_range = false;
+    auto check = [&](float v) {
+        out_of_range |= v != 0.f && !(fabsf(v) >= 0x1p-60f && fabsf(v) <= 0x1p60f);
+    };
     if (i < N) {
-        for (int d = 0; d <= dim; ++d) tree_s[(size_t)d * N + pt] = tree[(size_t)d * ld + i];
+        for (int d = 0; d <= dim; ++d) {
+            const float v = tree[(size_t)d * ld + i];
+            if (d < dim) check(v);
+            tree_s[(size_t)d * N + pt] = v;
+        }
         perm[pt] = i;
     }
     const float c = i < Q ? budgets[i] : 0.f;
     const int bq = i < Q ? sort_bucket(c, lo, scale) : -1;
     const int pq = grouped_add(S->query_cur, bq);
     if (i < Q) {
-        for (int d = 0; d < dim; ++d) q_s[(size_t)d * Q + pq] = queries[(size_t)d * Q + i];
+        for (int d = 0; d < dim; ++d) {
+            const float v = queries[(size_t)d * Q + i];
+            check(v);
+            q_s[(size_t)d * Q + pq] = v;
+        }
         c_s[pq] = c;
         qperm[pq] = i;
     }
+    if (out_of_range) S->exact_only = 1;
 }
 
 // Vertices a block of bq consecutive (ordered) queries must scan: up to the
@@ -648,23 +761,23 @@ __global__ void sort_count_pairs(const int *__restrict__ cut, int qblocks, int Q
 
 // out_idx null: only count the scanned pairs into *pairs (synchronises).
 template <int DIM>
-mrpop_status nearest_qpt_sorted(const float *tree, int N, int64_t ld, const float *queries,
+mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *queries,
                                 const float *budgets, int Q, int64_t *out_idx, cudaStream_t st,
                                 int64_t *pairs = nullptr) {
     int dev = 0, sms = 1, bps = 1;
     MRPOP_CUDA_TRY(cudaGetDevice(&dev));
     MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     MRPOP_CUDA_TRY(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_qpt_kernel<DIM>, kQThreads, 0));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_tc_kernel<DIM>, kTcThreads, 0));
     bps = std::max(bps, 1);
-    const int bq = kQThreads * kQPT;
+    const int bq = kTcQueries;
     const int qblocks = (Q + bq - 1) / bq;
     // about four waves of (query block, tree slice) pieces before the cut
     // removes some: the dynamic block scheduler then evens out the blocks
     // that stop early
     int splits = std::max(1, (4 * sms * bps + qblocks - 1) / qblocks);
     int chunk = (N + splits - 1) / splits;
-    chunk = std::max(kTile, ((chunk + kTile - 1) / kTile) * kTile);
+    chunk = std::max(kSliceAlign, ((chunk + kSliceAlign - 1) / kSliceAlign) * kSliceAlign);
     splits = std::max(1, (N + chunk - 1) / chunk);
     if (splits > 65535) return set_error(MRPOP_EINVAL, "nearest: tree too large");
     // one stream-ordered arena: sort state, ordered tree and queries,
@@ -719,8 +832,8 @@ mrpop_status nearest_qpt_sorted(const float *tree, int N, int64_t ld, const floa
     }
     nearest_seed<DIM><<<(Q + 127) / 128, 128, 0, st>>>(tree_s, N, q_s, c_s, Q, seed);
     dim3 grid(qblocks, splits);
-    nearest_qpt_kernel<DIM><<<grid, kQThreads, 0, st>>>(tree_s, N, N, q_s, c_s, Q, chunk, nullptr,
-                                                        partial, perm, cut, seed);
+    nearest_tc_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk, partial,
+                                                        perm, cut, seed, &S->exact_only);
     nearest_sorted_reduce<<<(Q + 255) / 256, 256, 0, st>>>(partial, cut, chunk, Q, bq, qperm,
                                                            out_idx);
     const cudaError_t e = cudaGetLastError();
@@ -861,12 +974,12 @@ mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
     // Large batches: queries in registers against shared-memory tree tiles.
     if (Q >= 2048 && N > 0) {
         switch (dim) {
-            case 3: return nearest_qpt_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 6: return nearest_qpt_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 7: return nearest_qpt_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 14: return nearest_qpt_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 21: return nearest_qpt_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 28: return nearest_qpt_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 3: return nearest_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 6: return nearest_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 7: return nearest_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 14: return nearest_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 21: return nearest_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 28: return nearest_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st);
             default: break;
         }
     }
@@ -894,12 +1007,12 @@ mrpop_status nearest_pairs(const float *tree, int64_t N, int64_t ld, int dim, co
     *pairs = N * Q;  // the small-batch kernels scan every vertex
     if (Q >= 2048 && N > 0) {
         switch (dim) {
-            case 3: return nearest_qpt_sorted<3>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
-            case 6: return nearest_qpt_sorted<6>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
-            case 7: return nearest_qpt_sorted<7>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
-            case 14: return nearest_qpt_sorted<14>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
-            case 21: return nearest_qpt_sorted<21>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
-            case 28: return nearest_qpt_sorted<28>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 3: return nearest_sorted<3>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 6: return nearest_sorted<6>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 7: return nearest_sorted<7>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 14: return nearest_sorted<14>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 21: return nearest_sorted<21>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
+            case 28: return nearest_sorted<28>(tree, n, ld, queries, budgets, q, nullptr, st, pairs);
             default: break;
         }
     }

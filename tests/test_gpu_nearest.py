@@ -153,8 +153,8 @@ def test_path_cost_parity(mp, orc):
 @pytest.mark.parametrize("D,N,Q", [(14, 3000, 4096), (28, 2000, 2048), (6, 5000, 3000),
                                    (3, 700, 2500), (7, 257, 2049), (21, 1500, 2100)])
 def test_nearest_query_blocked_parity(mp, orc, D, N, Q):
-    """Batches of >= 2048 queries take the query-blocked kernel (expansion
-    filter + exact re-check); sampled queries against the oracle, duplicates
+    """Batches of >= 2048 queries take the budget-ordered path (tensor-core
+    expansion filter + exact re-check); sampled queries against the oracle, duplicates
     in the tree for ties, and the whole batch against the small-batch kernel
     (called in chunks of < 2048 queries), which must agree index for index."""
     lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
@@ -191,3 +191,33 @@ def test_nearest_work_counts(mp, orc):
     assert 0 < pairs < Q * N
     got = mp.nearest(t, q, _dev(cs)).cpu().numpy()
     _check_nearest(orc, tree, qs, cs, got, sample=np.arange(0, Q, 37))
+
+
+@pytest.mark.parametrize("case", ["offset", "tiny", "huge", "nan"])
+def test_nearest_tensor_filter_range(mp, orc, case):
+    """The tensor-core filter's error bound is relative to |q|^2 + |x|^2: a
+    box far from the origin (large norms, small distances) must stay exact;
+    a nonzero coordinate below 2^-60 or above 2^60, or a NaN, turns the
+    filter off so that every pair is checked exactly.  Results must equal
+    the small-batch kernel's and the oracle's."""
+    D, N, Q = 14, 1500, 2048
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, N, lo, hi, seed=31, dup_frac=0.05)
+    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=32, budget_lo=0.0, budget_hi=25.0)
+    qs[:, :32] = tree[:D, :32]
+    if case == "offset":
+        tree[:D] += np.float32(1000.0)
+        qs += np.float32(1000.0)
+    elif case == "tiny":
+        qs[3, 5] = np.float32(1e-25)
+    elif case == "huge":
+        tree[2, 7] = np.float32(2.0 ** 61)
+    else:
+        tree[4, 11] = np.nan
+    big = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    small = np.concatenate([
+        mp.nearest(_dev(tree), _dev(np.ascontiguousarray(qs[:, i:i + 1000])),
+                   _dev(cs[i:i + 1000])).cpu().numpy() for i in range(0, Q, 1000)])
+    np.testing.assert_array_equal(big, small)
+    sample = np.concatenate([np.arange(40), np.random.default_rng(7).choice(Q, 120, replace=False)])
+    _check_nearest(orc, tree, qs, cs, big, sample=sample)
