@@ -12,6 +12,7 @@
 // further down, whose filter runs on the tensor cores.
 #include <algorithm>
 #include <cfloat>
+#include <cuda_fp16.h>
 #include <mutex>
 
 #include "mrpop_internal.cuh"
@@ -171,36 +172,50 @@ mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const flo
 // ---------------------------------------------------------------------------
 // NEAREST filter on the tensor cores.  The expansion
 //   e(q, x) = |q|^2 + |x|^2 - 2 q.x
-// is one contraction over K = D + 2 (padded to a multiple of 8) once the norms
-// ride along as two extra coordinates: A[q] = (-2 q, 1, |q|^2) and
-// B[x] = (x, |x|^2 (1 - kTc), 1).  A warp owns 32 queries (two 16-row
-// m-tiles, A fragments in registers for the whole kernel) and walks the block's
-// shared-memory vertex tile 8 vertices at a time (one ldmatrix per two k-steps,
-// one TF32 mma.sync per m-tile and k-step); the accumulators are the filter
-// values, compared in registers against the running bound of their query.
+// is one contraction over D + 2 terms once the norms ride along as two extra
+// coordinates: A[q] = (-2 q, 1, |q|^2) and B[x] = (x, |x|^2 (1 - kTc), 1),
+// zero-padded to K.  A warp owns 32 queries (two 16-row m-tiles, A fragments
+// in registers for the whole kernel) and walks the block's shared-memory
+// vertex tile 8 vertices at a time with ldmatrix and mma.sync; the
+// accumulators are the filter values, compared in registers against the
+// running bound of their query.  Two operand types:
 //
-// Error bound.  TF32 keeps 10 of the 23 stored mantissa bits (truncation, or
-// rounding, of each operand: relative error <= 2^-10), products are exact and
-// the accumulation error stays below 2^-14 of sum |a_k b_k| for K <= 32.  With
-// sum |a_k b_k| <= 2 (|q|^2 + |x|^2), the computed value is within
-// 1.04 * 2^-8 (|q|^2 + |x|^2) of e.  The vertex half of that error is taken
-// out of B (|x|^2 scaled by 1 - kTc), the query half goes into the bound
+//  - FP16 for D + 2 <= 16 (nearest_tc16_kernel: one m16n8k16 per m-tile and
+//    8 vertices).  The coordinates are first multiplied by a power of two 2^s
+//    (exact), chosen from the largest coordinate magnitude of the batch so
+//    that every scaled coordinate is below 16 and every scaled squared norm
+//    below 256 D: the operands stay inside FP16's range.  Rounding to FP16
+//    costs at most 2^-11 of an operand, or the operand itself when it is
+//    below 2^-14 (a flush); with scaled coordinates below 16 the flushes add
+//    less than 48 D 2^-14 + 2^-13 < kAbs = 2^-4 in all.
+//  - TF32 for larger D (nearest_tc_kernel: m16n8k8 steps).  TF32 keeps 10 of
+//    the 23 stored mantissa bits (truncation or rounding: 2^-10 of an
+//    operand); there is no scaling, and every nonzero coordinate must lie in
+//    [2^-60, 2^60] (normal products, no overflow).
+//
+// Products are exact and the FP32 accumulation error stays below 2^-14 of
+// sum |a_k b_k| for K <= 32.  With sum |a_k b_k| <= 2 (|q|^2 + |x|^2) the
+// computed value is within 1.0625 * 2^-9 (FP16; 1.04 * 2^-8 for TF32) of
+// (|q|^2 + |x|^2), plus kAbs for FP16, from e (scaled units).  The vertex half
+// of that error is taken out of B (kTc), the query half goes into the bound
 // (kTq |q|^2).  The exact FP32 squared distance (sum of fmaf((q_d - x_d)^2))
-// is within 4 (D + 2) u d^2 of the true one (u = 2^-24), so a bound built
-// from the exact distance d2 of any admissible vertex as
-//   lim = (d2 (1 + 4 (D + 2) u) + kTq |q|^2) (1 + 4 u)
+// is within 4 (D + 2) u d^2 of the true one (u = 2^-24), so a bound built from
+// the exact distance d2 of any admissible vertex as
+//   lim = (d2 2^2s (1 + 4 (D + 2) u) + kTq |q|^2 + kAbs) (1 + 4 u)
 // is never below the computed filter value of the true nearest vertex.  Every
-// vertex that passes is re-evaluated with the exact formula, which alone
-// decides: the results equal the plain scan's.  The bound holds while every
-// nonzero coordinate has a magnitude in [2^-60, 2^60] (normal products, no
-// overflow); the ordering pass flags any other input and the kernel then sends
-// every pair to the exact check.
+// vertex that passes is re-evaluated with the exact formula on the unscaled
+// FP32 coordinates, which alone decides: the results equal the plain scan's.
+// The ordering pass flags inputs outside the operand type's range (NaN and
+// infinities always) and the kernel then sends every pair to the exact check.
 constexpr int kTcWarps = 8;
 constexpr int kSliceAlign = 256;           // tree slices are whole tiles
 constexpr int kTcThreads = kTcWarps * 32;
 constexpr int kTcQueries = kTcWarps * 32;  // queries per block
-constexpr float kTc = 1.125f / 256.f;      // folded into |x|^2
-constexpr float kTq = 1.25f / 256.f;       // widening by |q|^2
+constexpr float kTc = 1.125f / 256.f;      // TF32: folded into |x|^2
+constexpr float kTq = 1.25f / 256.f;       // TF32: widening by |q|^2
+constexpr float kTc16 = 1.125f / 512.f;    // FP16: folded into |x|^2
+constexpr float kTq16 = 1.25f / 512.f;     // FP16: widening by |q|^2
+constexpr float kAbs16 = 1.f / 16.f;       // FP16: flushed operands (scaled units)
 
 template <int DIM>
 struct TcShape {
@@ -473,11 +488,15 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
                     const float dq = qp[d * kTcQueries] - xr[4 * ((d >> 2) ^ sw) + (d & 3)];
                     d2 = fmaf(dq, dq, d2);
                 }
-                // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index)
-                const int id = __ldg(perm + v0 + vl);
+                // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index).
+                // The running best keeps the vertex's position in the g order;
+                // original indices (perm) are looked up only to break an exact
+                // (d^2, g) tie, and once per row at the end.
+                const int pos = v0 + vl;
                 if (d2 <= b_r.d2 && g + __fsqrt_rn(d2) < c_r &&
-                    (d2 < b_r.d2 || g < b_r.g || (g == b_r.g && id < b_r.idx))) {
-                    b_r = Best{d2, g, id};
+                    (d2 < b_r.d2 || g < b_r.g ||
+                     (g == b_r.g && __ldg(perm + pos) < __ldg(perm + b_r.idx)))) {
+                    b_r = Best{d2, g, pos};
                     if (!exact_only) {
                         l_r = fminf(l_r, fmaf(d2, 1.f + kC1, kTq * q_r) * (1.f + 4.f * kU));
                         atomicMin(shared_lim + q, __float_as_uint(d2));
@@ -496,9 +515,294 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
             }
         }
     }
-    // the four lanes of a quad hold the same rows: combine, lane tig == 0 writes
+    // the four lanes of a quad hold the same rows: combine (by original index),
+    // lane tig == 0 writes
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
+        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            const Best other = shfl_best(best[r], o);
+            if (better(other, best[r])) best[r] = other;
+        }
+        const int q = row_q(r);
+        if (tig == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
+    }
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                        unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);  // lo in the low 16 bits
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+
+// FP16 form of the filter for D + 2 <= 16 (K = 16: one m16n8k16 per m-tile
+// and 8 vertices; two groups of 8 vertices per ldmatrix.x4).  Same inputs as
+// nearest_tc_kernel plus the ordering pass's largest coordinate magnitude
+// (*maxabs, as float bits) and its non-finite flag (*nonfinite).  Vertex rows
+// hold 16 halves (32 bytes, two 16-byte chunks swizzled by bit 2 of the
+// vertex); the unscaled FP32 coordinates of the tile are kept beside them
+// (SoA) for the exact checks.
+template <int DIM>
+__global__ void __launch_bounds__(kTcThreads)
+nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
+                    const float *__restrict__ budgets, int Q, int chunk,
+                    Best *__restrict__ partial, const int *__restrict__ perm,
+                    const int *__restrict__ cut, float *__restrict__ seed,
+                    const unsigned *__restrict__ maxabs, const int *__restrict__ nonfinite) {
+    static_assert(DIM + 2 <= 16, "FP16 filter holds K = 16");
+    constexpr int VT = kTcThreads;                   // vertices per tile
+    __shared__ __align__(16) unsigned xh[VT * 8];    // FP16 rows, swizzled chunks
+    __shared__ float xf[DIM][VT];                    // unscaled FP32 coordinates
+    __shared__ float gt[VT];
+    __shared__ float qsm[DIM][kTcQueries];           // the block's queries (exact checks)
+    __shared__ float red_g[kTcWarps];
+    constexpr float kU = 5.9604645e-8f;            // 2^-24
+    constexpr float kC1 = 4.f * (DIM + 2.f) * kU;  // exact-distance relative error
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int qb = blockIdx.x * kTcQueries;
+    const int vs = blockIdx.y * chunk;
+    const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
+    if (vs >= ve) return;  // no partial record: the reduce skips this slice
+
+    // power-of-two scale: largest magnitude in [2^(ex-1), 2^ex) -> [8, 16)
+    int ex = 0;
+    frexpf(__uint_as_float(*maxabs), &ex);
+    const int sh = 4 - ex;
+    const bool exact_only = *nonfinite != 0 || sh > 126;
+    const float sc = exact_only ? 1.f : ldexpf(1.f, sh);
+
+    {
+        const int j = threadIdx.x;  // kTcThreads == kTcQueries
+        const bool ok = qb + j < Q;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) qsm[d][j] = ok ? __ldg(queries + (size_t)d * Q + qb + j) : 0.f;
+    }
+    __syncthreads();
+    auto row_l = [&](int r) { return warp * 32 + (r >> 1) * 16 + grp + (r & 1) * 8; };
+    auto row_q = [&](int r) { return qb + row_l(r); };
+    float cq[4], qs2[4], lim[4];  // qs2: scaled |q|^2
+    Best best[4];
+    unsigned a[2][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = row_q(r);
+        float n2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const float v = qsm[d][row_l(r)] * sc;
+            n2 = fmaf(v, v, n2);
+        }
+        qs2[r] = n2;
+        cq[r] = q < Q ? budgets[q] : -FLT_MAX;  // nothing is admissible for padding
+        best[r] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+        lim[r] = FLT_MAX * 2.f;
+    }
+    // A fragments (16 x 16, row-major): register i holds row grp + 8 (i & 1),
+    // columns 2 tig + 8 (i >> 1) and the next one
+    auto a_val = [&](int r, int k) {
+        if (k < DIM) return -2.f * (qsm[k][row_l(r)] * sc);
+        if (k == DIM) return 1.f;
+        if (k == DIM + 1) return qs2[r];
+        return 0.f;
+    };
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 2 * mt + (i & 1), k = 2 * tig + 8 * (i >> 1);
+            a[mt][i] = pack_half2(a_val(r, k), a_val(r, k + 1));
+        }
+    unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
+    // bound from the exact (unscaled) squared distance of an admissible vertex
+    auto bound = [&](int r, float d2) {
+        return fmaf((d2 * sc) * sc, 1.f + kC1, fmaf(kTq16, qs2[r], kAbs16)) * (1.f + 4.f * kU);
+    };
+    auto widen = [&](int r, float sd) {
+        if (sd <= FLT_MAX) lim[r] = fminf(lim[r], bound(r, sd));
+    };
+    unsigned pend[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = row_q(r);
+        pend[r] = q < Q ? __ldcg(shared_lim + q) : 0x7f800000u;
+        widen(r, __uint_as_float(pend[r]));
+    }
+    {
+        // an admissible vertex of this slice has |q - x| < c - g_min(slice)
+        float gm = FLT_MAX;
+#pragma unroll 4
+        for (int v = vs + threadIdx.x; v < ve; v += kTcThreads)
+            gm = fminf(gm, __ldg(tree + (size_t)DIM * N + v));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
+        if (lane == 0) red_g[warp] = gm;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kTcWarps; ++k) gm = fminf(gm, red_g[k]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (!(cq[r] > gm)) {
+                lim[r] = -FLT_MAX * 2.f;
+            } else if (exact_only) {
+                lim[r] = FLT_MAX * 2.f;
+            } else {
+                const float t = __fsub_ru(cq[r], gm);
+                lim[r] = fminf(lim[r], bound(r, __fmul_ru(t, t)));
+            }
+        }
+    }
+    const unsigned xh_s = (unsigned)__cvta_generic_to_shared(xh);
+    // ldmatrix.x4 row address of this lane: matrix lane >> 3 = (group of 8
+    // vertices lane >> 4, chunk (lane >> 3) & 1), vertex row lane & 7
+    const int lrow = lane & 7, lchunk = (lane >> 3) & 1, lgrp = lane >> 4;
+    // next tile's vertex of this thread, loaded while the current one is scanned
+    const int t_ld = threadIdx.x;
+    float px[DIM + 1];
+    auto prefetch = [&](int v0n) {
+        const bool ok = t_ld < min(VT, ve - v0n);
+        const unsigned base = (unsigned)(v0n + t_ld);
+#pragma unroll
+        for (int d = 0; d <= DIM; ++d) px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)N)) : 0.f;
+        if (!ok) px[DIM] = FLT_MAX * 2.f;  // padding vertex: g = +inf
+    };
+    prefetch(vs);
+    for (int v0 = vs; v0 < ve; v0 += VT) {
+        const int nv = min(VT, ve - v0);
+        __syncthreads();
+        {
+            const bool ok = t_ld < nv;
+            float h[16];
+            float n2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                xf[d][t_ld] = px[d];
+                h[d] = px[d] * sc;
+                n2 = fmaf(h[d], h[d], n2);
+            }
+            h[DIM] = ok ? n2 * (1.f - kTc16) : FLT_MAX * 2.f;  // padding: never passes
+            h[DIM + 1] = 1.f;
+#pragma unroll
+            for (int d = DIM + 2; d < 16; ++d) h[d] = 0.f;
+            gt[t_ld] = px[DIM];
+            uint4 *row = reinterpret_cast<uint4 *>(xh + t_ld * 8);
+            const int sw = (t_ld >> 2) & 1;
+            row[0 ^ sw] = make_uint4(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]),
+                                     pack_half2(h[4], h[5]), pack_half2(h[6], h[7]));
+            row[1 ^ sw] = make_uint4(pack_half2(h[8], h[9]), pack_half2(h[10], h[11]),
+                                     pack_half2(h[12], h[13]), pack_half2(h[14], h[15]));
+        }
+        __syncthreads();
+        if (v0 + VT < ve) prefetch(v0 + VT);
+        if (!exact_only) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int q = row_q(r);
+                widen(r, __uint_as_float(pend[r]));
+                if (q < Q) pend[r] = __ldcg(shared_lim + q);
+            }
+        }
+        const int ng2 = (nv + 15) >> 4;  // pairs of 8-vertex groups
+        for (int np = 0; np < ng2; ++np) {
+            const int vrow = (2 * np + lgrp) * 8 + lrow;
+            unsigned b[2][2];
+            ldsm_x4(xh_s + (unsigned)(vrow * 32 + 16 * (lchunk ^ ((vrow >> 2) & 1))), b[0][0],
+                    b[0][1], b[1][0], b[1][1]);
+            float acc[2][2][4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[j][mt][i] = 0.f;
+                    mma_f16(acc[j][mt], a[mt], b[j][0], b[j][1]);
+                }
+            // element (j, mt, i): row grp + 8 (i >> 1) of m-tile mt, vertex
+            // 8 (2 np + j) + 2 tig + (i & 1)
+            bool any = exact_only;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) any |= acc[j][mt][i] <= lim[2 * mt + (i >> 1)];
+            if (!__any_sync(kFull, any)) continue;
+            unsigned pass = 0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        pass |= (exact_only || acc[j][mt][i] <= lim[2 * mt + (i >> 1)])
+                                    ? 1u << (8 * j + 4 * mt + i) : 0u;
+            while (pass) {
+                const int e = __ffs(pass) - 1;
+                pass &= pass - 1;
+                const int r = 2 * ((e >> 2) & 1) + ((e >> 1) & 1);
+                const int q = row_q(r);
+                const int vl = (2 * np + (e >> 3)) * 8 + 2 * tig + (e & 1);
+                if (q >= Q || vl >= nv) continue;
+                float c_r = cq[0], l_r = lim[0];
+                Best b_r = best[0];
+#pragma unroll
+                for (int k = 1; k < 4; ++k)
+                    if (r == k) { c_r = cq[k]; l_r = lim[k]; b_r = best[k]; }
+                const float g = gt[vl];
+                // a vertex with g >= c is never admissible
+                if (!(g < c_r)) continue;
+                float d2 = 0.f;
+                const float *qp = &qsm[0][q - qb];
+                const float *xp = &xf[0][vl];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const float dq = qp[d * kTcQueries] - xp[d * VT];
+                    d2 = fmaf(dq, dq, d2);
+                }
+                // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2, g, index).
+                // The running best keeps the vertex's position in the g order;
+                // original indices (perm) are looked up only to break an exact
+                // (d^2, g) tie, and once per row at the end.
+                const int pos = v0 + vl;
+                if (d2 <= b_r.d2 && g + __fsqrt_rn(d2) < c_r &&
+                    (d2 < b_r.d2 || g < b_r.g ||
+                     (g == b_r.g && __ldg(perm + pos) < __ldg(perm + b_r.idx)))) {
+                    b_r = Best{d2, g, pos};
+                    if (!exact_only) {
+                        float bq = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (r == k) bq = bound(k, d2);
+                        l_r = fminf(l_r, bq);
+                        atomicMin(shared_lim + q, __float_as_uint(d2));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (r == k) { lim[k] = l_r; best[k] = b_r; }
+                }
+            }
+            // the quad's lanes scan different vertex columns of the same
+            // rows: a record of one tightens the bound of all four
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 1));
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 2));
+            }
+        }
+    }
+    // the four lanes of a quad hold the same rows: combine (by original index),
+    // lane tig == 0 writes
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
 #pragma unroll
         for (int o = 1; o <= 2; o <<= 1) {
             const Best other = shfl_best(best[r], o);
@@ -522,7 +826,9 @@ constexpr int kSortBuckets = 1024;
 
 struct SortState {
     int gmin, gmax;                      // order-preserving keys of the finite g range
-    int exact_only;                      // a coordinate lies outside the filter's range
+    int exact_only;                      // a coordinate lies outside the TF32 filter's range
+    int nonfinite;                       // a coordinate is NaN or infinite
+    unsigned maxabs;                     // largest finite coordinate magnitude (float bits)
     int tree_off[kSortBuckets + 1];      // bucket starts of the g-ordered tree
     int tree_cur[kSortBuckets];
     int query_off[kSortBuckets + 1];
@@ -556,6 +862,8 @@ __global__ void sort_init(SortState *S) {
         S->gmin = 0x7fffffff;
         S->gmax = (int)0x80000000;
         S->exact_only = 0;
+        S->nonfinite = 0;
+        S->maxabs = 0u;
     }
     if (i <= kSortBuckets) S->tree_off[i] = S->query_off[i] = 0;
 }
@@ -635,11 +943,16 @@ __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, 
     g_scale(*S, &lo, &scale);
     const int bt = i < N ? sort_bucket(tree[(size_t)dim * ld + i], lo, scale) : -1;
     const int pt = grouped_add(S->tree_cur, bt);
-    // the tensor-core filter's error bound needs every nonzero coordinate in
-    // [2^-60, 2^60]; anything else (NaN and infinities included) turns it off
-    bool out_of_range = false;
+    // the TF32 filter's error bound needs every nonzero coordinate in
+    // [2^-60, 2^60]; the FP16 filter scales by the largest finite magnitude;
+    // NaN and infinities turn either off
+    bool out_of_range = false, nonfinite = false;
+    unsigned mx = 0u;
     auto check = [&](float v) {
-        out_of_range |= v != 0.f && !(fabsf(v) >= 0x1p-60f && fabsf(v) <= 0x1p60f);
+        const float a = fabsf(v);
+        out_of_range |= v != 0.f && !(a >= 0x1p-60f && a <= 0x1p60f);
+        nonfinite |= !(a <= FLT_MAX);
+        if (a <= FLT_MAX) mx = max(mx, __float_as_uint(a));
     };
     if (i < N) {
         for (int d = 0; d <= dim; ++d) {
@@ -662,6 +975,9 @@ __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, 
         qperm[pq] = i;
     }
     if (out_of_range) S->exact_only = 1;
+    if (nonfinite) S->nonfinite = 1;
+    mx = __reduce_max_sync(kFull, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&S->maxabs, mx);
 }
 
 // Vertices a block of bq consecutive (ordered) queries must scan: up to the
@@ -767,8 +1083,13 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     int dev = 0, sms = 1, bps = 1;
     MRPOP_CUDA_TRY(cudaGetDevice(&dev));
     MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MRPOP_CUDA_TRY(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_tc_kernel<DIM>, kTcThreads, 0));
+    constexpr bool f16 = DIM + 2 <= 16;  // FP16 filter (K = 16), else TF32
+    if constexpr (f16)
+        MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_tc16_kernel<DIM>,
+                                                                     kTcThreads, 0));
+    else
+        MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_tc_kernel<DIM>,
+                                                                     kTcThreads, 0));
     bps = std::max(bps, 1);
     const int bq = kTcQueries;
     const int qblocks = (Q + bq - 1) / bq;
@@ -832,8 +1153,13 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     }
     nearest_seed<DIM><<<(Q + 127) / 128, 128, 0, st>>>(tree_s, N, q_s, c_s, Q, seed);
     dim3 grid(qblocks, splits);
-    nearest_tc_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk, partial,
-                                                        perm, cut, seed, &S->exact_only);
+    if constexpr (f16)
+        nearest_tc16_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk,
+                                                              partial, perm, cut, seed,
+                                                              &S->maxabs, &S->nonfinite);
+    else
+        nearest_tc_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk, partial,
+                                                            perm, cut, seed, &S->exact_only);
     nearest_sorted_reduce<<<(Q + 255) / 256, 256, 0, st>>>(partial, cut, chunk, Q, bq, qperm,
                                                            out_idx);
     const cudaError_t e = cudaGetLastError();
