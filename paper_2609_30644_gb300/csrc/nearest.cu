@@ -256,6 +256,58 @@ __device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned &r0, unsigned &r
                  : "memory");
 }
 
+// Pieces shared by both filter kernels.
+//
+// Stage the block's kTcQueries queries (SoA rows of the ordered batch) in
+// shared memory, one per thread (kTcThreads == kTcQueries).
+template <int DIM>
+__device__ __forceinline__ void tc_stage_queries(float (*qsm)[kTcQueries],
+                                                 const float *__restrict__ queries, int Q, int qb) {
+    const int j = threadIdx.x;
+    const bool ok = qb + j < Q;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) qsm[d][j] = ok ? __ldg(queries + (size_t)d * Q + qb + j) : 0.f;
+}
+
+// Smallest g of the tree slice [vs, ve) (row DIM of the ordered tree), for
+// every thread of the block: an admissible vertex of the slice has
+// |q - x| < c - that minimum.
+template <int DIM>
+__device__ __forceinline__ float tc_slice_gmin(const float *__restrict__ tree, int N, int vs, int ve,
+                                               float *red_g) {
+    float gm = FLT_MAX;
+#pragma unroll 4
+    for (int v = vs + threadIdx.x; v < ve; v += kTcThreads)
+        gm = fminf(gm, __ldg(tree + (size_t)DIM * N + v));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
+    if ((threadIdx.x & 31) == 0) red_g[threadIdx.x >> 5] = gm;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTcWarps; ++k) gm = fminf(gm, red_g[k]);
+    return gm;
+}
+
+// The four lanes of a quad hold the same four rows (queries row_q(r)), each
+// with the best of its own vertex columns, as a position in the g order:
+// translate to original indices (perm), combine by key, and let lane
+// tig == 0 write the slice's partial bests.
+template <typename RowQ>
+__device__ __forceinline__ void tc_write_rows(Best (&best)[4], const int *__restrict__ perm,
+                                              RowQ row_q, int Q, Best *__restrict__ partial) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            const Best other = shfl_best(best[r], o);
+            if (better(other, best[r])) best[r] = other;
+        }
+        const int q = row_q(r);
+        if ((threadIdx.x & 3) == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
+    }
+}
+
 // Inputs: the g-ordered tree (SoA rows, ld = N) with perm (ordered -> original
 // index), the budget-ordered queries, cut (vertices each query block scans),
 // the shared bound seed (see below); *exhaustive != 0 turns the filter off.
@@ -285,13 +337,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
     if (vs >= ve) return;  // no partial record: the reduce skips this slice
     const bool exact_only = *exhaustive != 0;
 
-    {
-        // kTcThreads == kTcQueries: thread t stages query qb + t (independent loads)
-        const int j = threadIdx.x;
-        const bool ok = qb + j < Q;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) qsm[d][j] = ok ? __ldg(queries + (size_t)d * Q + qb + j) : 0.f;
-    }
+    tc_stage_queries<DIM>(qsm, queries, Q, qb);
     __syncthreads();
     // rows of this thread: slot r = 2 * mt + h is query qb + 32 warp + 16 mt + grp + 8 h
     auto row_l = [&](int r) { return warp * 32 + (r >> 1) * 16 + grp + (r & 1) * 8; };
@@ -348,16 +394,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
     }
     {
         // an admissible vertex of this slice has |q - x| < c - g_min(slice)
-        float gm = FLT_MAX;
-#pragma unroll 4
-        for (int v = vs + threadIdx.x; v < ve; v += kTcThreads)
-            gm = fminf(gm, __ldg(tree + (size_t)DIM * N + v));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
-        if (lane == 0) red_g[warp] = gm;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kTcWarps; ++k) gm = fminf(gm, red_g[k]);
+        const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (!(cq[r] > gm)) {
@@ -515,19 +552,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
             }
         }
     }
-    // the four lanes of a quad hold the same rows: combine (by original index),
-    // lane tig == 0 writes
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
-#pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
-            const Best other = shfl_best(best[r], o);
-            if (better(other, best[r])) best[r] = other;
-        }
-        const int q = row_q(r);
-        if (tig == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
-    }
+    tc_write_rows(best, perm, row_q, Q, partial);
 }
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
@@ -580,12 +605,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
     const bool exact_only = *nonfinite != 0 || sh > 126;
     const float sc = exact_only ? 1.f : ldexpf(1.f, sh);
 
-    {
-        const int j = threadIdx.x;  // kTcThreads == kTcQueries
-        const bool ok = qb + j < Q;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) qsm[d][j] = ok ? __ldg(queries + (size_t)d * Q + qb + j) : 0.f;
-    }
+    tc_stage_queries<DIM>(qsm, queries, Q, qb);
     __syncthreads();
     auto row_l = [&](int r) { return warp * 32 + (r >> 1) * 16 + grp + (r & 1) * 8; };
     auto row_q = [&](int r) { return qb + row_l(r); };
@@ -638,16 +658,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
     }
     {
         // an admissible vertex of this slice has |q - x| < c - g_min(slice)
-        float gm = FLT_MAX;
-#pragma unroll 4
-        for (int v = vs + threadIdx.x; v < ve; v += kTcThreads)
-            gm = fminf(gm, __ldg(tree + (size_t)DIM * N + v));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
-        if (lane == 0) red_g[warp] = gm;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kTcWarps; ++k) gm = fminf(gm, red_g[k]);
+        const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (!(cq[r] > gm)) {
@@ -798,19 +809,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
             }
         }
     }
-    // the four lanes of a quad hold the same rows: combine (by original index),
-    // lane tig == 0 writes
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
-#pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
-            const Best other = shfl_best(best[r], o);
-            if (better(other, best[r])) best[r] = other;
-        }
-        const int q = row_q(r);
-        if (tig == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
-    }
+    tc_write_rows(best, perm, row_q, Q, partial);
 }
 
 // ---------------------------------------------------------------------------

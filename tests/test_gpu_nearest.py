@@ -193,17 +193,22 @@ def test_nearest_work_counts(mp, orc):
     _check_nearest(orc, tree, qs, cs, got, sample=np.arange(0, Q, 37))
 
 
-@pytest.mark.parametrize("case", ["offset", "tiny", "huge", "nan"])
-def test_nearest_tensor_filter_range(mp, orc, case):
+@pytest.mark.parametrize("D,case", [(D, c) for D in (14, 21)
+                                    for c in ("offset", "tiny", "huge", "nan")]
+                         + [(14, "scaled_down"), (14, "scaled_up"), (7, "scaled_down")])
+def test_nearest_tensor_filter_range(mp, orc, D, case):
     """The tensor-core filter's error bound is relative to |q|^2 + |x|^2: a
-    box far from the origin (large norms, small distances) must stay exact;
-    a nonzero coordinate below 2^-60 or above 2^60, or a NaN, turns the
-    filter off so that every pair is checked exactly.  Results must equal
-    the small-batch kernel's and the oracle's."""
-    D, N, Q = 14, 1500, 2048
+    box far from the origin (large norms, small distances) must stay exact.
+    The FP16 filter (D <= 14) scales the batch by a power of two taken from
+    its largest magnitude: boxes shrunk by 1e-12 or grown by 1e15 must stay
+    exact, as must a single tiny or huge coordinate.  For the TF32 filter
+    (D = 21) a nonzero coordinate below 2^-60 or above 2^60 turns the filter
+    off; a NaN does so for both.  Results must equal the small-batch
+    kernel's and the oracle's."""
+    N, Q = 1500, 2048
     lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
-    tree = synth.random_tree(D, N, lo, hi, seed=31, dup_frac=0.05)
-    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=32, budget_lo=0.0, budget_hi=25.0)
+    tree = synth.random_tree(D, N, lo, hi, seed=31 + D, dup_frac=0.05)
+    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=32 + D, budget_lo=0.0, budget_hi=25.0)
     qs[:, :32] = tree[:D, :32]
     if case == "offset":
         tree[:D] += np.float32(1000.0)
@@ -212,8 +217,15 @@ def test_nearest_tensor_filter_range(mp, orc, case):
         qs[3, 5] = np.float32(1e-25)
     elif case == "huge":
         tree[2, 7] = np.float32(2.0 ** 61)
-    else:
+    elif case == "nan":
         tree[4, 11] = np.nan
+    else:
+        # every coordinate, the costs and the budgets scaled alike: the
+        # nearest vertex is the same, distances scale by f
+        f = np.float32(1e-12 if case == "scaled_down" else 1e15)
+        tree *= f
+        qs *= f
+        cs *= f
     big = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
     small = np.concatenate([
         mp.nearest(_dev(tree), _dev(np.ascontiguousarray(qs[:, i:i + 1000])),
