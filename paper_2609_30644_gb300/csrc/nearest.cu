@@ -575,8 +575,9 @@ __device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
 // hold 16 halves (32 bytes, two 16-byte chunks swizzled by bit 2 of the
 // vertex); the unscaled FP32 coordinates of the tile are kept beside them
 // (SoA) for the exact checks.
+// Registers are capped so that 3 blocks (24 warps) stay resident per SM.
 template <int DIM>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, 3)
 nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
                     const float *__restrict__ budgets, int Q, int chunk,
                     Best *__restrict__ partial, const int *__restrict__ perm,
@@ -722,6 +723,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
             }
         }
         const int ng2 = (nv + 15) >> 4;  // pairs of 8-vertex groups
+#pragma unroll 2
         for (int np = 0; np < ng2; ++np) {
             const int vrow = (2 * np + lgrp) * 8 + lrow;
             unsigned b[2][2];
@@ -738,13 +740,17 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
                 }
             // element (j, mt, i): row grp + 8 (i >> 1) of m-tile mt, vertex
             // 8 (2 np + j) + 2 tig + (i & 1)
+            // the common case, nothing passes: one compare per row on the
+            // minimum of its four values (a NaN never passes either way)
             bool any = exact_only;
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) any |= acc[j][mt][i] <= lim[2 * mt + (i >> 1)];
+                for (int h = 0; h < 2; ++h) {
+                    const float m = fminf(fminf(acc[0][mt][2 * h], acc[0][mt][2 * h + 1]),
+                                          fminf(acc[1][mt][2 * h], acc[1][mt][2 * h + 1]));
+                    any |= m <= lim[2 * mt + h];
+                }
             if (!__any_sync(kFull, any)) continue;
             unsigned pass = 0;
 #pragma unroll
