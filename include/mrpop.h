@@ -22,7 +22,12 @@
  *     joint vectors in robot order (Sec. III-A); D = sum of the robots' dof.
  *     Batches are SoA float32 [D][n]: element (i, e) at ptr[i * n + e].
  *   - A problem handle owns device copies of its robots and obstacles; it may
- *     be used from one host thread at a time.
+ *     be used from one host thread at a time.  Its validation calls
+ *     (mrpop_validate_edges[_ex], mrpop_edge_clearance, mrpop_validate_work,
+ *     mrpop_autotune) hand out edges through one device work counter of the
+ *     handle, which the last warp of each launch resets: launches on one
+ *     handle must not overlap on the GPU.  Enqueue them on one stream, or
+ *     order the streams (events); two handles never share a counter.
  */
 #ifndef MRPOP_H
 #define MRPOP_H
@@ -236,6 +241,30 @@ mrpop_status mrpop_nearest(const float *tree, int64_t n_vertices, int64_t ld, in
                            const float *queries, const float *budgets, int64_t n_queries,
                            int64_t *out_idx, void *cuda_stream);
 
+/* Filters of the large-batch NEAREST path (mrpop_nearest_ex).  Batches of
+ * >= 2048 queries in dimensions 3, 6, 7, 14, 21 or 28 order the tree by g and
+ * the queries by budget, then pass each (query, vertex) pair through an
+ * expansion filter |q|^2 + |x|^2 - 2 q.x <= bound, whose rounding error is
+ * bounded so that it never drops the nearest admissible vertex; every vertex
+ * that passes is decided with the exact FP32 distance, so the indices do not
+ * depend on the filter.
+ *   MRPOP_NEAREST_FILTER_FP32    FP32 fused multiply-adds on the FMA pipe
+ *                                (the default of mrpop_nearest)
+ *   MRPOP_NEAREST_FILTER_TENSOR  the cross term on the tensor cores
+ *                                (mma.sync: FP16 operands under an exact
+ *                                power-of-two scaling for dim <= 14, TF32
+ *                                above); a deliberate option beside the
+ *                                FP32 path, faster on this GPU */
+#define MRPOP_NEAREST_FILTER_FP32 0
+#define MRPOP_NEAREST_FILTER_TENSOR 1
+
+/* mrpop_nearest with an explicit large-batch filter (one of the two above;
+ * EINVAL otherwise).  Other batches take the small-batch scan whatever the
+ * filter.  Same arguments, results and errors as mrpop_nearest. */
+mrpop_status mrpop_nearest_ex(const float *tree, int64_t n_vertices, int64_t ld, int32_t dim,
+                              const float *queries, const float *budgets, int64_t n_queries,
+                              int32_t filter, int64_t *out_idx, void *cuda_stream);
+
 /* How many (query, vertex) pairs mrpop_nearest evaluates for these inputs
  * (a diagnostic for roofline accounting; no paper counterpart).  A vertex
  * with g_v >= c is never admissible, so for batches of >= 2048 queries in
@@ -263,9 +292,10 @@ mrpop_status mrpop_nearest_work(const float *tree, int64_t n_vertices, int64_t l
  * GPU loading this library holds until the process exits.
  *   - n_queries > MRPOP_NEAREST_NOALLOC_MAX_QUERIES is rejected with
  *     MRPOP_EINVAL; nothing is launched.
- *   - The first call on a device (with that device current) looks up the
- *     array's device address once; make that first call before any stream
- *     capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (an allocation-free query once the library's module is loaded there,
+ *     which the first call on a device does); make that first call before
+ *     any stream capture.
  *   - All calls share the array: calls that overlap on the GPU (for example
  *     on two streams) race and must be serialised by the caller.  Each call
  *     writes every record it reads, so nothing needs clearing between calls.
@@ -382,7 +412,8 @@ mrpop_status mrpop_plan_history(const mrpop_problem *p, int64_t index, float *pa
                                 int64_t path_cap, int64_t *path_len, double *cost);
 
 /* Measured FP32 FMA throughput of the current device in TFLOP/s, the
- * roofline denominator of this library's kernels (all FP32 SIMT).  The paper
+ * roofline denominator of this library's FP32 SIMT kernels (validation,
+ * NEIGHBORS, path cost and the default NEAREST filter).  The paper
  * has no counterpart: this is a calibration utility.  It launches 8
  * independent FMA chains per thread of iters steps each on 2,048 threads per
  * SM, once to warm up and then 5 times timed with CUDA events on cuda_stream

@@ -84,6 +84,8 @@ def _load():
             "orc_neighbors": (i64, [vp, i64, i64, i32, vp, f32, i64, vp, pd]),
             "orc_path_cost": (f64, [vp, i64, i32]),
             "orc_path_valid": (i32, [vp, vp, i64, f32, f64, vp]),
+            "orc_edge_method_work": (i32, [vp, vp, vp, i64, f32, f64, i32, vp]),
+            "orc_method_work_edges": (None, [vp, vp, vp, i64, i64, i64, f32, f64, i32, vp, vp]),
             "orc_plan": (i32, [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -92,6 +94,11 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+# Units counted by OracleScene.method_work, in the order of the C enum.
+WORK_UNITS = ("checkpoints", "joints", "coarse_points", "coarse_sphere", "coarse_cuboid",
+              "coarse_pair", "fine_points", "fine_sphere", "fine_cuboid", "fine_pair")
 
 
 class OracleScene:
@@ -201,6 +208,20 @@ class OracleScene:
         _load().orc_validate_edges(self.ptr, _p(qa), _p(qb), ld, e0, n, res, margin,
                                    int(early_exit), _p(valid), _p(mc), _p(fh), _p(npt))
         return {"valid": valid, "min_clear": mc, "first_hit": fh, "npoints": npt}
+
+    def method_work(self, qa, qb, res: float, margin: float = 0.0,
+                    early_exit: bool = False) -> tuple:
+        """Work units of the paper's two-stage check (Sec. III-E) over the SoA
+        edges qa, qb float32 [D, E], summed over the edges (see WORK_UNITS),
+        and each edge's verdict."""
+        qa = np.ascontiguousarray(qa, dtype=np.float32)
+        qb = np.ascontiguousarray(qb, dtype=np.float32)
+        n = qa.shape[1]
+        counts = np.zeros(len(WORK_UNITS), dtype=np.int64)
+        valid = np.zeros(n, dtype=np.uint8)
+        _load().orc_method_work_edges(self.ptr, _p(qa), _p(qb), n, 0, n, res, margin,
+                                      int(early_exit), _p(counts), _p(valid))
+        return counts, valid
 
     def path_valid(self, path, res: float, margin: float = 0.0) -> tuple:
         path = np.ascontiguousarray(path, dtype=np.float32)

@@ -6,7 +6,10 @@
  *                excludes robot-obstacle and robot-robot collisions; path cost
  *                C(sigma) = sum_j ||q_{j+1} - q_j||.
  *   Sec. III-E   robots are approximated by collision spheres; an edge is
- *                discretised into motions and every checkpoint is checked.
+ *                discretised into motions and every checkpoint is checked;
+ *                the two-stage check (one conservative sphere per link, then
+ *                the fine spheres of the links it hit) only for counting its
+ *                work (orc_edge_method_work).
  *   Alg. 2       NEAREST(V, q, c) = argmin over {g_v + ||q - q_v|| < c} of
  *                ||q - q_v||; NEIGHBORS(V, c, delta) = vertices within delta.
  *   Sec. III-D   ties between vertices at one configuration go to lowest cost.
@@ -364,4 +367,227 @@ int32_t orc_path_valid(const orc_scene *s, const float *path, int64_t M, float r
     }
     if (bad_segment) *bad_segment = -1;
     return 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Work of the two-stage check (Sec. III-E)                                   */
+/* ------------------------------------------------------------------------- */
+
+/* Coarse sphere of every link of every robot, in its link frame: centre and
+ * radius [4] per link (radius < 0: the link has no sphere). */
+static void coarse_spheres(const orc_scene *s, double *coarse) {
+    for (int32_t k = 0; k < s->K; ++k) {
+        const int32_t j0 = joint_offset(s, k), s0 = sphere_offset(s, k);
+        for (int32_t j = 0; j < s->dof[k]; ++j) {
+            double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+            int32_t any = 0;
+            for (int32_t i = 0; i < s->n_spheres[k]; ++i) {
+                if (s->sphere_link[s0 + i] != j) continue;
+                const float *sp = s->sphere_xyzr + 4 * (s0 + i);
+                for (int a = 0; a < 3; ++a) {
+                    if (sp[a] < lo[a]) lo[a] = sp[a];
+                    if (sp[a] > hi[a]) hi[a] = sp[a];
+                }
+                any = 1;
+            }
+            double *c = coarse + 4 * (j0 + j);
+            if (!any) {
+                c[0] = c[1] = c[2] = 0.0;
+                c[3] = -1.0;
+                continue;
+            }
+            for (int a = 0; a < 3; ++a) c[a] = 0.5 * (lo[a] + hi[a]);
+            double r = 0.0;
+            for (int32_t i = 0; i < s->n_spheres[k]; ++i) {
+                if (s->sphere_link[s0 + i] != j) continue;
+                const float *sp = s->sphere_xyzr + 4 * (s0 + i);
+                const double dx = sp[0] - c[0], dy = sp[1] - c[1], dz = sp[2] - c[2];
+                const double e = sqrt(dx * dx + dy * dy + dz * dz) + sp[3];
+                if (e > r) r = e;
+            }
+            c[3] = r + 1e-4;
+        }
+    }
+}
+
+/* Do links (global joint rows) a < b belong to a pair that is tested? */
+static int32_t link_pair_tested(const orc_scene *s, const int32_t *robot_of, const int32_t *link_of,
+                                int32_t a, int32_t b) {
+    if (robot_of[a] != robot_of[b]) return 1;
+    if (!s->self_collision) return 0;
+    const int32_t lo = link_of[a] < link_of[b] ? link_of[a] : link_of[b];
+    const int32_t hi = link_of[a] < link_of[b] ? link_of[b] : link_of[a];
+    if (hi == lo) return 0;
+    return s->self_mask ? (s->self_mask[joint_offset(s, robot_of[a]) + hi] >> lo) & 1
+                        : hi - lo >= 2;
+}
+
+/* Two-stage check of one configuration q; returns validity, adds units. */
+static int32_t method_config(const orc_scene *s, const double *coarse, const int32_t *robot_of,
+                             const int32_t *link_of, const double *q, double margin,
+                             double *frames, double *cw, int32_t *hit_link, int64_t *counts) {
+    const int32_t L = total_dof(s);
+    const int32_t NS = s->n_obs_spheres, NC = s->n_obs_cuboids;
+    counts[ORC_WORK_CHECKPOINTS] += 1;
+    /* stage 1: FK and a coarse centre per link */
+    for (int32_t k = 0; k < s->K; ++k) {
+        const int32_t j0 = joint_offset(s, k);
+        orc_link_frames(s, k, q + j0, frames + 16 * j0);
+        counts[ORC_WORK_JOINTS] += s->dof[k];
+    }
+    for (int32_t l = 0; l < L; ++l) {
+        hit_link[l] = 0;
+        if (coarse[4 * l + 3] < 0.0) continue;
+        m4_apply(frames + 16 * l, coarse + 4 * l, cw + 4 * l);
+        cw[4 * l + 3] = coarse[4 * l + 3];
+        counts[ORC_WORK_COARSE_POINTS] += 1;
+    }
+    /* coarse tests; the hits are kept for stage 2 */
+    uint8_t *hs = (uint8_t *)calloc((size_t)L * (size_t)(NS > 0 ? NS : 1), 1);
+    uint8_t *hc = (uint8_t *)calloc((size_t)L * (size_t)(NC > 0 ? NC : 1), 1);
+    uint8_t *hp = (uint8_t *)calloc((size_t)L * (size_t)L, 1);
+    for (int32_t l = 0; l < L; ++l) {
+        if (coarse[4 * l + 3] < 0.0) continue;
+        const double *c = cw + 4 * l;
+        for (int32_t o = 0; o < NS; ++o) {
+            const float *ob = s->obs_spheres + 4 * o;
+            const double oc[3] = {ob[0], ob[1], ob[2]};
+            counts[ORC_WORK_COARSE_SPHERE] += 1;
+            if (orc_sphere_sphere_clearance(c, c[3], oc, ob[3]) < margin) {
+                hs[(size_t)l * NS + o] = 1;
+                hit_link[l] = 1;
+            }
+        }
+        for (int32_t o = 0; o < NC; ++o) {
+            counts[ORC_WORK_COARSE_CUBOID] += 1;
+            if (orc_sphere_cuboid_clearance(c, c[3], s->obs_cuboids + 15 * o) < margin) {
+                hc[(size_t)l * NC + o] = 1;
+                hit_link[l] = 1;
+            }
+        }
+        for (int32_t m = l + 1; m < L; ++m) {
+            if (coarse[4 * m + 3] < 0.0 || !link_pair_tested(s, robot_of, link_of, l, m)) continue;
+            counts[ORC_WORK_COARSE_PAIR] += 1;
+            if (orc_sphere_sphere_clearance(c, c[3], cw + 4 * m, cw[4 * m + 3]) < margin) {
+                hp[(size_t)l * L + m] = 1;
+                hit_link[l] = hit_link[m] = 1;
+            }
+        }
+    }
+    /* stage 2: fine spheres of the links that a coarse test hit */
+    int32_t valid = 1;
+    int32_t total_s = sphere_offset(s, s->K);
+    double *fw = (double *)malloc(sizeof(double) * 4 * (size_t)(total_s > 0 ? total_s : 1));
+    int32_t *first = (int32_t *)malloc(sizeof(int32_t) * (size_t)(L + 1));
+    int32_t *cnt = (int32_t *)calloc((size_t)(L > 0 ? L : 1), sizeof(int32_t));
+    for (int32_t k = 0; k < s->K; ++k) {
+        const int32_t j0 = joint_offset(s, k), s0 = sphere_offset(s, k);
+        for (int32_t j = 0; j < s->dof[k]; ++j) first[j0 + j] = -1;
+        for (int32_t i = 0; i < s->n_spheres[k]; ++i) {
+            const int32_t l = j0 + s->sphere_link[s0 + i];
+            if (first[l] < 0) first[l] = s0 + i;
+            cnt[l] += 1;
+        }
+    }
+    for (int32_t l = 0; l < L; ++l) {
+        if (!hit_link[l]) continue;
+        for (int32_t i = first[l]; i < first[l] + cnt[l]; ++i) {
+            const float *sp = s->sphere_xyzr + 4 * i;
+            const double p[3] = {sp[0], sp[1], sp[2]};
+            m4_apply(frames + 16 * l, p, fw + 4 * i);
+            fw[4 * i + 3] = sp[3];
+        }
+        counts[ORC_WORK_FINE_POINTS] += cnt[l];
+    }
+    for (int32_t l = 0; l < L; ++l) {
+        if (!hit_link[l]) continue;
+        for (int32_t o = 0; o < NS; ++o) {
+            if (!hs[(size_t)l * NS + o]) continue;
+            const float *ob = s->obs_spheres + 4 * o;
+            const double oc[3] = {ob[0], ob[1], ob[2]};
+            for (int32_t i = first[l]; i < first[l] + cnt[l]; ++i) {
+                counts[ORC_WORK_FINE_SPHERE] += 1;
+                if (orc_sphere_sphere_clearance(fw + 4 * i, fw[4 * i + 3], oc, ob[3]) < margin)
+                    valid = 0;
+            }
+        }
+        for (int32_t o = 0; o < NC; ++o) {
+            if (!hc[(size_t)l * NC + o]) continue;
+            for (int32_t i = first[l]; i < first[l] + cnt[l]; ++i) {
+                counts[ORC_WORK_FINE_CUBOID] += 1;
+                if (orc_sphere_cuboid_clearance(fw + 4 * i, fw[4 * i + 3],
+                                                s->obs_cuboids + 15 * o) < margin)
+                    valid = 0;
+            }
+        }
+        for (int32_t m = l + 1; m < L; ++m) {
+            if (!hp[(size_t)l * L + m]) continue;
+            for (int32_t i = first[l]; i < first[l] + cnt[l]; ++i)
+                for (int32_t j = first[m]; j < first[m] + cnt[m]; ++j) {
+                    counts[ORC_WORK_FINE_PAIR] += 1;
+                    if (orc_sphere_sphere_clearance(fw + 4 * i, fw[4 * i + 3], fw + 4 * j,
+                                                    fw[4 * j + 3]) < margin)
+                        valid = 0;
+                }
+        }
+    }
+    free(fw);
+    free(first);
+    free(cnt);
+    free(hs);
+    free(hc);
+    free(hp);
+    return valid;
+}
+
+int32_t orc_edge_method_work(const orc_scene *s, const float *qa, const float *qb,
+                             int64_t stride, float res, double margin, int32_t early_exit,
+                             int64_t *counts) {
+    const int32_t D = total_dof(s);
+    const int32_t n = orc_edge_npoints(qa, qb, stride, D, res);
+    const size_t LL = (size_t)(D > 0 ? D : 1);
+    double *coarse = (double *)malloc(sizeof(double) * 4 * LL);
+    double *frames = (double *)malloc(sizeof(double) * 16 * LL);
+    double *cw = (double *)malloc(sizeof(double) * 4 * LL);
+    double *q = (double *)malloc(sizeof(double) * LL);
+    int32_t *robot_of = (int32_t *)malloc(sizeof(int32_t) * LL);
+    int32_t *link_of = (int32_t *)malloc(sizeof(int32_t) * LL);
+    int32_t *hit_link = (int32_t *)malloc(sizeof(int32_t) * LL);
+    coarse_spheres(s, coarse);
+    for (int32_t k = 0; k < s->K; ++k)
+        for (int32_t j = 0; j < s->dof[k]; ++j) {
+            robot_of[joint_offset(s, k) + j] = k;
+            link_of[joint_offset(s, k) + j] = j;
+        }
+    int32_t valid = 1;
+    for (int32_t k = 0; k <= n; ++k) {
+        const double t = (double)k / (double)n;
+        for (int32_t i = 0; i < D; ++i) {
+            const double a = qa[i * stride], b = qb[i * stride];
+            q[i] = a + t * (b - a);
+        }
+        if (!method_config(s, coarse, robot_of, link_of, q, margin, frames, cw, hit_link,
+                           counts)) {
+            valid = 0;
+            if (early_exit) break;
+        }
+    }
+    free(coarse);
+    free(frames);
+    free(cw);
+    free(q);
+    free(robot_of);
+    free(link_of);
+    free(hit_link);
+    return valid;
+}
+
+void orc_method_work_edges(const orc_scene *s, const float *qa, const float *qb, int64_t ld,
+                           int64_t e0, int64_t n, float res, double margin, int32_t early_exit,
+                           int64_t *counts, uint8_t *valid) {
+    for (int64_t e = 0; e < n; ++e) {
+        const int32_t ok = orc_edge_method_work(s, qa + e0 + e, qb + e0 + e, ld, res, margin,
+                                                early_exit, counts);
+        if (valid) valid[e] = (uint8_t)ok;
+    }
 }

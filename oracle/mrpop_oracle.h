@@ -105,6 +105,48 @@ int32_t orc_path_valid(const orc_scene *s, const float *path, int64_t M, float r
                        double margin, int64_t *bad_segment);
 
 /* ------------------------------------------------------------------------- */
+/* Work of the paper's two-stage check (Sec. III-E), for roofline accounting. */
+/* ------------------------------------------------------------------------- */
+/* Each checkpoint first runs FK with one conservative (coarse) sphere per
+ * link and tests it against every obstacle and against every link of every
+ * other robot (and, with self_collision, the link pairs of the adjacency
+ * mask); only then the fine spheres of a link that a coarse test hit are
+ * placed and tested, against the obstacles and links that its coarse sphere
+ * hit.  A link's coarse sphere (the paper takes it from its sphere model) is
+ * built here from the link's fine spheres: centre at the midpoint of the box
+ * around their centres, radius max(|c - c_s| + r_s) + 1e-4.  Links without
+ * spheres take part in no test.  Units counted (added to counts[]):        */
+enum {
+    ORC_WORK_CHECKPOINTS = 0,      /* checkpoints evaluated                  */
+    ORC_WORK_JOINTS = 1,           /* joint transforms (FK of every robot)   */
+    ORC_WORK_COARSE_POINTS = 2,    /* coarse centres placed (one per link)   */
+    ORC_WORK_COARSE_SPHERE = 3,    /* coarse sphere vs obstacle sphere tests */
+    ORC_WORK_COARSE_CUBOID = 4,    /* coarse sphere vs cuboid tests          */
+    ORC_WORK_COARSE_PAIR = 5,      /* coarse sphere vs coarse sphere tests   */
+    ORC_WORK_FINE_POINTS = 6,      /* fine centres placed (links with a hit) */
+    ORC_WORK_FINE_SPHERE = 7,      /* fine sphere vs obstacle sphere tests   */
+    ORC_WORK_FINE_CUBOID = 8,      /* fine sphere vs cuboid tests            */
+    ORC_WORK_FINE_PAIR = 9,        /* fine sphere vs fine sphere tests       */
+    ORC_WORK_UNITS = 10
+};
+
+/* Runs the two-stage check over the checkpoints of edge qa -> qb (as in
+ * orc_edge_valid, k = 0..n in order), adds its units to counts
+ * [ORC_WORK_UNITS] and returns the edge's validity (1 free, 0 colliding),
+ * which equals orc_edge_valid's because the coarse spheres enclose the fine
+ * ones.  With early_exit the checkpoints after the first colliding one are
+ * not evaluated (the colliding one is). */
+int32_t orc_edge_method_work(const orc_scene *s, const float *qa, const float *qb,
+                             int64_t stride, float res, double margin, int32_t early_exit,
+                             int64_t *counts);
+
+/* Batched form over SoA edges qa, qb [D][ld], edges e0 .. e0+n-1; counts are
+ * summed over the edges; valid (may be NULL) receives each verdict. */
+void orc_method_work_edges(const orc_scene *s, const float *qa, const float *qb, int64_t ld,
+                           int64_t e0, int64_t n, float res, double margin, int32_t early_exit,
+                           int64_t *counts, uint8_t *valid);
+
+/* ------------------------------------------------------------------------- */
 /* FP64 reference planner (mrpop_ref_planner.c): Alg. 1 and Alg. 2 run one    */
 /* iteration at a time on one host thread.                                    */
 /* ------------------------------------------------------------------------- */

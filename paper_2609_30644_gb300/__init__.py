@@ -13,7 +13,8 @@ from __future__ import annotations
 _OPS = ("MrpopError", "Problem", "edge_clearance", "fk", "lib", "library_path", "nearest",
         "neighbors", "path_cost", "validate_edges", "validate_work", "EXPORTS", "plan", "plan_trace",
         "plan_batch", "plan_result", "Server", "autotune", "set_launch",
-        "plan_history", "fp32_peak", "nearest_work")
+        "plan_history", "fp32_peak", "nearest_work", "NEAREST_FILTER_FP32",
+        "NEAREST_FILTER_TENSOR")
 
 
 def __getattr__(name):

@@ -30,6 +30,7 @@ EXPORTS = (
     "mrpop_autotune",
     "mrpop_set_launch",
     "mrpop_nearest",
+    "mrpop_nearest_ex",
     "mrpop_nearest_noalloc",
     "mrpop_nearest_work",
     "mrpop_neighbors",
@@ -97,6 +98,7 @@ def _load() -> C.CDLL:
         "mrpop_autotune": (i32, [vp, vp, vp, i64, vp, vp, vp, vp]),
         "mrpop_set_launch": (i32, [vp, i32, i32, i32]),
         "mrpop_nearest": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
+        "mrpop_nearest_ex": (i32, [vp, i64, i64, i32, vp, vp, i64, i32, vp, vp]),
         "mrpop_nearest_noalloc": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_nearest_work": (i32, [vp, i64, i64, i32, vp, vp, i64, vp, vp]),
         "mrpop_neighbors": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp]),
@@ -287,10 +289,16 @@ def set_launch(p: Problem, warps_per_block: int, order: int, fine_stage: int = 0
     _check(lib.mrpop_set_launch(p.handle, int(warps_per_block), int(order), int(fine_stage)))
 
 
+NEAREST_FILTER_FP32 = 0     # MRPOP_NEAREST_FILTER_FP32 (the default)
+NEAREST_FILTER_TENSOR = 1   # MRPOP_NEAREST_FILTER_TENSOR
+
+
 def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
             n_vertices: Optional[int] = None, out: Optional[torch.Tensor] = None,
-            stream=None) -> torch.Tensor:
-    """tree [dim+1, ld] (row dim = g), queries [dim, Q], budgets [Q] -> int64 [Q]."""
+            stream=None, filter: int = NEAREST_FILTER_FP32) -> torch.Tensor:
+    """tree [dim+1, ld] (row dim = g), queries [dim, Q], budgets [Q] -> int64 [Q].
+    filter picks the large-batch expansion filter (FP32 FMA or tensor cores);
+    the indices do not depend on it."""
     dim = int(tree.shape[0]) - 1
     ld = int(tree.shape[1])
     N = ld if n_vertices is None else int(n_vertices)
@@ -299,10 +307,10 @@ def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
         raise ValueError("queries must be [dim, Q] and budgets [Q]")
     if out is None:
         out = torch.empty(Q, dtype=torch.int64, device=queries.device)
-    _check(lib.mrpop_nearest(_dptr(tree, torch.float32, "tree"), N, ld, dim,
-                             _dptr(queries, torch.float32, "queries"),
-                             _dptr(budgets, torch.float32, "budgets"), Q,
-                             _dptr(out, torch.int64, "out_idx"), _stream(stream)))
+    _check(lib.mrpop_nearest_ex(_dptr(tree, torch.float32, "tree"), N, ld, dim,
+                                _dptr(queries, torch.float32, "queries"),
+                                _dptr(budgets, torch.float32, "budgets"), Q, int(filter),
+                                _dptr(out, torch.int64, "out_idx"), _stream(stream)))
     return out
 
 

@@ -365,19 +365,29 @@ extern "C" mrpop_status mrpop_validate_work(mrpop_problem *p, const float *qa, c
                            (unsigned long long *)counters, s);
 }
 
-extern "C" mrpop_status mrpop_nearest(const float *tree, int64_t N, int64_t ld, int32_t dim,
-                                      const float *queries, const float *budgets, int64_t Q,
-                                      int64_t *out_idx, void *stream) {
+extern "C" mrpop_status mrpop_nearest_ex(const float *tree, int64_t N, int64_t ld, int32_t dim,
+                                         const float *queries, const float *budgets, int64_t Q,
+                                         int32_t filter, int64_t *out_idx, void *stream) {
     if (dim < 1 || dim > MRPOP_MAX_LINKS)
         return set_error(MRPOP_EINVAL, "mrpop_nearest: dim=%d outside [1, %d]", dim,
                          MRPOP_MAX_LINKS);
     if (N < 0 || Q < 0 || ld < N || N > (int64_t)INT32_MAX || Q > (int64_t)INT32_MAX)
         return set_error(MRPOP_EINVAL, "mrpop_nearest: bad sizes N=%lld ld=%lld Q=%lld",
                          (long long)N, (long long)ld, (long long)Q);
+    if (filter != MRPOP_NEAREST_FILTER_FP32 && filter != MRPOP_NEAREST_FILTER_TENSOR)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_ex: filter=%d is not a filter", filter);
     if (Q == 0) return MRPOP_OK;
     if (!queries || !budgets || !out_idx || (N > 0 && !tree))
         return set_error(MRPOP_EINVAL, "mrpop_nearest: NULL buffer");
-    return launch_nearest(tree, N, ld, dim, queries, budgets, Q, out_idx, (cudaStream_t)stream);
+    return launch_nearest(tree, N, ld, dim, queries, budgets, Q, out_idx, (cudaStream_t)stream,
+                          filter);
+}
+
+extern "C" mrpop_status mrpop_nearest(const float *tree, int64_t N, int64_t ld, int32_t dim,
+                                      const float *queries, const float *budgets, int64_t Q,
+                                      int64_t *out_idx, void *stream) {
+    return mrpop_nearest_ex(tree, N, ld, dim, queries, budgets, Q, MRPOP_NEAREST_FILTER_FP32,
+                            out_idx, stream);
 }
 
 extern "C" mrpop_status mrpop_nearest_work(const float *tree, int64_t N, int64_t ld, int32_t dim,

@@ -147,7 +147,8 @@ mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int spl,
 mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, cudaStream_t st);
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,
-                            int64_t *out_idx, cudaStream_t st);
+                            int64_t *out_idx, cudaStream_t st,
+                            int filter = MRPOP_NEAREST_FILTER_FP32);
 // Number of (query, vertex) pairs launch_nearest scans for these inputs.
 mrpop_status nearest_pairs(const float *tree, int64_t N, int64_t ld, int dim, const float *queries,
                            const float *budgets, int64_t Q, int64_t *pairs, cudaStream_t st);

@@ -819,6 +819,253 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
 }
 
 // ---------------------------------------------------------------------------
+// NEAREST filter in FP32 on the FMA pipe (the default for large batches).
+// The same expansion as the tensor-core filters, e(q, x) = |q|^2 + |x|^2 -
+// 2 q.x, is computed per (query, vertex) pair as a chain of D fused
+// multiply-adds that starts from the vertex's folded squared norm:
+//   acc = xn + sum_d (-2 q_d) x_d,   xn = fl(|x|^2) (1 - 4 gamma),
+// and a pair passes when acc <= T_q, a per-query threshold with |q|^2 taken
+// out.  A thread owns 8 queries x 8 vertices of each 64-vertex step (a
+// register tile of 64 accumulators); the operands are read as float4 from
+// dimension-major shared arrays, 4 shared loads per 64 FMAs, every load a
+// broadcast or a conflict-free row.  Warp lanes 8 ty' + tx share the queries
+// of ty (8 lanes) and the vertex columns of tx.
+//
+// Error bound (u = 2^-24, gamma = 1.25 (D + 2) u; the ordering pass sends
+// every pair to the exact check unless every nonzero coordinate lies in
+// [2^-60, 2^60], so no product or squared norm over- or underflows):
+//   * fl(|x|^2) is within gamma |x|^2, so xn + gamma (xn + |x|^2) <= |x|^2;
+//   * the chain adds at most gamma (xn + sum |2 q_d x_d|) <=
+//     gamma (xn + |q|^2 + |x|^2), hence acc <= |q - x|^2 - |q|^2 (1 - gamma);
+//   * qn = fl(|q|^2) is within gamma |q|^2, hence acc <= |q - x|^2 - qn +
+//     2 gamma qn.
+// The exact formula's d2 of any admissible vertex is at least |q - x*|^2 /
+// (1 + kC1) for the true nearest admissible x* (kC1 = 4 (D + 2) u), so
+//   T_q = fl_up( fl(fmaf(d2, 1 + kC1, 2.5 (D + 2) u qn)) (1 + 4 u) - qn )
+// satisfies acc(x*) <= T_q: the filter never drops the true nearest vertex.
+// Every vertex that passes is decided by the exact formula on the FP32
+// coordinates, so the results equal the plain scan's, ties included.
+// ---------------------------------------------------------------------------
+constexpr int kF32Vt = 256;   // vertices per shared-memory tile
+constexpr int kF32Step = 64;  // vertices per register-tile step
+
+template <int DIM>
+constexpr size_t f32_smem_bytes() {
+    return sizeof(float) * ((size_t)2 * DIM * kTcQueries + (size_t)(DIM + 2) * kF32Vt);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kTcThreads, 1)
+nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
+                   const float *__restrict__ budgets, int Q, int chunk,
+                   Best *__restrict__ partial, const int *__restrict__ perm,
+                   const int *__restrict__ cut, float *__restrict__ seed,
+                   const int *__restrict__ exact_only_flag) {
+    constexpr int VT = kF32Vt;
+    // dynamic shared memory (f32_smem_bytes<DIM>): -2 q_d of the block's
+    // queries [DIM][256], q_d for the exact checks [DIM][256], the tile
+    // [DIM + 2][VT] (x_d, folded |x|^2, g)
+    extern __shared__ __align__(16) float f32_sm[];
+    float(*am)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(f32_sm);
+    float(*qsm)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(f32_sm + DIM * kTcQueries);
+    float(*xs)[VT] = reinterpret_cast<float(*)[VT]>(f32_sm + 2 * DIM * kTcQueries);
+    __shared__ float qn_s[kTcQueries];                   // fl(|q|^2)
+    __shared__ float cq_s[kTcQueries];                   // budgets
+    __shared__ float red_g[kTcWarps];
+    constexpr float kU = 5.9604645e-8f;                   // 2^-24
+    constexpr float kC1 = 4.f * (DIM + 2.f) * kU;         // exact-distance relative error
+    constexpr float kG = 1.25f * (DIM + 2.f) * kU;        // gamma
+    const int tid = threadIdx.x;
+    const int ty = tid >> 3, tx = tid & 7;
+    const int qb = blockIdx.x * kTcQueries;
+    const int vs = blockIdx.y * chunk;
+    const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
+    if (vs >= ve) return;  // no partial record: the reduce skips this slice
+    const bool exact_only = *exact_only_flag != 0;
+
+    tc_stage_queries<DIM>(qsm, queries, Q, qb);
+    {
+        const int j = tid;
+        float n2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const float v = qsm[d][j];
+            am[d][j] = -2.f * v;
+            n2 = fmaf(v, v, n2);
+        }
+        qn_s[j] = n2;
+        cq_s[j] = qb + j < Q ? budgets[qb + j] : -FLT_MAX;  // padding admits nothing
+    }
+    __syncthreads();
+    // row r of this thread: query ql(r) of the block
+    auto ql = [&](int r) { return r < 4 ? ty * 4 + r : 128 + ty * 4 + (r - 4); };
+    unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
+    auto bound = [&](int r, float d2) {
+        const float qn = qn_s[ql(r)];
+        return __fsub_ru(fmaf(d2, 1.f + kC1, 2.5f * (DIM + 2.f) * kU * qn) * (1.f + 4.f * kU), qn);
+    };
+    float lim[8];
+    Best best[8];
+    unsigned pend[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        best[r] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+        lim[r] = FLT_MAX * 2.f;
+        const int q = qb + ql(r);
+        pend[r] = q < Q ? __ldcg(shared_lim + q) : 0x7f800000u;
+        const float sd = __uint_as_float(pend[r]);
+        if (sd <= FLT_MAX) lim[r] = fminf(lim[r], bound(r, sd));
+    }
+    {
+        // an admissible vertex of this slice has |q - x| < c - g_min(slice)
+        const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float c = cq_s[ql(r)];
+            if (!(c > gm)) {
+                lim[r] = -FLT_MAX * 2.f;
+            } else if (exact_only) {
+                lim[r] = FLT_MAX * 2.f;
+            } else {
+                const float t = __fsub_ru(c, gm);
+                lim[r] = fminf(lim[r], bound(r, __fmul_ru(t, t)));
+            }
+        }
+    }
+    // next tile's vertex of this thread, loaded while the current one is scanned
+    float px[DIM + 1];
+    auto prefetch = [&](int v0n) {
+        const bool ok = tid < min(VT, ve - v0n);
+        const unsigned base = (unsigned)(v0n + tid);
+#pragma unroll
+        for (int d = 0; d <= DIM; ++d)
+            px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)N)) : 0.f;
+        if (!ok) px[DIM] = FLT_MAX * 2.f;  // padding vertex: g = +inf
+    };
+    prefetch(vs);
+    for (int v0 = vs; v0 < ve; v0 += VT) {
+        const int nv = min(VT, ve - v0);
+        __syncthreads();
+        {
+            float n2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                xs[d][tid] = px[d];
+                n2 = fmaf(px[d], px[d], n2);
+            }
+            // padding columns never pass (+inf stays +inf along the chain)
+            xs[DIM][tid] = tid < nv ? n2 * (1.f - 4.f * kG) : FLT_MAX * 2.f;
+            xs[DIM + 1][tid] = px[DIM];
+        }
+        __syncthreads();
+        if (v0 + VT < ve) prefetch(v0 + VT);
+        if (!exact_only) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int q = qb + ql(r);
+                const float sd = __uint_as_float(pend[r]);
+                if (sd <= FLT_MAX) lim[r] = fminf(lim[r], bound(r, sd));
+                if (q < Q) pend[r] = __ldcg(shared_lim + q);
+            }
+        }
+        const int steps = (nv + kF32Step - 1) / kF32Step;
+        for (int s = 0; s < steps; ++s) {
+            const int c0 = s * kF32Step + tx * 4;  // columns c0..c0+3 and c0+32..c0+35
+            float acc[8][8];
+            {
+                const float4 n0 = *reinterpret_cast<const float4 *>(&xs[DIM][c0]);
+                const float4 n1 = *reinterpret_cast<const float4 *>(&xs[DIM][c0 + 32]);
+                const float xn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(&am[d][ty * 4]);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(&am[d][128 + ty * 4]);
+                    const float4 x0 = *reinterpret_cast<const float4 *>(&xs[d][c0]);
+                    const float4 x1 = *reinterpret_cast<const float4 *>(&xs[d][c0 + 32]);
+                    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            acc[r][c] = fmaf(a[r], x[c], d == 0 ? xn[c] : acc[r][c]);
+                }
+            }
+            // the common case, nothing passes: one compare per row on the
+            // minimum of its eight values (a NaN never passes either way)
+            bool any = exact_only;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                float m = acc[r][0];
+#pragma unroll
+                for (int c = 1; c < 8; ++c) m = fminf(m, acc[r][c]);
+                any |= m <= lim[r];
+            }
+            if (!__any_sync(kFull, any)) continue;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                unsigned pass = 0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    pass |= (exact_only || acc[r][c] <= lim[r]) ? 1u << c : 0u;
+                const int qlr = ql(r), q = qb + qlr;
+                if (q >= Q) pass = 0;
+                while (pass) {
+                    const int c = __ffs(pass) - 1;
+                    pass &= pass - 1;
+                    const int vl = c0 + (c < 4 ? c : 28 + c);
+                    if (vl >= nv) continue;
+                    const float g = xs[DIM + 1][vl];
+                    const float cr = cq_s[qlr];
+                    // a vertex with g >= c is never admissible
+                    if (!(g < cr)) continue;
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        const float dq = qsm[d][qlr] - xs[d][vl];
+                        d2 = fmaf(dq, dq, d2);
+                    }
+                    // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2,
+                    // g, index), the running best keeps the vertex's position in
+                    // the g order (original indices break exact ties)
+                    const int pos = v0 + vl;
+                    const Best b = best[r];
+                    if (d2 <= b.d2 && g + __fsqrt_rn(d2) < cr &&
+                        (d2 < b.d2 || g < b.g ||
+                         (g == b.g && __ldg(perm + pos) < __ldg(perm + b.idx)))) {
+                        best[r] = Best{d2, g, pos};
+                        if (!exact_only) {
+                            lim[r] = fminf(lim[r], bound(r, d2));
+                            atomicMin(shared_lim + q, __float_as_uint(d2));
+                        }
+                    }
+                }
+            }
+            // the 8 lanes of a query group scan different vertex columns of
+            // the same rows: a record of one tightens the bound of all
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 1));
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 2));
+                lim[r] = fminf(lim[r], __shfl_xor_sync(kFull, lim[r], 4));
+            }
+        }
+    }
+    // original indices, then the best of the query group's 8 lanes
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
+#pragma unroll
+        for (int o = 1; o <= 4; o <<= 1) {
+            const Best other = shfl_best(best[r], o);
+            if (better(other, best[r])) best[r] = other;
+        }
+        const int q = qb + ql(r);
+        if (tx == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Budget-ordered NEAREST for large batches.  A vertex with g_v >= c is never
 // admissible (distances are >= 0), so once the tree is ordered by g and the
 // queries by budget, a block of queries only needs the prefix of the tree
@@ -1080,21 +1327,50 @@ __global__ void sort_count_pairs(const int *__restrict__ cut, int qblocks, int Q
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// Raises the FP32 filter's dynamic shared-memory limit once per device and
+// returns its resident blocks per SM.
+template <int DIM>
+mrpop_status f32_filter_setup(int dev, int *bps) {
+    static std::mutex mu;
+    static int done[64] = {};
+    static int occ[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return set_error(MRPOP_EINVAL, "nearest: device ordinal %d", dev);
+    if (!done[dev]) {
+        MRPOP_CUDA_TRY(cudaFuncSetAttribute(nearest_f32_kernel<DIM>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)f32_smem_bytes<DIM>()));
+        MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ[dev], nearest_f32_kernel<DIM>, kTcThreads, f32_smem_bytes<DIM>()));
+        done[dev] = 1;
+    }
+    *bps = occ[dev];
+    return MRPOP_OK;
+}
+
 // out_idx null: only count the scanned pairs into *pairs (synchronises).
+// filter: MRPOP_NEAREST_FILTER_FP32 (FMA-pipe expansion filter) or
+// MRPOP_NEAREST_FILTER_TENSOR (FP16 / TF32 mma.sync expansion filter); both
+// decide every survivor exactly, so the indices do not depend on it.
 template <int DIM>
 mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *queries,
                                 const float *budgets, int Q, int64_t *out_idx, cudaStream_t st,
-                                int64_t *pairs = nullptr) {
+                                int64_t *pairs = nullptr, int filter = MRPOP_NEAREST_FILTER_FP32) {
     int dev = 0, sms = 1, bps = 1;
     MRPOP_CUDA_TRY(cudaGetDevice(&dev));
     MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    constexpr bool f16 = DIM + 2 <= 16;  // FP16 filter (K = 16), else TF32
-    if constexpr (f16)
+    constexpr bool f16 = DIM + 2 <= 16;  // FP16 tensor filter (K = 16), else TF32
+    const bool tensor = filter == MRPOP_NEAREST_FILTER_TENSOR;
+    if (!tensor) {
+        const mrpop_status fs = f32_filter_setup<DIM>(dev, &bps);
+        if (fs != MRPOP_OK) return fs;
+    } else if constexpr (f16) {
         MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_tc16_kernel<DIM>,
                                                                      kTcThreads, 0));
-    else
+    } else {
         MRPOP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, nearest_tc_kernel<DIM>,
                                                                      kTcThreads, 0));
+    }
     bps = std::max(bps, 1);
     const int bq = kTcQueries;
     const int qblocks = (Q + bq - 1) / bq;
@@ -1158,7 +1434,10 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     }
     nearest_seed<DIM><<<(Q + 127) / 128, 128, 0, st>>>(tree_s, N, q_s, c_s, Q, seed);
     dim3 grid(qblocks, splits);
-    if constexpr (f16)
+    if (!tensor)
+        nearest_f32_kernel<DIM><<<grid, kTcThreads, f32_smem_bytes<DIM>(), st>>>(
+            tree_s, N, q_s, c_s, Q, chunk, partial, perm, cut, seed, &S->exact_only);
+    else if constexpr (f16)
         nearest_tc16_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk,
                                                               partial, perm, cut, seed,
                                                               &S->maxabs, &S->nonfinite);
@@ -1300,17 +1579,18 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int n,
 
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,
-                            int64_t *out_idx, cudaStream_t st) {
+                            int64_t *out_idx, cudaStream_t st, int filter) {
     const int n = (int)N, q = (int)Q;
-    // Large batches: queries in registers against shared-memory tree tiles.
+    // Large batches: budget-ordered tree and queries, expansion filter with
+    // exact decisions over shared-memory tree tiles.
     if (Q >= 2048 && N > 0) {
         switch (dim) {
-            case 3: return nearest_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 6: return nearest_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 7: return nearest_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 14: return nearest_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 21: return nearest_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st);
-            case 28: return nearest_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st);
+            case 3: return nearest_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
+            case 6: return nearest_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
+            case 7: return nearest_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
+            case 14: return nearest_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
+            case 21: return nearest_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
+            case 28: return nearest_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
             default: break;
         }
     }
@@ -1430,9 +1710,12 @@ namespace mrpop {
 // loads this library holds until the process exits.
 //
 // Host code cannot use the array's name as a device address (it is a host-side
-// stand-in), so the first call on each device, with that device current, looks
-// the address up with cudaGetSymbolAddress and caches it.  That first call
-// should therefore come before any stream capture.  All calls share the array;
+// stand-in), so every call looks the address up with cudaGetSymbolAddress on
+// the current device.  The lookup allocates nothing once the module is loaded
+// on that device, which the first call on a device (or any earlier call of
+// this library there) does; that first call should therefore come before any
+// stream capture.  Not caching the address keeps it right after a device reset
+// reloads the module at a new address.  All calls share the array;
 // two calls that overlap on the GPU (for example on two streams) race on it.
 // Every partial record a call reads was written earlier by the same call, so
 // nothing needs clearing between calls.
@@ -1440,28 +1723,15 @@ namespace mrpop {
 namespace {
 
 constexpr int kNoAllocRecords = 2 * MRPOP_NEAREST_NOALLOC_MAX_QUERIES;
-constexpr int kNoAllocMaxDevices = 64;
 
 __device__ __align__(256) Best g_nearest_noalloc_scratch[kNoAllocRecords];
 
-std::mutex g_noalloc_mu;
-Best *g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
+// Device address of the array on the current device (looked up on every call).
 mrpop_status noalloc_scratch(Best **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return set_error(MRPOP_EINVAL, "mrpop_nearest_noalloc: device ordinal %d >= %d", dev,
-                         kNoAllocMaxDevices);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_nearest_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(nearest scratch)");
-        g_noalloc_ptr[dev] = static_cast<Best *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_nearest_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(nearest scratch)");
+    *out = static_cast<Best *>(p);
     return MRPOP_OK;
 }
 

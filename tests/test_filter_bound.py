@@ -135,3 +135,67 @@ def test_bound_without_widening_fails(form, D):
     q = rng.uniform(-2.9, 2.9, (20000, D)).astype(np.float32)
     assert _excess(q, q.copy(), form).max() <= 0.0
     assert _excess(q, q.copy(), form, widen=False).max() > 0.0
+
+
+# ----------------------------------------------------------------------------
+# FP32 filter on the FMA pipe (nearest_f32_kernel, the default)
+# ----------------------------------------------------------------------------
+# acc = xn + sum_d (-2 q_d) x_d by a chain of fused multiply-adds in FP32,
+# xn = fl(|x|^2) (1 - 4 gamma), gamma = kG (D + 2) u; a pair passes when
+#   acc <= T = fl_up(fl(fmaf(d2, 1 + kC1, kQ (D + 2) u qn)) (1 + 4 u) - qn).
+
+def _f32_const(pattern):
+    m = re.search(pattern, open(SRC).read())
+    assert m, pattern
+    return float(m.group(1))
+
+
+KG = _f32_const(r"constexpr float kG = ([0-9.]+)f \* \(DIM \+ 2\.f\) \* kU;")
+KQ = _f32_const(r"fmaf\(d2, 1\.f \+ kC1, ([0-9.]+)f \* \(DIM \+ 2\.f\) \* kU \* qn\)")
+
+
+def _fma32(a, b, c):
+    """FP32 fused multiply-add: the product of two floats is exact in float64,
+    the sum is rounded once more there, then to float32 (the extra float64
+    rounding is far below the allowances checked)."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def _excess_f32(q, x, widen=True):
+    q = np.asarray(q, np.float32)
+    x = np.asarray(x, np.float32)
+    D = q.shape[1]
+    kC1 = 4.0 * (D + 2) * U
+    gamma = KG * (D + 2) * U if widen else 0.0
+    kq = KQ * (D + 2) * U if widen else 0.0
+    n2 = np.zeros(len(x), np.float32)
+    for d in range(D):
+        n2 = _fma32(x[:, d], x[:, d], n2)
+    xn = (n2 * np.float32(1.0 - 4.0 * gamma)).astype(np.float32)
+    acc = xn
+    for d in range(D):
+        acc = _fma32((np.float32(-2.0) * q[:, d]).astype(np.float32), x[:, d], acc)
+    qn = np.zeros(len(q), np.float32)
+    for d in range(D):
+        qn = _fma32(q[:, d], q[:, d], qn)
+    d2 = ((q.astype(np.float64) - x.astype(np.float64)) ** 2).sum(1)
+    d2_f32_low = d2 * (1.0 - kC1)   # the exact formula's smallest possible value
+    T = (d2_f32_low * (1.0 + kC1) + kq * qn.astype(np.float64)) * (1.0 + 4 * U) - qn
+    return acc.astype(np.float64) - T
+
+
+@pytest.mark.parametrize("D", [3, 6, 7, 14, 21, 28])
+def test_fp32_filter_bound(D):
+    rng = np.random.default_rng(300 + D)
+    for name, q, x in _cases(D, 20000, rng):  # all inside the [2^-60, 2^60] rule
+        ex = _excess_f32(q, x)
+        assert ex.max() <= 0.0, (name, float(ex.max()))
+
+
+def test_fp32_bound_without_widening_fails():
+    """Without the fold of |x|^2 and the query-side widening, a query placed
+    on a vertex far from the origin already fails the check: rounding alone."""
+    rng = np.random.default_rng(8)
+    q = (rng.uniform(-2.9, 2.9, (20000, 14)) + 1000.0).astype(np.float32)
+    assert _excess_f32(q, q.copy()).max() <= 0.0
+    assert _excess_f32(q, q.copy(), widen=False).max() > 0.0

@@ -106,14 +106,20 @@ def test_nearest_split_tree_few_queries(mp, orc):
     _check_nearest(orc, tree, qs, cs, got, N=N)
 
 
+FILTERS = (0, 1)   # NEAREST_FILTER_FP32 (default), NEAREST_FILTER_TENSOR
+
+
 def test_nearest_full_size_sampled(mp, orc):
     """65,536 queries against a 16,384-vertex 14-D tree (the benchmark's
-    launch configuration), 200 sampled queries re-checked by the oracle."""
+    launch configuration), 200 sampled queries re-checked by the oracle, for
+    both large-batch filters, which must also agree index for index."""
     D = 14
     lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
     tree = synth.random_tree_fast(D, 16384, lo, hi, seed=1)
     qs, cs = synth.nn_queries(D, 65536, lo, hi, seed=2, budget_lo=10, budget_hi=40)
     got = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    tc = mp.nearest(_dev(tree), _dev(qs), _dev(cs), filter=1).cpu().numpy()
+    np.testing.assert_array_equal(got, tc)
     sample = np.random.default_rng(0).choice(65536, 200, replace=False)
     _check_nearest(orc, tree, qs, cs, got, sample=sample)
 
@@ -150,18 +156,20 @@ def test_path_cost_parity(mp, orc):
         assert got == pytest.approx(ref, rel=1e-6, abs=1e-12)
 
 
+@pytest.mark.parametrize("filt", FILTERS)
 @pytest.mark.parametrize("D,N,Q", [(14, 3000, 4096), (28, 2000, 2048), (6, 5000, 3000),
                                    (3, 700, 2500), (7, 257, 2049), (21, 1500, 2100)])
-def test_nearest_query_blocked_parity(mp, orc, D, N, Q):
-    """Batches of >= 2048 queries take the budget-ordered path (tensor-core
-    expansion filter + exact re-check); sampled queries against the oracle, duplicates
-    in the tree for ties, and the whole batch against the small-batch kernel
-    (called in chunks of < 2048 queries), which must agree index for index."""
+def test_nearest_query_blocked_parity(mp, orc, D, N, Q, filt):
+    """Batches of >= 2048 queries take the budget-ordered path (FP32 or
+    tensor-core expansion filter + exact re-check); sampled queries against
+    the oracle, duplicates in the tree for ties, and the whole batch against
+    the small-batch kernel (called in chunks of < 2048 queries), which must
+    agree index for index."""
     lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
     tree = synth.random_tree(D, N, lo, hi, seed=100 + D, dup_frac=0.1)
     qs, cs = synth.nn_queries(D, Q, lo, hi, seed=200 + D, budget_lo=0.0, budget_hi=25.0)
     qs[:, :64] = tree[:D, :64]            # queries exactly on (duplicated) vertices
-    big = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    big = mp.nearest(_dev(tree), _dev(qs), _dev(cs), filter=filt).cpu().numpy()
     small = np.concatenate([
         mp.nearest(_dev(tree), _dev(np.ascontiguousarray(qs[:, i:i + 1000])),
                    _dev(cs[i:i + 1000])).cpu().numpy() for i in range(0, Q, 1000)])
@@ -193,17 +201,18 @@ def test_nearest_work_counts(mp, orc):
     _check_nearest(orc, tree, qs, cs, got, sample=np.arange(0, Q, 37))
 
 
+@pytest.mark.parametrize("filt", FILTERS)
 @pytest.mark.parametrize("D,case", [(D, c) for D in (14, 21)
                                     for c in ("offset", "tiny", "huge", "nan")]
                          + [(14, "scaled_down"), (14, "scaled_up"), (7, "scaled_down")])
-def test_nearest_tensor_filter_range(mp, orc, D, case):
-    """The tensor-core filter's error bound is relative to |q|^2 + |x|^2: a
-    box far from the origin (large norms, small distances) must stay exact.
-    The FP16 filter (D <= 14) scales the batch by a power of two taken from
-    its largest magnitude: boxes shrunk by 1e-12 or grown by 1e15 must stay
-    exact, as must a single tiny or huge coordinate.  For the TF32 filter
-    (D = 21) a nonzero coordinate below 2^-60 or above 2^60 turns the filter
-    off; a NaN does so for both.  Results must equal the small-batch
+def test_nearest_filter_range(mp, orc, D, case, filt):
+    """Both filters' error bounds are relative to |q|^2 + |x|^2: a box far
+    from the origin (large norms, small distances) must stay exact.  The
+    FP16 tensor filter (D <= 14) scales the batch by a power of two taken
+    from its largest magnitude: boxes shrunk by 1e-12 or grown by 1e15 must
+    stay exact, as must a single tiny or huge coordinate.  For the FP32 and
+    TF32 filters a nonzero coordinate below 2^-60 or above 2^60 turns the
+    filter off; a NaN does so for all.  Results must equal the small-batch
     kernel's and the oracle's."""
     N, Q = 1500, 2048
     lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
@@ -226,7 +235,7 @@ def test_nearest_tensor_filter_range(mp, orc, D, case):
         tree *= f
         qs *= f
         cs *= f
-    big = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    big = mp.nearest(_dev(tree), _dev(qs), _dev(cs), filter=filt).cpu().numpy()
     small = np.concatenate([
         mp.nearest(_dev(tree), _dev(np.ascontiguousarray(qs[:, i:i + 1000])),
                    _dev(cs[i:i + 1000])).cpu().numpy() for i in range(0, Q, 1000)])

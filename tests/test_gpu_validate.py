@@ -39,11 +39,24 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _check_verdicts(valid_gpu, ref, margin):
+def _check_verdicts(valid_gpu, ref, margin, report=None, label=""):
+    """Bit-exact verdicts outside the contact band; the band itself is a thin
+    shell of the clearance range, so it may hold only a few edges of a batch
+    (at most 3, or 2 % of a large batch).  Returns the in-band count; with a
+    report list, also records how the GPU decided the in-band edges: 'toward
+    collision' (GPU rejects an edge the oracle accepts) or 'toward free'."""
+    valid_gpu = np.asarray(valid_gpu).astype(np.uint8)
     inband = np.abs(ref["min_clear"] - margin) <= BAND
     bad = (valid_gpu != ref["valid"]) & ~inband
     assert not bad.any(), f"{bad.sum()} verdict mismatches outside the contact band: {np.nonzero(bad)[0][:10]}"
-    return int(inband.sum())
+    n_in = int(inband.sum())
+    assert n_in <= max(3, 0.02 * valid_gpu.size), f"{n_in} of {valid_gpu.size} edges in the band"
+    if report is not None:
+        to_coll = int((inband & (valid_gpu == 0) & (ref["valid"] == 1)).sum())
+        to_free = int((inband & (valid_gpu == 1) & (ref["valid"] == 0)).sum())
+        report.append(f"{label}: margin {margin:g} m, {valid_gpu.size} edges, {n_in} in band, "
+                      f"differing toward collision {to_coll}, toward free {to_free}")
+    return n_in
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -75,7 +88,7 @@ def test_clearance_parity(mp, orc, name, n_edges):
 
 @pytest.mark.parametrize("margin", [0.0, 1e-4, 0.02])
 @pytest.mark.parametrize("name,n_edges", [("planar_pair", 600), ("table_pair", 300), ("grid4", 60)])
-def test_verdict_parity(mp, orc, name, n_edges, margin):
+def test_verdict_parity(mp, orc, band_report, name, n_edges, margin):
     """Mixed candidate edges, long enough to span several 32-point tiles with
     ragged tails (step up to 3 rad)."""
     scene = SCENES[name]()
@@ -100,8 +113,8 @@ def test_verdict_parity(mp, orc, name, n_edges, margin):
         # the reassigned fine stage (load-proportional work items)
         mp.set_launch(p, 0, 0, 1)
         v3 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
-    _check_verdicts(v, ref, margin)
-    _check_verdicts(v3, ref, margin)
+    _check_verdicts(v, ref, margin, band_report, f"{name} union")
+    _check_verdicts(v3, ref, margin, band_report, f"{name} reassigned")
 
 
 def test_verdict_matches_gpu_clearance(mp):
@@ -116,9 +129,10 @@ def test_verdict_matches_gpu_clearance(mp):
     np.testing.assert_array_equal(v[decided], (c[decided] >= 1e-4).astype(np.uint8))
 
 
-def test_full_size_batch_sampled(mp, orc):
+def test_full_size_batch_sampled(mp, orc, band_report):
     """65,536-edge batch of the 2 x 7-DOF table scene in the benchmark's launch
-    configuration; a seeded sample of edges is re-checked by the oracle."""
+    configuration; a seeded sample of edges is re-checked by the oracle, at the
+    kernel's margin and (the planner's safety property) at margin 0."""
     scene = synth.table_pair_scene(0)
     qa, qb = synth.candidate_edges(scene, 65536, seed=0)
     with mp.Problem(scene, resolution=0.02, margin=1e-4) as p:
@@ -127,8 +141,54 @@ def test_full_size_batch_sampled(mp, orc):
     idx = np.sort(rng.choice(65536, 256, replace=False))
     o = orc.OracleScene(scene)
     ref = o.validate_edges(qa[:, idx], qb[:, idx], 0.02, 1e-4, early_exit=False)
-    _check_verdicts(v[idx], ref, 1e-4)
+    _check_verdicts(v[idx], ref, 1e-4, band_report, "table_pair 65,536-edge batch, sample")
     assert 0.2 < v.mean() < 0.8
+    ref0 = o.validate_edges(qa[:, idx], qb[:, idx], 0.02, 0.0, early_exit=False)
+    unsafe = (v[idx] == 1) & (ref0["valid"] == 0)
+    assert not unsafe.any(), f"GPU accepted at 1e-4 what the oracle rejects at 0: {idx[unsafe]}"
+
+
+def _eight_arm_scene():
+    for i in range(40):
+        sc = synth.batched_scene(i)
+        if sc.K >= 7:
+            return sc
+    raise AssertionError("no batched scene with 7 or more arms")
+
+
+SAFETY_CASES = {
+    "planar_pair": (lambda: synth.planar_pair_scene(0), 600, dict(step_hi=3.0)),
+    "table_pair": (lambda: synth.table_pair_scene(0), 300, dict(step_hi=3.0)),
+    "grid4": (lambda: synth.grid4_scene(0), 60, dict(step_hi=3.0)),
+    "eight_arm_batched": (_eight_arm_scene, 24, dict(step_lo=0.02, step_hi=0.2)),
+}
+
+
+@pytest.mark.parametrize("name", list(SAFETY_CASES))
+def test_planner_margin_never_admits_a_collision(mp, orc, band_report, name):
+    """The planner's safety property on the primitive itself.  The planner
+    validates with margin 1e-4 m and its paths must pass the FP64 oracle at
+    margin 0, so on every edge -- in the contact band included -- a GPU
+    verdict 'free' at 1e-4 implies an oracle verdict 'free' at 0: FP32
+    rounding (micrometres here) never exceeds the 1e-4 m of inflation.  The
+    same batch is also compared at equal margins, where verdicts must be
+    bit-exact outside the band and the in-band edges are counted by the
+    direction in which the GPU differs."""
+    make, n_edges, kw = SAFETY_CASES[name]
+    scene = make()
+    o = orc.OracleScene(scene)
+    qa, qb = synth.candidate_edges(scene, n_edges, seed=19, **kw)
+    ref0 = o.validate_edges(qa, qb, 0.02, 0.0, early_exit=False)
+    ref1 = o.validate_edges(qa, qb, 0.02, 1e-4, early_exit=False)
+    assert 0 < ref0["valid"].sum() < n_edges
+    with mp.Problem(scene, resolution=0.02, margin=1e-4) as p:
+        v1 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+    with mp.Problem(scene, resolution=0.02, margin=0.0) as p:
+        v0 = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+    unsafe = (v1 == 1) & (ref0["valid"] == 0)
+    assert not unsafe.any(), f"GPU accepted at 1e-4 what the oracle rejects at 0: {np.nonzero(unsafe)[0]}"
+    _check_verdicts(v1, ref1, 1e-4, band_report, f"{name} (safety batch)")
+    _check_verdicts(v0, ref0, 0.0, band_report, f"{name} (safety batch)")
 
 
 def test_edge_cases(mp, orc):
@@ -179,10 +239,7 @@ def test_single_robot_and_obstacle_variants(mp, orc):
 def test_batched_scene_eight_arms(mp, orc):
     """Largest composite problem of the batched workload (up to 8 arms,
     56-DOF, hundreds of obstacles): fewer warps per block, same verdicts."""
-    for idx in range(40):
-        sc = synth.batched_scene(idx)
-        if sc.K >= 7:
-            break
+    sc = _eight_arm_scene()
     o = orc.OracleScene(sc)
     qa, qb = synth.candidate_edges(sc, 24, seed=2, step_lo=0.02, step_hi=0.2)
     ref = o.validate_edges(qa, qb, 0.02, 0.0)

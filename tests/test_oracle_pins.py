@@ -529,3 +529,105 @@ def test_self_collision_allpairs_planar(orc, masked):
         n_bad += not ok
         n_self += ref < 0.0 <= ref_other
     assert n_bad > 0 and n_self > 0
+
+
+# ----------------------------------------------------------------------------
+# work of the paper's two-stage check (Sec. III-E), counted for the roofline
+# ----------------------------------------------------------------------------
+
+def _two_link_arm(x, y):
+    """Planar 2-link arm (links 0.3 m along +x at q = 0, base at (x, y)) with
+    2 spheres of r = 0.02 per link, at 0.075 and 0.225 m along each link."""
+    base = np.array([1, 0, 0, x, 0, 1, 0, y, 0, 0, 1, 0], np.float32)
+    return synth.planar_arm(base, n_links=2, link_len=0.3, spheres_per_link=2, radius=0.02)
+
+
+def _units(counts, orc):
+    return dict(zip(orc.WORK_UNITS, (int(c) for c in counts)))
+
+
+def test_method_work_hand_counted_one_arm(orc):
+    """One arm at q = (0, 0), one obstacle sphere (0.45, 0.12, 0), r = 0.05;
+    the zero-length edge has n = 1, so 2 checkpoints.  By hand: link coarse
+    spheres have centres (0.15, 0, 0) and (0.45, 0, 0) and radius 0.075 +
+    0.02 + 1e-4 = 0.0951.  Link 1's centre is 0.12 from the obstacle centre
+    (< 0.0951 + 0.05): a coarse hit; link 0's is 0.323 away: none.  The fine
+    spheres of link 1, at (0.375, 0, 0) and (0.525, 0, 0), are 0.1415 from it
+    (> 0.02 + 0.05): the edge is free.  Per checkpoint: 2 joints, 2 coarse
+    centres, 2 coarse sphere tests, then link 1's 2 fine centres and 2 fine
+    sphere tests."""
+    sc = synth.Scene([_two_link_arm(0.0, 0.0)], np.array([[0.45, 0.12, 0.0, 0.05]], np.float32),
+                     np.zeros((0, 15), np.float32))
+    o = orc.OracleScene(sc)
+    q = np.zeros((2, 1), np.float32)
+    counts, valid = o.method_work(q, q, 0.02, 0.0)
+    assert valid.tolist() == [1]
+    assert _units(counts, orc) == dict(checkpoints=2, joints=4, coarse_points=4, coarse_sphere=4,
+                                       coarse_cuboid=0, coarse_pair=0, fine_points=4,
+                                       fine_sphere=4, fine_cuboid=0, fine_pair=0)
+    # moving the obstacle out of every coarse sphere leaves stage 1 only
+    sc.obs_spheres[0, :2] = (0.45, 0.5)
+    counts, valid = orc.OracleScene(sc).method_work(q, q, 0.02, 0.0)
+    assert valid.tolist() == [1]
+    assert _units(counts, orc)["fine_points"] == 0 and _units(counts, orc)["fine_sphere"] == 0
+    assert _units(counts, orc)["coarse_sphere"] == 4
+
+
+def test_method_work_hand_counted_two_arms(orc):
+    """Arms at y = 0 and y = 0.15 (both along +x) and the obstacle of the
+    one-arm case.  By hand, per checkpoint: 4 links, 4 coarse centres, 4
+    coarse sphere tests (hits: link 1 of both arms, 0.12 and 0.03 away), 4
+    coarse pair tests (hits: link 0 with link 0 and link 1 with link 1, 0.15
+    apart < 2 x 0.0951; the crossed pairs are 0.335 apart).  Every link has a
+    hit: 8 fine centres; fine sphere tests 2 + 2 (the two links 1); fine pair
+    tests 2 x 2 for each of the two hit pairs = 8.  Closest fine distances:
+    pairs 0.15 (> 0.04), arm 2's link 1 to the obstacle 0.0808 (> 0.07): free.
+    A cuboid far from both arms adds 4 coarse box tests and nothing else."""
+    far_box = np.zeros((1, 15), np.float32)
+    far_box[0, :6] = (0.0, -1.0, 0.0, 0.05, 0.05, 0.05)
+    far_box[0, 6:] = np.eye(3, dtype=np.float32).ravel()
+    sc = synth.Scene([_two_link_arm(0.0, 0.0), _two_link_arm(0.0, 0.15)],
+                     np.array([[0.45, 0.12, 0.0, 0.05]], np.float32), far_box)
+    o = orc.OracleScene(sc)
+    q = np.zeros((4, 1), np.float32)
+    counts, valid = o.method_work(q, q, 0.02, 0.0)
+    assert valid.tolist() == [1]
+    assert _units(counts, orc) == dict(checkpoints=2, joints=8, coarse_points=8, coarse_sphere=8,
+                                       coarse_cuboid=8, coarse_pair=8, fine_points=16,
+                                       fine_sphere=8, fine_cuboid=0, fine_pair=16)
+    # a 0.1 rad edge of the first joint: n = ceil(0.1 / 0.02) = 5, 6 checkpoints
+    qb = q.copy()
+    qb[0, 0] = 0.1
+    counts, _ = o.method_work(q, qb, 0.02, 0.0)
+    u = _units(counts, orc)
+    assert u["checkpoints"] == 6 and u["joints"] == 24 and u["coarse_points"] == 24
+    assert u["coarse_pair"] == 24 and u["coarse_sphere"] == 24 and u["coarse_cuboid"] == 24
+
+
+@pytest.mark.parametrize("make,self_collision", [(lambda: synth.planar_pair_scene(0), False),
+                                                 (lambda: synth.planar_pair_scene(0), True),
+                                                 (lambda: synth.table_pair_scene(0), False)])
+def test_method_work_verdicts_equal_all_pairs(orc, make, self_collision):
+    """The two-stage check decides exactly what the all-pairs definition
+    decides (each coarse sphere encloses its link's fine spheres), and the
+    early-exit count never exceeds the full count; on free edges both agree."""
+    sc = make()
+    o = orc.OracleScene(sc, self_collision=self_collision)
+    qa, qb = synth.candidate_edges(sc, 60, seed=23, step_hi=1.5)
+    ref = o.validate_edges(qa, qb, 0.02, 1e-4)
+    full, v_full = o.method_work(qa, qb, 0.02, 1e-4)
+    early, v_early = o.method_work(qa, qb, 0.02, 1e-4, early_exit=True)
+    np.testing.assert_array_equal(v_full, ref["valid"])
+    np.testing.assert_array_equal(v_early, ref["valid"])
+    assert 0 < ref["valid"].sum() < 60
+    assert (early <= full).all() and early[0] < full[0]
+    free = np.nonzero(ref["valid"])[0]
+    f_full, _ = o.method_work(qa[:, free], qb[:, free], 0.02, 1e-4)
+    f_early, _ = o.method_work(qa[:, free], qb[:, free], 0.02, 1e-4, early_exit=True)
+    np.testing.assert_array_equal(f_full, f_early)
+    u = _units(f_full, orc)
+    assert u["checkpoints"] == int((ref["npoints"][free] + 1).sum())
+    assert u["joints"] == u["checkpoints"] * sc.D
+    n_obs = len(sc.obs_spheres) + len(sc.obs_cuboids)
+    assert u["coarse_sphere"] + u["coarse_cuboid"] == u["coarse_points"] * n_obs
+    assert u["fine_points"] <= u["checkpoints"] * sum(r.n_spheres for r in sc.robots)

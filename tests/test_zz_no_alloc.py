@@ -11,9 +11,16 @@ Both entry points are called through the C ABI on the same inputs, two calls
 in a row with different shapes (so stale contents of the shared array would
 show), and must return identical indices -- the tolerance of the NEAREST tests
 for two GPU results: the key (distance, g, index) is a total order, so how the
-tree is split across blocks cannot change the answer.  This file is collected
-last and also passes when run on its own in a fresh process.
+tree is split across blocks cannot change the answer.  A second test checks
+the defining property itself: after a warm-up call, a call of the no-alloc
+entry point leaves the device's stream-ordered memory pool (its high-water
+mark), torch's caching allocator and the device's free memory unchanged,
+while the same check does see mrpop_nearest's split-tree scratch (a positive
+control).  This file is collected last and also passes when run on its own
+in a fresh process.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -36,14 +43,17 @@ def _call(fn, tree, qs, cs, out, n_vertices):
               qs.shape[1], out.data_ptr(), torch.cuda.current_stream().cuda_stream)
 
 
+def _inputs(D, N, Q, seed):
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = torch.from_numpy(synth.random_tree_fast(D, N, lo, hi, seed=seed)).cuda()
+    qs_np, cs_np = synth.nn_queries(D, Q, lo, hi, seed=seed + 10, budget_lo=2.0, budget_hi=30.0)
+    return tree, torch.from_numpy(qs_np).cuda(), torch.from_numpy(cs_np).cuda()
+
+
 @pytest.mark.parametrize("shapes", [((14, 200_000, 5), (7, 50_000, 4096))])
 def test_noalloc_matches_nearest_two_calls(lib, shapes):
     for call, (D, N, Q) in enumerate(shapes):
-        lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
-        tree = torch.from_numpy(synth.random_tree_fast(D, N, lo, hi, seed=40 + call)).cuda()
-        qs_np, cs_np = synth.nn_queries(D, Q, lo, hi, seed=50 + call, budget_lo=2.0,
-                                        budget_hi=30.0)
-        qs, cs = torch.from_numpy(qs_np).cuda(), torch.from_numpy(cs_np).cuda()
+        tree, qs, cs = _inputs(D, N, Q, 40 + call)
         ref = torch.full((Q,), -7, dtype=torch.int64, device="cuda")
         got = torch.full((Q,), -7, dtype=torch.int64, device="cuda")
         assert _call(lib.mrpop_nearest, tree, qs, cs, ref, N) == 0
@@ -52,6 +62,75 @@ def test_noalloc_matches_nearest_two_calls(lib, shapes):
         torch.cuda.synchronize()
         assert torch.equal(got, ref), f"call {call}: {(got != ref).sum().item()} indices differ"
         assert (got >= 0).any() and (got >= -1).all()
+
+
+class _Pool:
+    """The current device's default stream-ordered memory pool, through the
+    CUDA driver API (cuDeviceGetDefaultMemPool, cuMemPoolGet/SetAttribute)."""
+    USED_MEM_CURRENT = 7   # CU_MEMPOOL_ATTR_USED_MEM_CURRENT
+    USED_MEM_HIGH = 8      # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)   # resets the high-water mark to the current use
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH,
+                                             ctypes.byref(zero)) == 0
+
+    def free_bytes(self):
+        free, total = ctypes.c_size_t(), ctypes.c_size_t()
+        assert self.cu.cuMemGetInfo_v2(ctypes.byref(free), ctypes.byref(total)) == 0
+        return free.value
+
+
+def _allocations_during(fn):
+    """Runs fn (one library call, then a synchronize) and returns the growth of
+    the pool's high-water mark over its use before, the change of torch's
+    allocation count and the change of the device's free memory."""
+    pool = _Pool()
+    torch.cuda.synchronize()
+    pool.reset_high()
+    used0 = pool.get(_Pool.USED_MEM_CURRENT)
+    torch_allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    free0 = pool.free_bytes()
+    fn()
+    torch.cuda.synchronize()
+    return (pool.get(_Pool.USED_MEM_HIGH) - used0,
+            torch.cuda.memory_stats().get("allocation.all.allocated", 0) - torch_allocs0,
+            free0 - pool.free_bytes())
+
+
+def test_noalloc_allocates_nothing(lib):
+    D, N, Q = 14, 200_000, 5           # few queries, large tree: split across blocks
+    tree, qs, cs = _inputs(D, N, Q, 60)
+    ref = torch.empty(Q, dtype=torch.int64, device="cuda")
+    got = torch.empty(Q, dtype=torch.int64, device="cuda")
+    # warm-up: loads the modules (and with them the fixed array) on this device
+    assert _call(lib.mrpop_nearest, tree, qs, cs, ref, N) == 0
+    assert _call(lib.mrpop_nearest_noalloc, tree, qs, cs, got, N) == 0
+    torch.cuda.synchronize()
+    # positive control: the split-tree scratch of mrpop_nearest shows in the pool
+    pool_grew, _, _ = _allocations_during(
+        lambda: _call(lib.mrpop_nearest, tree, qs, cs, ref, N))
+    assert pool_grew > 0, "the check does not see stream-ordered scratch"
+    # the no-alloc entry point, twice: nothing from the pool, torch or cudaMalloc
+    for _ in range(2):
+        pool_grew, torch_allocs, free_drop = _allocations_during(
+            lambda: _call(lib.mrpop_nearest_noalloc, tree, qs, cs, got, N))
+        # (free memory may rise when the pool trims what the control left)
+        assert pool_grew == 0 and torch_allocs == 0 and free_drop <= 0, \
+            (pool_grew, torch_allocs, free_drop)
+        assert torch.equal(got, ref)
 
 
 def test_noalloc_rejects_batches_beyond_its_limit(lib):
