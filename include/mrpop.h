@@ -422,6 +422,43 @@ mrpop_status mrpop_plan_history(const mrpop_problem *p, int64_t index, float *pa
  * outside 1 .. 2^24), ECUDA. */
 mrpop_status mrpop_fp32_peak(int32_t packed, int32_t iters, double *tflops, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Test hooks for the planner's internal NEAREST and NEIGHBORS kernels (the
+ * search step and ROADMAP rounds run their own forms of Alg. 2's NEAREST and
+ * NEIGHBORS on the device-resident trees and roadmaps).  Each hook runs one
+ * pass of that kernel on caller-given device arrays and synchronises the
+ * stream; results follow the primitives' definitions, so they can be
+ * compared with an oracle directly.
+ * ------------------------------------------------------------------------- */
+#define MRPOP_PLANNER_STEP_ITERS 256   /* queries per planner NEAREST pass      */
+#define MRPOP_ROADMAP_DEGREE_CAP 64    /* neighbours kept per roadmap vertex    */
+
+/* NEAREST(V, q, c) of Alg. 2 as a planner search step runs it: pass 0 (the
+ * expanded tree, q_rand and c_rand) or pass 1 (the opposite tree, q_new and
+ * the budget c_best - g_new); same definition and tie rule as mrpop_nearest.
+ *   tree     device SoA [dim+1][ld], row dim = g;  n_vertices <= ld
+ *   queries  device SoA [dim][n_queries];  budgets device [n_queries]
+ *   out_idx  device int64 [n_queries], -1 when no vertex qualifies
+ * 1 <= n_queries <= MRPOP_PLANNER_STEP_ITERS, dim <= MRPOP_MAX_LINKS.
+ * Errors: EINVAL, ENOMEM / ECUDA. */
+mrpop_status mrpop_planner_nearest_pass(const float *tree, int64_t n_vertices, int64_t ld,
+                                        int32_t dim, const float *queries, const float *budgets,
+                                        int32_t n_queries, int32_t pass, int64_t *out_idx,
+                                        void *cuda_stream);
+
+/* NEIGHBORS(V_r, c, delta) of Alg. 2 as a ROADMAP round runs it on a robot's
+ * roadmap: the first MRPOP_ROADMAP_DEGREE_CAP vertices (ascending index) with
+ * |c - v| <= delta, the rest of each row -1, and the full count.
+ *   V        device SoA [dof][ld] (roadmap vertices), n_vertices <= ld
+ *   queries  device SoA [dof][n_queries]
+ *   out_idx  device int64 [n_queries][MRPOP_ROADMAP_DEGREE_CAP]
+ *   out_cnt  device int64 [n_queries]
+ * dof <= MRPOP_MAX_DOF.  Errors: EINVAL, ENOMEM / ECUDA. */
+mrpop_status mrpop_planner_neighbors_pass(const float *V, int64_t n_vertices, int64_t ld,
+                                          int32_t dof, const float *queries, int64_t n_queries,
+                                          float delta, int64_t *out_idx, int64_t *out_cnt,
+                                          void *cuda_stream);
+
 /* Incumbent history of the problem's planner: times[i] (seconds since the
  * start of the mrpop_plan call that found it) and costs[i], in order, at most
  * cap entries; *n receives the full count and *iterations the planner

@@ -14,7 +14,8 @@ _OPS = ("MrpopError", "Problem", "edge_clearance", "fk", "lib", "library_path", 
         "neighbors", "path_cost", "validate_edges", "validate_work", "EXPORTS", "plan", "plan_trace",
         "plan_batch", "plan_result", "Server", "autotune", "set_launch",
         "plan_history", "fp32_peak", "nearest_work", "NEAREST_FILTER_FP32",
-        "NEAREST_FILTER_TENSOR")
+        "NEAREST_FILTER_TENSOR", "planner_nearest_pass", "planner_neighbors_pass",
+        "ROADMAP_DEGREE_CAP")
 
 
 def __getattr__(name):

@@ -46,6 +46,8 @@ EXPORTS = (
     "mrpop_server_stats",
     "mrpop_server_destroy",
     "mrpop_fp32_peak",
+    "mrpop_planner_nearest_pass",
+    "mrpop_planner_neighbors_pass",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -114,6 +116,8 @@ def _load() -> C.CDLL:
         "mrpop_server_stats": (i32, [vp, vp]),
         "mrpop_server_destroy": (i32, [vp]),
         "mrpop_fp32_peak": (i32, [i32, i32, vp, vp]),
+        "mrpop_planner_nearest_pass": (i32, [vp, i64, i64, i32, vp, vp, i32, i32, vp, vp]),
+        "mrpop_planner_neighbors_pass": (i32, [vp, i64, i64, i32, vp, i64, f32, vp, vp, vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -312,6 +316,42 @@ def nearest(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
                                 _dptr(budgets, torch.float32, "budgets"), Q, int(filter),
                                 _dptr(out, torch.int64, "out_idx"), _stream(stream)))
     return out
+
+
+ROADMAP_DEGREE_CAP = 64    # MRPOP_ROADMAP_DEGREE_CAP
+
+
+def planner_nearest_pass(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
+                         pass_: int = 0, n_vertices: Optional[int] = None,
+                         stream=None) -> torch.Tensor:
+    """One pass of the planner's own NEAREST kernel (test hook): tree [dim+1,
+    ld], queries [dim, Q <= 256], budgets [Q] -> int64 [Q]."""
+    dim, ld = int(tree.shape[0]) - 1, int(tree.shape[1])
+    N = ld if n_vertices is None else int(n_vertices)
+    Q = int(queries.shape[1])
+    out = torch.empty(Q, dtype=torch.int64, device=queries.device)
+    _check(lib.mrpop_planner_nearest_pass(_dptr(tree, torch.float32, "tree"), N, ld, dim,
+                                          _dptr(queries, torch.float32, "queries"),
+                                          _dptr(budgets, torch.float32, "budgets"), Q,
+                                          int(pass_), _dptr(out, torch.int64, "out_idx"),
+                                          _stream(stream)))
+    return out
+
+
+def planner_neighbors_pass(V: torch.Tensor, queries: torch.Tensor, delta: float,
+                           n_vertices: Optional[int] = None, stream=None):
+    """One pass of the planner's roadmap NEIGHBORS kernel (test hook): V [dof,
+    ld], queries [dof, Q] -> (int64 [Q, 64], int64 [Q])."""
+    dof, ld = int(V.shape[0]), int(V.shape[1])
+    N = ld if n_vertices is None else int(n_vertices)
+    Q = int(queries.shape[1])
+    idx = torch.empty((Q, ROADMAP_DEGREE_CAP), dtype=torch.int64, device=queries.device)
+    cnt = torch.empty(Q, dtype=torch.int64, device=queries.device)
+    _check(lib.mrpop_planner_neighbors_pass(_dptr(V, torch.float32, "V"), N, ld, dof,
+                                            _dptr(queries, torch.float32, "queries"), Q,
+                                            float(delta), _dptr(idx, torch.int64, "out_idx"),
+                                            _dptr(cnt, torch.int64, "out_cnt"), _stream(stream)))
+    return idx, cnt
 
 
 def nearest_work(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,

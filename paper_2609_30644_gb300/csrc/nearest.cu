@@ -825,15 +825,19 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
 // multiply-adds that starts from the vertex's folded squared norm:
 //   acc = xn + sum_d (-2 q_d) x_d,   xn = fl(|x|^2) (1 - 4 gamma),
 // and a pair passes when acc <= T_q, a per-query threshold with |q|^2 taken
-// out.  A thread owns 8 queries x 8 vertices of each 64-vertex step (a
-// register tile of 64 accumulators); the operands are read as float4 from
-// dimension-major shared arrays, 4 shared loads per 64 FMAs, every load a
-// broadcast or a conflict-free row.  Warp lanes 8 ty' + tx share the queries
-// of ty (8 lanes) and the vertex columns of tx.
+// out.  The ordering pass stores xn as an extra row of the ordered tree.  A
+// thread owns 8 queries x 8 vertices of each 64-vertex step (a register tile
+// of 64 accumulators); the operands are read as float4 from dimension-major
+// shared arrays, 4 shared loads per 64 FMAs, every load a broadcast or one
+// conflict-free 128-byte row.  Warp lanes 8 ty' + tx share the queries of ty
+// (8 lanes) and the vertex columns of tx.  Tree tiles come in by cp.async
+// into a double buffer, one barrier per tile; the running best of each
+// (thread, query) sits in shared memory and is touched only when a pair
+// passes, so that two blocks (16 warps) stay resident per SM.
 //
-// Error bound (u = 2^-24, gamma = 1.25 (D + 2) u; the ordering pass sends
-// every pair to the exact check unless every nonzero coordinate lies in
-// [2^-60, 2^60], so no product or squared norm over- or underflows):
+// Error bound (u = 2^-24, gamma = kF32G (D + 2) = 1.25 (D + 2) u; the ordering
+// pass sends every pair to the exact check unless every nonzero coordinate
+// lies in [2^-60, 2^60], so no product or squared norm over- or underflows):
 //   * fl(|x|^2) is within gamma |x|^2, so xn + gamma (xn + |x|^2) <= |x|^2;
 //   * the chain adds at most gamma (xn + sum |2 q_d x_d|) <=
 //     gamma (xn + |q|^2 + |x|^2), hence acc <= |q - x|^2 - |q|^2 (1 - gamma);
@@ -841,40 +845,65 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
 //     2 gamma qn.
 // The exact formula's d2 of any admissible vertex is at least |q - x*|^2 /
 // (1 + kC1) for the true nearest admissible x* (kC1 = 4 (D + 2) u), so
-//   T_q = fl_up( fl(fmaf(d2, 1 + kC1, 2.5 (D + 2) u qn)) (1 + 4 u) - qn )
+//   T_q = fl_up( fl(fmaf(d2, 1 + kC1, 2 gamma qn)) (1 + 4 u) - qn )
 // satisfies acc(x*) <= T_q: the filter never drops the true nearest vertex.
 // Every vertex that passes is decided by the exact formula on the FP32
 // coordinates, so the results equal the plain scan's, ties included.
 // ---------------------------------------------------------------------------
-constexpr int kF32Vt = 256;   // vertices per shared-memory tile
-constexpr int kF32Step = 64;  // vertices per register-tile step
+constexpr float kF32G = 1.25f * 5.9604645e-8f;  // gamma / (D + 2)
+constexpr int kF32Step = 64;                     // vertices per register-tile step
+
+template <int DIM>
+struct F32Shape {
+    // vertices per shared-memory tile: two blocks of 256 threads fit an SM
+    static constexpr int VT = DIM <= 14 ? 256 : DIM <= 21 ? 128 : 64;
+    static constexpr int ROWS = DIM + 2;              // x_d, g, folded |x|^2
+};
 
 template <int DIM>
 constexpr size_t f32_smem_bytes() {
-    return sizeof(float) * ((size_t)2 * DIM * kTcQueries + (size_t)(DIM + 2) * kF32Vt);
+    // -2 q [DIM][256], q [DIM][256], two tiles [ROWS][VT], best d2, best
+    // position and bound [8][256] each
+    return sizeof(float) * ((size_t)2 * DIM * kTcQueries + (size_t)2 * F32Shape<DIM>::ROWS *
+                                                               F32Shape<DIM>::VT +
+                            (size_t)3 * 8 * kTcQueries);
 }
 
+// Source of the padding columns' folded norms: +inf never passes the filter.
+__device__ const float g_f32_pad_inf = __builtin_inff();
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+                 "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int DIM>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
 nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
                    const float *__restrict__ budgets, int Q, int chunk,
                    Best *__restrict__ partial, const int *__restrict__ perm,
                    const int *__restrict__ cut, float *__restrict__ seed,
                    const int *__restrict__ exact_only_flag) {
-    constexpr int VT = kF32Vt;
-    // dynamic shared memory (f32_smem_bytes<DIM>): -2 q_d of the block's
-    // queries [DIM][256], q_d for the exact checks [DIM][256], the tile
-    // [DIM + 2][VT] (x_d, folded |x|^2, g)
+    constexpr int VT = F32Shape<DIM>::VT, ROWS = F32Shape<DIM>::ROWS;
     extern __shared__ __align__(16) float f32_sm[];
     float(*am)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(f32_sm);
     float(*qsm)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(f32_sm + DIM * kTcQueries);
-    float(*xs)[VT] = reinterpret_cast<float(*)[VT]>(f32_sm + 2 * DIM * kTcQueries);
+    float *tiles = f32_sm + 2 * DIM * kTcQueries;                 // [2][ROWS][VT]
+    float(*sb_d2)[kTcQueries] =
+        reinterpret_cast<float(*)[kTcQueries]>(tiles + 2 * ROWS * VT);  // [8][256]
+    int(*sb_pos)[kTcQueries] = reinterpret_cast<int(*)[kTcQueries]>(sb_d2 + 8);
+    float(*lim_s)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(sb_pos + 8);
     __shared__ float qn_s[kTcQueries];                   // fl(|q|^2)
     __shared__ float cq_s[kTcQueries];                   // budgets
+    __shared__ unsigned sl_s[kTcQueries];                // shared bounds, one tile old
     __shared__ float red_g[kTcWarps];
     constexpr float kU = 5.9604645e-8f;                   // 2^-24
     constexpr float kC1 = 4.f * (DIM + 2.f) * kU;         // exact-distance relative error
-    constexpr float kG = 1.25f * (DIM + 2.f) * kU;        // gamma
+    constexpr float kG = kF32G * (DIM + 2.f);             // gamma
     const int tid = threadIdx.x;
     const int ty = tid >> 3, tx = tid & 7;
     const int qb = blockIdx.x * kTcQueries;
@@ -882,6 +911,24 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
     if (vs >= ve) return;  // no partial record: the reduce skips this slice
     const bool exact_only = *exact_only_flag != 0;
+    unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
+
+    // first tile in flight while the queries are staged
+    auto issue_tile = [&](int v0n, int buf) {
+        const int nvn = min(VT, ve - v0n);
+        float *dst = tiles + buf * ROWS * VT;
+        for (int i = tid; i < ROWS * VT; i += kTcThreads) {
+            const int d = i / VT, j = i - d * VT;
+            if (j < nvn)
+                cp_async4(dst + i, tree + ((size_t)d * N + v0n + j), true);
+            else if (d == DIM + 1)
+                cp_async4(dst + i, &g_f32_pad_inf, true);  // padding: never passes
+            else
+                cp_async4(dst + i, tree, false);            // zero fill
+        }
+        cp_async_commit();
+    };
+    issue_tile(vs, 0);
 
     tc_stage_queries<DIM>(qsm, queries, Q, qb);
     {
@@ -895,27 +942,24 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
         }
         qn_s[j] = n2;
         cq_s[j] = qb + j < Q ? budgets[qb + j] : -FLT_MAX;  // padding admits nothing
+        sl_s[j] = qb + j < Q ? __ldcg(shared_lim + qb + j) : 0x7f800000u;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            sb_d2[r][j] = FLT_MAX * 2.f;
+            sb_pos[r][j] = -1;
+        }
     }
     __syncthreads();
-    // row r of this thread: query ql(r) of the block
+    // row r of this thread: query ql(r) of the block; rows of real queries
     auto ql = [&](int r) { return r < 4 ? ty * 4 + r : 128 + ty * 4 + (r - 4); };
-    unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
+    unsigned row_ok = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) row_ok |= qb + ql(r) < Q ? 1u << r : 0u;
     auto bound = [&](int r, float d2) {
         const float qn = qn_s[ql(r)];
-        return __fsub_ru(fmaf(d2, 1.f + kC1, 2.5f * (DIM + 2.f) * kU * qn) * (1.f + 4.f * kU), qn);
+        return __fsub_ru(fmaf(d2, 1.f + kC1, 2.f * kG * qn) * (1.f + 4.f * kU), qn);
     };
     float lim[8];
-    Best best[8];
-    unsigned pend[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        best[r] = Best{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
-        lim[r] = FLT_MAX * 2.f;
-        const int q = qb + ql(r);
-        pend[r] = q < Q ? __ldcg(shared_lim + q) : 0x7f800000u;
-        const float sd = __uint_as_float(pend[r]);
-        if (sd <= FLT_MAX) lim[r] = fminf(lim[r], bound(r, sd));
-    }
     {
         // an admissible vertex of this slice has |q - x| < c - g_min(slice)
         const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
@@ -928,44 +972,26 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
                 lim[r] = FLT_MAX * 2.f;
             } else {
                 const float t = __fsub_ru(c, gm);
-                lim[r] = fminf(lim[r], bound(r, __fmul_ru(t, t)));
+                lim[r] = bound(r, __fmul_ru(t, t));
             }
         }
     }
-    // next tile's vertex of this thread, loaded while the current one is scanned
-    float px[DIM + 1];
-    auto prefetch = [&](int v0n) {
-        const bool ok = tid < min(VT, ve - v0n);
-        const unsigned base = (unsigned)(v0n + tid);
-#pragma unroll
-        for (int d = 0; d <= DIM; ++d)
-            px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)N)) : 0.f;
-        if (!ok) px[DIM] = FLT_MAX * 2.f;  // padding vertex: g = +inf
-    };
-    prefetch(vs);
-    for (int v0 = vs; v0 < ve; v0 += VT) {
+    unsigned sl_next = 0x7f800000u;  // this thread's query tid, for the next tile
+    int buf = 0;
+    for (int v0 = vs; v0 < ve; v0 += VT, buf ^= 1) {
         const int nv = min(VT, ve - v0);
-        __syncthreads();
-        {
-            float n2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                xs[d][tid] = px[d];
-                n2 = fmaf(px[d], px[d], n2);
-            }
-            // padding columns never pass (+inf stays +inf along the chain)
-            xs[DIM][tid] = tid < nv ? n2 * (1.f - 4.f * kG) : FLT_MAX * 2.f;
-            xs[DIM + 1][tid] = px[DIM];
-        }
-        __syncthreads();
-        if (v0 + VT < ve) prefetch(v0 + VT);
+        const float(*xs)[VT] = reinterpret_cast<const float(*)[VT]>(tiles + buf * ROWS * VT);
+        cp_async_wait_all();
+        // (a newer bound than another thread's view is still a valid bound)
+        if (v0 > vs) sl_s[tid] = sl_next;
+        __syncthreads();  // tile visible; every thread is done with the other buffer
+        if (v0 + VT < ve) issue_tile(v0 + VT, buf ^ 1);
+        if (qb + tid < Q) sl_next = __ldcg(shared_lim + qb + tid);
         if (!exact_only) {
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const int q = qb + ql(r);
-                const float sd = __uint_as_float(pend[r]);
+                const float sd = __uint_as_float(sl_s[ql(r)]);
                 if (sd <= FLT_MAX) lim[r] = fminf(lim[r], bound(r, sd));
-                if (q < Q) pend[r] = __ldcg(shared_lim + q);
             }
         }
         const int steps = (nv + kF32Step - 1) / kF32Step;
@@ -973,8 +999,8 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
             const int c0 = s * kF32Step + tx * 4;  // columns c0..c0+3 and c0+32..c0+35
             float acc[8][8];
             {
-                const float4 n0 = *reinterpret_cast<const float4 *>(&xs[DIM][c0]);
-                const float4 n1 = *reinterpret_cast<const float4 *>(&xs[DIM][c0 + 32]);
+                const float4 n0 = *reinterpret_cast<const float4 *>(&xs[DIM + 1][c0]);
+                const float4 n1 = *reinterpret_cast<const float4 *>(&xs[DIM + 1][c0 + 32]);
                 const float xn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
@@ -992,30 +1018,40 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
                 }
             }
             // the common case, nothing passes: one compare per row on the
-            // minimum of its eight values (a NaN never passes either way)
-            bool any = exact_only;
+            // minimum of its eight values (a NaN never passes either way);
+            // rows of padding queries (q >= Q) never pass
+            unsigned rows = 0;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 float m = acc[r][0];
 #pragma unroll
                 for (int c = 1; c < 8; ++c) m = fminf(m, acc[r][c]);
-                any |= m <= lim[r];
+                rows |= (exact_only || m <= lim[r]) ? 1u << r : 0u;
             }
-            if (!__any_sync(kFull, any)) continue;
+            rows &= row_ok;
+            if (!__any_sync(kFull, rows != 0u)) continue;
+            // pass bits r * 8 + c of the rows that pass, then one loop over
+            // them with the bounds in shared memory (dynamic row index)
+            unsigned long long pass = 0ull;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                unsigned pass = 0;
+            for (int r = 0; r < 8; ++r)
+                if ((rows >> r) & 1u) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    pass |= (exact_only || acc[r][c] <= lim[r]) ? 1u << c : 0u;
-                const int qlr = ql(r), q = qb + qlr;
-                if (q >= Q) pass = 0;
+                    for (int c = 0; c < 8; ++c)
+                        if (exact_only || acc[r][c] <= lim[r]) pass |= 1ull << (8 * r + c);
+                }
+            if (pass) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) lim_s[r][tid] = lim[r];
+#pragma unroll 1
                 while (pass) {
-                    const int c = __ffs(pass) - 1;
+                    const int bit = __ffsll((long long)pass) - 1;
                     pass &= pass - 1;
+                    const int r = bit >> 3, c = bit & 7;
                     const int vl = c0 + (c < 4 ? c : 28 + c);
                     if (vl >= nv) continue;
-                    const float g = xs[DIM + 1][vl];
+                    const float g = xs[DIM][vl];
+                    const int qlr = r < 4 ? ty * 4 + r : 128 + ty * 4 + (r - 4);
                     const float cr = cq_s[qlr];
                     // a vertex with g >= c is never admissible
                     if (!(g < cr)) continue;
@@ -1027,19 +1063,30 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
                     }
                     // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2,
                     // g, index), the running best keeps the vertex's position in
-                    // the g order (original indices break exact ties)
-                    const int pos = v0 + vl;
-                    const Best b = best[r];
-                    if (d2 <= b.d2 && g + __fsqrt_rn(d2) < cr &&
-                        (d2 < b.d2 || g < b.g ||
-                         (g == b.g && __ldg(perm + pos) < __ldg(perm + b.idx)))) {
-                        best[r] = Best{d2, g, pos};
+                    // the g order (its g is looked up there; original indices
+                    // break exact ties)
+                    const float bd2 = sb_d2[r][tid];
+                    if (!(d2 <= bd2) || !(g + __fsqrt_rn(d2) < cr)) continue;
+                    const int bpos = sb_pos[r][tid];
+                    bool take = d2 < bd2 || bpos < 0;
+                    if (!take) {
+                        const float bg = __ldg(tree + (size_t)DIM * N + bpos);
+                        take = g < bg || (g == bg && __ldg(perm + v0 + vl) < __ldg(perm + bpos));
+                    }
+                    if (take) {
+                        sb_d2[r][tid] = d2;
+                        sb_pos[r][tid] = v0 + vl;
                         if (!exact_only) {
-                            lim[r] = fminf(lim[r], bound(r, d2));
-                            atomicMin(shared_lim + q, __float_as_uint(d2));
+                            const float qn = qn_s[qlr];
+                            const float bq = __fsub_ru(
+                                fmaf(d2, 1.f + kC1, 2.f * kG * qn) * (1.f + 4.f * kU), qn);
+                            lim_s[r][tid] = fminf(lim_s[r][tid], bq);
+                            atomicMin(shared_lim + qb + qlr, __float_as_uint(d2));
                         }
                     }
                 }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) lim[r] = lim_s[r][tid];
             }
             // the 8 lanes of a query group scan different vertex columns of
             // the same rows: a record of one tightens the bound of all
@@ -1054,14 +1101,16 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     // original indices, then the best of the query group's 8 lanes
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        if (best[r].idx >= 0) best[r].idx = __ldg(perm + best[r].idx);
+        const int pos = sb_pos[r][tid];
+        Best b{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+        if (pos >= 0) b = Best{sb_d2[r][tid], __ldg(tree + (size_t)DIM * N + pos), __ldg(perm + pos)};
 #pragma unroll
         for (int o = 1; o <= 4; o <<= 1) {
-            const Best other = shfl_best(best[r], o);
-            if (better(other, best[r])) best[r] = other;
+            const Best other = shfl_best(b, o);
+            if (better(other, b)) b = other;
         }
         const int q = qb + ql(r);
-        if (tx == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = best[r];
+        if (tx == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = b;
     }
 }
 
@@ -1207,11 +1256,17 @@ __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, 
         if (a <= FLT_MAX) mx = max(mx, __float_as_uint(a));
     };
     if (i < N) {
+        // row dim + 1: the FP32 filter's folded squared norm fl(|x|^2) (1 - 4 gamma)
+        float n2 = 0.f;
         for (int d = 0; d <= dim; ++d) {
             const float v = tree[(size_t)d * ld + i];
-            if (d < dim) check(v);
+            if (d < dim) {
+                check(v);
+                n2 = fmaf(v, v, n2);
+            }
             tree_s[(size_t)d * N + pt] = v;
         }
+        tree_s[(size_t)(dim + 1) * N + pt] = n2 * (1.f - 4.f * (kF32G * (dim + 2.f)));
         perm[pt] = i;
     }
     const float c = i < Q ? budgets[i] : 0.f;
@@ -1386,7 +1441,7 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     // permutations, cuts, partial bests
     auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_state = align(sizeof(SortState));
-    const size_t b_tree = align(sizeof(float) * (size_t)(DIM + 1) * N);
+    const size_t b_tree = align(sizeof(float) * (size_t)(DIM + 2) * N);  // + folded norms
     const size_t b_perm = align(sizeof(int) * (size_t)N);
     const size_t b_q = align(sizeof(float) * (size_t)DIM * Q);
     const size_t b_c = align(sizeof(float) * (size_t)Q);

@@ -19,6 +19,7 @@
 // robot of every problem that needs one at once: each phase is one launch
 // with a job dimension, and the round ends with one host synchronisation.
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -1942,5 +1943,127 @@ extern "C" mrpop_status mrpop_plan_history(const mrpop_problem *p, int64_t index
                              (long long)M);
         std::memcpy(path, h.data(), sizeof(float) * h.size());
     }
+    return MRPOP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Test hooks: one pass of the planner's own NEAREST kernel (k_nearest, both
+// passes of a search step) and roadmap NEIGHBORS kernel (k_rmb_neighbors) on
+// caller-given arrays, through a minimal slot / job built on the device, so
+// that these kernels can be compared with the oracle directly.
+// ---------------------------------------------------------------------------
+extern "C" mrpop_status mrpop_planner_nearest_pass(const float *tree, int64_t n_vertices,
+                                                   int64_t ld, int32_t dim, const float *queries,
+                                                   const float *budgets, int32_t n_queries,
+                                                   int32_t pass, int64_t *out_idx, void *stream) {
+    using namespace mrpop;
+    if (dim < 1 || dim > MRPOP_MAX_LINKS || n_vertices < 0 || ld < n_vertices ||
+        ld > (int64_t)INT32_MAX || n_queries < 1 || n_queries > kStepIters ||
+        (pass != 0 && pass != 1))
+        return set_error(MRPOP_EINVAL,
+                         "mrpop_planner_nearest_pass: dim=%d n_vertices=%lld ld=%lld "
+                         "n_queries=%d pass=%d out of range", dim, (long long)n_vertices,
+                         (long long)ld, n_queries, pass);
+    if (!queries || !budgets || !out_idx || (n_vertices > 0 && !tree))
+        return set_error(MRPOP_EINVAL, "mrpop_planner_nearest_pass: NULL buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    // one arena: slot, control block, counts, padded queries [dim][256],
+    // budgets [256] (padding admits nothing), results [256]
+    const size_t b_slot = 256 * ((sizeof(Slot) + 255) / 256);
+    const size_t b_ctrl = 256 * ((sizeof(Ctrl) + 255) / 256);
+    const size_t b_q = sizeof(float) * (size_t)dim * kStepIters;
+    const size_t b_c = sizeof(float) * kStepIters;
+    char *arena = nullptr;
+    PL_TRY(cudaMallocAsync((void **)&arena, b_slot + b_ctrl + 256 + b_q + b_c +
+                                                sizeof(int64_t) * kStepIters, st));
+    Slot *d_slot = (Slot *)arena;
+    Ctrl *d_ctrl = (Ctrl *)(arena + b_slot);
+    int *d_tn = (int *)(arena + b_slot + b_ctrl);
+    float *d_q = (float *)(arena + b_slot + b_ctrl + 256);
+    float *d_c = (float *)((char *)d_q + b_q);
+    int64_t *d_out = (int64_t *)((char *)d_c + b_c);
+    Slot S{};
+    S.D = dim;
+    S.tcap = (int)ld;
+    S.tq[0] = S.tq[1] = const_cast<float *>(tree);
+    S.tn = d_tn;
+    S.qrand = S.qnew = d_q;
+    S.crand = S.budget2 = d_c;
+    S.near = S.conn = d_out;
+    S.ctrl = d_ctrl;
+    Ctrl C{};
+    C.tree_a = 0;  // pass 0 reads tree tree_a, pass 1 tree 1 - tree_a: both are `tree`
+    const int tn[2] = {(int)n_vertices, (int)n_vertices};
+    std::vector<float> pad_c(kStepIters, -FLT_MAX);
+    cudaError_t e = cudaMemcpyAsync(d_slot, &S, sizeof(Slot), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctrl, &C, sizeof(Ctrl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tn, tn, sizeof(tn), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_q, 0, b_q, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, pad_c.data(), b_c, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_q, sizeof(float) * kStepIters, queries, sizeof(float) * n_queries,
+                              sizeof(float) * n_queries, dim, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_c, budgets, sizeof(float) * n_queries, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        const dim3 grid(kStepIters / kPQB, 1);
+        if (pass == 0)
+            k_nearest<0><<<grid, kPThreads, 0, st>>>(d_slot);
+        else
+            k_nearest<1><<<grid, kPThreads, 0, st>>>(d_slot);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_idx, d_out, sizeof(int64_t) * n_queries, cudaMemcpyDeviceToDevice,
+                            st);
+    // the host-side copies above read stack memory: finish before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(arena, st);
+    if (e != cudaSuccess) return cuda_error(e, "mrpop_planner_nearest_pass");
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_planner_neighbors_pass(const float *V, int64_t n_vertices,
+                                                     int64_t ld, int32_t dof,
+                                                     const float *queries, int64_t n_queries,
+                                                     float delta, int64_t *out_idx,
+                                                     int64_t *out_cnt, void *stream) {
+    using namespace mrpop;
+    if (dof < 1 || dof > MRPOP_MAX_DOF || n_vertices < 0 || ld < n_vertices ||
+        ld > (int64_t)INT32_MAX || n_queries < 0 || n_queries > (int64_t)INT32_MAX / kKmax)
+        return set_error(MRPOP_EINVAL,
+                         "mrpop_planner_neighbors_pass: dof=%d n_vertices=%lld ld=%lld "
+                         "n_queries=%lld out of range", dof, (long long)n_vertices, (long long)ld,
+                         (long long)n_queries);
+    if (n_queries == 0) return MRPOP_OK;
+    if (!queries || !out_idx || !out_cnt || (n_vertices > 0 && !V))
+        return set_error(MRPOP_EINVAL, "mrpop_planner_neighbors_pass: NULL buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *arena = nullptr;
+    const size_t b_job = 256 * ((sizeof(RmJob) + 255) / 256);
+    PL_TRY(cudaMallocAsync((void **)&arena, b_job + 256, st));
+    RmJob *d_job = (RmJob *)arena;
+    int *d_count = (int *)(arena + b_job);
+    RmJob J{};
+    J.q = const_cast<float *>(V);
+    J.rcap = (int)ld;
+    J.dof = dof;
+    J.count = d_count;
+    J.gq = const_cast<float *>(queries);
+    J.m = (int)n_queries;
+    J.nb = out_idx;
+    J.cnt = out_cnt;
+    J.delta = delta;
+    const int n = (int)n_vertices;
+    cudaError_t e = cudaMemcpyAsync(d_job, &J, sizeof(RmJob), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_count, &n, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const dim3 grid((unsigned)((n_queries + kRmNbWarps - 1) / kRmNbWarps), 1);
+        k_rmb_neighbors<<<grid, kRmNbWarps * 32, 0, st>>>(d_job);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host copies read stack memory
+    cudaFreeAsync(arena, st);
+    if (e != cudaSuccess) return cuda_error(e, "mrpop_planner_neighbors_pass");
     return MRPOP_OK;
 }

@@ -150,8 +150,8 @@ def _f32_const(pattern):
     return float(m.group(1))
 
 
-KG = _f32_const(r"constexpr float kG = ([0-9.]+)f \* \(DIM \+ 2\.f\) \* kU;")
-KQ = _f32_const(r"fmaf\(d2, 1\.f \+ kC1, ([0-9.]+)f \* \(DIM \+ 2\.f\) \* kU \* qn\)")
+KG = _f32_const(r"constexpr float kF32G = ([0-9.]+)f \* 5\.9604645e-8f;")
+KQ = _f32_const(r"fmaf\(d2, 1\.f \+ kC1, ([0-9.]+)f \* kG \* qn\)") * KG
 
 
 def _fma32(a, b, c):

@@ -290,3 +290,73 @@ def test_plan_grid4(mp, orc):
         t, c, iters = mp.plan_trace(p)
     assert np.all(np.diff(c) < 0)
     _check_path(orc, o, path, cost, qs, qg)
+
+
+# ----------------------------------------------------------------------------
+# the planner's own NEAREST and NEIGHBORS kernels against the oracle
+# ----------------------------------------------------------------------------
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("pass_", [0, 1])
+@pytest.mark.parametrize("D,N", [(14, 3000), (28, 1500), (7, 257), (21, 1)])
+def test_planner_nearest_kernel_parity(mp, orc, D, N, pass_):
+    """k_nearest (both passes of a search step) on a tree with duplicated
+    vertices, queries placed exactly on vertices (exact ties: lowest g, then
+    lowest index), unbounded, tight and empty budgets: indices equal the
+    oracle's, with the primitives' allowance for genuine FP32/FP64 near-ties."""
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, N, lo, hi, seed=60 + D, dup_frac=0.1)
+    Q = 256
+    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=70 + D, budget_lo=0.0, budget_hi=25.0)
+    k = min(N, 48)
+    qs[:, :k] = tree[:D, :k]                       # on (duplicated) vertices
+    cs[200:216] = np.inf                           # unbounded
+    cs[216:232] = -1.0                             # nothing admissible
+    got = mp.planner_nearest_pass(_dev(tree), _dev(qs), _dev(cs), pass_).cpu().numpy()
+    assert (got[216:232] == -1).all()
+    ties = 0
+    for i in range(Q):
+        ref, bd, sd, gap = orc.nearest(tree, qs[:, i], cs[i])
+        if got[i] == ref:
+            continue
+        scale = max(1.0, abs(float(cs[i])) if np.isfinite(cs[i]) else 1.0)
+        assert (np.isfinite(sd) and sd - bd <= 1e-5 * max(bd, 1e-30)) or gap <= 1e-5 * scale, \
+            (i, got[i], ref, bd, sd, gap)
+        ties += 1
+    assert ties <= 3
+    # fewer queries than a step holds: the rest of the step is padding
+    part = mp.planner_nearest_pass(_dev(tree), _dev(qs[:, :37]), _dev(cs[:37]), pass_)
+    np.testing.assert_array_equal(part.cpu().numpy(), got[:37])
+
+
+@pytest.mark.parametrize("dof,N,Q,delta", [(7, 3000, 300, 2.5), (7, 500, 64, 1.2),
+                                           (3, 40, 33, 10.0), (16, 2000, 100, 6.0)])
+def test_planner_neighbors_kernel_parity(mp, orc, dof, N, Q, delta):
+    """k_rmb_neighbors on a roadmap: ascending indices within delta, capped at
+    64 per vertex (the roadmap degree cap; the rest of the row -1), and the
+    full count, against the oracle's radius query.  Queries sitting on
+    vertices and duplicated vertices are included."""
+    rng = np.random.default_rng(dof + N)
+    V = rng.uniform(-2.9, 2.9, (dof, N)).astype(np.float32)
+    V[:, N // 2:N // 2 + 8] = V[:, :8]              # duplicated vertices
+    qs = rng.uniform(-2.9, 2.9, (dof, Q)).astype(np.float32)
+    qs[:, :8] = V[:, :8]
+    idx, cnt = mp.planner_neighbors_pass(_dev(V), _dev(qs), delta)
+    idx, cnt = idx.cpu().numpy(), cnt.cpu().numpy()
+    tree = np.vstack([V, np.zeros((1, N), np.float32)])   # g row: ignored
+    cap = mp.ROADMAP_DEGREE_CAP
+    for i in range(Q):
+        ref, rc, gap = orc.neighbors(tree, qs[:, i], np.float32(delta), cap, dims=dof)
+        if gap > 1e-5 * delta:
+            assert cnt[i] == rc, (i, cnt[i], rc)
+            np.testing.assert_array_equal(idx[i, :len(ref)], ref)
+        else:
+            assert abs(int(cnt[i]) - rc) <= 2
+        kept = min(int(cnt[i]), cap)
+        assert (np.diff(idx[i, :kept]) > 0).all()
+        assert (idx[i, kept:] == -1).all()
+    if N > 2 * cap and delta >= 5:           # the cap is exercised on the wide radius
+        assert cnt.max() > cap
