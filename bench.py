@@ -526,6 +526,63 @@ def measured_peaks():
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_profile_leg(args) -> None:
+    """--profile-leg: one kernel's leg of the step alone, for ncu captures of
+    a known launch.  validate-free: the free-set construction (one validation
+    launch), then W warm-up and K timed launches on the free set;
+    validate-mixed: W + K launches on the step's mixed batch; nearest: W + K
+    NEAREST calls (one filter launch each).  The validation launch shape is
+    --launch (warps per block, order, fine stage).  Prints one JSON line with
+    the mean time of the timed launches."""
+    import numpy as np
+    import torch
+
+    import paper_2609_30644_gb300 as mp
+    from paper_2609_30644_gb300 import synth as _synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    scene, x = make_inputs(0)
+    stream = torch.cuda.current_stream()
+    w, o, f = (int(v) for v in args.launch.split(","))
+    with mp.Problem(scene, resolution=RES, margin=MARGIN) as prob:
+        mp.set_launch(prob, w, o, f)
+        if args.profile_leg == "validate-free":
+            cqa, cqb = _synth.candidate_edges(scene, 3 * E_EDGES, seed=1000)
+            cqa_d, cqb_d = torch.from_numpy(cqa).to(dev), torch.from_numpy(cqb).to(dev)
+            keep = mp.validate_edges(prob, cqa_d, cqb_d).bool()
+            sel = torch.nonzero(keep).flatten()[:E_EDGES]
+            qa, qb = cqa_d[:, sel].contiguous(), cqb_d[:, sel].contiguous()
+            run = lambda out: mp.validate_edges(prob, qa, qb, out)
+            out = torch.empty(E_EDGES, dtype=torch.uint8, device=dev)
+        elif args.profile_leg == "validate-mixed":
+            qa = torch.from_numpy(x["qa"]).to(dev)
+            qb = torch.from_numpy(x["qb"]).to(dev)
+            run = lambda out: mp.validate_edges(prob, qa, qb, out)
+            out = torch.empty(E_EDGES, dtype=torch.uint8, device=dev)
+        else:
+            tree = torch.from_numpy(x["tree"]).to(dev)
+            qs = torch.from_numpy(x["qs"]).to(dev)
+            cs = torch.from_numpy(x["cs"]).to(dev)
+            run = lambda out: mp.nearest(tree, qs, cs, out=out)
+            out = torch.empty(NN_QUERIES, dtype=torch.int64, device=dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            run(out)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run(out)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    print(json.dumps({"profile_leg": args.profile_leg, "launch": args.launch,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "ms": statistics.mean(ms) if ms else None}), flush=True)
+
+
 def run_ours(args) -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -967,9 +1024,15 @@ def main():
                     help="comma-separated Poisson arrival rates of the serving leg (1/s)")
     ap.add_argument("--serving-requests", type=int, default=SERVE_REQUESTS,
                     help="requests per serving rate")
+    ap.add_argument("--profile-leg", choices=["validate-free", "validate-mixed", "nearest"],
+                    default=None, help="run one kernel's leg alone (for ncu captures)")
+    ap.add_argument("--launch", default="4,1,0",
+                    help="validation launch of --profile-leg: warps per block, order, fine stage")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_leg:
+        run_profile_leg(args)
     else:
         run_ours(args)
 

@@ -211,6 +211,30 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
         std::memcpy(f4(t.off_sph + s_glob), r.sphere_xyzr, 4 * sizeof(float) * r.n_spheres);
         s_glob += r.n_spheres;
     }
+    // workspace corner below every reachable coarse centre: |origin_j - base|
+    // <= sum_i |(a_i, 0, d_i)| along the chain, |coarse centre - origin_j| <=
+    // the largest coarse-centre offset of the robot
+    {
+        double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL};
+        for (int k = 0; k < K; ++k) {
+            const mrpop_robot &r = robots[k];
+            double reach = 1.0, off = 0.0;
+            for (int j = 0; j < r.dof; ++j) {
+                const double a = r.dh[4 * j], d = r.dh[4 * j + 2];
+                reach += std::sqrt(a * a + d * d);
+                const float *A = f4(t.off_link + kLinkF4 * (t.link0[k] + j)) + 8;
+                off = std::max(off, std::sqrt((double)A[0] * A[0] + (double)A[1] * A[1] +
+                                              (double)A[2] * A[2]));
+            }
+            for (int a = 0; a < 3; ++a)
+                lo[a] = std::min(lo[a], (double)r.base[4 * a + 3] - reach - off);
+        }
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(lo[a]))
+                return set_error(MRPOP_EINVAL, "robot chain or base is not finite");
+            t.ws_lo[a] = std::nextafter((float)lo[a], -HUGE_VALF);
+        }
+    }
     if (t.NS > 0) std::memcpy(f4(t.off_os), obs->spheres, 4 * sizeof(float) * t.NS);
     for (int o = 0; o < t.NC; ++o) {
         const float *c = obs->cuboids + 15 * o;

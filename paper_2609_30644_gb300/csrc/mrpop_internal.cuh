@@ -33,6 +33,11 @@ struct Tables {
     int max_spheres_per_link = 0;
     int selfcol = 0;  // 1: also test links i, j >= i + 2 of one robot
     int off_base = 0, off_link = 0, off_sph = 0, off_os = 0, off_oc = 0, n_f4 = 0;
+    // A corner below every point that a link's coarse sphere centre can reach
+    // (each base origin minus its chain length, its farthest coarse centre and
+    // 1 m): coordinates taken relative to it are >= 0, so their float bits
+    // order like unsigned integers.
+    float ws_lo[3] = {0.f, 0.f, 0.f};
 };
 
 constexpr int kLinkF4 = 3;

@@ -51,13 +51,6 @@ constexpr int kCounters = MRPOP_WORK_COUNTERS;
 // test never drops a candidate that a checkpoint's own link-level test keeps.
 constexpr float kTileSlack = 4e-4f;
 
-// Order-preserving map of floats to signed integers (and back): for finite
-// values a < b exactly when ord(a) < ord(b).
-__device__ __forceinline__ int ord(float v) {
-    const int k = __float_as_int(v);
-    return k ^ ((k >> 31) & 0x7fffffff);
-}
-__device__ __forceinline__ float unord(int o) { return __int_as_float(o ^ ((o >> 31) & 0x7fffffff)); }
 
 enum Mode { kVerdict = 0, kClearance = 1, kCount = 2 };
 
@@ -308,6 +301,11 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
             const float tk = __fdiv_rn((float)k, (float)n);
             bool hit = false;
             if (MODE == kCount && active) cnt[0] += 1;
+            // joint angles' sine and cosine one link ahead, so that the
+            // special-function latency overlaps the previous link's tests
+            float sn_next, cs_next;
+            joint_sincos(__fmaf_rn(tk, dq_s[0], qa_s[0]) + tab[t.off_link + 1].x, &sn_next,
+                         &cs_next);
 
             for (int b = 0; b < K; ++b) {
                 const int l0 = t.link0[b], l1 = t.link0[b + 1];
@@ -317,9 +315,11 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                     const float4 LA = tab[t.off_link + kLinkF4 * l];
                     const float4 LB = tab[t.off_link + kLinkF4 * l + 1];
                     const float4 LC = tab[t.off_link + kLinkF4 * l + 2];
-                    const float th = __fmaf_rn(tk, dq_s[l], qa_s[l]) + LB.x;
-                    float sn, cs;
-                    joint_sincos(th, &sn, &cs);
+                    const float sn = sn_next, cs = cs_next;
+                    if (l + 1 < D)
+                        joint_sincos(__fmaf_rn(tk, dq_s[l + 1], qa_s[l + 1]) +
+                                         tab[t.off_link + kLinkF4 * (l + 1) + 1].x,
+                                     &sn_next, &cs_next);
                     const Frame F = rotz(Tm, cs, sn);
                     const float3 cc = apply(F, LC.x, LC.y, LC.z);
                     const int sf = __float_as_int(LB.y), ns = __float_as_int(LB.z);
@@ -327,22 +327,26 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
 
                     // Tile bound: one sphere around this link's coarse spheres at
                     // all 32 checkpoints of the tile (warp-uniform), built from the
-                    // exact axis-aligned box of the coarse centres: each float is
-                    // mapped to an order-preserving integer so that min and max are
-                    // single-instruction warp reductions.
+                    // exact axis-aligned box of the coarse centres.  Taken relative
+                    // to the workspace corner ws_lo the coordinates are >= 0, so
+                    // their float bits order like unsigned integers and min and max
+                    // are single-instruction warp reductions.
                     float4 bnd = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (MODE != kClearance) {
-                        const float x0 = unord(__reduce_min_sync(kFull, ord(cc.x)));
-                        const float x1 = unord(__reduce_max_sync(kFull, ord(cc.x)));
-                        const float y0 = unord(__reduce_min_sync(kFull, ord(cc.y)));
-                        const float y1 = unord(__reduce_max_sync(kFull, ord(cc.y)));
-                        const float z0 = unord(__reduce_min_sync(kFull, ord(cc.z)));
-                        const float z1 = unord(__reduce_max_sync(kFull, ord(cc.z)));
+                        const unsigned ux = __float_as_uint(cc.x - t.ws_lo[0]);
+                        const unsigned uy = __float_as_uint(cc.y - t.ws_lo[1]);
+                        const unsigned uz = __float_as_uint(cc.z - t.ws_lo[2]);
+                        const float x0 = __uint_as_float(__reduce_min_sync(kFull, ux));
+                        const float x1 = __uint_as_float(__reduce_max_sync(kFull, ux));
+                        const float y0 = __uint_as_float(__reduce_min_sync(kFull, uy));
+                        const float y1 = __uint_as_float(__reduce_max_sync(kFull, uy));
+                        const float z0 = __uint_as_float(__reduce_min_sync(kFull, uz));
+                        const float z1 = __uint_as_float(__reduce_max_sync(kFull, uz));
                         const float ex = 0.5f * (x1 - x0), ey = 0.5f * (y1 - y0),
                                     ez = 0.5f * (z1 - z0);
-                        bnd.x = 0.5f * (x0 + x1);
-                        bnd.y = 0.5f * (y0 + y1);
-                        bnd.z = 0.5f * (z0 + z1);
+                        bnd.x = t.ws_lo[0] + 0.5f * (x0 + x1);
+                        bnd.y = t.ws_lo[1] + 0.5f * (y0 + y1);
+                        bnd.z = t.ws_lo[2] + 0.5f * (z0 + z1);
                         bnd.w = __fsqrt_ru(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + LC.w + kTileSlack;
                         if (!(bnd.w < FLT_MAX)) bnd.w = FLT_MAX * 2.f;  // never for finite inputs
                         if (MODE == kCount && lane == 0) cnt[9] += 1;
@@ -357,21 +361,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                     }
                     bool vote = false;  // a fine stage ran: the early-exit vote is due
                     if (ns > 0) {
-                        float4 pw[SPL];
-                        bool have = false;
                         bool own_any = false;
-                        auto ensure = [&]() {
-                            if (!have) {
-#pragma unroll
-                                for (int s = 0; s < SPL; ++s)
-                                    if (s < ns) {
-                                        const float4 sp = tab[t.off_sph + sf + s];
-                                        const float3 p = apply(F, sp.x, sp.y, sp.z);
-                                        pw[s] = make_float4(p.x, p.y, p.z, sp.w);
-                                    }
-                                have = true;
-                            }
-                        };
                         if (MODE == kCount && active) cnt[7] += 1;  // coarse centre
                         const float rc = LC.w + m;
 
@@ -417,25 +407,23 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                 cnt[4] += (unsigned long long)__popc(own) * ns;
                                 own_any |= own != 0;
                             }
-                            if (wm) {
-                                ensure();
+                            // fine stage: each of the link's spheres is placed once and
+                            // tested against every obstacle of the warp's union mask
+                            for (int s = 0; wm && s < ns; ++s) {
+                                const float4 sp = tab[t.off_sph + sf + s];
+                                const float3 p = apply(F, sp.x, sp.y, sp.z);
                                 unsigned mm = wm;
                                 while (mm) {
                                     const int o = __ffs(mm) - 1;
                                     mm &= mm - 1;
                                     const float4 ob = tab[t.off_os + c0 + o];
-#pragma unroll
-                                    for (int s = 0; s < SPL; ++s)
-                                        if (s < ns) {
-                                            const float d2 =
-                                                dist2(pw[s].x, pw[s].y, pw[s].z, ob.x, ob.y, ob.z);
-                                            if (MODE == kClearance) {
-                                                minc = fminf(minc, __fsqrt_rn(d2) - pw[s].w - ob.w);
-                                            } else {
-                                                const float th2 = pw[s].w + ob.w + m;
-                                                hit |= d2 < th2 * th2;
-                                            }
-                                        }
+                                    const float d2 = dist2(p.x, p.y, p.z, ob.x, ob.y, ob.z);
+                                    if (MODE == kClearance) {
+                                        minc = fminf(minc, __fsqrt_rn(d2) - sp.w - ob.w);
+                                    } else {
+                                        const float th2 = sp.w + ob.w + m;
+                                        hit |= d2 < th2 * th2;
+                                    }
                                 }
                             }
                         }
@@ -486,27 +474,22 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                                 cnt[5] += (unsigned long long)__popc(own) * ns;
                                 own_any |= own != 0;
                             }
-                            if (wm) {
-                                ensure();
+                            for (int s = 0; wm && s < ns; ++s) {
+                                const float4 sp = tab[t.off_sph + sf + s];
+                                const float3 p = apply(F, sp.x, sp.y, sp.z);
                                 unsigned mm = wm;
                                 while (mm) {
                                     const int o = __ffs(mm) - 1;
                                     mm &= mm - 1;
                                     const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + o);
-                                    const float4 C = cbp[0], H = cbp[1], A0 = cbp[2], A1 = cbp[3],
-                                                 A2 = cbp[4];
-#pragma unroll
-                                    for (int s = 0; s < SPL; ++s)
-                                        if (s < ns) {
-                                            const float d2 =
-                                                box_dist2(pw[s].x, pw[s].y, pw[s].z, C, H, A0, A1, A2);
-                                            if (MODE == kClearance) {
-                                                minc = fminf(minc, __fsqrt_rn(d2) - pw[s].w);
-                                            } else {
-                                                const float th2 = pw[s].w + m;
-                                                hit |= d2 < th2 * th2;
-                                            }
-                                        }
+                                    const float d2 = box_dist2(p.x, p.y, p.z, cbp[0], cbp[1], cbp[2],
+                                                               cbp[3], cbp[4]);
+                                    if (MODE == kClearance) {
+                                        minc = fminf(minc, __fsqrt_rn(d2) - sp.w);
+                                    } else {
+                                        const float th2 = sp.w + m;
+                                        hit |= d2 < th2 * th2;
+                                    }
                                 }
                             }
                         }
@@ -584,29 +567,40 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4) {
                             }
                             for (int w = 0; w < 2; ++w) {
                                 unsigned mm = w == 0 ? w0 : w1;
-                                if (mm) ensure();
                                 while (mm) {
                                     const int i = __ffs(mm) - 1 + 32 * w;
                                     mm &= mm - 1;
                                     const Frame Fi = link_frame(tab, t, qa_s, dq_s, i, tk);
                                     const float4 LBi = tab[t.off_link + kLinkF4 * i + 1];
                                     const int sfi = __float_as_int(LBi.y), nsi = __float_as_int(LBi.z);
-                                    for (int s2 = 0; s2 < nsi; ++s2) {
-                                        const float4 sp = tab[t.off_sph + sfi + s2];
-                                        const float3 pa = apply(Fi, sp.x, sp.y, sp.z);
+                                    // the other link's spheres four at a time, this
+                                    // link's placed once per group of four
+                                    for (int g0 = 0; g0 < nsi; g0 += 4) {
+                                        float4 pa[4];
 #pragma unroll
-                                        for (int s = 0; s < SPL; ++s)
-                                            if (s < ns) {
+                                        for (int j = 0; j < 4; ++j) {
+                                            const float4 sp2 = tab[t.off_sph + sfi + min(g0 + j, nsi - 1)];
+                                            const float3 q3 = apply(Fi, sp2.x, sp2.y, sp2.z);
+                                            pa[j] = make_float4(q3.x, q3.y, q3.z, sp2.w);
+                                        }
+                                        const int gn = min(4, nsi - g0);
+                                        for (int s = 0; s < ns; ++s) {
+                                            const float4 sp = tab[t.off_sph + sf + s];
+                                            const float3 p = apply(F, sp.x, sp.y, sp.z);
+#pragma unroll
+                                            for (int j = 0; j < 4; ++j) {
+                                                if (j >= gn) break;
                                                 const float d2 =
-                                                    dist2(pw[s].x, pw[s].y, pw[s].z, pa.x, pa.y, pa.z);
+                                                    dist2(p.x, p.y, p.z, pa[j].x, pa[j].y, pa[j].z);
                                                 if (MODE == kClearance) {
                                                     minc = fminf(minc,
-                                                                 __fsqrt_rn(d2) - pw[s].w - sp.w);
+                                                                 __fsqrt_rn(d2) - sp.w - pa[j].w);
                                                 } else {
-                                                    const float th2 = pw[s].w + sp.w + m;
+                                                    const float th2 = sp.w + pa[j].w + m;
                                                     hit |= d2 < th2 * th2;
                                                 }
                                             }
+                                        }
                                     }
                                 }
                             }
