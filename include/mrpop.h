@@ -340,21 +340,52 @@ mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim, double *
 mrpop_status mrpop_plan(mrpop_problem *p, double time_budget_s, float *path, int64_t path_cap,
                         int64_t *path_len, double *cost);
 
-/* Plans n problems at once (the batched form of mrpop_plan): one search step
- * advances every problem by 256 iterations in a single replay of a captured
- * CUDA graph whose kernels take a problem dimension; problems that need a
- * ROADMAP round skip the steps until it completes.  Runs until time_budget_s
- * of wall time, or max_steps steps when max_steps > 0, or until every problem
- * has reached target_costs[i] (host [n], or NULL for none).  A problem's
- * planner evolves exactly as it would alone for the same number of steps
- * (per-problem random streams, ordered inserts), so results do not depend on
- * the mix.  statuses (host [n], may be NULL): MRPOP_OK, or MRPOP_EINVAL for a
- * problem whose start or goal is in collision.  Results: mrpop_plan_result,
- * mrpop_plan_trace.  Errors: EINVAL (NULL, repeated or start/goal-less
- * problems), ENOMEM / ECUDA. */
+/* Plans n problems at once (the batched form of mrpop_plan) in one
+ * persistent kernel launch, captured in a CUDA graph.  CTAs resident on every
+ * SM advance every problem through Alg. 1 on the device -- ROADMAP rounds
+ * (Alg. 2), search steps of 256 iterations, the re-check of each incumbent at
+ * resolution / 4 and the anytime bookkeeping -- each problem independently:
+ * its phases are cut into chunks that any CTA may claim, and the CTA finishing
+ * a phase starts the next one, so no problem waits for another and the host
+ * takes part only before and after the launch.  An outer iteration of Alg. 1
+ * (an optional ROADMAP round, then a search step) is one "step".  Runs until
+ * time_budget_s of wall time (checked at step boundaries), or max_steps steps
+ * per problem when max_steps > 0, or until every problem has reached
+ * target_costs[i] (host [n], or NULL for none).  A problem's planner evolves
+ * exactly as it would alone for the same number of steps (per-problem random
+ * streams, fixed-position writes, ordered inserts), so results do not depend
+ * on the mix.  statuses (host [n], may be NULL): MRPOP_OK, MRPOP_EINVAL for a
+ * problem whose start or goal is in collision, MRPOP_ETIMEOUT for a problem
+ * left unfinished when a bounded wait ran out (see
+ * mrpop_set_persistent_limits).  Results: mrpop_plan_result, mrpop_plan_trace.
+ * Errors: EINVAL (NULL, repeated or start/goal-less problems, tables too large
+ * for the launch's shared memory), ENOMEM / ECUDA, ETIMEOUT (an idle CTA's
+ * bounded wait for work ran out; results found until then are kept). */
 mrpop_status mrpop_plan_batch(mrpop_problem *const *ps, int32_t n, double time_budget_s,
                               int64_t max_steps, const double *target_costs,
                               mrpop_status *statuses);
+
+/* Batch forms of mrpop_plan_batch_ex. */
+#define MRPOP_BATCH_PERSISTENT 0  /* one persistent launch (mrpop_plan_batch)        */
+#define MRPOP_BATCH_STEPPED 1     /* every step a replay of a captured graph of 9
+                                   * launches with a problem dimension, ROADMAP
+                                   * rounds as launches with a robot dimension,
+                                   * host bookkeeping between steps (the form
+                                   * mrpop_plan runs one problem in)              */
+
+/* mrpop_plan_batch in either form (EINVAL for another value).  Same
+ * arguments, results and errors otherwise. */
+mrpop_status mrpop_plan_batch_ex(mrpop_problem *const *ps, int32_t n, double time_budget_s,
+                                 int64_t max_steps, const double *target_costs,
+                                 mrpop_status *statuses, int32_t form);
+
+/* Limits of the persistent launch, process-wide, for tests and diagnostics:
+ * ctas > 0 sets the number of CTAs (0: as many as fit on every SM);
+ * idle_polls > 0 lets a CTA that found no work give up after that many
+ * consecutive polls (0: only after the budget plus a grace period), setting
+ * the launch's timeout flag (mrpop_plan_batch then returns MRPOP_ETIMEOUT).
+ * Errors: EINVAL for negative values. */
+mrpop_status mrpop_set_persistent_limits(int32_t ctas, int64_t idle_polls);
 
 /* Best path and cost found so far for p (same outputs and errors as
  * mrpop_plan, without planning). */

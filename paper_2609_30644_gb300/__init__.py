@@ -15,7 +15,7 @@ _OPS = ("MrpopError", "Problem", "edge_clearance", "fk", "lib", "library_path", 
         "plan_batch", "plan_result", "Server", "autotune", "set_launch",
         "plan_history", "fp32_peak", "nearest_work", "NEAREST_FILTER_FP32",
         "NEAREST_FILTER_TENSOR", "planner_nearest_pass", "planner_neighbors_pass",
-        "ROADMAP_DEGREE_CAP")
+        "ROADMAP_DEGREE_CAP", "BATCH_PERSISTENT", "BATCH_STEPPED", "set_persistent_limits")
 
 
 def __getattr__(name):

@@ -48,6 +48,8 @@ EXPORTS = (
     "mrpop_fp32_peak",
     "mrpop_planner_nearest_pass",
     "mrpop_planner_neighbors_pass",
+    "mrpop_plan_batch_ex",
+    "mrpop_set_persistent_limits",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -118,6 +120,8 @@ def _load() -> C.CDLL:
         "mrpop_fp32_peak": (i32, [i32, i32, vp, vp]),
         "mrpop_planner_nearest_pass": (i32, [vp, i64, i64, i32, vp, vp, i32, i32, vp, vp]),
         "mrpop_planner_neighbors_pass": (i32, [vp, i64, i64, i32, vp, i64, f32, vp, vp, vp]),
+        "mrpop_plan_batch_ex": (i32, [vp, i32, C.c_double, i64, vp, vp, i32]),
+        "mrpop_set_persistent_limits": (i32, [i32, i64]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -434,15 +438,27 @@ def plan_trace(p: Problem) -> tuple:
     return t[:n.value], c[:n.value], it.value
 
 
-def plan_batch(problems, time_budget_s: float, max_steps: int = 0, targets=None) -> np.ndarray:
-    """Plans all problems at once; returns their int32 statuses."""
+BATCH_PERSISTENT = 0   # MRPOP_BATCH_PERSISTENT (mrpop_plan_batch)
+BATCH_STEPPED = 1      # MRPOP_BATCH_STEPPED
+
+
+def plan_batch(problems, time_budget_s: float, max_steps: int = 0, targets=None,
+               form: int = BATCH_PERSISTENT) -> np.ndarray:
+    """Plans all problems at once (one persistent launch, or the stepped
+    form); returns their int32 statuses."""
     n = len(problems)
     hs = (C.c_void_p * n)(*[p.handle.value for p in problems])
     st = np.zeros(n, dtype=np.int32)
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.float64)
-    _check(lib.mrpop_plan_batch(hs, n, float(time_budget_s), int(max_steps),
-                                None if tg is None else tg.ctypes.data, st.ctypes.data))
+    _check(lib.mrpop_plan_batch_ex(hs, n, float(time_budget_s), int(max_steps),
+                                   None if tg is None else tg.ctypes.data, st.ctypes.data,
+                                   int(form)))
     return st
+
+
+def set_persistent_limits(ctas: int = 0, idle_polls: int = 0) -> None:
+    """Process-wide limits of the persistent launch (tests, diagnostics)."""
+    _check(lib.mrpop_set_persistent_limits(int(ctas), int(idle_polls)))
 
 
 def plan_result(p: Problem, path_cap: int = 1 << 16) -> tuple:

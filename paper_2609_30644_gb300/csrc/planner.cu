@@ -19,6 +19,7 @@
 // robot of every problem that needs one at once: each phase is one launch
 // with a job dimension, and the round ends with one host synchronisation.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <chrono>
 #include <condition_variable>
@@ -33,6 +34,7 @@
 #include <vector>
 
 #include "mrpop_internal.cuh"
+#include "validate_body.cuh"
 
 namespace mrpop {
 
@@ -105,9 +107,7 @@ __device__ __forceinline__ float nanf_() { return __int_as_float(0x7fc00000); }
 
 // q_rand (uniform, or informed in the prolate hyperspheroid of c_best) and the
 // cost coordinate c_rand ~ U[g_lb(q_rand), c_best] (Alg. 2 AO-X).
-__global__ void k_sample(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.y];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sample_body(const Slot &S, int i) {
     const Ctrl &C = *S.ctrl;
     const int a = (S.tn[0] <= S.tn[1]) ? 0 : 1;  // expand the smaller tree
     if (i == 0) S.ctrl->tree_a = a;
@@ -169,6 +169,10 @@ __global__ void k_sample(const Slot *__restrict__ slots) {
     }
 }
 
+__global__ void k_sample(const Slot *__restrict__ slots) {
+    sample_body(slots[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // NEAREST over one of the slot's trees (pass 0: expanded tree with q_rand and
 // c_rand; pass 1: opposite tree with q_new and c_best - g_new).  Vertices
 // across the block's threads, 16 queries per block in shared memory, key
@@ -186,18 +190,25 @@ __device__ __forceinline__ bool pbetter(const PBest &a, const PBest &b) {
     return (unsigned)a.idx < (unsigned)b.idx;
 }
 
-template <int PASS>
-__global__ void __launch_bounds__(kPThreads) k_nearest(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.y];
+// Shared memory of one NEAREST chunk (16 queries) for a block of THREADS.
+template <int THREADS>
+struct NnShared {
+    float qs[kPQB][MRPOP_MAX_LINKS];
+    float cs[kPQB];
+    PBest wb[THREADS / 32][kPQB];
+};
+
+template <int PASS, int THREADS>
+__device__ __forceinline__ void nearest_body(const Slot &S, int chunk, NnShared<THREADS> &sh) {
     const Ctrl &C = *S.ctrl;
-    __shared__ float qs[kPQB][MRPOP_MAX_LINKS];
-    __shared__ float cs[kPQB];
-    __shared__ PBest wb[kPThreads / 32][kPQB];
+    float(&qs)[kPQB][MRPOP_MAX_LINKS] = sh.qs;
+    float(&cs)[kPQB] = sh.cs;
+    PBest(&wb)[THREADS / 32][kPQB] = sh.wb;
     const int B = kStepIters, D = S.D;
     const int t = PASS == 0 ? C.tree_a : 1 - C.tree_a;
     const float *tree = S.tq[t];
     const int N = min(S.tn[t], S.tcap);
-    const int q0 = blockIdx.x * kPQB;
+    const int q0 = chunk * kPQB;
     const float *Qs = PASS == 0 ? S.qrand : S.qnew;
     const float *Cs = PASS == 0 ? S.crand : S.budget2;
     for (int k = threadIdx.x; k < kPQB * D; k += blockDim.x) {
@@ -243,10 +254,16 @@ __global__ void __launch_bounds__(kPThreads) k_nearest(const Slot *__restrict__ 
     __syncthreads();
     if (threadIdx.x < kPQB) {
         PBest b = wb[0][threadIdx.x];
-        for (int w = 1; w < kPThreads / 32; ++w)
+        for (int w = 1; w < THREADS / 32; ++w)
             if (pbetter(wb[w][threadIdx.x], b)) b = wb[w][threadIdx.x];
         (PASS == 0 ? S.near : S.conn)[q0 + threadIdx.x] = b.idx;
     }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kPThreads) k_nearest(const Slot *__restrict__ slots) {
+    __shared__ NnShared<kPThreads> sh;
+    nearest_body<PASS, kPThreads>(slots[blockIdx.y], blockIdx.x, sh);
 }
 
 // Direction oracle.  dRRT (Solovey et al.): per robot, the roadmap neighbour v
@@ -254,10 +271,8 @@ __global__ void __launch_bounds__(kPThreads) k_nearest(const Slot *__restrict__ 
 // the robot stays put when no neighbour has a positive cosine.  AO-X: the same
 // choice, kept only when the extension is admissible, g_near + |q_new - q_near|
 // <= c_rand (Sec. III-D).
-__global__ void k_oracle(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.y];
+__device__ __forceinline__ void oracle_body(const Slot &S, int i) {
     const Ctrl &C = *S.ctrl;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kStepIters) return;
     const int B = kStepIters, D = S.D, a = C.tree_a;
     const int nr = (int)S.near[i];
@@ -338,14 +353,16 @@ __global__ void k_oracle(const Slot *__restrict__ slots) {
     S.gnew[i] = gnew;
 }
 
+__global__ void k_oracle(const Slot *__restrict__ slots) {
+    oracle_body(slots[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Insert z_new = (q_new, g_near + |q_new - q_near|) into the expanded tree and
 // prepare the connection budget c_best - g_new (AO-X) or +inf (dRRT).  One
 // block per slot; new vertices get consecutive indices in iteration order (a
 // block-wide prefix sum), so a slot's trees do not depend on thread timing.
-__global__ void __launch_bounds__(kStepIters) k_insert(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.y];
+__device__ __forceinline__ void insert_body(const Slot &S, int *wsum) {
     Ctrl &C = *S.ctrl;
-    __shared__ int wsum[kStepIters / 32];
     const int i = threadIdx.x;
     const int B = kStepIters, D = S.D, a = C.tree_a;
     const bool want = S.valid1[i] && S.gnew[i] < INFINITY;
@@ -380,9 +397,12 @@ __global__ void __launch_bounds__(kStepIters) k_insert(const Slot *__restrict__ 
     S.budget2[i] = idx < 0 ? -INFINITY : (C.mode == 1 ? C.c_best - S.gnew[i] : INFINITY);
 }
 
-__global__ void k_conn_prep(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.y];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kStepIters) k_insert(const Slot *__restrict__ slots) {
+    __shared__ int wsum[kStepIters / 32];
+    insert_body(slots[blockIdx.y], wsum);
+}
+
+__device__ __forceinline__ void conn_prep_body(const Slot &S, int i) {
     if (i >= kStepIters) return;
     const int B = kStepIters, D = S.D, b = 1 - S.ctrl->tree_a;
     const int c = (int)S.conn[i];
@@ -393,12 +413,14 @@ __global__ void k_conn_prep(const Slot *__restrict__ slots) {
     }
 }
 
+__global__ void k_conn_prep(const Slot *__restrict__ slots) {
+    conn_prep_body(slots[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // A checked connection closes a path start -> ... -> z_new -> z_conn -> ...
 // -> goal; the cheapest of the step wins (packed cost | iteration key).
-__global__ void k_solution(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.y];
+__device__ __forceinline__ void solution_body(const Slot &S, int i) {
     Ctrl &C = *S.ctrl;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kStepIters) return;
     const int B = kStepIters, D = S.D, b = 1 - C.tree_a;
     const int c = (int)S.conn[i];
@@ -414,13 +436,16 @@ __global__ void k_solution(const Slot *__restrict__ slots) {
     atomicMin(&C.best_key, key);
 }
 
+__global__ void k_solution(const Slot *__restrict__ slots) {
+    solution_body(slots[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Path of the winning iteration: root_a .. z_new, then z_conn .. root_b.
 // One thread follows the parents; the configurations are written to
 // out_q [cap][D] in that order (reversed to start -> goal by the host when the
 // expanded tree was the goal tree).
-__global__ void k_extract(const Slot *__restrict__ slots, int it, int *scratch, float *out_q,
-                          int cap, int *len_out) {
-    const Slot &S = slots[0];
+__device__ __forceinline__ void extract_body(const Slot &S, int it, int *scratch, float *out_q,
+                                             int cap, int *len_out) {
     const int a = S.ctrl->tree_a, b = 1 - a, D = S.D;
     int na = 0;
     for (int v = S.newidx[it]; v >= 0 && na < cap; v = S.tpar[a][v]) scratch[na++] = v;
@@ -430,6 +455,11 @@ __global__ void k_extract(const Slot *__restrict__ slots, int it, int *scratch, 
     for (int v = (int)S.conn[it]; v >= 0 && n < cap; v = S.tpar[b][v], ++n)
         for (int d = 0; d < D; ++d) out_q[(size_t)n * D + d] = S.tq[b][(size_t)d * S.tcap + v];
     *len_out = n;
+}
+
+__global__ void k_extract(const Slot *__restrict__ slots, int it, int *scratch, float *out_q,
+                          int cap, int *len_out) {
+    extract_body(slots[0], it, scratch, out_q, cap, len_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -549,13 +579,15 @@ struct RmJob {
     int m, first;           // written by k_rmb_gather
 };
 
-__global__ void k_rmb_sample(const RmJob *__restrict__ jobs) {
-    const RmJob &J = jobs[blockIdx.y];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rmb_sample_body(const RmJob &J, int i) {
     if (i >= J.nc) return;
     Rng rng{J.key, J.ctr + (unsigned long long)i * 64ull};
     for (int d = 0; d < J.dof; ++d)
         J.cand[(size_t)d * J.nc + i] = J.lo[d] + rng.uniform() * (J.hi[d] - J.lo[d]);
+}
+
+__global__ void k_rmb_sample(const RmJob *__restrict__ jobs) {
+    rmb_sample_body(jobs[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(kAppendThreads) k_rmb_append(const RmJob *__restrict__ jobs) {
@@ -565,28 +597,29 @@ __global__ void __launch_bounds__(kAppendThreads) k_rmb_append(const RmJob *__re
 
 // The vertices whose neighbours are searched: the new ones, and on the first
 // round also start and goal (vertices 0 and 1).
-__global__ void k_rmb_gather(RmJob *__restrict__ jobs) {
-    RmJob &J = jobs[blockIdx.y];
+__device__ __forceinline__ void rmb_gather_body(RmJob &J, int i, bool lead) {
     const int n_new = *J.count;
     const int first = J.n_old == 2 && n_new > 2 ? 0 : J.n_old;
     const int m = n_new - first;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (lead) {
         J.m = m;
         J.first = first;
     }
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     for (int d = 0; d < J.dof; ++d) J.gq[(size_t)d * m + i] = J.q[(size_t)d * J.rcap + first + i];
+}
+
+__global__ void k_rmb_gather(RmJob *__restrict__ jobs) {
+    rmb_gather_body(jobs[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x,
+                    blockIdx.x == 0 && threadIdx.x == 0);
 }
 
 // NEIGHBORS(V_r, c, delta) of Alg. 2 for the gathered vertices: one warp per
 // query scans V_r in index order (ballot + prefix count), keeping the first
 // kKmax indices within delta; the same test as the NEIGHBORS primitive.
 constexpr int kRmNbWarps = 8;
-__global__ void __launch_bounds__(kRmNbWarps * 32) k_rmb_neighbors(const RmJob *__restrict__ jobs) {
-    const RmJob &J = jobs[blockIdx.y];
+__device__ __forceinline__ void rmb_neighbors_body(const RmJob &J, int i) {
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kRmNbWarps + (threadIdx.x >> 5);
     const int m = J.m, n = *J.count, dof = J.dof;
     if (i >= m) return;
     float qv[MRPOP_MAX_DOF];
@@ -617,11 +650,13 @@ __global__ void __launch_bounds__(kRmNbWarps * 32) k_rmb_neighbors(const RmJob *
     if (lane == 0) J.cnt[i] = count;
 }
 
+__global__ void __launch_bounds__(kRmNbWarps * 32) k_rmb_neighbors(const RmJob *__restrict__ jobs) {
+    rmb_neighbors_body(jobs[blockIdx.y], blockIdx.x * kRmNbWarps + (threadIdx.x >> 5));
+}
+
 // Candidate roadmap edges (gathered vertex, earlier neighbour within delta);
 // unused slots up to emax get a NaN edge, which validation rejects unchecked.
-__global__ void k_rmb_edges(const RmJob *__restrict__ jobs) {
-    const RmJob &J = jobs[blockIdx.y];
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rmb_edges_body(const RmJob &J, int e) {
     if (e >= J.emax) return;
     const int E = J.m * kKmax, j = e / kKmax, k = e % kKmax;
     int v = -1, self = -1;
@@ -647,6 +682,10 @@ __global__ void k_rmb_edges(const RmJob *__restrict__ jobs) {
     J.eb[e] = v;
 }
 
+__global__ void k_rmb_edges(const RmJob *__restrict__ jobs) {
+    rmb_edges_body(jobs[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 __global__ void k_rmb_link(const RmJob *__restrict__ jobs) {
     const RmJob &J = jobs[blockIdx.y];
     link_edges(J.evalid, J.ea, J.eb, J.m * kKmax, J.adj, J.deg);
@@ -665,8 +704,7 @@ __global__ void k_rmb_collect(const RmJob *__restrict__ jobs, int nj, int *out) 
     out[2 * j + 1] = *jobs[j].conn;
 }
 
-__global__ void k_tree_reset(const Slot *__restrict__ slots) {
-    const Slot &S = slots[blockIdx.x];
+__device__ __forceinline__ void tree_reset_body(const Slot &S) {
     const int D = S.D;
     for (int t = 0; t < 2; ++t) {
         const float *root = t == 0 ? S.start : S.goal;
@@ -679,6 +717,8 @@ __global__ void k_tree_reset(const Slot *__restrict__ slots) {
         }
     }
 }
+
+__global__ void k_tree_reset(const Slot *__restrict__ slots) { tree_reset_body(slots[blockIdx.x]); }
 
 // ---------------------------------------------------------------------------
 // host side
@@ -705,6 +745,31 @@ struct RobotRoadmap {
     int vw_c = 1, vw_e = 1;
     size_t vs_c = 0, vs_e = 0;
 };
+
+// Device buffers of the persistent form, per planner (allocated on first use).
+struct PerBuffers {
+    Slot *slot = nullptr;
+    RmJob *jobs = nullptr;
+    VParams *vp = nullptr;
+    int *seg_parts = nullptr;
+    float *best = nullptr;
+    double *trace_c = nullptr;
+    unsigned long long *trace_ns = nullptr;
+    long long *trace_it = nullptr;
+    float *hist = nullptr;
+    int *hist_len = nullptr;
+    int hist_floats = 0;
+    VParams vfine{};
+    int vfine_w = 1;
+    size_t vfine_s = 0;
+};
+
+static void per_free(PerBuffers &b) {
+    cudaFree(b.slot); cudaFree(b.jobs); cudaFree(b.vp); cudaFree(b.seg_parts); cudaFree(b.best);
+    cudaFree(b.trace_c); cudaFree(b.trace_ns); cudaFree(b.trace_it); cudaFree(b.hist);
+    cudaFree(b.hist_len);
+    b = PerBuffers{};
+}
 
 struct Planner {
     mrpop_problem *p = nullptr;
@@ -744,6 +809,7 @@ struct Planner {
     int *d_path = nullptr;
     float *d_pathq = nullptr;
     int *d_len = nullptr;
+    PerBuffers per;  // persistent-form buffers (allocated on first use)
 };
 
 static mrpop_status make_sub(mrpop_problem *p, int k, float res, mrpop_problem **out) {
@@ -816,6 +882,7 @@ static void free_device(Planner *pl) {
     cudaFree(pl->fine_qa);
     cudaFree(pl->fine_qb);
     cudaFree(pl->fine_v);
+    per_free(pl->per);
     pl->fine_qa = pl->fine_qb = nullptr;
     pl->fine_v = nullptr;
     pl->fine_cap = 0;
@@ -1542,6 +1609,833 @@ static mrpop_status plan_batch(mrpop_problem *const *ps, int n, double budget, i
 
 
 // ---------------------------------------------------------------------------
+// Persistent batched planner.  One launch of CTAs resident on every SM runs
+// Alg. 1 for every problem of the batch until each is done (time budget,
+// step budget or target cost).  Every problem carries a state machine of
+// phases -- a ROADMAP round is sample, candidate validation, append,
+// NEIGHBORS, candidate edges, edge validation and link + BFS for each robot
+// in turn; a search step is the nine phases of the stepped form; an
+// incumbent candidate is re-checked at a quarter of the resolution -- and
+// each phase is cut into chunks (256 samples or iterations, 16 NEAREST
+// queries, 32 edges, 8 NEIGHBORS queries).  CTAs claim chunks of any problem
+// with one atomic add on the problem's phase word, which carries the phase
+// itself (kind, robot, chunk count) beside the next chunk, so a claim always
+// names the phase it belongs to.  The CTA that finishes a phase's last chunk
+// runs the transition (Alg. 1 bookkeeping on the device, in the stepped
+// form's order) and publishes the next phase.  No CTA waits for another: a
+// CTA that finds no chunk polls again after a short sleep, and gives up (a
+// timeout flag) only past a hard deadline or an optional poll limit.  Every
+// phase of a problem writes fixed positions, and its sequential parts run in
+// single-chunk phases, so a problem evolves the same alone or in a mix.
+// ---------------------------------------------------------------------------
+enum PKind : int {
+    PK_BEGIN = 0,
+    PK_RM_SAMPLE, PK_RM_VALC, PK_RM_APPEND, PK_RM_NB, PK_RM_EDGES, PK_RM_VALE, PK_RM_LINK,
+    PK_ST_SAMPLE, PK_ST_NN0, PK_ST_ORACLE, PK_ST_VAL1, PK_ST_INSERT, PK_ST_NN1, PK_ST_CONN,
+    PK_ST_VAL2, PK_ST_SOLUTION, PK_FINE_VAL, PK_FINE_ACCEPT,
+    PK_DONE
+};
+constexpr int kPerThreads = 256;          // threads per persistent CTA (= kStepIters)
+constexpr int kPerWarps = kPerThreads / 32;
+constexpr int kPerEdges = 32;             // edges per validation chunk
+constexpr int kFineCap = 16384;           // sub-edges per fine re-check window
+constexpr int kTraceCap = 256;            // incumbents recorded per problem
+constexpr int kHistCap = 64;              // incumbent paths kept per problem
+static_assert(kPerThreads == kStepIters, "one search-step iteration per thread");
+
+// Phase word: kind (6 bits) | robot (6) | chunk count (20) | next chunk (32).
+__host__ __device__ __forceinline__ unsigned long long phase_word(int kind, int robot, int total) {
+    return ((unsigned long long)kind << 58) | ((unsigned long long)(robot & 63) << 52) |
+           ((unsigned long long)(total & 0xFFFFF) << 32);
+}
+
+struct PState {
+    unsigned long long claim;  // phase word
+    int done;                  // chunks of the current phase finished
+    int finished;              // 1 once the problem reached PK_DONE
+    // Alg. 1 control (the stepped form keeps these on the host)
+    int mode, step, need_roadmap, reset_trees, roadmap_ready, active, reached, direct, K, D;
+    int timed_out;             // stopped by the time budget
+    long long iters_in_call, total_iters, max_iters, steps_done, max_steps;
+    double c_best, target;
+    unsigned long long seed;
+    int n_per_round, rcap;
+    float res4;                // resolution / 4 (fine re-check)
+    // incumbent candidate of the current step
+    int cand_len, fine_M, fine_done, fine_cnt, fine_bad, accepted;
+    double cand_cost;
+    // results
+    int best_len, n_trace, n_hist, hist_used;
+    // device buffers
+    Slot *slot;
+    RmJob *jobs;               // [K]
+    VParams *vp;               // [0] extension, [1] connection, [2] fine re-check,
+                               // [3 + k] candidates, [3 + K + k] roadmap edges of robot k
+    int *scratch;              // [path_cap] path indices, then segment offsets
+    int *seg_parts;            // [path_cap]
+    float *cand_path, *best_path;  // [path_cap][D]
+    int path_cap;
+    float *fine_qa, *fine_qb;  // [D][kFineCap]
+    uint8_t *fine_v;           // [kFineCap]
+    double *trace_c;           // [kTraceCap]
+    unsigned long long *trace_ns;
+    long long *trace_it;
+    float *hist;               // arena of hist_floats
+    int *hist_len;             // [kHistCap] (-1: did not fit)
+    int hist_floats;
+};
+
+struct PLaunch {
+    PState *states;
+    int n;
+    unsigned long long budget_ns, hard_ns;  // per problem budget; give-up horizon
+    long long idle_poll_limit;              // consecutive empty polls before giving up (0: none)
+    unsigned long long *t_start;            // earliest CTA start (globaltimer)
+    int *finished;                          // problems done
+    int *timeout;                           // an idle CTA gave up
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int chunks_of(int n, int per) { return n <= 0 ? 0 : (n + per - 1) / per; }
+
+// Validation of edges [chunk * 32, chunk * 32 + 32) of vp (count edges in all).
+__device__ __noinline__ void val_chunk(const VParams &vp, int chunk, int count, float4 *sm4,
+                                       int *s_next) {
+    if (threadIdx.x == 0) *s_next = 0;
+    const int e0 = chunk * kPerEdges, e1 = min(count, e0 + kPerEdges);
+    vb::validate_body<vb::kVerdict, false, true>(vp, sm4, e0, e1, s_next);
+    __syncthreads();
+}
+
+// Sub-edges [w0, w1) of the candidate path (segments cut into equal parts of
+// at most 31 intervals at resolution / 4, as in the stepped form) into the
+// fine re-check buffers, positions e - w0.
+__device__ void fine_window(PState &ps, int w0, int w1) {
+    const int len = ps.cand_len, D = ps.D;
+    const float *path = ps.cand_path;
+    for (int j = threadIdx.x; j + 1 < len; j += blockDim.x) {
+        const int off = ps.scratch[j], parts = ps.seg_parts[j];
+        for (int i = max(0, w0 - off); i < parts && off + i < w1; ++i) {
+            const int e = off + i - w0;
+            const double t0 = (double)i / parts, t1 = (double)(i + 1) / parts;
+            for (int d = 0; d < D; ++d) {
+                const double a = path[(size_t)j * D + d], b = path[(size_t)(j + 1) * D + d];
+                ps.fine_qa[(size_t)d * kFineCap + e] = i == 0 ? (float)a : (float)(a + t0 * (b - a));
+                ps.fine_qb[(size_t)d * kFineCap + e] =
+                    i + 1 == parts ? (float)b : (float)(a + t1 * (b - a));
+            }
+        }
+    }
+}
+
+// PK_ST_SOLUTION after k_solution's body: the cheapest connection of the step,
+// if any, is extracted, put in start -> goal order and costed in FP64 (fixed
+// summation order); a strictly cheaper one gets its fine re-check windows set up.
+__device__ void solution_candidate(PState &ps, double *red) {
+    const Slot &S = *ps.slot;
+    const int tid = threadIdx.x;
+    __syncthreads();
+    const unsigned long long key = S.ctrl->best_key;
+    if (tid == 0) ps.fine_M = 0;
+    if (key == ~0ull) return;
+    if (tid == 0)
+        extract_body(S, (int)(key & 0xffffffffu), ps.scratch, ps.cand_path, ps.path_cap,
+                     &ps.cand_len);
+    __syncthreads();
+    const int len = ps.cand_len, D = ps.D;
+    if (S.ctrl->tree_a == 1)  // the expanded tree was the goal tree: reverse
+        for (int k = tid; k < (len / 2) * D; k += blockDim.x) {
+            const int j = k / D, d = k % D;
+            float *x = ps.cand_path + (size_t)j * D + d, *y = ps.cand_path + (size_t)(len - 1 - j) * D + d;
+            const float t = *x;
+            *x = *y;
+            *y = t;
+        }
+    __syncthreads();
+    double c = 0.0;
+    for (int j = tid; j + 1 < len; j += blockDim.x) {
+        double s2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double t = (double)ps.cand_path[(size_t)(j + 1) * D + d] - ps.cand_path[(size_t)j * D + d];
+            s2 += t * t;
+        }
+        c += sqrt(s2);
+        const double n = ceil(sqrt(s2) / (double)ps.res4);
+        ps.seg_parts[j] = (int)fmin(4096.0, fmax(1.0, ceil(n / 31.0)));
+    }
+    red[tid] = c;
+    __syncthreads();
+    if (tid == 0) {
+        double cost = 0.0;
+        for (int k = 0; k < blockDim.x; ++k) cost += red[k];
+        ps.cand_cost = cost;
+        if (cost < ps.c_best && len >= 2) {
+            int M = 0;
+            for (int j = 0; j + 1 < len; ++j) {
+                ps.scratch[j] = M;  // the path indices are no longer needed
+                M += ps.seg_parts[j];
+            }
+            ps.fine_M = M;
+            ps.fine_done = 0;
+            ps.fine_bad = 0;
+            ps.accepted = 0;
+            ps.fine_cnt = min(M, kFineCap);
+        }
+    }
+    __syncthreads();
+    if (ps.fine_M > 0) fine_window(ps, 0, ps.fine_cnt);
+}
+
+// PK_FINE_ACCEPT: the window just checked; the next window, a rejection, or
+// the accepted incumbent (best path, trace entry, history entry).
+__device__ void fine_accept(PState &ps) {
+    const int tid = threadIdx.x;
+    bool bad = false;
+    for (int e = tid; e < ps.fine_cnt; e += blockDim.x) bad |= ps.fine_v[e] == 0;
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        if (tid == 0) {
+            ps.fine_bad = 1;
+            ps.accepted = 0;
+        }
+        return;
+    }
+    const int done = ps.fine_done + ps.fine_cnt;
+    if (done < ps.fine_M) {
+        const int cnt = min(kFineCap, ps.fine_M - done);
+        __syncthreads();
+        if (tid == 0) {
+            ps.fine_done = done;
+            ps.fine_cnt = cnt;
+        }
+        fine_window(ps, done, done + cnt);
+        return;
+    }
+    // accepted: every window valid at resolution / 4
+    const int len = ps.cand_len, D = ps.D;
+    for (int k = tid; k < len * D; k += blockDim.x) ps.best_path[k] = ps.cand_path[k];
+    const int h = ps.n_hist;
+    const bool keep = h < kHistCap && ps.hist_used + len * D <= ps.hist_floats;
+    if (keep)
+        for (int k = tid; k < len * D; k += blockDim.x) ps.hist[ps.hist_used + k] = ps.cand_path[k];
+    __syncthreads();
+    if (tid == 0) {
+        ps.fine_done = done;
+        ps.accepted = 1;
+        ps.c_best = ps.cand_cost;
+        ps.best_len = len;
+        const int t = ps.n_trace;
+        if (t < kTraceCap) {
+            ps.trace_c[t] = ps.cand_cost;
+            ps.trace_ns[t] = gtimer();
+            ps.trace_it[t] = ps.total_iters + kStepIters;  // this step's iterations included
+        }
+        ps.n_trace = t + 1;
+        if (h < kHistCap) {
+            ps.hist_len[h] = keep ? len : -1;
+            if (keep) ps.hist_used += len * D;
+            ps.n_hist = h + 1;
+        }
+    }
+}
+
+__device__ void run_chunk(PState &ps, int kind, int r, int c, float4 *sm4, NnShared<kPerThreads> &nn,
+                          int *wsum, int *s_next, double *red) {
+    const Slot &S = *ps.slot;
+    const int tid = threadIdx.x;
+    switch (kind) {
+        case PK_RM_SAMPLE: rmb_sample_body(ps.jobs[r], c * kPerThreads + tid); break;
+        case PK_RM_VALC: val_chunk(ps.vp[3 + r], c, ps.jobs[r].nc, sm4, s_next); break;
+        case PK_RM_APPEND: {
+            RmJob &J = ps.jobs[r];
+            append_valid(J.cand, J.cvalid, J.nc, J.dof, J.want, J.q, J.rcap, J.count);
+            __syncthreads();
+            const int n_new = *J.count;
+            const int first = J.n_old == 2 && n_new > 2 ? 0 : J.n_old;
+            for (int i = tid; i < max(n_new - first, 1); i += blockDim.x)
+                rmb_gather_body(J, i, i == 0);
+            break;
+        }
+        case PK_RM_NB: rmb_neighbors_body(ps.jobs[r], c * kPerWarps + (tid >> 5)); break;
+        case PK_RM_EDGES: rmb_edges_body(ps.jobs[r], c * kPerThreads + tid); break;
+        case PK_RM_VALE: val_chunk(ps.vp[3 + ps.K + r], c, ps.jobs[r].emax, sm4, s_next); break;
+        case PK_RM_LINK: {
+            const RmJob &J = ps.jobs[r];
+            if (tid < 32) link_edges(J.evalid, J.ea, J.eb, J.m * kKmax, J.adj, J.deg);
+            __syncthreads();
+            bfs_connected(J.adj, J.deg, *J.count, J.level, J.conn);
+            break;
+        }
+        case PK_ST_SAMPLE: sample_body(S, tid); break;
+        case PK_ST_NN0: nearest_body<0, kPerThreads>(S, c, nn); break;
+        case PK_ST_ORACLE: oracle_body(S, tid); break;
+        case PK_ST_VAL1: val_chunk(ps.vp[0], c, kStepIters, sm4, s_next); break;
+        case PK_ST_INSERT: insert_body(S, wsum); break;
+        case PK_ST_NN1: nearest_body<1, kPerThreads>(S, c, nn); break;
+        case PK_ST_CONN: conn_prep_body(S, tid); break;
+        case PK_ST_VAL2: val_chunk(ps.vp[1], c, kStepIters, sm4, s_next); break;
+        case PK_ST_SOLUTION:
+            solution_body(S, tid);
+            solution_candidate(ps, red);
+            break;
+        case PK_FINE_VAL: val_chunk(ps.vp[2], c, ps.fine_cnt, sm4, s_next); break;
+        case PK_FINE_ACCEPT: fine_accept(ps); break;
+        default: break;
+    }
+}
+
+// Alg. 1 bookkeeping between phases (thread 0), in the stepped form's order;
+// returns the next phase word.  *reset asks the block for a tree reset.
+struct PDecision {
+    unsigned long long word;
+    int reset;
+};
+
+__device__ unsigned long long round_setup(PState &ps, int k) {
+    RmJob &J = ps.jobs[k];
+    const int n = *J.count;
+    J.ctr = (unsigned long long)(ps.step + 1) * 0x100000ull + (unsigned long long)n * 4096ull;
+    J.want = n >= ps.rcap ? 0 : min(ps.n_per_round, ps.rcap - n);
+    J.n_old = n;
+    return phase_word(PK_RM_SAMPLE, k, chunks_of(J.nc, kPerThreads));
+}
+
+__device__ unsigned long long start_step(PState &ps) {
+    Ctrl &C = *ps.slot->ctrl;
+    C.c_best = ps.c_best < INFINITY ? (float)ps.c_best : INFINITY;
+    C.mode = ps.active && !ps.need_roadmap ? ps.mode : 2;
+    C.step = ps.step++;
+    C.seed = ps.seed;
+    C.tree_a = 0;
+    C.best_key = ~0ull;
+    C.overflow = 0;
+    if (C.mode == 2) return 0ull;  // an idle step changes nothing: the outer iteration ends
+    return phase_word(PK_ST_SAMPLE, 0, 1);
+}
+
+__device__ PDecision begin_outer(PState &ps, unsigned long long now, unsigned long long deadline);
+
+__device__ PDecision end_outer(PState &ps, unsigned long long now, unsigned long long deadline) {
+    ps.steps_done++;
+    return begin_outer(ps, now, deadline);
+}
+
+__device__ PDecision begin_outer(PState &ps, unsigned long long now, unsigned long long deadline) {
+    PDecision d{phase_word(PK_DONE, 0, 0), 0};
+    if (!ps.active) return d;
+    if (now >= deadline) {
+        ps.timed_out = 1;
+        return d;
+    }
+    if (ps.max_steps > 0 && ps.steps_done >= ps.max_steps) return d;
+    if (ps.need_roadmap && !ps.direct) {
+        d.word = round_setup(ps, 0);
+        return d;
+    }
+    if (ps.need_roadmap) {  // single robot: no roadmap, start from the roots
+        ps.need_roadmap = 0;
+        ps.roadmap_ready = 1;
+        ps.iters_in_call = 0;
+        if (ps.mode == 1 || ps.reset_trees) {
+            d.reset = 1;
+            ps.reset_trees = 0;
+        }
+    }
+    const unsigned long long w = start_step(ps);
+    if (w == 0ull) {
+        const PDecision e = end_outer(ps, now, deadline);
+        return PDecision{e.word, d.reset | e.reset};
+    }
+    d.word = w;
+    return d;
+}
+
+__device__ PDecision after_step(PState &ps, bool accepted, unsigned long long now,
+                                unsigned long long deadline) {
+    PDecision d{0ull, 0};
+    ps.iters_in_call += kStepIters;
+    ps.total_iters += kStepIters;
+    const long long max_it = ps.max_iters > kStepIters ? ps.max_iters : kStepIters;
+    const int overflow = ps.slot->ctrl->overflow;
+    if (accepted) {
+        ps.mode = 1;  // from now on: AO-X
+        ps.need_roadmap = 1;
+        if (ps.direct) {
+            ps.need_roadmap = 0;
+            ps.iters_in_call = 0;
+            d.reset = 1;
+        }
+        if (ps.c_best < INFINITY && ps.c_best <= ps.target) {
+            ps.active = 0;
+            ps.reached = 1;
+        }
+    } else if (ps.iters_in_call >= max_it || overflow) {
+        if (ps.direct) {
+            if (ps.mode == 1 || overflow) d.reset = 1;
+            ps.iters_in_call = 0;
+        } else {
+            ps.need_roadmap = 1;
+            if (overflow) ps.reset_trees = 1;
+        }
+    }
+    const PDecision e = end_outer(ps, now, deadline);
+    return PDecision{e.word, d.reset | e.reset};
+}
+
+__device__ PDecision decide(PState &ps, int kind, int r, unsigned long long now,
+                            unsigned long long deadline) {
+    switch (kind) {
+        case PK_BEGIN: return begin_outer(ps, now, deadline);
+        case PK_RM_SAMPLE: return {phase_word(PK_RM_VALC, r, chunks_of(ps.jobs[r].nc, kPerEdges)), 0};
+        case PK_RM_VALC: return {phase_word(PK_RM_APPEND, r, 1), 0};
+        case PK_RM_APPEND: return {phase_word(PK_RM_NB, r, chunks_of(ps.jobs[r].m, kPerWarps)), 0};
+        case PK_RM_NB: return {phase_word(PK_RM_EDGES, r, chunks_of(ps.jobs[r].emax, kPerThreads)), 0};
+        case PK_RM_EDGES: return {phase_word(PK_RM_VALE, r, chunks_of(ps.jobs[r].emax, kPerEdges)), 0};
+        case PK_RM_VALE: return {phase_word(PK_RM_LINK, r, 1), 0};
+        case PK_RM_LINK: {
+            if (r + 1 < ps.K) return {round_setup(ps, r + 1), 0};
+            // the round is over for every robot (Alg. 2 ROADMAP)
+            bool all = true;
+            for (int k = 0; k < ps.K; ++k) all = all && *ps.jobs[k].conn != 0;
+            ps.step++;
+            PDecision d{0ull, 0};
+            if (all) {
+                ps.roadmap_ready = 1;
+                ps.need_roadmap = 0;
+                ps.iters_in_call = 0;
+                if (ps.mode == 1 || ps.reset_trees) {
+                    d.reset = 1;
+                    ps.reset_trees = 0;
+                }
+            }
+            const unsigned long long w = start_step(ps);
+            if (w != 0ull) {
+                d.word = w;
+                return d;
+            }
+            const PDecision e = end_outer(ps, now, deadline);
+            return {e.word, d.reset | e.reset};
+        }
+        case PK_ST_SAMPLE: return {phase_word(PK_ST_NN0, 0, kStepIters / kPQB), 0};
+        case PK_ST_NN0: return {phase_word(PK_ST_ORACLE, 0, 1), 0};
+        case PK_ST_ORACLE: return {phase_word(PK_ST_VAL1, 0, kStepIters / kPerEdges), 0};
+        case PK_ST_VAL1: return {phase_word(PK_ST_INSERT, 0, 1), 0};
+        case PK_ST_INSERT: return {phase_word(PK_ST_NN1, 0, kStepIters / kPQB), 0};
+        case PK_ST_NN1: return {phase_word(PK_ST_CONN, 0, 1), 0};
+        case PK_ST_CONN: return {phase_word(PK_ST_VAL2, 0, kStepIters / kPerEdges), 0};
+        case PK_ST_VAL2: return {phase_word(PK_ST_SOLUTION, 0, 1), 0};
+        case PK_ST_SOLUTION:
+            if (ps.fine_M > 0) return {phase_word(PK_FINE_VAL, 0, chunks_of(ps.fine_cnt, kPerEdges)), 0};
+            return after_step(ps, false, now, deadline);
+        case PK_FINE_VAL: return {phase_word(PK_FINE_ACCEPT, 0, 1), 0};
+        case PK_FINE_ACCEPT:
+            if (ps.fine_bad) return after_step(ps, false, now, deadline);
+            if (!ps.accepted) return {phase_word(PK_FINE_VAL, 0, chunks_of(ps.fine_cnt, kPerEdges)), 0};
+            return after_step(ps, true, now, deadline);
+        default: return {phase_word(PK_DONE, 0, 0), 0};
+    }
+}
+
+__global__ void __launch_bounds__(kPerThreads) k_persistent(const PLaunch L) {
+    extern __shared__ float4 per_sm4[];
+    __shared__ NnShared<kPerThreads> nn;
+    __shared__ int wsum[kPerWarps];
+    __shared__ double red[kPerThreads];
+    __shared__ int s_q, s_kind, s_robot, s_chunk, s_total, s_last, s_exit, s_next, s_reset;
+    __shared__ unsigned long long s_t0, s_word;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const unsigned long long now = gtimer();
+        const unsigned long long prev = atomicMin(L.t_start, now);
+        s_t0 = prev < now ? prev : now;
+    }
+    __syncthreads();
+    const unsigned long long t0 = s_t0, deadline = t0 + L.budget_ns, hard = t0 + L.hard_ns;
+    int scan = blockIdx.x % max(L.n, 1);
+    long long idle = 0;
+    for (;;) {
+        if (tid == 0) {
+            s_q = -1;
+            s_exit = 0;
+            for (int j = 0; j < L.n && s_q < 0; ++j) {
+                const int q = (scan + j) % L.n;
+                PState &ps = L.states[q];
+                const unsigned long long w = *(volatile unsigned long long *)&ps.claim;
+                if ((unsigned)(w & 0xffffffffull) >= (unsigned)((w >> 32) & 0xFFFFF)) continue;
+                const unsigned long long got = atomicAdd(&ps.claim, 1ull);
+                const int tot = (int)((got >> 32) & 0xFFFFF), c = (int)(got & 0xffffffffull);
+                if (c >= tot) continue;
+                s_q = q;
+                s_kind = (int)(got >> 58);
+                s_robot = (int)((got >> 52) & 63);
+                s_total = tot;
+                s_chunk = c;
+                scan = q;  // stay with this problem while it has chunks
+            }
+            if (s_q < 0) {
+                if (*(volatile int *)L.finished >= L.n) {
+                    s_exit = 1;
+                } else if (gtimer() > hard || (L.idle_poll_limit > 0 && ++idle > L.idle_poll_limit)) {
+                    atomicExch(L.timeout, 1);  // bounded wait ran out
+                    s_exit = 1;
+                } else {
+                    scan = (scan + 1) % L.n;
+                    __nanosleep(2000);
+                }
+            } else {
+                idle = 0;
+            }
+        }
+        __syncthreads();
+        if (s_exit) break;
+        if (s_q < 0) continue;
+        __threadfence();  // acquire: the phase's inputs, written by other CTAs
+        PState &ps = L.states[s_q];
+        run_chunk(ps, s_kind, s_robot, s_chunk, per_sm4, nn, wsum, &s_next, red);
+        __threadfence();  // release: this chunk's results
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(&ps.done, 1) == s_total - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (tid == 0) {
+                const unsigned long long now = gtimer();
+                PDecision d = decide(ps, s_kind, s_robot, now, deadline);
+                // a phase without chunks (no new roadmap vertex to search
+                // around) is complete at once
+                for (int g = 0; g < 16; ++g) {
+                    const int k2 = (int)(d.word >> 58);
+                    if (k2 == PK_DONE || ((d.word >> 32) & 0xFFFFF) != 0) break;
+                    const PDecision d2 = decide(ps, k2, (int)((d.word >> 52) & 63), now, deadline);
+                    d = PDecision{d2.word, d.reset | d2.reset};
+                }
+                s_word = d.word;
+                s_reset = d.reset;
+            }
+            __syncthreads();
+            if (s_reset) tree_reset_body(*ps.slot);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                ps.done = 0;
+                const bool fin = (int)(s_word >> 58) == PK_DONE;
+                if (fin) ps.finished = 1;
+                __threadfence();
+                atomicExch(&ps.claim, s_word);  // publish the next phase
+                if (fin) atomicAdd(L.finished, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Test and diagnostic limits of the persistent launch (mrpop_set_persistent_limits).
+static std::atomic<int> g_per_ctas{0};
+static std::atomic<long long> g_per_idle_polls{0};
+
+// Static per-robot fields of the roadmap jobs (the round-dependent ones are
+// set on the device before each round).
+static RmJob make_job(Planner *pl, int k) {
+    mrpop_problem *p = pl->p;
+    RobotRoadmap &r = pl->rm[k];
+    const int off = pl->slot.qoff[k];
+    RmJob J{};
+    J.q = r.q; J.adj = r.adj; J.deg = r.deg; J.count = pl->rm_n + k;
+    J.rcap = pl->rcap; J.dof = p->robots[k].dof;
+    J.cand = r.cand; J.cvalid = r.cvalid; J.gq = r.gq; J.nb = r.nb; J.cnt = r.cnt;
+    J.ea_q = r.ea_q; J.eb_q = r.eb_q; J.evalid = r.evalid; J.ea = r.ea; J.eb = r.eb;
+    J.level = r.level; J.conn = r.d_conn;
+    J.lo = pl->d_lo + off; J.hi = pl->d_hi + off;
+    J.key = mix64(pl->seed * 31ull + 7ull * (unsigned long long)k + 1ull);
+    J.nc = kOversample * pl->n_per_round;
+    J.n_old = r.n;
+    J.emax = (pl->n_per_round + 2) * kKmax;
+    J.delta = p->cfg.delta;
+    return J;
+}
+
+// Allocates the planner's persistent-form buffers (once) and returns the
+// VParams of its validations: extension, connection, fine re-check, then the
+// robots' candidates and roadmap edges.
+static mrpop_status per_buffers(Planner *pl, std::vector<VParams> &vps) {
+    PerBuffers &b = pl->per;
+    const int K = pl->K, D = pl->D, cap = 2 * pl->tcap + 2;
+    if (!b.slot) {
+        PL_TRY(dalloc(&b.slot, 1));
+        PL_TRY(dalloc(&b.jobs, K));
+        PL_TRY(dalloc(&b.vp, 3 + 2 * K));
+        PL_TRY(dalloc(&b.seg_parts, cap));
+        PL_TRY(dalloc(&b.best, (size_t)cap * D));
+        PL_TRY(dalloc(&b.trace_c, kTraceCap));
+        PL_TRY(dalloc(&b.trace_ns, kTraceCap));
+        PL_TRY(dalloc(&b.trace_it, kTraceCap));
+        b.hist_floats = kHistCap * std::min(cap, 512) * D;
+        PL_TRY(dalloc(&b.hist, (size_t)b.hist_floats));
+        PL_TRY(dalloc(&b.hist_len, kHistCap));
+        if (pl->fine_cap < (size_t)kFineCap) {  // grow the fine re-check buffers
+            cudaFree(pl->fine_qa);
+            cudaFree(pl->fine_qb);
+            cudaFree(pl->fine_v);
+            pl->fine_qa = pl->fine_qb = nullptr;
+            pl->fine_v = nullptr;
+            pl->fine_cap = 0;
+            PL_TRY(cudaMalloc(&pl->fine_qa, sizeof(float) * D * kFineCap));
+            PL_TRY(cudaMalloc(&pl->fine_qb, sizeof(float) * D * kFineCap));
+            PL_TRY(cudaMalloc(&pl->fine_v, kFineCap));
+            pl->fine_cap = kFineCap;
+        }
+        std::vector<RmJob> jobs(K);
+        for (int k = 0; k < K; ++k) jobs[k] = make_job(pl, k);
+        PL_TRY(cudaMemcpy(b.jobs, jobs.data(), sizeof(RmJob) * K, cudaMemcpyHostToDevice));
+        PL_TRY(cudaMemcpy(b.slot, &pl->slot, sizeof(Slot), cudaMemcpyHostToDevice));
+    }
+    // (the stepped form may have grown the fine re-check buffers since)
+    ST_TRY(make_vparams(pl->fine, pl->fine_qa, pl->fine_qb, kFineCap, pl->fine_v, &b.vfine,
+                        &b.vfine_s, &b.vfine_w));
+    vps.clear();
+    vps.push_back(pl->vp[0]);
+    vps.push_back(pl->vp[1]);
+    vps.push_back(b.vfine);
+    for (int k = 0; k < K; ++k) vps.push_back(pl->rm[k].vp_c);
+    for (int k = 0; k < K; ++k) vps.push_back(pl->rm[k].vp_e);
+    for (VParams &v : vps) v.fine = 0;  // the persistent form takes the union fine stage
+    return MRPOP_OK;
+}
+
+static const mrpop_problem *vp_problem(Planner *pl, int j) {
+    if (j < 2) return pl->p;
+    if (j == 2) return pl->fine;
+    return pl->rm[(j - 3) % pl->K].sub;
+}
+
+// Runs Alg. 1 on every problem of ps in one persistent launch until the
+// budget ends, the step budget is used or every problem reached its target.
+static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, double budget,
+                                          int64_t max_steps, const double *targets,
+                                          mrpop_status *statuses) {
+    const double t0 = now_s();
+    cudaStream_t st;
+    PL_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct Guard {
+        cudaStream_t s;
+        ~Guard() { cudaStreamDestroy(s); }
+    } guard{st};
+    std::vector<Planner *> pls;
+    std::vector<SlotRun> run(n);
+    for (int i = 0; i < n; ++i) {
+        mrpop_problem *p = ps[i];
+        ST_TRY(ensure_planner(p));
+        pls.push_back(p->planner);
+        run[i].target = targets ? targets[i] : -INFINITY;
+        run[i].reset_trees = !p->planner->roadmap_ready;
+    }
+    ST_TRY(check_endpoints(pls, run, st));
+    // one shared-memory budget for every validation of the launch: as many
+    // of the 8 warps as fit in about 100 KB (two CTAs per SM), at least one
+    std::vector<std::vector<VParams>> vps(n);
+    size_t need1 = 0, need8 = 0;
+    for (int i = 0; i < n; ++i) {
+        ST_TRY(per_buffers(pls[i], vps[i]));
+        for (size_t j = 0; j < vps[i].size(); ++j) {
+            const size_t tab = (size_t)vp_problem(pls[i], (int)j)->dev.t.n_f4 * sizeof(float4);
+            const size_t per = (size_t)vps[i][j].warp_floats * sizeof(float);
+            need1 = std::max(need1, tab + per);
+            need8 = std::max(need8, tab + kPerWarps * per);
+        }
+    }
+    int dev = 0, optin = 0, sms = 1;
+    PL_TRY(cudaGetDevice(&dev));
+    PL_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    PL_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaFuncAttributes fa{};
+    PL_TRY(cudaFuncGetAttributes(&fa, k_persistent));
+    const size_t smem = std::max(need1, std::min(need8, (size_t)100 * 1024));
+    if (smem + fa.sharedSizeBytes > (size_t)optin)
+        return set_error(MRPOP_EINVAL, "plan_batch: a problem's tables exceed the persistent "
+                                       "kernel's shared memory (%zu bytes)", smem);
+    PL_TRY(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+    int bps = 0;
+    PL_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent, kPerThreads, smem));
+    if (bps < 1) return set_error(MRPOP_EINVAL, "plan_batch: persistent kernel does not fit an SM");
+    const int ctas = g_per_ctas.load() > 0 ? g_per_ctas.load() : sms * bps;
+
+    // per-problem state from the host mirrors (each call starts with a
+    // roadmap round, as Alg. 1 does)
+    std::vector<PState> hs(n);
+    int finished0 = 0;
+    const int64_t msteps = max_steps > 0 ? max_steps : 0;
+    for (int i = 0; i < n; ++i) {
+        Planner *pl = pls[i];
+        PerBuffers &b = pl->per;
+        for (size_t j = 0; j < vps[i].size(); ++j) {
+            const size_t tab = (size_t)vp_problem(pl, (int)j)->dev.t.n_f4 * sizeof(float4);
+            const size_t per = (size_t)vps[i][j].warp_floats * sizeof(float);
+            vps[i][j].warps = (int)std::max<size_t>(1, std::min<size_t>(kPerWarps, (smem - tab) / per));
+        }
+        PL_TRY(cudaMemcpyAsync(b.vp, vps[i].data(), sizeof(VParams) * vps[i].size(),
+                               cudaMemcpyHostToDevice, st));
+        PState &s = hs[i];
+        s = PState{};
+        const bool act = run[i].active;
+        s.claim = act ? phase_word(PK_BEGIN, 0, 1) : phase_word(PK_DONE, 0, 0);
+        s.finished = act ? 0 : 1;
+        finished0 += act ? 0 : 1;
+        s.mode = pl->mode;
+        s.step = pl->step;
+        s.need_roadmap = 1;
+        s.reset_trees = run[i].reset_trees ? 1 : 0;
+        s.roadmap_ready = pl->roadmap_ready ? 1 : 0;
+        s.active = act ? 1 : 0;
+        s.reached = run[i].reached ? 1 : 0;
+        s.direct = pl->direct ? 1 : 0;
+        s.K = pl->K;
+        s.D = pl->D;
+        s.iters_in_call = pl->iters_in_call;
+        s.total_iters = pl->total_iters;
+        s.max_iters = pl->p->cfg.max_iters;
+        s.max_steps = msteps;
+        s.c_best = pl->c_best;
+        s.target = run[i].target;
+        s.seed = pl->seed;
+        s.n_per_round = pl->n_per_round;
+        s.rcap = pl->rcap;
+        s.res4 = 0.25f * pl->p->cfg.resolution;
+        s.slot = b.slot;
+        s.jobs = b.jobs;
+        s.vp = b.vp;
+        s.scratch = pl->d_path;
+        s.seg_parts = b.seg_parts;
+        s.cand_path = pl->d_pathq;
+        s.best_path = b.best;
+        s.path_cap = 2 * pl->tcap + 2;
+        s.fine_qa = pl->fine_qa;
+        s.fine_qb = pl->fine_qb;
+        s.fine_v = pl->fine_v;
+        s.trace_c = b.trace_c;
+        s.trace_ns = b.trace_ns;
+        s.trace_it = b.trace_it;
+        s.hist = b.hist;
+        s.hist_len = b.hist_len;
+        s.hist_floats = b.hist_floats;
+    }
+    PState *d_states = nullptr;
+    unsigned long long *d_aux = nullptr;  // [0] start time, [1] finished | timeout << 32
+    PL_TRY(cudaMallocAsync(&d_states, sizeof(PState) * n, st));
+    PL_TRY(cudaMallocAsync(&d_aux, sizeof(unsigned long long) * 2, st));
+    struct Release {
+        void *a, *b;
+        cudaStream_t s;
+        ~Release() {
+            cudaFreeAsync(a, s);
+            cudaFreeAsync(b, s);
+        }
+    } release{d_states, d_aux, st};
+    PL_TRY(cudaMemcpyAsync(d_states, hs.data(), sizeof(PState) * n, cudaMemcpyHostToDevice, st));
+    const unsigned long long aux0[2] = {~0ull, (unsigned long long)finished0};
+    PL_TRY(cudaMemcpyAsync(d_aux, aux0, sizeof(aux0), cudaMemcpyHostToDevice, st));
+    PLaunch L{};
+    L.states = d_states;
+    L.n = n;
+    const double left = std::max(0.0, budget - (now_s() - t0));
+    L.budget_ns = (unsigned long long)(std::min(left, 1e6) * 1e9);
+    L.hard_ns = L.budget_ns + (unsigned long long)(std::min(30.0 + left, 1e6) * 1e9);
+    L.idle_poll_limit = g_per_idle_polls.load();
+    L.t_start = d_aux;
+    L.finished = reinterpret_cast<int *>(d_aux + 1);
+    L.timeout = reinterpret_cast<int *>(d_aux + 1) + 1;
+    // the launch, captured in a CUDA graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    PL_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    k_persistent<<<ctas, kPerThreads, smem, st>>>(L);
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    PL_TRY(le);
+    PL_TRY(ce);
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    const double t_launch = now_s() - t0;
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    PL_TRY(e);
+    unsigned long long aux[2];
+    PL_TRY(cudaMemcpy(hs.data(), d_states, sizeof(PState) * n, cudaMemcpyDeviceToHost));
+    PL_TRY(cudaMemcpy(aux, d_aux, sizeof(aux), cudaMemcpyDeviceToHost));
+    const bool timeout = (aux[1] >> 32) != 0;
+    // results and mirrors back to the host planners
+    for (int i = 0; i < n; ++i) {
+        Planner *pl = pls[i];
+        PerBuffers &b = pl->per;
+        const PState &s = hs[i];
+        const int D = pl->D;
+        const int nt = std::min(s.n_trace, kTraceCap), nh = std::min(s.n_hist, kHistCap);
+        if (nt > 0) {
+            std::vector<double> tc(nt);
+            std::vector<unsigned long long> tn(nt);
+            PL_TRY(cudaMemcpy(tc.data(), b.trace_c, sizeof(double) * nt, cudaMemcpyDeviceToHost));
+            PL_TRY(cudaMemcpy(tn.data(), b.trace_ns, sizeof(unsigned long long) * nt,
+                              cudaMemcpyDeviceToHost));
+            for (int k = 0; k < nt; ++k) {
+                pl->trace_t.push_back(t_launch + (double)(tn[k] - aux[0]) * 1e-9);
+                pl->trace_c.push_back(tc[k]);
+            }
+            std::vector<int> hl(std::max(nh, 1));
+            if (nh > 0)
+                PL_TRY(cudaMemcpy(hl.data(), b.hist_len, sizeof(int) * nh, cudaMemcpyDeviceToHost));
+            size_t off = 0;
+            for (int k = 0; k < nh; ++k) {
+                std::vector<float> path;
+                if (hl[k] > 0) {
+                    path.resize((size_t)hl[k] * D);
+                    PL_TRY(cudaMemcpy(path.data(), b.hist + off, sizeof(float) * path.size(),
+                                      cudaMemcpyDeviceToHost));
+                    off += path.size();
+                }
+                pl->history.push_back(std::move(path));
+            }
+            for (int k = nh; k < nt; ++k) pl->history.emplace_back();  // did not fit
+            pl->best_path.resize((size_t)s.best_len * D);
+            PL_TRY(cudaMemcpy(pl->best_path.data(), b.best, sizeof(float) * pl->best_path.size(),
+                              cudaMemcpyDeviceToHost));
+            pl->c_best = s.c_best;
+        }
+        pl->mode = s.mode;
+        pl->step = s.step;
+        pl->iters_in_call = s.iters_in_call;
+        pl->total_iters = s.total_iters;
+        const bool clean = s.finished != 0;
+        pl->roadmap_ready = clean && s.roadmap_ready != 0;
+        std::vector<int> counts(pl->K);
+        PL_TRY(cudaMemcpy(counts.data(), pl->rm_n, sizeof(int) * pl->K, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < pl->K; ++k) {
+            int c = 0;
+            PL_TRY(cudaMemcpy(&c, pl->rm[k].d_conn, sizeof(int), cudaMemcpyDeviceToHost));
+            pl->rm[k].n = counts[k];
+            pl->rm[k].connected = c != 0;
+        }
+        if (!clean) {
+            // stopped mid-phase (an idle CTA gave up): the next call starts
+            // from fresh trees and a new roadmap round
+            pl->roadmap_ready = false;
+            if (run[i].status == MRPOP_OK) run[i].status = MRPOP_ETIMEOUT;
+        }
+    }
+    if (statuses)
+        for (int i = 0; i < n; ++i) statuses[i] = run[i].status;
+    if (timeout)
+        return set_error(MRPOP_ETIMEOUT, "plan_batch: a bounded wait of the persistent launch ran "
+                                         "out before every problem finished");
+    return MRPOP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Serving: continuous batching.  A server thread keeps up to max_slots
 // requests on the device and advances all of them by one planner iteration
 // per loop (the same per-slot logic as mrpop_plan_batch, direct launches
@@ -1798,7 +2692,36 @@ extern "C" mrpop_status mrpop_plan_batch(mrpop_problem *const *ps, int32_t n, do
         for (int j = 0; j < i; ++j)
             if (ps[j] == ps[i]) return set_error(MRPOP_EINVAL, "mrpop_plan_batch: problem %d repeated", i);
     }
+    return plan_batch_persistent(ps, n, time_budget_s, max_steps, target_costs, statuses);
+}
+
+extern "C" mrpop_status mrpop_plan_batch_ex(mrpop_problem *const *ps, int32_t n,
+                                            double time_budget_s, int64_t max_steps,
+                                            const double *target_costs, mrpop_status *statuses,
+                                            int32_t form) {
+    if (form != MRPOP_BATCH_PERSISTENT && form != MRPOP_BATCH_STEPPED)
+        return set_error(MRPOP_EINVAL, "mrpop_plan_batch_ex: form=%d is not a batch form", form);
+    if (form == MRPOP_BATCH_PERSISTENT)
+        return mrpop_plan_batch(ps, n, time_budget_s, max_steps, target_costs, statuses);
+    if (!ps || n < 1) return set_error(MRPOP_EINVAL, "mrpop_plan_batch_ex: no problems");
+    if (!(time_budget_s >= 0.0)) return set_error(MRPOP_EINVAL, "mrpop_plan_batch_ex: negative budget");
+    for (int i = 0; i < n; ++i) {
+        if (!ps[i]) return set_error(MRPOP_EINVAL, "mrpop_plan_batch_ex: problem %d is NULL", i);
+        if (ps[i]->start.empty() || ps[i]->goal.empty())
+            return set_error(MRPOP_EINVAL, "mrpop_plan_batch_ex: problem %d has no start/goal", i);
+        for (int j = 0; j < i; ++j)
+            if (ps[j] == ps[i])
+                return set_error(MRPOP_EINVAL, "mrpop_plan_batch_ex: problem %d repeated", i);
+    }
     return plan_batch(ps, n, time_budget_s, max_steps, target_costs, statuses);
+}
+
+extern "C" mrpop_status mrpop_set_persistent_limits(int32_t ctas, int64_t idle_polls) {
+    if (ctas < 0 || idle_polls < 0)
+        return set_error(MRPOP_EINVAL, "mrpop_set_persistent_limits: negative limit");
+    mrpop::g_per_ctas.store(ctas);
+    mrpop::g_per_idle_polls.store(idle_polls);
+    return MRPOP_OK;
 }
 
 extern "C" mrpop_status mrpop_plan_result(mrpop_problem *p, float *path, int64_t path_cap,

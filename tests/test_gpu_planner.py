@@ -221,6 +221,74 @@ def test_plan_batch_alone_equals_mix(mp, orc):
         p.close()
 
 
+def test_plan_batch_stepped_form(mp, orc):
+    """The stepped batch form (a captured graph per step, host bookkeeping
+    between steps) on the same kind of batch: every result is oracle-valid."""
+    probs = [_planar_problem(mp, orc, s) for s in (0, 3)]
+    st = mp.plan_batch([p for p, *_ in probs], 3.0, form=mp.BATCH_STEPPED)
+    assert (st == 0).all()
+    for p, qs, qg, o in probs:
+        path, cost = mp.plan_result(p)
+        _check_path(orc, o, path, cost, qs, qg)
+        p.close()
+
+
+def test_plan_batch_persistent_heterogeneous(mp, orc):
+    """One persistent launch over problems of different robot counts and
+    dimensions (planar 6-DOF, single-robot, two 7-DOF arms, four arms):
+    whatever each found is oracle-valid at res/4, its incumbents decrease,
+    and a second call continues from the device state."""
+    probs = [_planar_problem(mp, orc, s) for s in (0, 6)]
+    table = synth.table_pair_scene(0)
+    tqs, tqg, to = _start_goal(orc, table, 5, check=False)
+    probs.append((mp.Problem(table, resolution=RES, margin=1e-4, delta=2.5, seed=3,
+                             start=tqs, goal=tqg), tqs, tqg, to))
+    arm = synth.Scene([table.robots[0]], table.obs_spheres, table.obs_cuboids)
+    aqs, aqg, ao = _start_goal(orc, arm, 3, check=False)
+    probs.append((mp.Problem(arm, resolution=RES, margin=1e-4, delta=0.6, seed=4,
+                             start=aqs, goal=aqg), aqs, aqg, ao))
+    ps = [p for p, *_ in probs]
+    st = mp.plan_batch(ps, 4.0)
+    assert (st == 0).all()
+    st = mp.plan_batch(ps, 2.0)
+    assert (st == 0).all()
+    solved = 0
+    for p, qs, qg, o in probs:
+        path, cost = mp.plan_result(p)
+        t, c, _ = mp.plan_trace(p)
+        if path is not None:
+            solved += 1
+            _check_path(orc, o, path, cost, qs, qg)
+            assert c[-1] == pytest.approx(cost)
+            # (times count from the start of the call that found each incumbent)
+            assert np.all(np.diff(c) < 0) and np.all(t >= 0)
+        p.close()
+    assert solved >= 3
+
+
+def test_plan_batch_bounded_wait_times_out(mp, orc):
+    """The persistent launch's only wait is a CTA polling for work.  With
+    more CTAs than the problem has chunks and a poll limit of four, idle CTAs
+    give up: the call reports MRPOP_ETIMEOUT instead of waiting, whatever was
+    found stays valid, and the context and the planner keep working."""
+    p, qs, qg, o = _planar_problem(mp, orc, 0)
+    mp.set_persistent_limits(ctas=16, idle_polls=4)
+    try:
+        with pytest.raises(mp.MrpopError) as ei:
+            mp.plan_batch([p], 2.0, max_steps=60)
+        assert ei.value.status == 5          # MRPOP_ETIMEOUT
+    finally:
+        mp.set_persistent_limits(0, 0)
+    path, cost = mp.plan_result(p)
+    if path is not None:
+        _check_path(orc, o, path, cost, qs, qg)
+    st = mp.plan_batch([p], 2.0)
+    assert (st == 0).all()
+    path, cost = mp.plan_result(p)
+    _check_path(orc, o, path, cost, qs, qg)
+    p.close()
+
+
 def test_plan_batch_stops_at_target(mp, orc):
     p, qs, qg, o = _planar_problem(mp, orc, 3)
     st = mp.plan_batch([p], 5.0, targets=[1e9])   # any solution reaches the target
