@@ -390,9 +390,16 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
         p.close()
     probs = [make(e) for e in entries]                 # all problems at once
     t0 = time.perf_counter()
-    mp.plan_batch(probs, batched_budget)
+    mp.plan_batch(probs, batched_budget)               # one persistent launch
     batched_wall = time.perf_counter() - t0
     traces["batched"] = [mp.plan_trace(p)[:2] for p in probs]
+    for p in probs:
+        p.close()
+    probs = [make(e) for e in entries]                 # the stepped batch form
+    t0 = time.perf_counter()
+    mp.plan_batch(probs, batched_budget, form=mp.BATCH_STEPPED)
+    stepped_wall = time.perf_counter() - t0
+    traces["batched_stepped"] = [mp.plan_trace(p)[:2] for p in probs]
     for p in probs:
         p.close()
     # a long batched run that only supplies best-cost candidates
@@ -406,9 +413,10 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
     # finish a first roadmap on most of them within the GPU's budget)
     ref_out, ref_workers, ref_wall = run_reference_planner(sample, LONG_FACTOR * PLAN_BUDGET_S)
     traces["cpu_reference"] = [(np.asarray(t), np.asarray(c)) for t, c, _, _ in ref_out]
-    kinds = ("plain", "batched", "cpu_reference")
+    kinds = ("plain", "batched", "batched_stepped", "cpu_reference")
     final = lambda c: c[-1] if len(c) else np.inf
-    best = np.array([final(c) for t, c in traces["batched"]])
+    best = np.minimum(np.array([final(c) for t, c in traces["batched"]]),
+                      np.array([final(c) for t, c in traces["batched_stepped"]]))
     m = len(sample)
     for cand in ([final(c) for t, c in traces["plain"]], [final(c) for t, c in traces["cpu_reference"]],
                  long_final):
@@ -416,7 +424,10 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
     res = {"problems": len(entries), "plain_sample": m, "budget_s": PLAN_BUDGET_S,
            "batched_budget_s": batched_budget,
            "robots": [int(e[1].K) for e in entries], "batched_wall_s": batched_wall,
-           "best_cost_from": (f"minimum final cost over the plain and batched runs, a "
+           "batched_stepped_wall_s": stepped_wall,
+           "batched_form": "one persistent launch (mrpop_plan_batch)",
+           "batched_stepped_form": "a captured graph per step (mrpop_plan_batch_ex, stepped)",
+           "best_cost_from": (f"minimum final cost over the plain and both batched runs, a "
                               f"{LONG_FACTOR}x-budget batched run and the FP64 reference "
                               f"(the last three on the first {m} problems)")}
     for k in kinds:
@@ -428,11 +439,12 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
                 ttfs.append(float(t[0]))
         solved = sum(r is not None for r in reach)
         budget = {"plain": PLAN_BUDGET_S, "batched": batched_budget,
+                  "batched_stepped": batched_budget,
                   "cpu_reference": LONG_FACTOR * PLAN_BUDGET_S}[k]
         spent = [r if r is not None else budget for r in reach]
         # plain: problems run back to back; batched: all at once; the CPU
         # reference: back to back on each of its cores (sum / cores)
-        wall = (sum(spent) if k == "plain" else max(spent) if k == "batched"
+        wall = (sum(spent) if k == "plain" else max(spent) if k.startswith("batched")
                 else sum(spent) / ref_workers)
         res[k] = {"problems": len(reach), "solved_to_1.1x_best": solved, "wall_s": wall,
                   "problems_per_s": solved / wall if wall > 0 else 0.0,
@@ -446,6 +458,9 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
         "statuses": [int(x[3]) for x in ref_out]})
     if res["plain"]["problems_per_s"] > 0:
         res["batched_over_plain"] = res["batched"]["problems_per_s"] / res["plain"]["problems_per_s"]
+    if res["batched_stepped"]["problems_per_s"] > 0:
+        res["persistent_over_stepped"] = (res["batched"]["problems_per_s"] /
+                                          res["batched_stepped"]["problems_per_s"])
     return res, entries, best
 
 

@@ -229,6 +229,56 @@ mrpop_status mrpop_autotune(mrpop_problem *p, const float *qa, const float *qb, 
 mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_block, int32_t order,
                               int32_t fine_stage);
 
+/* mrpop_set_launch plus the register budget of the kernel: registers 0
+ * (compact: the compiler's choice, about 72 registers, the most warps per SM)
+ * or 1 (wide: up to 128 registers, four blocks per SM, no spills where
+ * many-arm scenes run their robot-robot fine tests).  mrpop_autotune times
+ * both budgets too.  Errors: EINVAL for any other value. */
+mrpop_status mrpop_set_launch_ex(mrpop_problem *p, int32_t warps_per_block, int32_t order,
+                                 int32_t fine_stage, int32_t registers);
+
+/* The problem's current validation launch (host int32 [4]): warps per
+ * block, order, fine stage, register budget.  Errors: EINVAL for NULL. */
+mrpop_status mrpop_get_launch(const mrpop_problem *p, int32_t *config);
+
+/* ---------------------------------------------------------------------------
+ * Tuned-launch cache.  mrpop_autotune, mrpop_nearest_autotune and
+ * mrpop_neighbors_autotune keep their choice in a process-wide cache keyed by
+ * (GPU architecture, shape of the work): for validation the problem's robot,
+ * link, sphere and obstacle counts (mrpop_create_problem applies a cached
+ * launch to a new problem of that shape); for NEAREST and NEIGHBORS the
+ * dimension and the base-2 logarithms of the tree size and the batch size
+ * (later calls of that shape use it).  The cache can be saved to and loaded
+ * from a text file, one "<key> = <values>" line per entry.
+ * ------------------------------------------------------------------------- */
+mrpop_status mrpop_autotune_cache_save(const char *path);
+/* Adds (or replaces) the file's entries; EINVAL on a malformed line. */
+mrpop_status mrpop_autotune_cache_load(const char *path);
+mrpop_status mrpop_autotune_cache_clear(void);
+
+/* Times mrpop_nearest_ex on the caller's inputs with the budget-ordered path
+ * split into 2, 4 or 8 waves of (query block, tree slice) pieces per SM
+ * capacity, keeps the fastest for calls of this shape and filter, and
+ * reports it (*waves, host; *ms_per_call, host, may be NULL).  out_idx
+ * receives the results.  Batches that take the small-batch path are timed
+ * too, but the waves do not apply to them.  Synchronises the stream.
+ * Errors: as mrpop_nearest_ex. */
+mrpop_status mrpop_nearest_autotune(const float *tree, int64_t n_vertices, int64_t ld,
+                                    int32_t dim, const float *queries, const float *budgets,
+                                    int64_t n_queries, int32_t filter, int64_t *out_idx,
+                                    int32_t *waves, float *ms_per_call, void *cuda_stream);
+
+/* Times mrpop_neighbors on the caller's inputs with the vertex ranges sized
+ * for 14, 54 or 216 warps per SM (few queries are split over vertex ranges
+ * so that the GPU fills), keeps the fastest for calls of this shape and
+ * reports it (*warps_per_sm, host).  Synchronises the stream.  Errors: as
+ * mrpop_neighbors. */
+mrpop_status mrpop_neighbors_autotune(const float *tree, int64_t n_vertices, int64_t ld,
+                                      int32_t dim, const float *queries, int64_t n_queries,
+                                      float delta, int64_t k_max, int64_t *out_idx,
+                                      int64_t *out_cnt, int32_t *warps_per_sm,
+                                      float *ms_per_call, void *cuda_stream);
+
 /* NEAREST(V, q, c) of Alg. 2 for n_queries queries: among tree vertices with
  * g_v + |q - q_v| < c, the one closest to q; ties go to the lowest g, then the
  * lowest index (Sec. III-D); -1 when no vertex qualifies.

@@ -15,7 +15,9 @@ _OPS = ("MrpopError", "Problem", "edge_clearance", "fk", "lib", "library_path", 
         "plan_batch", "plan_result", "Server", "autotune", "set_launch",
         "plan_history", "fp32_peak", "nearest_work", "NEAREST_FILTER_FP32",
         "NEAREST_FILTER_TENSOR", "planner_nearest_pass", "planner_neighbors_pass",
-        "ROADMAP_DEGREE_CAP", "BATCH_PERSISTENT", "BATCH_STEPPED", "set_persistent_limits")
+        "ROADMAP_DEGREE_CAP", "BATCH_PERSISTENT", "BATCH_STEPPED", "set_persistent_limits",
+        "get_launch", "autotune_cache_save", "autotune_cache_load", "autotune_cache_clear",
+        "nearest_autotune", "neighbors_autotune")
 
 
 def __getattr__(name):

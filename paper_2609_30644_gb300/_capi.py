@@ -50,6 +50,13 @@ EXPORTS = (
     "mrpop_planner_neighbors_pass",
     "mrpop_plan_batch_ex",
     "mrpop_set_persistent_limits",
+    "mrpop_set_launch_ex",
+    "mrpop_get_launch",
+    "mrpop_autotune_cache_save",
+    "mrpop_autotune_cache_load",
+    "mrpop_autotune_cache_clear",
+    "mrpop_nearest_autotune",
+    "mrpop_neighbors_autotune",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -122,6 +129,14 @@ def _load() -> C.CDLL:
         "mrpop_planner_neighbors_pass": (i32, [vp, i64, i64, i32, vp, i64, f32, vp, vp, vp]),
         "mrpop_plan_batch_ex": (i32, [vp, i32, C.c_double, i64, vp, vp, i32]),
         "mrpop_set_persistent_limits": (i32, [i32, i64]),
+        "mrpop_set_launch_ex": (i32, [vp, i32, i32, i32, i32]),
+        "mrpop_get_launch": (i32, [vp, vp]),
+        "mrpop_autotune_cache_save": (i32, [C.c_char_p]),
+        "mrpop_autotune_cache_load": (i32, [C.c_char_p]),
+        "mrpop_autotune_cache_clear": (i32, []),
+        "mrpop_nearest_autotune": (i32, [vp, i64, i64, i32, vp, vp, i64, i32, vp, vp, vp, vp]),
+        "mrpop_neighbors_autotune": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp, vp,
+                                           vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -293,8 +308,64 @@ def autotune(p: Problem, qa: torch.Tensor, qb: torch.Tensor, stream=None) -> tup
     return int(cfg[0]), int(cfg[1]), int(cfg[2]), ms.value
 
 
-def set_launch(p: Problem, warps_per_block: int, order: int, fine_stage: int = 0) -> None:
-    _check(lib.mrpop_set_launch(p.handle, int(warps_per_block), int(order), int(fine_stage)))
+def set_launch(p: Problem, warps_per_block: int, order: int, fine_stage: int = 0,
+               registers: int = 0) -> None:
+    _check(lib.mrpop_set_launch_ex(p.handle, int(warps_per_block), int(order), int(fine_stage),
+                                   int(registers)))
+
+
+def get_launch(p: Problem) -> tuple:
+    """(warps per block, order, fine stage, register budget) of p's validation."""
+    out = (C.c_int32 * 4)()
+    _check(lib.mrpop_get_launch(p.handle, out))
+    return tuple(int(v) for v in out)
+
+
+def autotune_cache_save(path: str) -> None:
+    _check(lib.mrpop_autotune_cache_save(os.fsencode(path)))
+
+
+def autotune_cache_load(path: str) -> None:
+    _check(lib.mrpop_autotune_cache_load(os.fsencode(path)))
+
+
+def autotune_cache_clear() -> None:
+    _check(lib.mrpop_autotune_cache_clear())
+
+
+def nearest_autotune(tree: torch.Tensor, queries: torch.Tensor, budgets: torch.Tensor,
+                     filter: int = 0, stream=None) -> tuple:
+    """Tunes the budget-ordered NEAREST's slice waves for this shape; returns
+    (indices, waves, ms per call)."""
+    dim, ld = int(tree.shape[0]) - 1, int(tree.shape[1])
+    Q = int(queries.shape[1])
+    out = torch.empty(Q, dtype=torch.int64, device=queries.device)
+    w, ms = C.c_int32(), C.c_float()
+    _check(lib.mrpop_nearest_autotune(_dptr(tree, torch.float32, "tree"), ld, ld, dim,
+                                      _dptr(queries, torch.float32, "queries"),
+                                      _dptr(budgets, torch.float32, "budgets"), Q, int(filter),
+                                      _dptr(out, torch.int64, "out_idx"), C.byref(w),
+                                      C.byref(ms), _stream(stream)))
+    return out, w.value, ms.value
+
+
+def neighbors_autotune(tree: torch.Tensor, queries: torch.Tensor, delta: float, k_max: int,
+                       dim: Optional[int] = None, stream=None) -> tuple:
+    """Tunes NEIGHBORS's vertex ranges for this shape; returns (indices,
+    counts, warps per SM, ms per call)."""
+    dim = int(queries.shape[0]) if dim is None else int(dim)
+    ld = int(tree.shape[1])
+    Q = int(queries.shape[1])
+    idx = torch.empty((Q, max(k_max, 1)), dtype=torch.int64, device=queries.device)
+    cnt = torch.empty(Q, dtype=torch.int64, device=queries.device)
+    t, ms = C.c_int32(), C.c_float()
+    _check(lib.mrpop_neighbors_autotune(_dptr(tree, torch.float32, "tree"), ld, ld, dim,
+                                        _dptr(queries, torch.float32, "queries"), Q,
+                                        float(delta), int(k_max),
+                                        _dptr(idx, torch.int64, "out_idx"),
+                                        _dptr(cnt, torch.int64, "out_cnt"), C.byref(t),
+                                        C.byref(ms), _stream(stream)))
+    return idx[:, :k_max], cnt, t.value, ms.value
 
 
 NEAREST_FILTER_FP32 = 0     # MRPOP_NEAREST_FILTER_FP32 (the default)

@@ -6,7 +6,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
 
 #include "mrpop_internal.cuh"
 
@@ -25,6 +29,61 @@ mrpop_status set_error(mrpop_status st, const char *fmt, ...) {
 mrpop_status cuda_error(cudaError_t e, const char *what) {
     return set_error(e == cudaErrorMemoryAllocation ? MRPOP_ENOMEM : MRPOP_ECUDA,
                      "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// Tuned launch cache
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::string, std::vector<int>> g_tune;
+
+std::string tune_arch() {
+    static std::string arch;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0, ma = 0, mi = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+            arch = "sm_" + std::to_string(ma) + std::to_string(mi);
+        else
+            arch = "sm_unknown";
+    });
+    return arch;
+}
+
+bool tune_lookup(const std::string &key, std::vector<int> *val) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    *val = it->second;
+    return true;
+}
+
+void tune_store(const std::string &key, const std::vector<int> &val) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = val;
+}
+
+int log2_bucket(int64_t n) {
+    int b = 0;
+    while (n > 1) {
+        n >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+// Shape of a problem's validation work (robots, links, spheres, obstacles,
+// largest spheres per link, self-collision): problems of one shape share a
+// tuned launch.
+std::string validate_tune_key(const mrpop_problem *p) {
+    const Tables &t = p->dev.t;
+    std::ostringstream k;
+    k << "validate " << tune_arch() << " K=" << t.K << " L=" << t.L << " S=" << t.S
+      << " NS=" << t.NS << " NC=" << t.NC << " spl=" << t.max_spheres_per_link
+      << " self=" << t.selfcol;
+    return k.str();
 }
 
 static bool finite_all(const float *v, int64_t n) {
@@ -308,6 +367,14 @@ extern "C" mrpop_status mrpop_create_problem(const mrpop_robot *robots, int32_t 
         return fail(cuda_error(e, "cudaMalloc(counter)"));
     if ((e = cudaMemset(p->dev.edge_counter, 0, sizeof(int) * 4)) != cudaSuccess)
         return fail(cuda_error(e, "cudaMemset(counter)"));
+    // a launch tuned earlier for a problem of this shape (mrpop_autotune)
+    std::vector<int> tuned;
+    if (tune_lookup(validate_tune_key(p), &tuned) && tuned.size() >= 4) {
+        p->tuned_warps = tuned[0];
+        p->tuned_order = tuned[1];
+        p->tuned_fine = tuned[2];
+        p->tuned_regs = tuned[3];
+    }
     *out = p;
     return MRPOP_OK;
 }
@@ -447,6 +514,36 @@ extern "C" mrpop_status mrpop_neighbors(const float *tree, int64_t N, int64_t ld
                             (cudaStream_t)stream);
 }
 
+extern "C" mrpop_status mrpop_nearest_autotune(const float *tree, int64_t N, int64_t ld,
+                                               int32_t dim, const float *queries,
+                                               const float *budgets, int64_t Q, int32_t filter,
+                                               int64_t *out_idx, int32_t *waves,
+                                               float *ms_per_call, void *stream) {
+    if (dim < 1 || dim > MRPOP_MAX_LINKS || N < 0 || Q < 1 || ld < N || N > (int64_t)INT32_MAX ||
+        Q > (int64_t)INT32_MAX)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_autotune: bad sizes");
+    if (filter != MRPOP_NEAREST_FILTER_FP32 && filter != MRPOP_NEAREST_FILTER_TENSOR)
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_autotune: filter=%d is not a filter", filter);
+    if (!queries || !budgets || !out_idx || (N > 0 && !tree))
+        return set_error(MRPOP_EINVAL, "mrpop_nearest_autotune: NULL buffer");
+    return autotune_nearest(tree, N, ld, dim, queries, budgets, Q, filter, out_idx, waves,
+                            ms_per_call, (cudaStream_t)stream);
+}
+
+extern "C" mrpop_status mrpop_neighbors_autotune(const float *tree, int64_t N, int64_t ld,
+                                                 int32_t dim, const float *queries, int64_t Q,
+                                                 float delta, int64_t k_max, int64_t *out_idx,
+                                                 int64_t *out_cnt, int32_t *warps_per_sm,
+                                                 float *ms_per_call, void *stream) {
+    if (dim < 1 || dim > MRPOP_MAX_LINKS || N < 0 || Q < 1 || ld < N || k_max < 0 ||
+        N > (int64_t)INT32_MAX || Q > (int64_t)INT32_MAX || !std::isfinite(delta))
+        return set_error(MRPOP_EINVAL, "mrpop_neighbors_autotune: bad arguments");
+    if (!queries || !out_cnt || (k_max > 0 && !out_idx) || (N > 0 && !tree))
+        return set_error(MRPOP_EINVAL, "mrpop_neighbors_autotune: NULL buffer");
+    return autotune_neighbors(tree, N, ld, dim, queries, Q, delta, k_max, out_idx, out_cnt,
+                              warps_per_sm, ms_per_call, (cudaStream_t)stream);
+}
+
 extern "C" mrpop_status mrpop_path_cost(const float *path, int64_t M, int32_t dim,
                                         double *cost_out, void *stream) {
     if (dim < 1 || M < 0) return set_error(MRPOP_EINVAL, "mrpop_path_cost: bad sizes");
@@ -476,5 +573,76 @@ extern "C" mrpop_status mrpop_set_launch(mrpop_problem *p, int32_t warps_per_blo
     p->tuned_warps = warps_per_block;
     p->tuned_order = order;
     p->tuned_fine = fine_stage;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_set_launch_ex(mrpop_problem *p, int32_t warps_per_block,
+                                           int32_t order, int32_t fine_stage,
+                                           int32_t registers) {
+    if (registers != 0 && registers != 1)
+        return set_error(MRPOP_EINVAL, "mrpop_set_launch_ex: registers must be 0 or 1");
+    const mrpop_status s = mrpop_set_launch(p, warps_per_block, order, fine_stage);
+    if (s != MRPOP_OK) return s;
+    p->tuned_regs = registers;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_get_launch(const mrpop_problem *p, int32_t *config) {
+    if (!p || !config) return set_error(MRPOP_EINVAL, "mrpop_get_launch: NULL argument");
+    config[0] = p->tuned_warps;
+    config[1] = p->tuned_order;
+    config[2] = p->tuned_fine;
+    config[3] = p->tuned_regs;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_autotune_cache_save(const char *path) {
+    if (!path) return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_save: path is NULL");
+    std::ofstream f(path);
+    if (!f) return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_save: cannot write %s", path);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    f << "# mrpop tuned launches: <key> = <values>\n";
+    for (const auto &kv : g_tune) {
+        f << kv.first << " =";
+        for (int v : kv.second) f << ' ' << v;
+        f << '\n';
+    }
+    return f ? MRPOP_OK : set_error(MRPOP_EINVAL, "mrpop_autotune_cache_save: write failed");
+}
+
+extern "C" mrpop_status mrpop_autotune_cache_load(const char *path) {
+    if (!path) return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_load: path is NULL");
+    std::ifstream f(path);
+    if (!f) return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_load: cannot read %s", path);
+    std::string line;
+    std::map<std::string, std::vector<int>> add;
+    int no = 0;
+    while (std::getline(f, line)) {
+        ++no;
+        if (line.empty() || line[0] == '#') continue;
+        const size_t eq = line.rfind(" = ");
+        if (eq == std::string::npos || eq == 0)
+            return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_load: %s:%d: no ' = '", path, no);
+        std::istringstream vs(line.substr(eq + 3));
+        std::vector<int> v;
+        long long x;
+        while (vs >> x) {
+            if (x < -(1ll << 30) || x > (1ll << 30))
+                return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_load: %s:%d: value out of range",
+                                 path, no);
+            v.push_back((int)x);
+        }
+        if (!vs.eof() || v.empty())
+            return set_error(MRPOP_EINVAL, "mrpop_autotune_cache_load: %s:%d: bad values", path, no);
+        add[line.substr(0, eq)] = v;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto &kv : add) g_tune[kv.first] = kv.second;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_autotune_cache_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
     return MRPOP_OK;
 }

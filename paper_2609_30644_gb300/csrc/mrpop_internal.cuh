@@ -117,9 +117,20 @@ struct mrpop_problem {
     int tuned_warps = 0;  // autotuned warps per block (0: largest that fits)
     int tuned_order = 0;  // autotuned checkpoint order
     int tuned_fine = 0;   // autotuned fine-test mode (0 union, 1 reassigned)
+    int tuned_regs = 0;   // autotuned register budget (0 compact: most warps, 1 wide)
 };
 
 namespace mrpop {
+
+// Process-wide cache of tuned launch choices (capi.cu), keyed by a text key
+// that names the kernel family, the GPU architecture and the shape of the
+// work (e.g. "validate sm_103 K=2 L=14 ..."); values are small integer lists.
+// Thread-safe.  Saved to and loaded from text files by mrpop_autotune_cache_*.
+std::string tune_arch();
+bool tune_lookup(const std::string &key, std::vector<int> *val);
+void tune_store(const std::string &key, const std::vector<int> &val);
+std::string validate_tune_key(const mrpop_problem *p);
+int log2_bucket(int64_t n);
 
 // Thread-local error reporting.
 mrpop_status set_error(mrpop_status st, const char *fmt, ...);
@@ -153,13 +164,24 @@ mrpop_status launch_fk(mrpop_problem *p, const float *q, int64_t n, float *out, 
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,
                             int64_t *out_idx, cudaStream_t st,
-                            int filter = MRPOP_NEAREST_FILTER_FP32);
+                            int filter = MRPOP_NEAREST_FILTER_FP32, int waves = 0);
+int nearest_tuned(int dim, int64_t N, int64_t Q, int filter);
+int neighbors_tuned(int dim, int64_t N, int64_t Q);
+mrpop_status autotune_nearest(const float *tree, int64_t N, int64_t ld, int dim,
+                              const float *queries, const float *budgets, int64_t Q,
+                              int filter, int64_t *out_idx, int32_t *waves_out, float *ms_out,
+                              cudaStream_t st);
+mrpop_status autotune_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
+                                const float *queries, int64_t Q, float delta, int64_t k_max,
+                                int64_t *out_idx, int64_t *out_cnt, int32_t *target_out,
+                                float *ms_out, cudaStream_t st);
 // Number of (query, vertex) pairs launch_nearest scans for these inputs.
 mrpop_status nearest_pairs(const float *tree, int64_t N, int64_t ld, int dim, const float *queries,
                            const float *budgets, int64_t Q, int64_t *pairs, cudaStream_t st);
 mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
                               const float *queries, int64_t Q, float delta, int64_t k_max,
-                              int64_t *out_idx, int64_t *out_cnt, cudaStream_t st);
+                              int64_t *out_idx, int64_t *out_cnt, cudaStream_t st,
+                              int warps_per_sm = 0);
 mrpop_status launch_path_cost(const float *path, int64_t M, int dim, double *out,
                               cudaStream_t st);
 

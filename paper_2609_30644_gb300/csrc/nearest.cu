@@ -1410,7 +1410,8 @@ mrpop_status f32_filter_setup(int dev, int *bps) {
 template <int DIM>
 mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *queries,
                                 const float *budgets, int Q, int64_t *out_idx, cudaStream_t st,
-                                int64_t *pairs = nullptr, int filter = MRPOP_NEAREST_FILTER_FP32) {
+                                int64_t *pairs = nullptr, int filter = MRPOP_NEAREST_FILTER_FP32,
+                                int waves = 4) {
     int dev = 0, sms = 1, bps = 1;
     MRPOP_CUDA_TRY(cudaGetDevice(&dev));
     MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1432,7 +1433,7 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     // about four waves of (query block, tree slice) pieces before the cut
     // removes some: the dynamic block scheduler then evens out the blocks
     // that stop early
-    int splits = std::max(1, (4 * sms * bps + qblocks - 1) / qblocks);
+    int splits = std::max(1, (std::max(1, waves) * sms * bps + qblocks - 1) / qblocks);
     int chunk = (N + splits - 1) / splits;
     chunk = std::max(kSliceAlign, ((chunk + kSliceAlign - 1) / kSliceAlign) * kSliceAlign);
     splits = std::max(1, (N + chunk - 1) / chunk);
@@ -1632,20 +1633,103 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int n,
 
 }  // namespace
 
+// Tuned-launch cache keys and lookups: the budget-ordered NEAREST's slice
+// waves (default 4) and NEIGHBORS's vertex-range target (default 54 warps per
+// SM), per (architecture, dimension, log2 of the tree size, log2 of the batch).
+static std::string nn_key(const char *kind, int dim, int64_t N, int64_t Q, int filter) {
+    return std::string(kind) + " " + tune_arch() + " dim=" + std::to_string(dim) + " N=2^" +
+           std::to_string(log2_bucket(N)) + " Q=2^" + std::to_string(log2_bucket(Q)) +
+           (filter >= 0 ? " filter=" + std::to_string(filter) : std::string());
+}
+
+int nearest_tuned(int dim, int64_t N, int64_t Q, int filter) {
+    std::vector<int> v;
+    return tune_lookup(nn_key("nearest", dim, N, Q, filter), &v) && !v.empty() && v[0] > 0 ? v[0] : 4;
+}
+
+int neighbors_tuned(int dim, int64_t N, int64_t Q) {
+    std::vector<int> v;
+    return tune_lookup(nn_key("neighbors", dim, N, Q, -1), &v) && !v.empty() && v[0] > 0 ? v[0] : 54;
+}
+
+// Times candidates[] (the value passed as the launch knob) with `run`, keeps
+// the fastest under key.
+template <class Run>
+static mrpop_status tune_candidates(const std::string &key, const int *cand, int nc, int reps,
+                                    Run run, cudaStream_t st, int32_t *best_out, float *ms_out) {
+    cudaEvent_t a, b;
+    MRPOP_CUDA_TRY(cudaEventCreate(&a));
+    MRPOP_CUDA_TRY(cudaEventCreate(&b));
+    float best = INFINITY;
+    int bv = 0;
+    mrpop_status s = MRPOP_OK;
+    for (int i = 0; i < nc && s == MRPOP_OK; ++i) {
+        s = run(cand[i]);  // warm
+        float tot = 0.f;
+        for (int r = 0; r < reps && s == MRPOP_OK; ++r) {
+            cudaEventRecord(a, st);
+            s = run(cand[i]);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            tot += ms;
+        }
+        if (s == MRPOP_OK && tot < best) {
+            best = tot;
+            bv = cand[i];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != MRPOP_OK) return s;
+    tune_store(key, {bv});
+    if (best_out) *best_out = bv;
+    if (ms_out) *ms_out = best / std::max(1, reps);
+    return MRPOP_OK;
+}
+
+mrpop_status autotune_nearest(const float *tree, int64_t N, int64_t ld, int dim,
+                              const float *queries, const float *budgets, int64_t Q,
+                              int filter, int64_t *out_idx, int32_t *waves_out, float *ms_out,
+                              cudaStream_t st) {
+    static const int cand[] = {2, 4, 8};
+    return tune_candidates(nn_key("nearest", dim, N, Q, filter), cand, 3, 3,
+                           [&](int w) {
+                               return launch_nearest(tree, N, ld, dim, queries, budgets, Q,
+                                                     out_idx, st, filter, w);
+                           },
+                           st, waves_out, ms_out);
+}
+
+mrpop_status autotune_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
+                                const float *queries, int64_t Q, float delta, int64_t k_max,
+                                int64_t *out_idx, int64_t *out_cnt, int32_t *target_out,
+                                float *ms_out, cudaStream_t st) {
+    static const int cand[] = {14, 54, 216};
+    return tune_candidates(nn_key("neighbors", dim, N, Q, -1), cand, 3, 3,
+                           [&](int t) {
+                               return launch_neighbors(tree, N, ld, dim, queries, Q, delta, k_max,
+                                                       out_idx, out_cnt, st, t);
+                           },
+                           st, target_out, ms_out);
+}
+
 mrpop_status launch_nearest(const float *tree, int64_t N, int64_t ld, int dim,
                             const float *queries, const float *budgets, int64_t Q,
-                            int64_t *out_idx, cudaStream_t st, int filter) {
+                            int64_t *out_idx, cudaStream_t st, int filter, int waves) {
     const int n = (int)N, q = (int)Q;
     // Large batches: budget-ordered tree and queries, expansion filter with
     // exact decisions over shared-memory tree tiles.
     if (Q >= 2048 && N > 0) {
+        const int w = waves > 0 ? waves : nearest_tuned(dim, N, Q, filter);
         switch (dim) {
-            case 3: return nearest_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
-            case 6: return nearest_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
-            case 7: return nearest_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
-            case 14: return nearest_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
-            case 21: return nearest_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
-            case 28: return nearest_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter);
+            case 3: return nearest_sorted<3>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter, w);
+            case 6: return nearest_sorted<6>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter, w);
+            case 7: return nearest_sorted<7>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter, w);
+            case 14: return nearest_sorted<14>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter, w);
+            case 21: return nearest_sorted<21>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter, w);
+            case 28: return nearest_sorted<28>(tree, n, ld, queries, budgets, q, out_idx, st, nullptr, filter, w);
             default: break;
         }
     }
@@ -1687,18 +1771,21 @@ mrpop_status nearest_pairs(const float *tree, int64_t N, int64_t ld, int dim, co
 
 mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
                               const float *queries, int64_t Q, float delta, int64_t k_max,
-                              int64_t *out_idx, int64_t *out_cnt, cudaStream_t st) {
+                              int64_t *out_idx, int64_t *out_cnt, cudaStream_t st,
+                              int warps_per_sm) {
+    if (warps_per_sm <= 0) warps_per_sm = neighbors_tuned(dim, N, Q);
     const int blocks = (int)((Q + kNbWarps - 1) / kNbWarps);
     const size_t smem = sizeof(float) * (size_t)dim * kNbTile;
     if (smem > 48 * 1024)
         MRPOP_CUDA_TRY(cudaFuncSetAttribute(neighbors_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // Few queries leave most SMs idle with one warp per query: split the
-    // vertices into ranges (at least one tile each) until about 8,192 warps run.
+    // vertices into ranges (at least one tile each) until about warps_per_sm
+    // warps per SM run (54 by default: about 8,192 on 152 SMs; tunable).
     int sms = 1, dev = 0;
     MRPOP_CUDA_TRY(cudaGetDevice(&dev));
     MRPOP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t want = std::max<int64_t>(1, (int64_t)sms * 54 / std::max<int64_t>(Q, 1));
+    const int64_t want = std::max<int64_t>(1, (int64_t)sms * std::max(1, warps_per_sm) / std::max<int64_t>(Q, 1));
     const int ranges = (int)std::min<int64_t>(std::min<int64_t>(want, (N + kNbTile - 1) / kNbTile),
                                               std::max<int64_t>(1, 65535));
     if (ranges <= 1 || k_max > 4096) {

@@ -52,6 +52,15 @@ __global__ void __launch_bounds__(kWarpsMax * 32) validate_kernel(const VParams 
     validate_body<MODE, RA>(P, sm4);
 }
 
+// The same kernel with a wide register budget (up to 128 registers: four
+// blocks of four warps per SM): fewer warps, no spills in the robot-robot
+// fine stage, which many-arm scenes reach often.  An autotuner dimension.
+template <int MODE, bool RA>
+__global__ void __launch_bounds__(kWarpsMax * 32, 4) validate_kernel_wide(const VParams P) {
+    extern __shared__ float4 sm4[];
+    validate_body<MODE, RA>(P, sm4);
+}
+
 // Many problems in one launch: block row y serves problem y (its parameters
 // are staged in shared memory once per block).
 template <bool RA>
@@ -96,7 +105,8 @@ static mrpop_status cached_occupancy(const void *kern, int device, int smem_opti
 template <int MODE, bool RA>
 mrpop_status launch_mode(mrpop_problem *p, VParams &V, int warps, size_t smem,
                          cudaStream_t st) {
-    auto kern = validate_kernel<MODE, RA>;
+    auto kern = MODE == kVerdict && p->tuned_regs ? validate_kernel_wide<MODE, RA>
+                                                  : validate_kernel<MODE, RA>;
     int bps = 0;
     const mrpop_status os = cached_occupancy((const void *)kern, p->device, (int)p->smem_optin,
                                              warps * 32, smem, &bps);
@@ -249,8 +259,9 @@ mrpop_status launch_validate_batch(const VParams *d_params, int nslots, int /*sp
 
 // Times the validation kernel on the caller's edges for every candidate
 // launch (warps per block 1, 2, 4 that fit; strided or contiguous checkpoint
-// order; union or reassigned fine tests), keeps the fastest in the problem
-// and reports it.
+// order; union or reassigned fine tests; compact or wide register budget),
+// keeps the fastest in the problem and in the tuned-launch cache under the
+// problem's shape, and reports it.
 mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *qb, int64_t n,
                                uint8_t *valid, int reps, int32_t *out, float *ms_out,
                                cudaStream_t st) {
@@ -258,18 +269,21 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
     MRPOP_CUDA_TRY(cudaEventCreate(&a));
     MRPOP_CUDA_TRY(cudaEventCreate(&b));
     float best = INFINITY;
-    int bw = 0, bo = 0, bf = 0;
-    const int save_w = p->tuned_warps, save_o = p->tuned_order, save_f = p->tuned_fine;
+    int bw = 0, bo = 0, bf = 0, br = 0;
+    const int save_w = p->tuned_warps, save_o = p->tuned_order, save_f = p->tuned_fine,
+              save_r = p->tuned_regs;
     mrpop_status s = MRPOP_OK;
     for (int w = 1; w <= kWarpsMax && s == MRPOP_OK; w *= 2)
         for (int o = 0; o < 2 && s == MRPOP_OK; ++o)
-        for (int f = 0; f < 2 && s == MRPOP_OK; ++f) {
+        for (int f = 0; f < 2 && s == MRPOP_OK; ++f)
+        for (int rg = 0; rg < 2 && s == MRPOP_OK; ++rg) {
             const size_t need = (size_t)p->dev.t.n_f4 * sizeof(float4) +
                                 (size_t)w * validate_warp_floats(p->dev.t, f) * sizeof(float);
             if (need + sizeof(VParams) + 1024 > p->smem_optin) continue;
             p->tuned_warps = w;
             p->tuned_order = o;
             p->tuned_fine = f;
+            p->tuned_regs = rg;
             s = launch_validate(p, qa, qb, n, valid, nullptr, nullptr, nullptr, nullptr, st);  // warm
             float tot = 0.f;
             for (int r = 0; r < reps && s == MRPOP_OK; ++r) {
@@ -286,6 +300,7 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
                 bw = w;
                 bo = o;
                 bf = f;
+                br = rg;
             }
         }
     cudaEventDestroy(a);
@@ -294,11 +309,14 @@ mrpop_status autotune_validate(mrpop_problem *p, const float *qa, const float *q
         p->tuned_warps = save_w;
         p->tuned_order = save_o;
         p->tuned_fine = save_f;
+        p->tuned_regs = save_r;
         return s != MRPOP_OK ? s : set_error(MRPOP_EINVAL, "no launch configuration fits");
     }
     p->tuned_warps = bw;
     p->tuned_order = bo;
     p->tuned_fine = bf;
+    p->tuned_regs = br;
+    tune_store(validate_tune_key(p), {bw, bo, bf, br});
     if (out) {
         out[0] = bw;
         out[1] = bo;

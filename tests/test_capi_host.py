@@ -105,3 +105,38 @@ def test_nearest_rejects_bad_dim(capi):
     st = lib.mrpop_nearest(None, 10, 5, 3, None, None, 1, None, None)   # ld < N
     assert st == 1
     assert lib.mrpop_nearest(None, 0, 0, 3, None, None, 0, None, None) == 0  # Q = 0: no-op
+
+
+def test_autotune_cache_save_load_roundtrip(capi, tmp_path):
+    """The tuned-launch cache is host data: entries loaded from a file come
+    back out of a save unchanged, later loads replace keys, a malformed line
+    is refused with MRPOP_EINVAL, and clearing empties it."""
+    src = tmp_path / "in.txt"
+    src.write_text("# comment\n"
+                   "validate sm_00 K=2 L=14 S=120 NS=32 NC=32 spl=9 self=0 = 4 0 0 1\n"
+                   "nearest sm_00 dim=14 N=2^14 Q=2^16 filter=0 = 8\n")
+    capi.autotune_cache_clear()
+    capi.autotune_cache_load(str(src))
+    capi.autotune_cache_load(str(src))                 # idempotent
+    out = tmp_path / "out.txt"
+    capi.autotune_cache_save(str(out))
+    entries = {l.split(" = ")[0]: l.split(" = ")[1] for l in out.read_text().splitlines()
+               if l and not l.startswith("#")}
+    assert entries == {"validate sm_00 K=2 L=14 S=120 NS=32 NC=32 spl=9 self=0": "4 0 0 1",
+                       "nearest sm_00 dim=14 N=2^14 Q=2^16 filter=0": "8"}
+    upd = tmp_path / "upd.txt"
+    upd.write_text("nearest sm_00 dim=14 N=2^14 Q=2^16 filter=0 = 2\n")
+    capi.autotune_cache_load(str(upd))
+    capi.autotune_cache_save(str(out))
+    assert "nearest sm_00 dim=14 N=2^14 Q=2^16 filter=0 = 2" in out.read_text()
+    bad = tmp_path / "bad.txt"
+    bad.write_text("no separator here\n")
+    with pytest.raises(capi.MrpopError) as e:
+        capi.autotune_cache_load(str(bad))
+    assert e.value.status == 1
+    bad.write_text("k = 1 x\n")
+    with pytest.raises(capi.MrpopError):
+        capi.autotune_cache_load(str(bad))
+    capi.autotune_cache_clear()
+    capi.autotune_cache_save(str(out))
+    assert [l for l in out.read_text().splitlines() if not l.startswith("#")] == []

@@ -242,3 +242,42 @@ def test_nearest_filter_range(mp, orc, D, case, filt):
     np.testing.assert_array_equal(big, small)
     sample = np.concatenate([np.arange(40), np.random.default_rng(7).choice(Q, 120, replace=False)])
     _check_nearest(orc, tree, qs, cs, big, sample=sample)
+
+
+def test_nearest_and_neighbors_tuned_launches_same_results(mp, orc, tmp_path):
+    """The autotuners' knobs (NEAREST's slice waves, NEIGHBORS's vertex-range
+    target) change the launch, never the result: every candidate, forced
+    through the tuned-launch cache (saved, edited and loaded back), returns
+    the same indices as the default launch."""
+    D = 14
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree(D, 4000, lo, hi, seed=81, dup_frac=0.05)
+    qs, cs = synth.nn_queries(D, 3000, lo, hi, seed=82, budget_lo=0.0, budget_hi=25.0)
+    t, q, c = _dev(tree), _dev(qs), _dev(cs)
+    mp.autotune_cache_clear()
+    ref = mp.nearest(t, q, c).cpu().numpy()
+    got, waves, ms = mp.nearest_autotune(t, q, c)
+    assert waves in (2, 4, 8) and ms > 0
+    np.testing.assert_array_equal(got.cpu().numpy(), ref)
+    rq = np.ascontiguousarray(qs[:7, :256])
+    rtree = np.ascontiguousarray(tree[:8])
+    rref, rcnt = mp.neighbors(_dev(rtree), _dev(rq), 2.0, 32, dim=7)
+    ridx, rc2, target, _ = mp.neighbors_autotune(_dev(rtree), _dev(rq), 2.0, 32, dim=7)
+    assert target in (14, 54, 216)
+    np.testing.assert_array_equal(ridx.cpu().numpy(), rref.cpu().numpy())
+    np.testing.assert_array_equal(rc2.cpu().numpy(), rcnt.cpu().numpy())
+    path = tmp_path / "tuned.txt"
+    mp.autotune_cache_save(str(path))
+    lines = [l for l in path.read_text().splitlines() if l and not l.startswith("#")]
+    nkey = [l.split(" = ")[0] for l in lines if l.startswith("nearest ")]
+    bkey = [l.split(" = ")[0] for l in lines if l.startswith("neighbors ")]
+    assert len(nkey) == 1 and len(bkey) == 1
+    for wv, tg in ((2, 14), (8, 216), (4, 54)):
+        path.write_text(f"{nkey[0]} = {wv}\n{bkey[0]} = {tg}\n")
+        mp.autotune_cache_load(str(path))
+        np.testing.assert_array_equal(mp.nearest(t, q, c).cpu().numpy(), ref)
+        i2, c2 = mp.neighbors(_dev(rtree), _dev(rq), 2.0, 32, dim=7)
+        np.testing.assert_array_equal(i2.cpu().numpy(), rref.cpu().numpy())
+        np.testing.assert_array_equal(c2.cpu().numpy(), rcnt.cpu().numpy())
+    _check_nearest(orc, tree, qs, cs, ref, sample=np.arange(0, 3000, 97))
+    mp.autotune_cache_clear()

@@ -308,14 +308,25 @@ def test_launch_configs_and_autotune_same_verdicts(mp, orc):
         for w in (1, 2, 4):
             for order in (0, 1):
                 for fine in (0, 1):
-                    mp.set_launch(p, w, order, fine)
-                    got = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
-                    np.testing.assert_array_equal(got, ref)
+                    for regs in (0, 1):
+                        mp.set_launch(p, w, order, fine, regs)
+                        got = mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy()
+                        np.testing.assert_array_equal(got, ref)
         with pytest.raises(mp.MrpopError):
             mp.set_launch(p, 4, 0, 2)
+        with pytest.raises(mp.MrpopError):
+            mp.set_launch(p, 4, 0, 0, 2)
         w, order, fine, ms = mp.autotune(p, _dev(qa), _dev(qb))
         assert w in (1, 2, 4) and order in (0, 1) and fine in (0, 1) and ms > 0
+        tuned = mp.get_launch(p)
+        assert tuned[:3] == (w, order, fine) and tuned[3] in (0, 1)
         np.testing.assert_array_equal(mp.validate_edges(p, _dev(qa), _dev(qb)).cpu().numpy(), ref)
+    # a new problem of the same shape starts with the tuned launch (cache)
+    with mp.Problem(synth.table_pair_scene(3), margin=1e-4) as p2:
+        assert mp.get_launch(p2) == tuned
+    # another shape does not
+    with mp.Problem(synth.planar_pair_scene(0)) as p3:
+        assert mp.get_launch(p3) == (0, 0, 0, 0)
     o = orc.OracleScene(scene)
     idx = np.arange(0, 4096, 97)
     _check_verdicts(ref[idx], o.validate_edges(qa[:, idx], qb[:, idx], 0.02, 1e-4), 1e-4)
