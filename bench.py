@@ -653,9 +653,14 @@ def run_ours(args) -> None:
             ev[4].record(stream)
         return idx, cnt
 
-    # launch shape from the autotuner, then the algorithmic work of the
-    # validation launch on this batch (both untimed)
+    # launch shapes from the autotuners (validation, NEAREST, NEIGHBORS),
+    # then the algorithmic work of the validation launch on this batch (all
+    # untimed)
     tuned = mp.autotune(prob, g["qa"], g["qb"])
+    tuned_regs = mp.get_launch(prob)[3]
+    _, nn_waves, _ = mp.nearest_autotune(g["tree"], g["qs"], g["cs"])
+    _, _, nb_target, _ = mp.neighbors_autotune(g["roadmap"], g["rq"], RM_DELTA, RM_KMAX,
+                                               dim=scene.robots[0].dof)
     counters = mp.validate_work(prob, g["qa"], g["qb"]).cpu().numpy()
     flops_per_launch = algorithmic_flops(counters)
     # (query, vertex) pairs NEAREST evaluates: vertices whose cost-to-come
@@ -946,7 +951,10 @@ def run_ours(args) -> None:
                        "validate_launch": {"warps_per_block": tuned[0],
                                            "order": ["strided", "contiguous"][tuned[1]],
                                            "fine_stage": ["union", "reassigned"][tuned[2]],
+                                           "registers": ["compact", "wide"][tuned_regs],
                                            "autotune_ms": tuned[3]},
+                       "nearest_launch": {"slice_waves": nn_waves},
+                       "neighbors_launch": {"warps_per_sm": nb_target},
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline_nearest": {
                 "bound": "alu", "kernel": nn_kernel, "filter": "FP32 FMA (default)",

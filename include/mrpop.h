@@ -46,7 +46,8 @@ typedef enum {
     MRPOP_ECAPACITY = 4,   /* a tree, roadmap or path buffer is full           */
     MRPOP_ETIMEOUT = 5,    /* a bounded device wait gave up                    */
     MRPOP_ENOSOLUTION = 6, /* no path was found within the budget             */
-    MRPOP_EBUSY = 7        /* the object is in use by another request          */
+    MRPOP_EBUSY = 7,       /* the object is in use by another request          */
+    MRPOP_ECANCELLED = 8   /* a serving request was cancelled                  */
 } mrpop_status;
 
 /* Limits checked by mrpop_create_problem. */
@@ -479,6 +480,26 @@ mrpop_status mrpop_server_poll(mrpop_server *s, int64_t ticket, int32_t *state, 
 /* Counters (host int64 [6]): requests admitted, completed, peak concurrent
  * requests, peak admitted device memory (bytes), memory budget, queue length. */
 mrpop_status mrpop_server_stats(mrpop_server *s, int64_t *stats);
+
+/* Cancels a request: a queued one is dropped before admission, a running one
+ * ends after the iteration in flight; either finishes with MRPOP_ECANCELLED
+ * (reported by mrpop_server_poll once done), keeping any path it found.  A
+ * request already done is left as it is.  Errors: EINVAL (unknown ticket). */
+mrpop_status mrpop_server_cancel(mrpop_server *s, int64_t ticket);
+
+/* Host-side fault injection for tests of the serving loop's failure paths
+ * (nothing faults on the GPU):
+ *   MRPOP_FAULT_ADMIT_ENOMEM  the next count admissions fail as if their
+ *                             device allocation had been refused: each such
+ *                             request finishes with MRPOP_ENOMEM and the
+ *                             server carries on with the others;
+ *   MRPOP_FAULT_STALL_MS      the server loop stalls once for count
+ *                             milliseconds, outside its lock (submit, poll
+ *                             and cancel stay responsive).
+ * Errors: EINVAL (unknown fault, negative count). */
+#define MRPOP_FAULT_ADMIT_ENOMEM 1
+#define MRPOP_FAULT_STALL_MS 2
+mrpop_status mrpop_server_inject(mrpop_server *s, int32_t fault, int64_t count);
 
 /* Stops the server: running requests finish at once, queued ones are
  * dropped, the thread is joined.  NULL is accepted. */

@@ -57,10 +57,12 @@ EXPORTS = (
     "mrpop_autotune_cache_clear",
     "mrpop_nearest_autotune",
     "mrpop_neighbors_autotune",
+    "mrpop_server_cancel",
+    "mrpop_server_inject",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
-          6: "ENOSOLUTION", 7: "EBUSY"}
+          6: "ENOSOLUTION", 7: "EBUSY", 8: "ECANCELLED"}
 
 
 class MrpopError(RuntimeError):
@@ -137,6 +139,8 @@ def _load() -> C.CDLL:
         "mrpop_nearest_autotune": (i32, [vp, i64, i64, i32, vp, vp, i64, i32, vp, vp, vp, vp]),
         "mrpop_neighbors_autotune": (i32, [vp, i64, i64, i32, vp, i64, f32, i64, vp, vp, vp, vp,
                                            vp]),
+        "mrpop_server_cancel": (i32, [vp, i64]),
+        "mrpop_server_inject": (i32, [vp, i32, i64]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -543,6 +547,10 @@ def plan_result(p: Problem, path_cap: int = 1 << 16) -> tuple:
     return buf[:n.value].copy(), cost.value
 
 
+FAULT_ADMIT_ENOMEM = 1   # MRPOP_FAULT_ADMIT_ENOMEM
+FAULT_STALL_MS = 2       # MRPOP_FAULT_STALL_MS
+
+
 class Server:
     """Continuous-batching planning server (mrpop_server_*)."""
 
@@ -566,6 +574,25 @@ class Server:
         _check(lib.mrpop_server_poll(self._h, int(ticket), C.byref(st), times.ctypes.data,
                                      C.byref(cost)))
         return st.value, times, cost.value
+
+    def poll_status(self, ticket: int) -> tuple:
+        """(state, times[4], cost, status): like poll, with a failed or
+        cancelled request's status returned instead of raised."""
+        st = C.c_int32()
+        times = np.zeros(4)
+        cost = C.c_double()
+        status = lib.mrpop_server_poll(self._h, int(ticket), C.byref(st), times.ctypes.data,
+                                       C.byref(cost))
+        if status == 1:   # EINVAL: unknown ticket
+            _check(status)
+        return st.value, times, cost.value, int(status)
+
+    def cancel(self, ticket: int) -> None:
+        _check(lib.mrpop_server_cancel(self._h, int(ticket)))
+
+    def inject(self, fault: int, count: int) -> None:
+        """Host-side fault injection (FAULT_ADMIT_ENOMEM, FAULT_STALL_MS)."""
+        _check(lib.mrpop_server_inject(self._h, int(fault), int(count)))
 
     def stats(self) -> dict:
         v = np.zeros(6, dtype=np.int64)

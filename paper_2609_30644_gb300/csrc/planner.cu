@@ -2469,6 +2469,7 @@ struct Request {
     mrpop_status status = MRPOP_OK;
     SlotRun run;
     size_t mem = 0;
+    bool cancel = false;  // set by mrpop_server_cancel (under the server's lock)
 };
 
 }  // namespace mrpop
@@ -2492,6 +2493,10 @@ struct mrpop_server {
     mrpop::VParams *d_vp = nullptr;
     mrpop::Ctrl *d_ctrl = nullptr, *h_ctrl = nullptr;
     std::thread th;
+    // host-side fault injection (mrpop_server_inject)
+    int64_t inject_admit_enomem = 0;  // admissions still to refuse
+    int64_t inject_stall_ms = 0;      // one stall of the loop, then 0
+    int64_t cancelled = 0;
 };
 
 namespace mrpop {
@@ -2551,9 +2556,27 @@ static void server_loop(mrpop_server *sv) {
     };
     for (;;) {
         std::vector<Request *> admit;
+        std::vector<bool> refuse;
+        int64_t stall = 0;
         {
             std::unique_lock<std::mutex> lock(sv->mu);
             if (sv->stop) break;
+            stall = sv->inject_stall_ms;
+            sv->inject_stall_ms = 0;
+            // cancelled requests leave the queue before admission
+            for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+                if ((*it)->cancel) {
+                    Request *r = *it;
+                    it = sv->queue.erase(it);
+                    r->state = 2;
+                    r->status = MRPOP_ECANCELLED;
+                    r->t_done = now_s() - r->t_submit;
+                    ++sv->completed;
+                    ++sv->cancelled;
+                } else {
+                    ++it;
+                }
+            }
             while ((int)(sv->active.size() + admit.size()) < sv->max_slots && !sv->queue.empty()) {
                 Request *r = sv->queue.front();
                 const size_t need = planner_bytes(r->p);
@@ -2565,18 +2588,26 @@ static void server_loop(mrpop_server *sv) {
                 sv->mem_used += need;
                 sv->peak_mem = std::max(sv->peak_mem, sv->mem_used);
                 admit.push_back(r);
+                refuse.push_back(sv->inject_admit_enomem > 0);
+                if (sv->inject_admit_enomem > 0) --sv->inject_admit_enomem;
             }
-            if (sv->active.empty() && admit.empty()) {
+            if (sv->active.empty() && admit.empty() && stall == 0) {
                 sv->cv.wait_for(lock, std::chrono::milliseconds(2));
                 continue;
             }
         }
-        for (Request *r : admit) {
-            mrpop_status s = ensure_planner(r->p);
+        if (stall > 0)  // injected stall, outside the lock: submit and poll stay responsive
+            std::this_thread::sleep_for(std::chrono::milliseconds(stall));
+        for (size_t ai = 0; ai < admit.size(); ++ai) {
+            Request *r = admit[ai];
+            // an injected refusal stands in for a failed device allocation
+            mrpop_status s = refuse[ai] ? set_error(MRPOP_ENOMEM, "injected allocation failure")
+                                        : ensure_planner(r->p);
             std::vector<Planner *> one{r->p->planner};
             std::vector<SlotRun> run(1);
             run[0].target = r->target;
             run[0].reset_trees = s == MRPOP_OK && !r->p->planner->roadmap_ready;
+            if (s != MRPOP_OK) one.clear();
             if (s == MRPOP_OK) s = check_endpoints(one, run, st);
             if (s == MRPOP_OK) s = run[0].status;
             const double now = now_s();
@@ -2628,10 +2659,20 @@ static void server_loop(mrpop_server *sv) {
             const double t = now - r->t_submit;
             if (r->t_first < 0 && !pl->trace_c.empty()) r->t_first = t;
             if (r->t_target < 0 && reached_target(pl->c_best, r->target)) r->t_target = t;
-            const bool done = r->run.reached || !r->run.active ||
+            bool cancel;
+            {
+                std::lock_guard<std::mutex> lock(sv->mu);
+                cancel = r->cancel;
+            }
+            const bool done = cancel || r->run.reached || !r->run.active ||
                               now - (r->t_submit + r->t_admit) >= r->budget ||
                               (r->max_steps > 0 && r->steps >= r->max_steps);
             if (done) {
+                if (cancel) {
+                    r->status = MRPOP_ECANCELLED;
+                    std::lock_guard<std::mutex> lock(sv->mu);
+                    ++sv->cancelled;
+                }
                 server_finish(sv, r, now);
                 changed = true;
             } else {
@@ -2817,6 +2858,30 @@ extern "C" mrpop_status mrpop_server_poll(mrpop_server *sv, int64_t ticket, int3
     if (cost) *cost = (r.state == 2 && r.p->planner) ? r.p->planner->c_best : INFINITY;
     if (r.state == 2 && r.status != MRPOP_OK) return set_error(r.status, "request failed");
     if (sv->fatal != MRPOP_OK) return set_error(sv->fatal, "server stopped on an error");
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_cancel(mrpop_server *sv, int64_t ticket) {
+    if (!sv) return set_error(MRPOP_EINVAL, "mrpop_server_cancel: server is NULL");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return set_error(MRPOP_EINVAL, "mrpop_server_cancel: unknown ticket");
+    if (it->second->state != 2) it->second->cancel = true;
+    sv->cv.notify_all();
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_server_inject(mrpop_server *sv, int32_t fault, int64_t count) {
+    if (!sv) return set_error(MRPOP_EINVAL, "mrpop_server_inject: server is NULL");
+    if (count < 0) return set_error(MRPOP_EINVAL, "mrpop_server_inject: negative count");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (fault == MRPOP_FAULT_ADMIT_ENOMEM)
+        sv->inject_admit_enomem = count;
+    else if (fault == MRPOP_FAULT_STALL_MS)
+        sv->inject_stall_ms = count;
+    else
+        return set_error(MRPOP_EINVAL, "mrpop_server_inject: fault=%d is not a fault", fault);
+    sv->cv.notify_all();
     return MRPOP_OK;
 }
 

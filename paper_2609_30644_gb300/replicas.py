@@ -52,3 +52,46 @@ def max_over_ranks(dist, value: float, device: Optional[object] = None) -> float
 def barrier(dist) -> None:
     if dist is not None:
         dist.barrier()
+
+
+def assign(costs, world: int) -> list:
+    """Whole problems to ranks (one GPU each): the largest estimated cost
+    first, each to the rank with the least load so far (ties: the lower
+    rank), so that loads differ by at most one problem's cost.  Returns, per
+    rank, its problem indices in ascending order; every rank computing this
+    from the same costs gets the same partition."""
+    loads = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i)):
+        r = min(range(world), key=lambda k: (loads[k], k))
+        loads[r] += float(costs[i])
+        out[r].append(i)
+    return [sorted(o) for o in out]
+
+
+def problem_cost(scene) -> float:
+    """Planning cost estimate of a scene for assign(): robots and obstacles
+    drive the validation work (robot pairs, link-obstacle tests)."""
+    K = len(scene.robots)
+    n_obs = len(scene.obs_spheres) + len(scene.obs_cuboids)
+    links = sum(r.dof for r in scene.robots)
+    return float(links * (n_obs + 1) + 49 * K * (K - 1) // 2)
+
+
+def dispatch(dist, costs, solve, rank: int, world: int) -> list:
+    """Runs solve(i) for this rank's problems (assign) and gathers every
+    rank's results; returns the results of all problems in problem order on
+    every rank (None for a problem nobody solved).  With dist None (one
+    rank) everything runs here.  solve's result must be picklable."""
+    mine = assign(costs, world)[rank] if world > 1 else list(range(len(costs)))
+    local = {i: solve(i) for i in mine}
+    if dist is None or world <= 1:
+        parts = [local]
+    else:
+        parts = [None] * world
+        dist.all_gather_object(parts, local)
+    out = [None] * len(costs)
+    for part in parts:
+        for i, v in part.items():
+            out[i] = v
+    return out
