@@ -512,16 +512,24 @@ def run_serving_leg(mp, synth, entries, best, rate: float,
             "first_solutions": int(len(first)), "peak_concurrent": stats["peak_active"]}
 
 
-def profiled_traffic(kernel_file: str, name: str):
+def kernel_source_sha(kernel_files: str) -> str:
+    """sha256 over the kernel's source files ('+'-separated names under csrc/,
+    concatenated in that order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in kernel_files.split("+"):
+        h.update(open(os.path.join(ROOT, "paper_2609_30644_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel_files: str, name: str):
     """DRAM bytes per launch of a kernel from the committed ncu summary
     profiles/<name>.txt, when that summary was taken on the current source of
-    kernel_file (its sha256 is recorded there); None otherwise."""
-    import hashlib
+    kernel_files (their sha256 is recorded there); None otherwise."""
     path = os.path.join(ROOT, "profiles", name + ".txt")
     try:
         rec = dict(l.split(":", 1) for l in open(path) if ":" in l and not l.startswith("#"))
-        src = os.path.join(ROOT, "paper_2609_30644_gb300", "csrc", kernel_file)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = kernel_source_sha(kernel_files)
         if rec.get("source_sha256", "").strip() != sha:
             return None
         return float(rec["dram_bytes_per_launch"])
@@ -545,8 +553,8 @@ def run_profile_leg(args) -> None:
     """--profile-leg: one kernel's leg of the step alone, for ncu captures of
     a known launch.  validate-free: the free-set construction (one validation
     launch), then W warm-up and K timed launches on the free set;
-    validate-mixed: W + K launches on the step's mixed batch; nearest: W + K
-    NEAREST calls (one filter launch each).  The validation launch shape is
+    validate-mixed: W + K launches on the step's mixed batch; nearest (FP32
+    filter) and nearest-tensor: W + K NEAREST calls (one filter launch each).  The validation launch shape is
     --launch (warps per block, order, fine stage).  Prints one JSON line with
     the mean time of the timed launches."""
     import numpy as np
@@ -578,7 +586,9 @@ def run_profile_leg(args) -> None:
             tree = torch.from_numpy(x["tree"]).to(dev)
             qs = torch.from_numpy(x["qs"]).to(dev)
             cs = torch.from_numpy(x["cs"]).to(dev)
-            run = lambda out: mp.nearest(tree, qs, cs, out=out)
+            filt = (mp.NEAREST_FILTER_TENSOR if args.profile_leg == "nearest-tensor"
+                    else mp.NEAREST_FILTER_FP32)
+            run = lambda out: mp.nearest(tree, qs, cs, out=out, filter=filt)
             out = torch.empty(NN_QUERIES, dtype=torch.int64, device=dev)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         for _ in range(args.warmup):
@@ -907,7 +917,8 @@ def run_ours(args) -> None:
             "edge_set": "free (65,536 accepted edges, no early exit)",
             "peak": peak_tflops, "unit": "TFLOP/s", "peak_source": peak_source,
             "ms": statistics.mean(free_ms), "edges_per_s": E_EDGES / free_avg_s,
-            "traffic": profiled_traffic("validate.cu", "validate_kernel_table_pair_free"),
+            "traffic": profiled_traffic("validate.cu+validate_body.cuh",
+                                        "validate_kernel_table_pair_free"),
             "kernel_flops_per_launch": free_flops,
             "kernel_achieved": free_achieved, "kernel_frac": free_achieved / peak_tflops,
             "kernel_tile_level_flops": free_tile,
@@ -987,7 +998,7 @@ def run_ours(args) -> None:
                                         "edge_set": "mixed (the step's batch)",
                                         "achieved": achieved, "peak": peak_tflops,
                                         "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                                        "traffic": profiled_traffic("validate.cu",
+                                        "traffic": profiled_traffic("validate.cu+validate_body.cuh",
                                                                     "validate_kernel_table_pair"),
                                         "peak_source": peak_source,
                                         "flops_per_launch": flops_per_launch,
@@ -1047,7 +1058,8 @@ def main():
                     help="comma-separated Poisson arrival rates of the serving leg (1/s)")
     ap.add_argument("--serving-requests", type=int, default=SERVE_REQUESTS,
                     help="requests per serving rate")
-    ap.add_argument("--profile-leg", choices=["validate-free", "validate-mixed", "nearest"],
+    ap.add_argument("--profile-leg", choices=["validate-free", "validate-mixed", "nearest",
+                                              "nearest-tensor"],
                     default=None, help="run one kernel's leg alone (for ncu captures)")
     ap.add_argument("--launch", default="4,1,0",
                     help="validation launch of --profile-leg: warps per block, order, fine stage")

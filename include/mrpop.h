@@ -257,6 +257,16 @@ mrpop_status mrpop_autotune_cache_save(const char *path);
 mrpop_status mrpop_autotune_cache_load(const char *path);
 mrpop_status mrpop_autotune_cache_clear(void);
 
+/* Counters of the library's stream-ordered scratch pool on the current
+ * device (host int64 [3]): bytes in use, the high-water mark of bytes in use,
+ * bytes reserved from the device.  The library takes every temporary device
+ * buffer (split-tree NEAREST partials, the ordering arena of large NEAREST
+ * batches, NEIGHBORS partials, path-cost partials, planner staging) from
+ * this pool, which keeps up to 1 GiB of freed memory across
+ * synchronisations.  reset_high 1 resets the high-water mark after reading
+ * it.  A diagnostic with no paper counterpart.  Errors: EINVAL (NULL), ECUDA. */
+mrpop_status mrpop_scratch_stats(int32_t reset_high, int64_t *stats);
+
 /* Times mrpop_nearest_ex on the caller's inputs with the budget-ordered path
  * split into 2, 4 or 8 waves of (query block, tree slice) pieces per SM
  * capacity, keeps the fastest for calls of this shape and filter, and

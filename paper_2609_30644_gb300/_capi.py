@@ -59,6 +59,7 @@ EXPORTS = (
     "mrpop_neighbors_autotune",
     "mrpop_server_cancel",
     "mrpop_server_inject",
+    "mrpop_scratch_stats",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -141,6 +142,7 @@ def _load() -> C.CDLL:
                                            vp]),
         "mrpop_server_cancel": (i32, [vp, i64]),
         "mrpop_server_inject": (i32, [vp, i32, i64]),
+        "mrpop_scratch_stats": (i32, [i32, vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)

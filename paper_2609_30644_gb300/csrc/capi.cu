@@ -86,6 +86,47 @@ std::string validate_tune_key(const mrpop_problem *p) {
     return k.str();
 }
 
+// ---------------------------------------------------------------------------
+// Stream-ordered scratch from a library-owned memory pool per device.  The
+// device's default pool returns freed memory to the system at every
+// synchronisation, so a call that follows one would map its scratch again
+// (about 0.1 ms for a NEAREST batch); this pool keeps up to 1 GiB of it.
+// ---------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaError_t scratch_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        unsigned long long keep = 1ull << 30;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) !=
+            cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = scratch_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
 static bool finite_all(const float *v, int64_t n) {
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(v[i])) return false;
@@ -638,6 +679,25 @@ extern "C" mrpop_status mrpop_autotune_cache_load(const char *path) {
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (auto &kv : add) g_tune[kv.first] = kv.second;
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_scratch_stats(int32_t reset_high, int64_t *stats) {
+    if (!stats) return set_error(MRPOP_EINVAL, "mrpop_scratch_stats: stats is NULL");
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(&pool);
+    if (e != cudaSuccess) return cuda_error(e, "mrpop_scratch_stats");
+    unsigned long long v[3] = {0, 0, 0};
+    if ((e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v[0])) != cudaSuccess ||
+        (e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v[1])) != cudaSuccess ||
+        (e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v[2])) != cudaSuccess)
+        return cuda_error(e, "mrpop_scratch_stats");
+    for (int i = 0; i < 3; ++i) stats[i] = (int64_t)v[i];
+    if (reset_high) {
+        unsigned long long zero = 0;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero)) != cudaSuccess)
+            return cuda_error(e, "mrpop_scratch_stats");
+    }
     return MRPOP_OK;
 }
 

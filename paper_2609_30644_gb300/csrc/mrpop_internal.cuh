@@ -132,6 +132,10 @@ void tune_store(const std::string &key, const std::vector<int> &val);
 std::string validate_tune_key(const mrpop_problem *p);
 int log2_bucket(int64_t n);
 
+// Stream-ordered scratch from the library's memory pool on the current device
+// (keeps freed memory across synchronisations); free with cudaFreeAsync.
+cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st);
+
 // Thread-local error reporting.
 mrpop_status set_error(mrpop_status st, const char *fmt, ...);
 mrpop_status cuda_error(cudaError_t e, const char *what);

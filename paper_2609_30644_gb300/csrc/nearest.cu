@@ -155,7 +155,7 @@ mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const flo
     splits = std::max(1, (N + chunk - 1) / chunk);
     Best *partial = nullptr;
     if (splits > 1)
-        MRPOP_CUDA_TRY(cudaMallocAsync((void **)&partial, sizeof(Best) * (size_t)splits * Q, st));
+        MRPOP_CUDA_TRY(scratch_alloc((void **)&partial, sizeof(Best) * (size_t)splits * Q, st));
     dim3 grid(groups, splits);
     nearest_kernel<DP><<<grid, kNNThreads, 0, st>>>(tree, N, ld, dim, queries, budgets, Q, chunk,
                                                     out_idx, partial);
@@ -1451,7 +1451,7 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     const size_t b_part = align(sizeof(Best) * (size_t)splits * Q);
     const size_t b_seed = align(sizeof(float) * (size_t)Q);
     char *arena = nullptr;
-    MRPOP_CUDA_TRY(cudaMallocAsync((void **)&arena,
+    MRPOP_CUDA_TRY(scratch_alloc((void **)&arena,
                                    b_state + b_tree + b_perm + b_q + b_c + b_qp + b_cut + b_part +
                                        b_seed,
                                    st));
@@ -1799,7 +1799,7 @@ mrpop_status launch_neighbors(const float *tree, int64_t N, int64_t ld, int dim,
     const int nr = (int)((N + chunk - 1) / chunk);
     int64_t *part = nullptr;
     const size_t kidx = (size_t)Q * nr * (size_t)std::max<int64_t>(k_max, 1);
-    MRPOP_CUDA_TRY(cudaMallocAsync((void **)&part, sizeof(int64_t) * (kidx + (size_t)Q * nr), st));
+    MRPOP_CUDA_TRY(scratch_alloc((void **)&part, sizeof(int64_t) * (kidx + (size_t)Q * nr), st));
     neighbors_kernel<<<dim3(blocks, nr), kNbWarps * 32, smem, st>>>(
         tree, (int)N, ld, dim, queries, (int)Q, delta, k_max, part, part + kidx, chunk);
     neighbors_merge<<<(int)((Q + 127) / 128), 128, 0, st>>>(part, part + kidx, nr, (int)Q, k_max,
@@ -1823,7 +1823,7 @@ mrpop_status launch_path_cost(const float *path, int64_t M, int dim, double *out
     const int64_t chunk = (segs + blocks - 1) / blocks;
     blocks = (int)((segs + chunk - 1) / chunk);
     double *partial = nullptr;
-    MRPOP_CUDA_TRY(cudaMallocAsync((void **)&partial, sizeof(double) * blocks, st));
+    MRPOP_CUDA_TRY(scratch_alloc((void **)&partial, sizeof(double) * blocks, st));
     path_cost_kernel<<<blocks, threads, 0, st>>>(path, M, dim, chunk, partial);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {

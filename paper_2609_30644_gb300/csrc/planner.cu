@@ -1169,9 +1169,9 @@ static mrpop_status roadmap_round_jobs(const std::vector<Planner *> &pls, cudaSt
     RmJob *d_jobs = nullptr;
     VParams *d_vp = nullptr;
     int *d_out = nullptr;
-    PL_TRY(cudaMallocAsync(&d_jobs, sizeof(RmJob) * nj, st));
-    PL_TRY(cudaMallocAsync(&d_vp, sizeof(VParams) * 2 * nj, st));
-    PL_TRY(cudaMallocAsync(&d_out, sizeof(int) * 2 * nj, st));
+    PL_TRY(scratch_alloc((void **)&d_jobs, sizeof(RmJob) * nj, st));
+    PL_TRY(scratch_alloc((void **)&d_vp, sizeof(VParams) * 2 * nj, st));
+    PL_TRY(scratch_alloc((void **)&d_out, sizeof(int) * 2 * nj, st));
     struct Release {
         void *a, *b, *c;
         cudaStream_t s;
@@ -2326,8 +2326,8 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
     }
     PState *d_states = nullptr;
     unsigned long long *d_aux = nullptr;  // [0] start time, [1] finished | timeout << 32
-    PL_TRY(cudaMallocAsync(&d_states, sizeof(PState) * n, st));
-    PL_TRY(cudaMallocAsync(&d_aux, sizeof(unsigned long long) * 2, st));
+    PL_TRY(scratch_alloc((void **)&d_states, sizeof(PState) * n, st));
+    PL_TRY(scratch_alloc((void **)&d_aux, sizeof(unsigned long long) * 2, st));
     struct Release {
         void *a, *b;
         cudaStream_t s;
@@ -2962,7 +2962,7 @@ extern "C" mrpop_status mrpop_planner_nearest_pass(const float *tree, int64_t n_
     const size_t b_q = sizeof(float) * (size_t)dim * kStepIters;
     const size_t b_c = sizeof(float) * kStepIters;
     char *arena = nullptr;
-    PL_TRY(cudaMallocAsync((void **)&arena, b_slot + b_ctrl + 256 + b_q + b_c +
+    PL_TRY(scratch_alloc((void **)&arena, b_slot + b_ctrl + 256 + b_q + b_c +
                                                 sizeof(int64_t) * kStepIters, st));
     Slot *d_slot = (Slot *)arena;
     Ctrl *d_ctrl = (Ctrl *)(arena + b_slot);
@@ -3029,7 +3029,7 @@ extern "C" mrpop_status mrpop_planner_neighbors_pass(const float *V, int64_t n_v
     cudaStream_t st = (cudaStream_t)stream;
     char *arena = nullptr;
     const size_t b_job = 256 * ((sizeof(RmJob) + 255) / 256);
-    PL_TRY(cudaMallocAsync((void **)&arena, b_job + 256, st));
+    PL_TRY(scratch_alloc((void **)&arena, b_job + 256, st));
     RmJob *d_job = (RmJob *)arena;
     int *d_count = (int *)(arena + b_job);
     RmJob J{};

@@ -13,11 +13,11 @@ show), and must return identical indices -- the tolerance of the NEAREST tests
 for two GPU results: the key (distance, g, index) is a total order, so how the
 tree is split across blocks cannot change the answer.  A second test checks
 the defining property itself: after a warm-up call, a call of the no-alloc
-entry point leaves the device's stream-ordered memory pool (its high-water
-mark), torch's caching allocator and the device's free memory unchanged,
-while the same check does see mrpop_nearest's split-tree scratch (a positive
-control).  This file is collected last and also passes when run on its own
-in a fresh process.
+entry point leaves the library's scratch pool and the device's default
+stream-ordered pool (their high-water marks), torch's caching allocator and
+the device's free memory unchanged, while the same check does see
+mrpop_nearest's split-tree scratch (a positive control).  This file is
+collected last and also passes when run on its own in a fresh process.
 """
 import ctypes
 
@@ -93,19 +93,29 @@ class _Pool:
         return free.value
 
 
-def _allocations_during(fn):
+def _scratch(lib, reset_high):
+    """The library's scratch pool on this device: (in use, high-water mark)."""
+    v = (ctypes.c_int64 * 3)()
+    assert lib.mrpop_scratch_stats(int(reset_high), v) == 0
+    return v[0], v[1]
+
+
+def _allocations_during(lib, fn):
     """Runs fn (one library call, then a synchronize) and returns the growth of
-    the pool's high-water mark over its use before, the change of torch's
-    allocation count and the change of the device's free memory."""
+    the pools' high-water marks (the library's scratch pool plus the device's
+    default pool) over their use before, the change of torch's allocation
+    count and the change of the device's free memory."""
     pool = _Pool()
     torch.cuda.synchronize()
     pool.reset_high()
     used0 = pool.get(_Pool.USED_MEM_CURRENT)
+    lib_used0, _ = _scratch(lib, reset_high=True)
     torch_allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
     free0 = pool.free_bytes()
     fn()
     torch.cuda.synchronize()
-    return (pool.get(_Pool.USED_MEM_HIGH) - used0,
+    _, lib_high = _scratch(lib, reset_high=False)
+    return (pool.get(_Pool.USED_MEM_HIGH) - used0 + lib_high - lib_used0,
             torch.cuda.memory_stats().get("allocation.all.allocated", 0) - torch_allocs0,
             free0 - pool.free_bytes())
 
@@ -121,12 +131,12 @@ def test_noalloc_allocates_nothing(lib):
     torch.cuda.synchronize()
     # positive control: the split-tree scratch of mrpop_nearest shows in the pool
     pool_grew, _, _ = _allocations_during(
-        lambda: _call(lib.mrpop_nearest, tree, qs, cs, ref, N))
+        lib, lambda: _call(lib.mrpop_nearest, tree, qs, cs, ref, N))
     assert pool_grew > 0, "the check does not see stream-ordered scratch"
     # the no-alloc entry point, twice: nothing from the pool, torch or cudaMalloc
     for _ in range(2):
         pool_grew, torch_allocs, free_drop = _allocations_during(
-            lambda: _call(lib.mrpop_nearest_noalloc, tree, qs, cs, got, N))
+            lib, lambda: _call(lib.mrpop_nearest_noalloc, tree, qs, cs, got, N))
         # (free memory may rise when the pool trims what the control left)
         assert pool_grew == 0 and torch_allocs == 0 and free_drop <= 0, \
             (pool_grew, torch_allocs, free_drop)
