@@ -555,7 +555,7 @@ def run_profile_leg(args) -> None:
     launch), then W warm-up and K timed launches on the free set;
     validate-mixed: W + K launches on the step's mixed batch; nearest (FP32
     filter) and nearest-tensor: W + K NEAREST calls (one filter launch each).  The validation launch shape is
-    --launch (warps per block, order, fine stage).  Prints one JSON line with
+    --launch (warps per block, order, fine stage, optional register budget).  Prints one JSON line with
     the mean time of the timed launches."""
     import numpy as np
     import torch
@@ -566,9 +566,9 @@ def run_profile_leg(args) -> None:
     torch.cuda.set_device(dev)
     scene, x = make_inputs(0)
     stream = torch.cuda.current_stream()
-    w, o, f = (int(v) for v in args.launch.split(","))
+    w, o, f, *r = (int(v) for v in args.launch.split(","))
     with mp.Problem(scene, resolution=RES, margin=MARGIN) as prob:
-        mp.set_launch(prob, w, o, f)
+        mp.set_launch(prob, w, o, f, registers=r[0] if r else 0)
         if args.profile_leg == "validate-free":
             cqa, cqb = _synth.candidate_edges(scene, 3 * E_EDGES, seed=1000)
             cqa_d, cqb_d = torch.from_numpy(cqa).to(dev), torch.from_numpy(cqb).to(dev)
@@ -1061,8 +1061,9 @@ def main():
     ap.add_argument("--profile-leg", choices=["validate-free", "validate-mixed", "nearest",
                                               "nearest-tensor"],
                     default=None, help="run one kernel's leg alone (for ncu captures)")
-    ap.add_argument("--launch", default="4,1,0",
-                    help="validation launch of --profile-leg: warps per block, order, fine stage")
+    ap.add_argument("--launch", default="4,0,0",
+                    help="validation launch of --profile-leg: warps per block, order, fine "
+                         "stage[, register budget]")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
