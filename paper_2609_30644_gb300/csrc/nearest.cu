@@ -331,9 +331,12 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
     constexpr float kC1 = 4.f * (DIM + 2.f) * kU;  // exact-distance relative error
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane >> 2, tig = lane & 3;
-    const int qb = blockIdx.x * kTcQueries;
+    // query blocks in descending budget order: the blocks with the longest
+    // tree prefixes start first and the short ones fill the last wave
+    const int qblk = gridDim.x - 1 - blockIdx.x;
+    const int qb = qblk * kTcQueries;
     const int vs = blockIdx.y * chunk;
-    const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
+    const int ve = min(min(N, cut[qblk]), vs + chunk);
     if (vs >= ve) return;  // no partial record: the reduce skips this slice
     const bool exact_only = *exhaustive != 0;
 
@@ -594,9 +597,12 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
     constexpr float kC1 = 4.f * (DIM + 2.f) * kU;  // exact-distance relative error
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane >> 2, tig = lane & 3;
-    const int qb = blockIdx.x * kTcQueries;
+    // query blocks in descending budget order: the blocks with the longest
+    // tree prefixes start first and the short ones fill the last wave
+    const int qblk = gridDim.x - 1 - blockIdx.x;
+    const int qb = qblk * kTcQueries;
     const int vs = blockIdx.y * chunk;
-    const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
+    const int ve = min(min(N, cut[qblk]), vs + chunk);
     if (vs >= ve) return;  // no partial record: the reduce skips this slice
 
     // power-of-two scale: largest magnitude in [2^(ex-1), 2^ex) -> [8, 16)
@@ -827,10 +833,17 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
 // and a pair passes when acc <= T_q, a per-query threshold with |q|^2 taken
 // out.  The ordering pass stores xn as an extra row of the ordered tree.  A
 // thread owns 8 queries x 8 vertices of each 64-vertex step (a register tile
-// of 64 accumulators); the operands are read as float4 from dimension-major
-// shared arrays, 4 shared loads per 64 FMAs, every load a broadcast or one
-// conflict-free 128-byte row.  Warp lanes 8 ty' + tx share the queries of ty
-// (8 lanes) and the vertex columns of tx.  Tree tiles come in by cp.async
+// of 64 accumulators); the operands are read as 16-byte vectors from
+// dimension-major shared arrays, every load a broadcast or one conflict-free
+// row.  For 8 <= D <= 21 the tile is updated with packed FP32 FMAs (fma.rn.f32x2:
+// two IEEE single-precision FMAs per instruction, each rounded as fmaf, so
+// the accumulators are bit-identical to the scalar chain): the multipliers
+// -2 q_d are kept twice in shared memory, {a, a}, and pair with two adjacent
+// vertex columns, 6 shared loads per 32 packed FMAs (64 FMAs).  That halves
+// the instructions the FMA chain issues; the pipe's FMA rate is unchanged, so
+// the other instructions of the scan fit in the issue slots it frees.  Warp
+// lanes 8 ty' + tx share the queries of ty (8 lanes) and the vertex columns
+// of tx.  Tree tiles come in by cp.async
 // into a double buffer, one barrier per tile; the running best of each
 // (thread, query) sits in shared memory and is touched only when a pair
 // passes, so that two blocks (16 warps) stay resident per SM.
@@ -855,18 +868,34 @@ constexpr int kF32Step = 64;                     // vertices per register-tile s
 
 template <int DIM>
 struct F32Shape {
+    // packed FMAs (the multipliers kept twice) where two blocks still fit and
+    // the tile's registers do not spill (they do below 8 dimensions)
+    static constexpr bool PACKED = DIM >= 8 && DIM <= 21;
     // vertices per shared-memory tile: two blocks of 256 threads fit an SM
-    static constexpr int VT = DIM <= 14 ? 256 : DIM <= 21 ? 128 : 64;
+    static constexpr int VT = DIM <= 14 ? 256 : (DIM <= 21 && !PACKED) ? 128 : 64;
     static constexpr int ROWS = DIM + 2;              // x_d, g, folded |x|^2
+    static constexpr int AM = PACKED ? 2 : 1;         // copies of each -2 q_d
 };
 
 template <int DIM>
 constexpr size_t f32_smem_bytes() {
-    // -2 q [DIM][256], q [DIM][256], two tiles [ROWS][VT], best d2, best
-    // position and bound [8][256] each
-    return sizeof(float) * ((size_t)2 * DIM * kTcQueries + (size_t)2 * F32Shape<DIM>::ROWS *
-                                                               F32Shape<DIM>::VT +
+    // -2 q [DIM][256] (twice when packed), q [DIM][256], two tiles
+    // [ROWS][VT], best d2, best position and bound [8][256] each
+    return sizeof(float) * ((size_t)(F32Shape<DIM>::AM + 1) * DIM * kTcQueries +
+                            (size_t)2 * F32Shape<DIM>::ROWS * F32Shape<DIM>::VT +
                             (size_t)3 * 8 * kTcQueries);
+}
+
+typedef unsigned long long f32x2_t;  // two floats, the first in the low half
+
+__device__ __forceinline__ f32x2_t fma_f32x2(f32x2_t a, f32x2_t b, f32x2_t c) {
+    f32x2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float f32x2_lo(f32x2_t v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f32x2_hi(f32x2_t v) {
+    return __uint_as_float((unsigned)(v >> 32));
 }
 
 // Source of the padding columns' folded norms: +inf never passes the filter.
@@ -888,11 +917,13 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
                    Best *__restrict__ partial, const int *__restrict__ perm,
                    const int *__restrict__ cut, float *__restrict__ seed,
                    const int *__restrict__ exact_only_flag) {
-    constexpr int VT = F32Shape<DIM>::VT, ROWS = F32Shape<DIM>::ROWS;
+    constexpr int VT = F32Shape<DIM>::VT, ROWS = F32Shape<DIM>::ROWS, AM = F32Shape<DIM>::AM;
     extern __shared__ __align__(16) float f32_sm[];
-    float(*am)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(f32_sm);
-    float(*qsm)[kTcQueries] = reinterpret_cast<float(*)[kTcQueries]>(f32_sm + DIM * kTcQueries);
-    float *tiles = f32_sm + 2 * DIM * kTcQueries;                 // [2][ROWS][VT]
+    // -2 q_d of query j at am[d][AM j .. AM j + AM - 1]
+    float(*am)[AM * kTcQueries] = reinterpret_cast<float(*)[AM * kTcQueries]>(f32_sm);
+    float(*qsm)[kTcQueries] =
+        reinterpret_cast<float(*)[kTcQueries]>(f32_sm + AM * DIM * kTcQueries);
+    float *tiles = f32_sm + (AM + 1) * DIM * kTcQueries;          // [2][ROWS][VT]
     float(*sb_d2)[kTcQueries] =
         reinterpret_cast<float(*)[kTcQueries]>(tiles + 2 * ROWS * VT);  // [8][256]
     int(*sb_pos)[kTcQueries] = reinterpret_cast<int(*)[kTcQueries]>(sb_d2 + 8);
@@ -906,9 +937,12 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     constexpr float kG = kF32G * (DIM + 2.f);             // gamma
     const int tid = threadIdx.x;
     const int ty = tid >> 3, tx = tid & 7;
-    const int qb = blockIdx.x * kTcQueries;
+    // query blocks in descending budget order: the blocks with the longest
+    // tree prefixes start first and the short ones fill the last wave
+    const int qblk = gridDim.x - 1 - blockIdx.x;
+    const int qb = qblk * kTcQueries;
     const int vs = blockIdx.y * chunk;
-    const int ve = min(min(N, cut[blockIdx.x]), vs + chunk);
+    const int ve = min(min(N, cut[qblk]), vs + chunk);
     if (vs >= ve) return;  // no partial record: the reduce skips this slice
     const bool exact_only = *exact_only_flag != 0;
     unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
@@ -937,7 +971,10 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const float v = qsm[d][j];
-            am[d][j] = -2.f * v;
+            if constexpr (AM == 2)
+                *reinterpret_cast<float2 *>(&am[d][2 * j]) = make_float2(-2.f * v, -2.f * v);
+            else
+                am[d][j] = -2.f * v;
             n2 = fmaf(v, v, n2);
         }
         qn_s[j] = n2;
@@ -998,7 +1035,39 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
         for (int s = 0; s < steps; ++s) {
             const int c0 = s * kF32Step + tx * 4;  // columns c0..c0+3 and c0+32..c0+35
             float acc[8][8];
-            {
+            if constexpr (AM == 2) {
+                // pairs of adjacent columns: p = 0, 1 -> c0 + 2p, 2 -> c0 + 32, 3 -> c0 + 34
+                const ulonglong2 n0 = *reinterpret_cast<const ulonglong2 *>(&xs[DIM + 1][c0]);
+                const ulonglong2 n1 = *reinterpret_cast<const ulonglong2 *>(&xs[DIM + 1][c0 + 32]);
+                const f32x2_t xn[4] = {n0.x, n0.y, n1.x, n1.y};
+                f32x2_t acc2[8][4];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    // {a, a} of rows 0-1, 2-3 (queries 4 ty ..) and 4-5, 6-7 (128 + 4 ty ..)
+                    const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(&am[d][8 * ty]);
+                    const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(&am[d][8 * ty + 4]);
+                    const ulonglong2 a2 =
+                        *reinterpret_cast<const ulonglong2 *>(&am[d][256 + 8 * ty]);
+                    const ulonglong2 a3 =
+                        *reinterpret_cast<const ulonglong2 *>(&am[d][256 + 8 * ty + 4]);
+                    const ulonglong2 x0 = *reinterpret_cast<const ulonglong2 *>(&xs[d][c0]);
+                    const ulonglong2 x1 = *reinterpret_cast<const ulonglong2 *>(&xs[d][c0 + 32]);
+                    const f32x2_t a[8] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y, a3.x, a3.y};
+                    const f32x2_t x[4] = {x0.x, x0.y, x1.x, x1.y};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+                            acc2[r][p] = fma_f32x2(a[r], x[p], d == 0 ? xn[p] : acc2[r][p]);
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        acc[r][2 * p] = f32x2_lo(acc2[r][p]);
+                        acc[r][2 * p + 1] = f32x2_hi(acc2[r][p]);
+                    }
+            } else {
                 const float4 n0 = *reinterpret_cast<const float4 *>(&xs[DIM + 1][c0]);
                 const float4 n1 = *reinterpret_cast<const float4 *>(&xs[DIM + 1][c0 + 32]);
                 const float xn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
