@@ -292,6 +292,47 @@ __device__ __forceinline__ float tc_slice_gmin(const float *__restrict__ tree, i
 // with the best of its own vertex columns, as a position in the g order:
 // translate to original indices (perm), combine by key, and let lane
 // tig == 0 write the slice's partial bests.
+// Where a budget-ordered filter block finishes its query block: the slice
+// blocks of query block b count themselves in qdone[b]; the last one to
+// finish reduces the partial bests of every slice, best key first, and writes
+// the original query's index.
+struct NnFinish {
+    int *qdone;            // [query blocks] slices finished (zero before the filter)
+    const int *qperm;      // ordered query -> original query index
+    int64_t *out_idx;      // [Q] by original query index
+};
+
+// No slice of the block has work (its cut is empty): no query of it has an
+// admissible vertex.
+__device__ __forceinline__ void nn_write_none(const NnFinish &fin, int qb, int Q) {
+    for (int j = threadIdx.x; j < kTcQueries; j += blockDim.x)
+        if (qb + j < Q) fin.out_idx[fin.qperm[qb + j]] = -1;
+}
+
+// Called by every thread of a slice block after its partial bests are
+// written; ns = slice blocks of this query block that have work.
+__device__ __forceinline__ void nn_finish(const Best *partial, const NnFinish &fin, int qblk,
+                                          int ns, int qb, int Q) {
+    __shared__ int s_last;
+    __threadfence();  // this thread's partial records, before the count
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(fin.qdone + qblk, 1) == ns - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < kTcQueries; j += blockDim.x) {
+        const int q = qb + j;
+        if (q >= Q) continue;
+        Best b{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
+        for (int y = 0; y < ns; ++y) {
+            const Best *rec = partial + (size_t)y * Q + q;
+            const Best o{__ldcg(&rec->d2), __ldcg(&rec->g), __ldcg(&rec->idx)};
+            if (better(o, b)) b = o;
+        }
+        fin.out_idx[fin.qperm[q]] = b.idx;
+    }
+}
+
 template <typename RowQ>
 __device__ __forceinline__ void tc_write_rows(Best (&best)[4], const int *__restrict__ perm,
                                               RowQ row_q, int Q, Best *__restrict__ partial) {
@@ -320,7 +361,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
                   const float *__restrict__ budgets, int Q, int chunk,
                   Best *__restrict__ partial, const int *__restrict__ perm,
                   const int *__restrict__ cut, float *__restrict__ seed,
-                  const int *__restrict__ exhaustive) {
+                  const int *__restrict__ exhaustive, NnFinish fin) {
     using S = TcShape<DIM>;
     constexpr int K = S::K, KS = S::KS, CH = S::CH, VT = S::VT;
     __shared__ __align__(16) float xt[VT * K];  // vertex rows, swizzled chunks
@@ -335,9 +376,13 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
     // tree prefixes start first and the short ones fill the last wave
     const int qblk = gridDim.x - 1 - blockIdx.x;
     const int qb = qblk * kTcQueries;
+    const int cut_q = min(N, cut[qblk]);
     const int vs = blockIdx.y * chunk;
-    const int ve = min(min(N, cut[qblk]), vs + chunk);
-    if (vs >= ve) return;  // no partial record: the reduce skips this slice
+    const int ve = min(cut_q, vs + chunk);
+    if (vs >= ve) {  // no partial record: this slice is not counted
+        if (blockIdx.y == 0) nn_write_none(fin, qb, Q);
+        return;
+    }
     const bool exact_only = *exhaustive != 0;
 
     tc_stage_queries<DIM>(qsm, queries, Q, qb);
@@ -556,6 +601,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
         }
     }
     tc_write_rows(best, perm, row_q, Q, partial);
+    nn_finish(partial, fin, qblk, (cut_q + chunk - 1) / chunk, qb, Q);
 }
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
@@ -585,7 +631,8 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
                     const float *__restrict__ budgets, int Q, int chunk,
                     Best *__restrict__ partial, const int *__restrict__ perm,
                     const int *__restrict__ cut, float *__restrict__ seed,
-                    const unsigned *__restrict__ maxabs, const int *__restrict__ nonfinite) {
+                    const unsigned *__restrict__ maxabs, const int *__restrict__ nonfinite,
+                    NnFinish fin) {
     static_assert(DIM + 2 <= 16, "FP16 filter holds K = 16");
     constexpr int VT = kTcThreads;                   // vertices per tile
     __shared__ __align__(16) unsigned xh[VT * 8];    // FP16 rows, swizzled chunks
@@ -601,9 +648,13 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
     // tree prefixes start first and the short ones fill the last wave
     const int qblk = gridDim.x - 1 - blockIdx.x;
     const int qb = qblk * kTcQueries;
+    const int cut_q = min(N, cut[qblk]);
     const int vs = blockIdx.y * chunk;
-    const int ve = min(min(N, cut[qblk]), vs + chunk);
-    if (vs >= ve) return;  // no partial record: the reduce skips this slice
+    const int ve = min(cut_q, vs + chunk);
+    if (vs >= ve) {  // no partial record: this slice is not counted
+        if (blockIdx.y == 0) nn_write_none(fin, qb, Q);
+        return;
+    }
 
     // power-of-two scale: largest magnitude in [2^(ex-1), 2^ex) -> [8, 16)
     int ex = 0;
@@ -822,6 +873,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
         }
     }
     tc_write_rows(best, perm, row_q, Q, partial);
+    nn_finish(partial, fin, qblk, (cut_q + chunk - 1) / chunk, qb, Q);
 }
 
 // ---------------------------------------------------------------------------
@@ -916,7 +968,7 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
                    const float *__restrict__ budgets, int Q, int chunk,
                    Best *__restrict__ partial, const int *__restrict__ perm,
                    const int *__restrict__ cut, float *__restrict__ seed,
-                   const int *__restrict__ exact_only_flag) {
+                   const int *__restrict__ exact_only_flag, NnFinish fin) {
     constexpr int VT = F32Shape<DIM>::VT, ROWS = F32Shape<DIM>::ROWS, AM = F32Shape<DIM>::AM;
     extern __shared__ __align__(16) float f32_sm[];
     // -2 q_d of query j at am[d][AM j .. AM j + AM - 1]
@@ -941,9 +993,13 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     // tree prefixes start first and the short ones fill the last wave
     const int qblk = gridDim.x - 1 - blockIdx.x;
     const int qb = qblk * kTcQueries;
+    const int cut_q = min(N, cut[qblk]);
     const int vs = blockIdx.y * chunk;
-    const int ve = min(min(N, cut[qblk]), vs + chunk);
-    if (vs >= ve) return;  // no partial record: the reduce skips this slice
+    const int ve = min(cut_q, vs + chunk);
+    if (vs >= ve) {  // no partial record: this slice is not counted
+        if (blockIdx.y == 0) nn_write_none(fin, qb, Q);
+        return;
+    }
     const bool exact_only = *exact_only_flag != 0;
     unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
 
@@ -1181,6 +1237,7 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
         const int q = qb + ql(r);
         if (tx == 0 && q < Q) partial[(size_t)blockIdx.y * Q + q] = b;
     }
+    nn_finish(partial, fin, qblk, (cut_q + chunk - 1) / chunk, qb, Q);
 }
 
 // ---------------------------------------------------------------------------
@@ -1199,6 +1256,7 @@ struct SortState {
     int exact_only;                      // a coordinate lies outside the TF32 filter's range
     int nonfinite;                       // a coordinate is NaN or infinite
     unsigned maxabs;                     // largest finite coordinate magnitude (float bits)
+    int arrive;                          // histogram blocks done (the last one scans)
     int tree_off[kSortBuckets + 1];      // bucket starts of the g-ordered tree
     int tree_cur[kSortBuckets];
     int query_off[kSortBuckets + 1];
@@ -1226,16 +1284,49 @@ __device__ __forceinline__ void g_scale(const SortState &S, float *lo, float *sc
     *scale = b > a ? (float)kSortBuckets / (b - a) : 0.f;
 }
 
-__global__ void sort_init(SortState *S) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        S->gmin = 0x7fffffff;
-        S->gmax = (int)0x80000000;
+// First pass of a call: resets the sort state and the filter's per-query-block
+// slice counters, and (with_range) finds the finite range of g in the same
+// single block; larger trees take sort_range after it.
+constexpr int kSetupThreads = 1024;
+constexpr int kSetupRangeMax = 1 << 17;  // largest N whose range the setup block finds
+
+__global__ void __launch_bounds__(kSetupThreads)
+sort_setup(const float *__restrict__ g, int N, SortState *S, int *__restrict__ qdone,
+           int qblocks, int with_range) {
+    __shared__ int red_lo[kSetupThreads / 32], red_hi[kSetupThreads / 32];
+    const int t = threadIdx.x;
+    for (int i = t; i <= kSortBuckets; i += kSetupThreads) S->tree_off[i] = S->query_off[i] = 0;
+    for (int i = t; i < qblocks; i += kSetupThreads) qdone[i] = 0;
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    if (with_range) {
+        for (int v = t; v < N; v += kSetupThreads) {
+            const float x = g[v];
+            if (fabsf(x) <= FLT_MAX) {
+                lo = min(lo, fkey(x));
+                hi = max(hi, fkey(x));
+            }
+        }
+        lo = __reduce_min_sync(kFull, lo);
+        hi = __reduce_max_sync(kFull, hi);
+        if ((t & 31) == 0) {
+            red_lo[t >> 5] = lo;
+            red_hi[t >> 5] = hi;
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int w = 1; w < kSetupThreads / 32; ++w) {
+                lo = min(lo, red_lo[w]);
+                hi = max(hi, red_hi[w]);
+            }
+    }
+    if (t == 0) {
+        S->gmin = lo;  // empty finite range: gmin > gmax
+        S->gmax = hi;
         S->exact_only = 0;
         S->nonfinite = 0;
         S->maxabs = 0u;
+        S->arrive = 0;
     }
-    if (i <= kSortBuckets) S->tree_off[i] = S->query_off[i] = 0;
 }
 
 __global__ void sort_range(const float *__restrict__ g, int N, SortState *S) {
@@ -1267,24 +1358,41 @@ __device__ __forceinline__ int grouped_add(int *counters, int b) {
     return base + __popc(grp & ((1u << lane) - 1u));
 }
 
-__global__ void sort_histogram(const float *__restrict__ g, int N, const float *__restrict__ c,
-                               int Q, SortState *S) {
+// Bucket counts of the tree's g and of the budgets; the last block to finish
+// turns both count arrays into bucket starts.
+constexpr int kHistThreads = 256;
+
+__global__ void __launch_bounds__(kHistThreads)
+sort_histogram(const float *__restrict__ g, int N, const float *__restrict__ c, int Q,
+               SortState *S) {
+    __shared__ int s_last;
+    __shared__ int part[kHistThreads / 32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float lo, scale;
     g_scale(*S, &lo, &scale);
     grouped_add(S->tree_off + 1, i < N ? sort_bucket(g[i], lo, scale) : -1);
     grouped_add(S->query_off + 1, i < Q ? sort_bucket(c[i], lo, scale) : -1);
-}
-
-// Inclusive scan of the shifted counts (one block of kSortBuckets threads):
-// off[b] becomes the start of bucket b; the cursors start there.
-__global__ void __launch_bounds__(kSortBuckets) sort_scan(SortState *S) {
-    __shared__ int part[kSortBuckets / 32];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&S->arrive, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // inclusive scan of the shifted counts: off[b] becomes the start of
+    // bucket b; each thread sums 4 consecutive buckets, then the block scans
+    // the 256 sums; the cursors start at the bucket starts
+    constexpr int kPer = kSortBuckets / kHistThreads;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     for (int which = 0; which < 2; ++which) {
         int *off = which ? S->query_off : S->tree_off;
         int *cur = which ? S->query_cur : S->tree_cur;
-        int x = off[t + 1];
+        int v[kPer], own = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            v[k] = __ldcg(off + 1 + kPer * t + k);
+            own += v[k];
+        }
+        int x = own;  // inclusive scan of the thread sums within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(kFull, x, o);
@@ -1292,13 +1400,15 @@ __global__ void __launch_bounds__(kSortBuckets) sort_scan(SortState *S) {
         }
         if (lane == 31) part[w] = x;
         __syncthreads();
-        int before = 0;
-        for (int k = 0; k < w; ++k) before += part[k];
-        __syncthreads();
-        off[t + 1] = x + before;
-        __syncthreads();
-        cur[t] = off[t];
-        __syncthreads();
+        int run = x - own;
+        for (int k = 0; k < w; ++k) run += part[k];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            cur[kPer * t + k] = run;  // start of bucket kPer t + k
+            run += v[k];
+            off[1 + kPer * t + k] = run;
+        }
+        __syncthreads();  // part is reused
     }
 }
 
@@ -1388,55 +1498,70 @@ __global__ void __launch_bounds__(256) sort_cut(const float *__restrict__ c_s, i
     }
 }
 
-// Seeding pass: for each (ordered) query, the smallest exact squared
-// distance (the kernel's own formula) among kSeedSamples evenly spaced vertices
-// of the g-ordered tree that are admissible for it; +inf when none is.
+// Seeding pass, one block per query block: for each (ordered) query, the
+// smallest exact squared distance (the filter's own formula) among
+// kSeedSamples evenly spaced vertices of the g-ordered tree that are
+// admissible for it (+inf when none is), four samples at a time; and the
+// block's cut, as sort_cut finds it.
 constexpr int kSeedSamples = 64;
 template <int DIM>
-__global__ void __launch_bounds__(128) nearest_seed(const float *__restrict__ tree_s, int N,
-                                                    const float *__restrict__ q_s,
-                                                    const float *__restrict__ c_s, int Q,
-                                                    float *__restrict__ seed) {
+__global__ void __launch_bounds__(kTcQueries)
+nearest_seed(const float *__restrict__ tree_s, int N, const float *__restrict__ q_s,
+             const float *__restrict__ c_s, int Q, const SortState *S, float *__restrict__ seed,
+             int *__restrict__ cut) {
     __shared__ float xs[DIM + 1][kSeedSamples];  // the sample vertices, g in the last row
+    __shared__ float red[kTcQueries / 32];
     const int n = min(N, kSeedSamples);
     for (int t = threadIdx.x; t < (DIM + 1) * kSeedSamples; t += blockDim.x) {
         const int d = t / kSeedSamples, k = t % kSeedSamples;
         xs[d][k] = k < n ? tree_s[(size_t)d * N + (int)(((int64_t)k * N) / n)] : 0.f;
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Q) return;
-    float q[DIM];
+    const int i = blockIdx.x * kTcQueries + threadIdx.x;
+    const float c = i < Q ? c_s[i] : -FLT_MAX;
+    if (i < Q) {
+        float q[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) q[d] = q_s[(size_t)d * Q + i];
-    const float c = c_s[i];
-    float best = FLT_MAX * 2.f;
-    for (int k = 0; k < n; ++k) {
-        const float g = xs[DIM][k];
-        if (!(g < c)) continue;
-        float d2 = 0.f;
+        for (int d = 0; d < DIM; ++d) q[d] = q_s[(size_t)d * Q + i];
+        float best = FLT_MAX * 2.f;
+        for (int k = 0; k < n; k += 4) {
+            float d2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const float a = q[d] - xs[d][k];
-            d2 = fmaf(a, a, d2);
+            for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float a = q[d] - xs[d][k + u];
+                    d2[u] = fmaf(a, a, d2[u]);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float g = xs[DIM][k + u];
+                if (k + u < n && g < c && g + __fsqrt_rn(d2[u]) < c) best = fminf(best, d2[u]);
+            }
         }
-        if (g + __fsqrt_rn(d2) < c) best = fminf(best, d2);
+        seed[i] = best;
     }
-    seed[i] = best;
-}
-
-__global__ void nearest_sorted_reduce(const Best *__restrict__ partial, const int *__restrict__ cut,
-                                      int chunk, int Q, int bq, const int *__restrict__ qperm,
-                                      int64_t *__restrict__ out_idx) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Q) return;
-    const int ns = (cut[i / bq] + chunk - 1) / chunk;
-    Best b{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
-    for (int s = 0; s < ns; ++s) {
-        const Best o = partial[(size_t)s * Q + i];
-        if (better(o, b)) b = o;
+    // the cut: up to the end of the bucket of the block's largest budget
+    float m = c;  // NaN budgets admit nothing and are ignored here
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kTcQueries / 32; ++k) m = fmaxf(m, red[k]);
+        float lo, scale;
+        g_scale(*S, &lo, &scale);
+        int nc;
+        if (S->gmin > S->gmax)
+            nc = 0;                                 // no finite g at all
+        else if (!(m > unkey(S->gmin)))
+            nc = 0;                                 // no vertex has g < m
+        else if (m > unkey(S->gmax))
+            nc = N;
+        else
+            nc = S->tree_off[sort_bucket(m, lo, scale) + 1];
+        cut[blockIdx.x] = nc;
     }
-    out_idx[qperm[i]] = b.idx;
 }
 
 // Pairs the budget-ordered pass scans: sum over query blocks of (queries in
@@ -1519,10 +1644,11 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     const size_t b_cut = align(sizeof(int) * (size_t)qblocks);
     const size_t b_part = align(sizeof(Best) * (size_t)splits * Q);
     const size_t b_seed = align(sizeof(float) * (size_t)Q);
+    const size_t b_qdone = align(sizeof(int) * (size_t)qblocks);
     char *arena = nullptr;
     MRPOP_CUDA_TRY(scratch_alloc((void **)&arena,
                                    b_state + b_tree + b_perm + b_q + b_c + b_qp + b_cut + b_part +
-                                       b_seed,
+                                       b_seed + b_qdone,
                                    st));
     char *at = arena;
     auto take = [&](size_t b) { char *r = at; at += b; return r; };
@@ -1535,16 +1661,20 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     int *cut = (int *)take(b_cut);
     Best *partial = (Best *)take(b_part);
     float *seed = (float *)take(b_seed);
+    int *qdone = (int *)take(b_qdone);
     const int n_max = std::max(N, Q);
     const float *g = tree + (size_t)DIM * ld;
-    sort_init<<<(kSortBuckets + 256) / 256, 256, 0, st>>>(S);
-    sort_range<<<(N + 255) / 256, 256, 0, st>>>(g, N, S);
-    sort_histogram<<<(n_max + 255) / 256, 256, 0, st>>>(g, N, budgets, Q, S);
-    sort_scan<<<1, kSortBuckets, 0, st>>>(S);
+    // five launches: setup (+ range), histogram (+ scan), scatter, seed (+
+    // cut), filter (+ reduce in each query block's last slice)
+    const bool setup_range = N <= kSetupRangeMax;
+    sort_setup<<<1, kSetupThreads, 0, st>>>(g, N, S, qdone, qblocks, setup_range ? 1 : 0);
+    if (!setup_range) sort_range<<<(N + 255) / 256, 256, 0, st>>>(g, N, S);
+    sort_histogram<<<(n_max + kHistThreads - 1) / kHistThreads, kHistThreads, 0, st>>>(
+        g, N, budgets, Q, S);
     sort_scatter<<<(n_max + 255) / 256, 256, 0, st>>>(tree, N, ld, DIM, queries, budgets, Q, S,
                                                        tree_s, perm, q_s, c_s, qperm);
-    sort_cut<<<qblocks, 256, 0, st>>>(c_s, Q, bq, S, N, cut);
     if (!out_idx) {
+        sort_cut<<<qblocks, 256, 0, st>>>(c_s, Q, bq, S, N, cut);
         unsigned long long *d_pairs = (unsigned long long *)seed;  // 8 bytes of the arena
         unsigned long long h = 0;
         cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st);
@@ -1557,20 +1687,19 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
         *pairs = (int64_t)h;
         return MRPOP_OK;
     }
-    nearest_seed<DIM><<<(Q + 127) / 128, 128, 0, st>>>(tree_s, N, q_s, c_s, Q, seed);
+    nearest_seed<DIM><<<qblocks, kTcQueries, 0, st>>>(tree_s, N, q_s, c_s, Q, S, seed, cut);
     dim3 grid(qblocks, splits);
+    const NnFinish fin{qdone, qperm, out_idx};
     if (!tensor)
         nearest_f32_kernel<DIM><<<grid, kTcThreads, f32_smem_bytes<DIM>(), st>>>(
-            tree_s, N, q_s, c_s, Q, chunk, partial, perm, cut, seed, &S->exact_only);
+            tree_s, N, q_s, c_s, Q, chunk, partial, perm, cut, seed, &S->exact_only, fin);
     else if constexpr (f16)
         nearest_tc16_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk,
                                                               partial, perm, cut, seed,
-                                                              &S->maxabs, &S->nonfinite);
+                                                              &S->maxabs, &S->nonfinite, fin);
     else
         nearest_tc_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk, partial,
-                                                            perm, cut, seed, &S->exact_only);
-    nearest_sorted_reduce<<<(Q + 255) / 256, 256, 0, st>>>(partial, cut, chunk, Q, bq, qperm,
-                                                           out_idx);
+                                                            perm, cut, seed, &S->exact_only, fin);
     const cudaError_t e = cudaGetLastError();
     cudaFreeAsync(arena, st);
     if (e != cudaSuccess) return cuda_error(e, "nearest (budget-ordered) launch");
