@@ -273,12 +273,12 @@ __device__ __forceinline__ void tc_stage_queries(float (*qsm)[kTcQueries],
 // every thread of the block: an admissible vertex of the slice has
 // |q - x| < c - that minimum.
 template <int DIM>
-__device__ __forceinline__ float tc_slice_gmin(const float *__restrict__ tree, int N, int vs, int ve,
-                                               float *red_g) {
+__device__ __forceinline__ float tc_slice_gmin(const float *__restrict__ tree, int ldt, int vs,
+                                               int ve, float *red_g) {
     float gm = FLT_MAX;
 #pragma unroll 4
     for (int v = vs + threadIdx.x; v < ve; v += kTcThreads)
-        gm = fminf(gm, __ldg(tree + (size_t)DIM * N + v));
+        gm = fminf(gm, __ldg(tree + (size_t)DIM * ldt + v));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gm = fminf(gm, __shfl_xor_sync(kFull, gm, o));
     if ((threadIdx.x & 31) == 0) red_g[threadIdx.x >> 5] = gm;
@@ -357,7 +357,7 @@ __device__ __forceinline__ void tc_write_rows(Best (&best)[4], const int *__rest
 // partial[y][q] for the reduce.
 template <int DIM>
 __global__ void __launch_bounds__(kTcThreads)
-nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
+nearest_tc_kernel(const float *__restrict__ tree, int N, int ldt, const float *__restrict__ queries,
                   const float *__restrict__ budgets, int Q, int chunk,
                   Best *__restrict__ partial, const int *__restrict__ perm,
                   const int *__restrict__ cut, float *__restrict__ seed,
@@ -442,7 +442,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
     }
     {
         // an admissible vertex of this slice has |q - x| < c - g_min(slice)
-        const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
+        const float gm = tc_slice_gmin<DIM>(tree, ldt, vs, ve, red_g);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (!(cq[r] > gm)) {
@@ -470,7 +470,7 @@ nearest_tc_kernel(const float *__restrict__ tree, int N, const float *__restrict
         const bool ok = t_ld < min(VT, ve - v0n);
         const unsigned base = (unsigned)(v0n + t_ld);
 #pragma unroll
-        for (int d = 0; d <= DIM; ++d) px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)N)) : 0.f;
+        for (int d = 0; d <= DIM; ++d) px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)ldt)) : 0.f;
         if (!ok) px[DIM] = FLT_MAX * 2.f;  // padding vertex: g = +inf
     };
     prefetch(vs);
@@ -627,7 +627,7 @@ __device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
 // Registers are capped so that 3 blocks (24 warps) stay resident per SM.
 template <int DIM>
 __global__ void __launch_bounds__(kTcThreads, 3)
-nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
+nearest_tc16_kernel(const float *__restrict__ tree, int N, int ldt, const float *__restrict__ queries,
                     const float *__restrict__ budgets, int Q, int chunk,
                     Best *__restrict__ partial, const int *__restrict__ perm,
                     const int *__restrict__ cut, float *__restrict__ seed,
@@ -716,7 +716,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
     }
     {
         // an admissible vertex of this slice has |q - x| < c - g_min(slice)
-        const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
+        const float gm = tc_slice_gmin<DIM>(tree, ldt, vs, ve, red_g);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if (!(cq[r] > gm)) {
@@ -740,7 +740,7 @@ nearest_tc16_kernel(const float *__restrict__ tree, int N, const float *__restri
         const bool ok = t_ld < min(VT, ve - v0n);
         const unsigned base = (unsigned)(v0n + t_ld);
 #pragma unroll
-        for (int d = 0; d <= DIM; ++d) px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)N)) : 0.f;
+        for (int d = 0; d <= DIM; ++d) px[d] = ok ? __ldg(tree + (base + (unsigned)d * (unsigned)ldt)) : 0.f;
         if (!ok) px[DIM] = FLT_MAX * 2.f;  // padding vertex: g = +inf
     };
     prefetch(vs);
@@ -938,6 +938,13 @@ constexpr size_t f32_smem_bytes() {
                             (size_t)3 * 8 * kTcQueries);
 }
 
+// Smallest of three floats (a NaN input is ignored while another is not NaN).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 typedef unsigned long long f32x2_t;  // two floats, the first in the low half
 
 __device__ __forceinline__ f32x2_t fma_f32x2(f32x2_t a, f32x2_t b, f32x2_t c) {
@@ -959,12 +966,19 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
                  "r"(ok ? 4 : 0)
                  : "memory");
 }
+// 16 bytes, of which the first src_bytes come from global memory and the
+// rest are zero (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int DIM>
 __global__ void __launch_bounds__(kTcThreads, 2)
-nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restrict__ queries,
+nearest_f32_kernel(const float *__restrict__ tree, int N, int ldt, const float *__restrict__ queries,
                    const float *__restrict__ budgets, int Q, int chunk,
                    Best *__restrict__ partial, const int *__restrict__ perm,
                    const int *__restrict__ cut, float *__restrict__ seed,
@@ -1004,17 +1018,25 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     unsigned *const shared_lim = reinterpret_cast<unsigned *>(seed);
 
     // first tile in flight while the queries are staged
+    // 16-byte pieces (rows start on 16-byte boundaries, slices and tiles on
+    // multiples of 4 vertices); a piece past the slice end is zero-filled, its
+    // folded norms +inf so that the padding columns never pass
     auto issue_tile = [&](int v0n, int buf) {
         const int nvn = min(VT, ve - v0n);
         float *dst = tiles + buf * ROWS * VT;
-        for (int i = tid; i < ROWS * VT; i += kTcThreads) {
-            const int d = i / VT, j = i - d * VT;
-            if (j < nvn)
-                cp_async4(dst + i, tree + ((size_t)d * N + v0n + j), true);
-            else if (d == DIM + 1)
-                cp_async4(dst + i, &g_f32_pad_inf, true);  // padding: never passes
-            else
-                cp_async4(dst + i, tree, false);            // zero fill
+        for (int i = tid; i < ROWS * (VT / 4); i += kTcThreads) {
+            const int d = i / (VT / 4), j = 4 * (i - d * (VT / 4));
+            float *to = dst + d * VT + j;
+            const float *from = tree + ((size_t)d * ldt + v0n + j);
+            if (j + 4 <= nvn) {
+                cp_async16(to, from, 16);
+            } else if (d == DIM + 1) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    cp_async4(to + k, j + k < nvn ? from + k : &g_f32_pad_inf, true);
+            } else {
+                cp_async16(to, j < nvn ? from : tree, 4 * max(0, nvn - j));
+            }
         }
         cp_async_commit();
     };
@@ -1055,7 +1077,7 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     float lim[8];
     {
         // an admissible vertex of this slice has |q - x| < c - g_min(slice)
-        const float gm = tc_slice_gmin<DIM>(tree, N, vs, ve, red_g);
+        const float gm = tc_slice_gmin<DIM>(tree, ldt, vs, ve, red_g);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const float c = cq_s[ql(r)];
@@ -1148,9 +1170,9 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
             unsigned rows = 0;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                float m = acc[r][0];
-#pragma unroll
-                for (int c = 1; c < 8; ++c) m = fminf(m, acc[r][c]);
+                const float m = fmin3(fmin3(acc[r][0], acc[r][1], acc[r][2]),
+                                      fmin3(acc[r][3], acc[r][4], acc[r][5]),
+                                      fminf(acc[r][6], acc[r][7]));
                 rows |= (exact_only || m <= lim[r]) ? 1u << r : 0u;
             }
             rows &= row_ok;
@@ -1195,7 +1217,7 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
                     const int bpos = sb_pos[r][tid];
                     bool take = d2 < bd2 || bpos < 0;
                     if (!take) {
-                        const float bg = __ldg(tree + (size_t)DIM * N + bpos);
+                        const float bg = __ldg(tree + (size_t)DIM * ldt + bpos);
                         take = g < bg || (g == bg && __ldg(perm + v0 + vl) < __ldg(perm + bpos));
                     }
                     if (take) {
@@ -1228,7 +1250,7 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, const float *__restric
     for (int r = 0; r < 8; ++r) {
         const int pos = sb_pos[r][tid];
         Best b{FLT_MAX * 2.f, FLT_MAX * 2.f, -1};
-        if (pos >= 0) b = Best{sb_d2[r][tid], __ldg(tree + (size_t)DIM * N + pos), __ldg(perm + pos)};
+        if (pos >= 0) b = Best{sb_d2[r][tid], __ldg(tree + (size_t)DIM * ldt + pos), __ldg(perm + pos)};
 #pragma unroll
         for (int o = 1; o <= 4; o <<= 1) {
             const Best other = shfl_best(b, o);
@@ -1415,7 +1437,7 @@ sort_histogram(const float *__restrict__ g, int N, const float *__restrict__ c, 
 // Scatter the tree (all D+1 rows) and the queries into bucket order.
 __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, int dim,
                              const float *__restrict__ queries, const float *__restrict__ budgets,
-                             int Q, SortState *S, float *__restrict__ tree_s,
+                             int Q, SortState *S, float *__restrict__ tree_s, int ldt,
                              int *__restrict__ perm, float *__restrict__ q_s,
                              float *__restrict__ c_s, int *__restrict__ qperm) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1443,9 +1465,9 @@ __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, 
                 check(v);
                 n2 = fmaf(v, v, n2);
             }
-            tree_s[(size_t)d * N + pt] = v;
+            tree_s[(size_t)d * ldt + pt] = v;
         }
-        tree_s[(size_t)(dim + 1) * N + pt] = n2 * (1.f - 4.f * (kF32G * (dim + 2.f)));
+        tree_s[(size_t)(dim + 1) * ldt + pt] = n2 * (1.f - 4.f * (kF32G * (dim + 2.f)));
         perm[pt] = i;
     }
     const float c = i < Q ? budgets[i] : 0.f;
@@ -1506,7 +1528,7 @@ __global__ void __launch_bounds__(256) sort_cut(const float *__restrict__ c_s, i
 constexpr int kSeedSamples = 64;
 template <int DIM>
 __global__ void __launch_bounds__(kTcQueries)
-nearest_seed(const float *__restrict__ tree_s, int N, const float *__restrict__ q_s,
+nearest_seed(const float *__restrict__ tree_s, int N, int ldt, const float *__restrict__ q_s,
              const float *__restrict__ c_s, int Q, const SortState *S, float *__restrict__ seed,
              int *__restrict__ cut) {
     __shared__ float xs[DIM + 1][kSeedSamples];  // the sample vertices, g in the last row
@@ -1514,7 +1536,7 @@ nearest_seed(const float *__restrict__ tree_s, int N, const float *__restrict__ 
     const int n = min(N, kSeedSamples);
     for (int t = threadIdx.x; t < (DIM + 1) * kSeedSamples; t += blockDim.x) {
         const int d = t / kSeedSamples, k = t % kSeedSamples;
-        xs[d][k] = k < n ? tree_s[(size_t)d * N + (int)(((int64_t)k * N) / n)] : 0.f;
+        xs[d][k] = k < n ? tree_s[(size_t)d * ldt + (int)(((int64_t)k * N) / n)] : 0.f;
     }
     __syncthreads();
     const int i = blockIdx.x * kTcQueries + threadIdx.x;
@@ -1636,7 +1658,10 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     // permutations, cuts, partial bests
     auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_state = align(sizeof(SortState));
-    const size_t b_tree = align(sizeof(float) * (size_t)(DIM + 2) * N);  // + folded norms
+    // rows of the ordered tree start on 16-byte boundaries (the FP32 filter
+    // copies them in 16-byte pieces)
+    const int ldt = (N + 3) & ~3;
+    const size_t b_tree = align(sizeof(float) * (size_t)(DIM + 2) * ldt);  // + folded norms
     const size_t b_perm = align(sizeof(int) * (size_t)N);
     const size_t b_q = align(sizeof(float) * (size_t)DIM * Q);
     const size_t b_c = align(sizeof(float) * (size_t)Q);
@@ -1672,7 +1697,7 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
     sort_histogram<<<(n_max + kHistThreads - 1) / kHistThreads, kHistThreads, 0, st>>>(
         g, N, budgets, Q, S);
     sort_scatter<<<(n_max + 255) / 256, 256, 0, st>>>(tree, N, ld, DIM, queries, budgets, Q, S,
-                                                       tree_s, perm, q_s, c_s, qperm);
+                                                       tree_s, ldt, perm, q_s, c_s, qperm);
     if (!out_idx) {
         sort_cut<<<qblocks, 256, 0, st>>>(c_s, Q, bq, S, N, cut);
         unsigned long long *d_pairs = (unsigned long long *)seed;  // 8 bytes of the arena
@@ -1687,18 +1712,18 @@ mrpop_status nearest_sorted(const float *tree, int N, int64_t ld, const float *q
         *pairs = (int64_t)h;
         return MRPOP_OK;
     }
-    nearest_seed<DIM><<<qblocks, kTcQueries, 0, st>>>(tree_s, N, q_s, c_s, Q, S, seed, cut);
+    nearest_seed<DIM><<<qblocks, kTcQueries, 0, st>>>(tree_s, N, ldt, q_s, c_s, Q, S, seed, cut);
     dim3 grid(qblocks, splits);
     const NnFinish fin{qdone, qperm, out_idx};
     if (!tensor)
         nearest_f32_kernel<DIM><<<grid, kTcThreads, f32_smem_bytes<DIM>(), st>>>(
-            tree_s, N, q_s, c_s, Q, chunk, partial, perm, cut, seed, &S->exact_only, fin);
+            tree_s, N, ldt, q_s, c_s, Q, chunk, partial, perm, cut, seed, &S->exact_only, fin);
     else if constexpr (f16)
-        nearest_tc16_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk,
+        nearest_tc16_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, ldt, q_s, c_s, Q, chunk,
                                                               partial, perm, cut, seed,
                                                               &S->maxabs, &S->nonfinite, fin);
     else
-        nearest_tc_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, q_s, c_s, Q, chunk, partial,
+        nearest_tc_kernel<DIM><<<grid, kTcThreads, 0, st>>>(tree_s, N, ldt, q_s, c_s, Q, chunk, partial,
                                                             perm, cut, seed, &S->exact_only, fin);
     const cudaError_t e = cudaGetLastError();
     cudaFreeAsync(arena, st);

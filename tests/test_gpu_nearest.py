@@ -158,7 +158,8 @@ def test_path_cost_parity(mp, orc):
 
 @pytest.mark.parametrize("filt", FILTERS)
 @pytest.mark.parametrize("D,N,Q", [(14, 3000, 4096), (28, 2000, 2048), (6, 5000, 3000),
-                                   (3, 700, 2500), (7, 257, 2049), (21, 1500, 2100)])
+                                   (3, 700, 2500), (7, 257, 2049), (21, 1501, 2100),
+                                   (14, 1001, 2300)])
 def test_nearest_query_blocked_parity(mp, orc, D, N, Q, filt):
     """Batches of >= 2048 queries take the budget-ordered path (FP32 or
     tensor-core expansion filter + exact re-check); sampled queries against
