@@ -57,7 +57,7 @@ FLOPS_PER = {
     "bound_test": 10,           # |c - c_o|^2 vs (r + r_o + m)^2
     "sphere_obstacle_test": 11,
     "cuboid_test": 31,          # R^T (c - c_b), clamp excess, squared norm
-    "box_bound_test": 31,       # same distance for a bounding sphere
+    "box_bound_test": 31,       # the same box distance for a tile bound
     "pair_test": 11,
     "point_transform": 18,      # R p + t
     "tile_bound": 390,          # centroid and max radius of 32 coarse centres

@@ -191,12 +191,14 @@ mrpop_status mrpop_edge_clearance(mrpop_problem *p, const float *qa, const float
  *   [4]  sphere-vs-sphere-obstacle tests   [5]  sphere-vs-cuboid tests
  *   [6]  robot-robot sphere-pair tests     [7]  point transforms (coarse
  *        centres and sphere centres)
- *   [8]  tile-level sphere tests (tile bound vs obstacle spheres and vs the
- *        tile bounds of earlier robots' links)
+ *   [8]  tile-level sphere tests (tile bound vs obstacle spheres, vs the
+ *        bounding spheres of cuboids and vs the tile bounds of earlier
+ *        robots' links)
  *   [9]  tile bounds built (one per tile and link: centroid and radius of the
  *        link's coarse spheres at the tile's 32 checkpoints)
  *   [10] checkpoint link-vs-cuboid box tests (tile candidates only)
- *   [11] tile-level box tests (tile bound vs cuboid)
+ *   [11] tile-level box tests (tile bound vs cuboid, where the cuboid's
+ *        bounding sphere is near the tile bound)
  * Per-checkpoint counts only include what that checkpoint decides: a
  * sphere-level test is counted only where the checkpoint's own link-level
  * test hit (the kernel may run more, warp-wide). */

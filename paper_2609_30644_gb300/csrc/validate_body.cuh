@@ -320,7 +320,13 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                         bnd.x = t.ws_lo[0] + 0.5f * (x0 + x1);
                         bnd.y = t.ws_lo[1] + 0.5f * (y0 + y1);
                         bnd.z = t.ws_lo[2] + 0.5f * (z0 + z1);
-                        bnd.w = __fsqrt_ru(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + LC.w + kTileSlack;
+                        // the hardware's approximate square root (an error of a few
+                        // ulps), padded by 2^-16 relative; kTileSlack covers the rest
+                        float rbox;
+                        asm("sqrt.approx.f32 %0, %1;"
+                            : "=f"(rbox)
+                            : "f"(fmaf(ex, ex, fmaf(ey, ey, ez * ez))));
+                        bnd.w = fmaf(rbox, 1.0000153f, LC.w + kTileSlack);
                         if (!(bnd.w < FLT_MAX)) bnd.w = FLT_MAX * 2.f;  // never for finite inputs
                         if (MODE == kCount && lane == 0) cnt[9] += 1;
                     }
@@ -411,13 +417,21 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                             if (MODE == kClearance) {
                                 own = low_mask(cn);
                             } else {
-                                bool h = false;
+                                // the box's bounding sphere first (the box lies within
+                                // it), its exact distance only when the sphere is near
+                                bool h = false, exact = false;
                                 if (lane < cn) {
                                     const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + lane);
-                                    const float d2 = box_dist2(bnd.x, bnd.y, bnd.z, cbp[0], cbp[1],
-                                                               cbp[2], cbp[3], cbp[4]);
-                                    const float th2 = bnd.w + m;
-                                    h = d2 < th2 * th2;
+                                    const float4 cb0 = cbp[0];
+                                    const float dc2 = dist2(bnd.x, bnd.y, bnd.z, cb0.x, cb0.y, cb0.z);
+                                    const float reach = cb0.w + bnd.w + m;
+                                    exact = dc2 < reach * reach;
+                                    if (exact) {
+                                        const float d2 = box_dist2(bnd.x, bnd.y, bnd.z, cb0, cbp[1],
+                                                                   cbp[2], cbp[3], cbp[4]);
+                                        const float th2 = bnd.w + m;
+                                        h = d2 < th2 * th2;
+                                    }
                                 }
                                 cand = __ballot_sync(kFull, h);
                                 unsigned cm = cand;
@@ -430,7 +444,8 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                     own |= (d2 < rc * rc) ? (1u << o) : 0u;
                                 }
                                 if (MODE == kCount) {
-                                    if (lane == 0) cnt[11] += cn;
+                                    if (lane == 0) cnt[8] += cn;  // the bounding-sphere tests
+                                    if (exact) cnt[11] += 1;
                                     if (active) cnt[10] += __popc(cand);
                                 }
                             }

@@ -251,8 +251,9 @@ def test_batched_scene_eight_arms(mp, orc):
 def test_work_counters_structure(mp, orc):
     """Counters on edges the oracle finds valid (no early exit): every
     checkpoint is evaluated once, every tile bounds every link once and tests
-    it against every obstacle and every earlier robot's link, and checkpoint
-    tests never exceed their tile candidates."""
+    it against every obstacle (a cuboid first through its bounding sphere)
+    and every earlier robot's link, and checkpoint tests never exceed their
+    tile candidates."""
     scene = synth.table_pair_scene(0)
     o = orc.OracleScene(scene)
     qa, qb = synth.candidate_edges(scene, 400, seed=17, step_hi=0.3)
@@ -271,8 +272,10 @@ def test_work_counters_structure(mp, orc):
     assert cnt[1] == pts * L
     NS, NC = len(scene.obs_spheres), len(scene.obs_cuboids)
     assert cnt[9] == tiles * L
-    assert cnt[8] == tiles * (L * NS + 7 * 7)      # robot 1's links vs robot 0's 7
-    assert cnt[11] == tiles * L * NC
+    # tile level: every obstacle sphere and every cuboid's bounding sphere,
+    # robot 1's links vs robot 0's 7; exact box tests where the sphere is near
+    assert cnt[8] == tiles * (L * NS + L * NC + 7 * 7)
+    assert 0 < cnt[11] <= tiles * L * NC
     assert cnt[2] <= pts * L * NS and cnt[10] <= pts * L * NC and cnt[3] <= pts * 7 * 7
     assert cnt[7] >= pts * L
 
