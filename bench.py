@@ -881,6 +881,7 @@ def run_ours(args) -> None:
         ov = torch.empty(E_EDGES, dtype=torch.uint8, device=dev)
         with mp.Problem(osc, resolution=RES, margin=MARGIN) as op:
             otuned = mp.autotune(op, oqa_d, oqb_d)
+            oregs = mp.get_launch(op)[3]
             for _ in range(max(args.warmup, 0)):
                 mp.validate_edges(op, oqa_d, oqb_d, ov)
             torch.cuda.synchronize()
@@ -900,7 +901,8 @@ def run_ours(args) -> None:
                         "valid_fraction": float(ov.float().mean().item()),
                         "validate_launch": {"warps_per_block": otuned[0],
                                             "order": ["strided", "contiguous"][otuned[1]],
-                                            "fine_stage": ["union", "reassigned"][otuned[2]]}}
+                                            "fine_stage": ["union", "reassigned"][otuned[2]],
+                                            "registers": ["compact", "wide"][oregs]}}
         del oqa_d, oqb_d
 
     # ---- CPU leg: the oracle's count of the paper's two-stage check on a
