@@ -237,6 +237,10 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
     if (warp >= P.warps) return;  // spare warps of a shared multi-problem launch
 
     const Tables &t = P.t;
+    // table offsets and the workspace corner read once (the loops below would
+    // otherwise reload them from the launch parameters at every use)
+    const int o_link = t.off_link, o_os = t.off_os, o_oc = t.off_oc, o_sph = t.off_sph;
+    const float wlx = t.ws_lo[0], wly = t.ws_lo[1], wlz = t.ws_lo[2];
     const int K = t.K, D = t.L, NS = t.NS, NC = t.NC;
     const float m = P.margin;
     unsigned long long cnt[kCounters];
@@ -277,7 +281,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
             // joint angles' sine and cosine one link ahead, so that the
             // special-function latency overlaps the previous link's tests
             float sn_next, cs_next;
-            joint_sincos(__fmaf_rn(tk, dq_s[0], qa_s[0]) + tab[t.off_link + 1].x, &sn_next,
+            joint_sincos(__fmaf_rn(tk, dq_s[0], qa_s[0]) + tab[o_link + 1].x, &sn_next,
                          &cs_next);
 
             for (int b = 0; b < K; ++b) {
@@ -285,13 +289,13 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                 const bool store = b < K - 1 || t.selfcol;
                 Frame Tm = load_base(tab, t, b);
                 for (int l = l0; l < l1; ++l) {
-                    const float4 LA = tab[t.off_link + kLinkF4 * l];
-                    const float4 LB = tab[t.off_link + kLinkF4 * l + 1];
-                    const float4 LC = tab[t.off_link + kLinkF4 * l + 2];
+                    const float4 LA = tab[o_link + kLinkF4 * l];
+                    const float4 LB = tab[o_link + kLinkF4 * l + 1];
+                    const float4 LC = tab[o_link + kLinkF4 * l + 2];
                     const float sn = sn_next, cs = cs_next;
                     if (l + 1 < D)
                         joint_sincos(__fmaf_rn(tk, dq_s[l + 1], qa_s[l + 1]) +
-                                         tab[t.off_link + kLinkF4 * (l + 1) + 1].x,
+                                         tab[o_link + kLinkF4 * (l + 1) + 1].x,
                                      &sn_next, &cs_next);
                     const Frame F = rotz(Tm, cs, sn);
                     const float3 cc = apply(F, LC.x, LC.y, LC.z);
@@ -306,9 +310,9 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                     // are single-instruction warp reductions.
                     float4 bnd = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (MODE != kClearance) {
-                        const unsigned ux = __float_as_uint(cc.x - t.ws_lo[0]);
-                        const unsigned uy = __float_as_uint(cc.y - t.ws_lo[1]);
-                        const unsigned uz = __float_as_uint(cc.z - t.ws_lo[2]);
+                        const unsigned ux = __float_as_uint(cc.x - wlx);
+                        const unsigned uy = __float_as_uint(cc.y - wly);
+                        const unsigned uz = __float_as_uint(cc.z - wlz);
                         const float x0 = __uint_as_float(__reduce_min_sync(kFull, ux));
                         const float x1 = __uint_as_float(__reduce_max_sync(kFull, ux));
                         const float y0 = __uint_as_float(__reduce_min_sync(kFull, uy));
@@ -317,9 +321,9 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                         const float z1 = __uint_as_float(__reduce_max_sync(kFull, uz));
                         const float ex = 0.5f * (x1 - x0), ey = 0.5f * (y1 - y0),
                                     ez = 0.5f * (z1 - z0);
-                        bnd.x = t.ws_lo[0] + 0.5f * (x0 + x1);
-                        bnd.y = t.ws_lo[1] + 0.5f * (y0 + y1);
-                        bnd.z = t.ws_lo[2] + 0.5f * (z0 + z1);
+                        bnd.x = wlx + 0.5f * (x0 + x1);
+                        bnd.y = wly + 0.5f * (y0 + y1);
+                        bnd.z = wlz + 0.5f * (z0 + z1);
                         // the hardware's approximate square root (an error of a few
                         // ulps), padded by 2^-16 relative; kTileSlack covers the rest
                         float rbox;
@@ -353,7 +357,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                             } else {
                                 bool h = false;
                                 if (lane < cn) {
-                                    const float4 ob = tab[t.off_os + c0 + lane];
+                                    const float4 ob = tab[o_os + c0 + lane];
                                     const float d2 = dist2(bnd.x, bnd.y, bnd.z, ob.x, ob.y, ob.z);
                                     const float th2 = bnd.w + ob.w + m;
                                     h = d2 < th2 * th2;
@@ -363,7 +367,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                 while (cm) {
                                     const int o = __ffs(cm) - 1;
                                     cm &= cm - 1;
-                                    const float4 ob = tab[t.off_os + c0 + o];
+                                    const float4 ob = tab[o_os + c0 + o];
                                     const float d2 = dist2(cc.x, cc.y, cc.z, ob.x, ob.y, ob.z);
                                     const float th2 = rc + ob.w;
                                     own |= (d2 < th2 * th2) ? (1u << o) : 0u;
@@ -389,13 +393,13 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                             // fine stage: each of the link's spheres is placed once and
                             // tested against every obstacle of the warp's union mask
                             for (int s = 0; wm && s < ns; ++s) {
-                                const float4 sp = tab[t.off_sph + sf + s];
+                                const float4 sp = tab[o_sph + sf + s];
                                 const float3 p = apply(F, sp.x, sp.y, sp.z);
                                 unsigned mm = wm;
                                 while (mm) {
                                     const int o = __ffs(mm) - 1;
                                     mm &= mm - 1;
-                                    const float4 ob = tab[t.off_os + c0 + o];
+                                    const float4 ob = tab[o_os + c0 + o];
                                     const float d2 = dist2(p.x, p.y, p.z, ob.x, ob.y, ob.z);
                                     if (MODE == kClearance) {
                                         minc = fminf(minc, __fsqrt_rn(d2) - sp.w - ob.w);
@@ -421,7 +425,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                 // it), its exact distance only when the sphere is near
                                 bool h = false, exact = false;
                                 if (lane < cn) {
-                                    const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + lane);
+                                    const float4 *cbp = tab + o_oc + kCuboidF4 * (c0 + lane);
                                     const float4 cb0 = cbp[0];
                                     const float dc2 = dist2(bnd.x, bnd.y, bnd.z, cb0.x, cb0.y, cb0.z);
                                     const float reach = cb0.w + bnd.w + m;
@@ -438,7 +442,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                 while (cm) {
                                     const int o = __ffs(cm) - 1;
                                     cm &= cm - 1;
-                                    const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + o);
+                                    const float4 *cbp = tab + o_oc + kCuboidF4 * (c0 + o);
                                     const float d2 = box_dist2(cc.x, cc.y, cc.z, cbp[0], cbp[1],
                                                                cbp[2], cbp[3], cbp[4]);
                                     own |= (d2 < rc * rc) ? (1u << o) : 0u;
@@ -463,13 +467,13 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                 own_any |= own != 0;
                             }
                             for (int s = 0; wm && s < ns; ++s) {
-                                const float4 sp = tab[t.off_sph + sf + s];
+                                const float4 sp = tab[o_sph + sf + s];
                                 const float3 p = apply(F, sp.x, sp.y, sp.z);
                                 unsigned mm = wm;
                                 while (mm) {
                                     const int o = __ffs(mm) - 1;
                                     mm &= mm - 1;
-                                    const float4 *cbp = tab + t.off_oc + kCuboidF4 * (c0 + o);
+                                    const float4 *cbp = tab + o_oc + kCuboidF4 * (c0 + o);
                                     const float d2 = box_dist2(p.x, p.y, p.z, cbp[0], cbp[1], cbp[2],
                                                                cbp[3], cbp[4]);
                                     if (MODE == kClearance) {
@@ -518,7 +522,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                         const int bit = __ffs(cm) - 1;
                                         cm &= cm - 1;
                                         const int i = bit + 32 * w;
-                                        const float4 LCi = tab[t.off_link + kLinkF4 * i + 2];
+                                        const float4 LCi = tab[o_link + kLinkF4 * i + 2];
                                         const float *x = xc + (size_t)i * kXcFloats * 32 + lane;
                                         const float d2 = dist2(cc.x, cc.y, cc.z, x[0], x[32], x[64]);
                                         const float th2 = LC.w + LCi.w + m;
@@ -547,7 +551,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                         const int i = __ffs(mm) - 1 + 32 * w;
                                         mm &= mm - 1;
                                         const int nsi =
-                                            __float_as_int(tab[t.off_link + kLinkF4 * i + 1].z);
+                                            __float_as_int(tab[o_link + kLinkF4 * i + 1].z);
                                         cnt[6] += (unsigned long long)nsi * ns;
                                         cnt[7] += nsi;
                                     }
@@ -559,7 +563,7 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                     const int i = __ffs(mm) - 1 + 32 * w;
                                     mm &= mm - 1;
                                     const Frame Fi = link_frame(tab, t, qa_s, dq_s, i, tk);
-                                    const float4 LBi = tab[t.off_link + kLinkF4 * i + 1];
+                                    const float4 LBi = tab[o_link + kLinkF4 * i + 1];
                                     const int sfi = __float_as_int(LBi.y), nsi = __float_as_int(LBi.z);
                                     // the other link's spheres four at a time, this
                                     // link's placed once per group of four
@@ -567,13 +571,13 @@ __device__ __forceinline__ void validate_body(const VParams &P, float4 *sm4, int
                                         float4 pa[4];
 #pragma unroll
                                         for (int j = 0; j < 4; ++j) {
-                                            const float4 sp2 = tab[t.off_sph + sfi + min(g0 + j, nsi - 1)];
+                                            const float4 sp2 = tab[o_sph + sfi + min(g0 + j, nsi - 1)];
                                             const float3 q3 = apply(Fi, sp2.x, sp2.y, sp2.z);
                                             pa[j] = make_float4(q3.x, q3.y, q3.z, sp2.w);
                                         }
                                         const int gn = min(4, nsi - g0);
                                         for (int s = 0; s < ns; ++s) {
-                                            const float4 sp = tab[t.off_sph + sf + s];
+                                            const float4 sp = tab[o_sph + sf + s];
                                             const float3 p = apply(F, sp.x, sp.y, sp.z);
 #pragma unroll
                                             for (int j = 0; j < 4; ++j) {
