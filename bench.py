@@ -689,17 +689,11 @@ def run_ours(args) -> None:
     s_rm = torch.cuda.Stream(device=dev)
     e_fork, e_nn, e_rm = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
 
-    def step_concurrent(inp, valid_done=None, rest_ready=None):
-        # valid_done: event recorded after validation; rest_ready: event the
-        # NEAREST / NEIGHBORS / path-cost streams wait for (their inputs)
+    def step_concurrent(inp):
         e_fork.record(stream)
-        for sx in (s_nn, s_rm):
-            sx.wait_event(e_fork)
-            if rest_ready is not None:
-                sx.wait_event(rest_ready)
+        s_nn.wait_event(e_fork)
+        s_rm.wait_event(e_fork)
         mp.validate_edges(prob, inp["qa"], inp["qb"], valid)
-        if valid_done is not None:
-            valid_done.record(stream)
         with torch.cuda.stream(s_nn):
             mp.nearest(g["tree"], inp["qs"], inp["cs"], out=nn_out)
             e_nn.record(s_nn)
@@ -785,38 +779,35 @@ def run_ours(args) -> None:
     h2d = sum(v.numel() * v.element_size() for v in pin.values())
     d2h = sum(t.numel() * t.element_size() for t in (h_valid, h_nn, h_idx, h_cnt, h_cost))
 
-    # One step with its copies overlapped: the edges go first on the main
-    # stream; the other inputs follow on a copy stream while the edges are
-    # validated (NEAREST, NEIGHBORS and path cost wait for them); each result
-    # goes back on the copy stream as soon as its part is done.  The step
-    # ends when the last copy has landed.
-    cstream = torch.cuda.Stream(device=dev)
-    ev_in, ev_rest, ev_val, ev_out = (torch.cuda.Event() for _ in range(4))
-
+    # One step with its copies overlapped: each of the three parts copies its
+    # own inputs in on its own stream, runs, and copies its results back, so
+    # every part starts as soon as its inputs have landed and the copies of
+    # the others overlap its kernels.  The step ends when all three are done.
     def e2e_step():
-        d_in["qa"].copy_(pin["qa"], non_blocking=True)
-        d_in["qb"].copy_(pin["qb"], non_blocking=True)
-        ev_in.record(stream)
-        with torch.cuda.stream(cstream):
-            cstream.wait_event(ev_in)
-            for k in ("qs", "cs", "rq", "path"):
-                d_in[k].copy_(pin[k], non_blocking=True)
-            ev_rest.record(cstream)
-        idx, cnt = step_concurrent(d_in, valid_done=ev_val, rest_ready=ev_rest)
-        with torch.cuda.stream(cstream):
-            cstream.wait_event(ev_val)
-            h_valid.copy_(valid, non_blocking=True)
-            cstream.wait_event(e_nn)
+        e_fork.record(stream)
+        s_nn.wait_event(e_fork)
+        s_rm.wait_event(e_fork)
+        with torch.cuda.stream(s_nn):
+            d_in["qs"].copy_(pin["qs"], non_blocking=True)
+            d_in["cs"].copy_(pin["cs"], non_blocking=True)
+            mp.nearest(g["tree"], d_in["qs"], d_in["cs"], out=nn_out)
             h_nn.copy_(nn_out, non_blocking=True)
-            cstream.wait_event(e_rm)
+            e_nn.record(s_nn)
+        with torch.cuda.stream(s_rm):
+            d_in["rq"].copy_(pin["rq"], non_blocking=True)
+            d_in["path"].copy_(pin["path"], non_blocking=True)
+            idx, cnt = mp.neighbors(g["roadmap"], d_in["rq"], RM_DELTA, RM_KMAX,
+                                    dim=scene.robots[0].dof)
+            mp.path_cost(d_in["path"], out=cost)
             h_idx.copy_(idx, non_blocking=True)
             h_cnt.copy_(cnt, non_blocking=True)
             h_cost.copy_(cost, non_blocking=True)
-            idx.record_stream(cstream)
-            cnt.record_stream(cstream)
-            ev_out.record(cstream)
+            e_rm.record(s_rm)
+        d_in["qa"].copy_(pin["qa"], non_blocking=True)
+        d_in["qb"].copy_(pin["qb"], non_blocking=True)
+        mp.validate_edges(prob, d_in["qa"], d_in["qb"], valid)
+        h_valid.copy_(valid, non_blocking=True)
         join()
-        stream.wait_event(ev_out)
 
     for _ in range(max(args.warmup, 1)):
         e2e_step()
