@@ -825,7 +825,7 @@ def run_ours(args) -> None:
     e2e_value = world * E_EDGES / (e2e_total / args.steps / 1000.0)
 
     # sanity: the e2e results equal the resident-input results
-    assert torch.equal(h_valid, valid.cpu())
+    assert torch.equal(h_valid, valid.cpu()) and torch.equal(h_nn, nn_out.cpu())
     step_valid_fraction = float(valid.float().mean().item())  # (valid is reused below)
 
     # ---- validation on a free edge set (every checkpoint runs to the end) --
