@@ -971,8 +971,10 @@ def run_ours(args) -> None:
         nn_tc_s = statistics.mean(nn_tc_ms) / 1000.0
         nn_f32_flops = float(nn_pairs) * 2 * scene.D
         nn_tc_flops = float(nn_pairs) * 2 * (scene.D + 2)
-        nn_flops = float(nn_pairs) * 3 * scene.D
-        nn_all_flops = float(NN_QUERIES) * NN_TREE * 3 * scene.D
+        # the definition's work per (query, vertex) pair: D differences and D
+        # squares added up (3D), the cost-to-come added and the budget compared
+        nn_flops = float(nn_pairs) * (3 * scene.D + 2)
+        nn_all_flops = float(NN_QUERIES) * NN_TREE * (3 * scene.D + 2)
         # HBM side of the same launches: each input is read once, each output
         # written once (algorithmic bytes)
         hbm_peak = float(peaks.get("hbm_gbs") or 6658.3)
