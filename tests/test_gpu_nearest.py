@@ -124,6 +124,22 @@ def test_nearest_full_size_sampled(mp, orc):
     _check_nearest(orc, tree, qs, cs, got, sample=sample)
 
 
+def test_nearest_large_tree_sampled(mp, orc):
+    """A tree past the size whose cost-to-come range the ordering's setup
+    block finds alone (131,072 vertices; larger trees take a separate range
+    pass), with a ragged vertex count and a ragged last query block: sampled
+    queries against the oracle, both large-batch filters index for index."""
+    D, N, Q = 7, 140_001, 2_500
+    lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
+    tree = synth.random_tree_fast(D, N, lo, hi, seed=21)
+    qs, cs = synth.nn_queries(D, Q, lo, hi, seed=22, budget_lo=2.0, budget_hi=30.0)
+    got = mp.nearest(_dev(tree), _dev(qs), _dev(cs)).cpu().numpy()
+    tc = mp.nearest(_dev(tree), _dev(qs), _dev(cs), filter=1).cpu().numpy()
+    np.testing.assert_array_equal(got, tc)
+    sample = np.concatenate([np.arange(Q - 60, Q), np.random.default_rng(3).choice(Q, 60, replace=False)])
+    _check_nearest(orc, tree, qs, cs, got, sample=sample)
+
+
 @pytest.mark.parametrize("D,N,Q,k_max", [(7, 3000, 200, 32), (14, 1000, 64, 8), (6, 65, 33, 100),
                                          (3, 10, 5, 0)])
 def test_neighbors_parity(mp, orc, D, N, Q, k_max):
