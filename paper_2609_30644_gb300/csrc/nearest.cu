@@ -349,12 +349,13 @@ __device__ __forceinline__ void tc_write_rows(Best (&best)[4], const int *__rest
     }
 }
 
-// Inputs: the g-ordered tree (SoA rows, ld = N) with perm (ordered -> original
-// index), the budget-ordered queries, cut (vertices each query block scans),
-// the shared bound seed (see below); *exhaustive != 0 turns the filter off.
-// Block (x, y) takes queries [256 x, 256 x + 256) and the tree slice
-// [y chunk, (y + 1) chunk) cut at cut[x]; its partial bests go to
-// partial[y][q] for the reduce.
+// Inputs: the g-ordered tree (SoA rows of stride ldt) with perm (ordered ->
+// original index), the budget-ordered queries, cut (vertices each query block
+// scans), the shared bound seed (see below); *exhaustive != 0 turns the filter
+// off.  Block (x, y) takes query block b = gridDim.x - 1 - x (queries
+// [256 b, 256 b + 256)) and the tree slice [y chunk, (y + 1) chunk) cut at
+// cut[b]; its partial bests go to partial[y][q], and the query block's last
+// slice block to finish reduces them (nn_finish).
 template <int DIM>
 __global__ void __launch_bounds__(kTcThreads)
 nearest_tc_kernel(const float *__restrict__ tree, int N, int ldt, const float *__restrict__ queries,
@@ -1490,7 +1491,8 @@ __global__ void sort_scatter(const float *__restrict__ tree, int N, int64_t ld, 
 
 // Vertices a block of bq consecutive (ordered) queries must scan: up to the
 // end of the bucket that holds the largest budget of the block (0 when no
-// finite vertex has g below it).
+// finite vertex has g below it).  Used by the pair count; a NEAREST call takes
+// the cuts from its seeding pass.
 __global__ void __launch_bounds__(256) sort_cut(const float *__restrict__ c_s, int Q, int bq,
                                                 const SortState *S, int N, int *__restrict__ cut) {
     __shared__ float red[8];
