@@ -396,6 +396,7 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
     t0 = time.perf_counter()
     mp.plan_batch(probs, batched_budget)               # one persistent launch
     batched_wall = time.perf_counter() - t0
+    phases = mp.plan_batch_phase_stats()
     traces["batched"] = [mp.plan_trace(p)[:2] for p in probs]
     for p in probs:
         p.close()
@@ -474,6 +475,15 @@ def run_planner_leg(mp, synth, n_problems: int = PLAN_PROBLEMS, plain_sample: in
         "statuses": [int(x[3]) for x in ref_out]})
     if res["plain"]["problems_per_s"] > 0:
         res["batched_over_plain"] = res["batched"]["problems_per_s"] / res["plain"]["problems_per_s"]
+    # where the persistent launch's CTA time went, by phase kind
+    busy = sum(phases[k][0] for k in mp.PLAN_PHASE_NAMES)
+    if busy > 0:
+        res["batched"]["phase_share"] = {k: round(phases[k][0] / busy, 4)
+                                         for k in mp.PLAN_PHASE_NAMES if phases[k][0] > 0}
+        res["batched"]["phase_chunks"] = {k: phases[k][1] for k in mp.PLAN_PHASE_NAMES
+                                          if phases[k][1] > 0}
+        res["batched"]["cta_busy_fraction"] = (busy / (phases["ctas"] * phases["wall_ns"])
+                                               if phases["ctas"] and phases["wall_ns"] else None)
     if res["batched_stepped"]["problems_per_s"] > 0:
         res["persistent_over_stepped"] = (res["batched"]["problems_per_s"] /
                                           res["batched_stepped"]["problems_per_s"])

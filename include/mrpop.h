@@ -450,6 +450,24 @@ mrpop_status mrpop_plan_batch_ex(mrpop_problem *const *ps, int32_t n, double tim
  * Errors: EINVAL for negative values. */
 mrpop_status mrpop_set_persistent_limits(int32_t ctas, int64_t idle_polls);
 
+/* Where the CTA time of the last persistent launch in this process went (a
+ * diagnostic of the batched planner, Alg. 1/2).  Host int64 arrays of
+ * MRPOP_PLAN_PHASES: ns[k] = summed time of the chunks of phase kind k (CTA
+ * nanoseconds, from the device timer), chunks[k] = their number; ctas_wall
+ * [2] = the launch's CTAs and its wall time (ns), so that sum(ns) /
+ * (ctas * wall) is the fraction of CTA time spent in chunks.  Kinds:
+ *    0 start              1 ROADMAP sample        2 ROADMAP candidate check
+ *    3 ROADMAP append     4 ROADMAP NEIGHBORS     5 ROADMAP candidate edges
+ *    6 ROADMAP edge check 7 ROADMAP link + BFS    8 search sample
+ *    9 NEAREST (own tree) 10 direction oracle     11 extension check
+ *   12 insert             13 NEAREST (other tree) 14 connection prep
+ *   15 connection check   16 solution             17 res/4 re-check
+ *   18 accept             19 phase transitions (no chunks: the time the
+ *                            finishing CTA spends deciding the next phase)
+ * Zeros before the first launch.  Errors: EINVAL for NULL. */
+#define MRPOP_PLAN_PHASES 20
+mrpop_status mrpop_plan_batch_phase_stats(int64_t *ns, int64_t *chunks, int64_t *ctas_wall);
+
 /* Best path and cost found so far for p (same outputs and errors as
  * mrpop_plan, without planning). */
 mrpop_status mrpop_plan_result(mrpop_problem *p, float *path, int64_t path_cap, int64_t *path_len,

@@ -17,7 +17,8 @@ _OPS = ("MrpopError", "Problem", "edge_clearance", "fk", "lib", "library_path", 
         "NEAREST_FILTER_TENSOR", "planner_nearest_pass", "planner_neighbors_pass",
         "ROADMAP_DEGREE_CAP", "BATCH_PERSISTENT", "BATCH_STEPPED", "set_persistent_limits",
         "get_launch", "autotune_cache_save", "autotune_cache_load", "autotune_cache_clear",
-        "nearest_autotune", "neighbors_autotune", "FAULT_ADMIT_ENOMEM", "FAULT_STALL_MS")
+        "nearest_autotune", "neighbors_autotune", "FAULT_ADMIT_ENOMEM", "FAULT_STALL_MS",
+        "plan_batch_phase_stats", "PLAN_PHASE_NAMES")
 
 
 def __getattr__(name):

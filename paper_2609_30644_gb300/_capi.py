@@ -60,6 +60,7 @@ EXPORTS = (
     "mrpop_server_cancel",
     "mrpop_server_inject",
     "mrpop_scratch_stats",
+    "mrpop_plan_batch_phase_stats",
 )
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "ETIMEOUT",
@@ -143,6 +144,7 @@ def _load() -> C.CDLL:
         "mrpop_server_cancel": (i32, [vp, i64]),
         "mrpop_server_inject": (i32, [vp, i32, i64]),
         "mrpop_scratch_stats": (i32, [i32, vp]),
+        "mrpop_plan_batch_phase_stats": (i32, [vp, vp, vp]),
     }
     for name in EXPORTS:
         fn = getattr(L, name)
@@ -531,6 +533,25 @@ def plan_batch(problems, time_budget_s: float, max_steps: int = 0, targets=None,
                                    None if tg is None else tg.ctypes.data, st.ctypes.data,
                                    int(form)))
     return st
+
+
+PLAN_PHASE_NAMES = ("start", "roadmap_sample", "roadmap_candidate_check", "roadmap_append",
+                    "roadmap_neighbors", "roadmap_candidate_edges", "roadmap_edge_check",
+                    "roadmap_link_bfs", "search_sample", "nearest_own_tree", "direction_oracle",
+                    "extension_check", "insert", "nearest_other_tree", "connection_prep",
+                    "connection_check", "solution", "res4_recheck", "accept",
+                    "phase_transitions")
+
+
+def plan_batch_phase_stats() -> dict:
+    """Where the last persistent launch's CTA time went: {phase: (ns, chunks)},
+    plus 'ctas' and 'wall_ns'."""
+    n = len(PLAN_PHASE_NAMES)
+    ns, ch, cw = (C.c_int64 * n)(), (C.c_int64 * n)(), (C.c_int64 * 2)()
+    _check(lib.mrpop_plan_batch_phase_stats(ns, ch, cw))
+    out = {k: (int(ns[i]), int(ch[i])) for i, k in enumerate(PLAN_PHASE_NAMES)}
+    out["ctas"], out["wall_ns"] = int(cw[0]), int(cw[1])
+    return out
 
 
 def set_persistent_limits(ctas: int = 0, idle_polls: int = 0) -> None:

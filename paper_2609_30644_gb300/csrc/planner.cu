@@ -1693,6 +1693,9 @@ struct PLaunch {
     unsigned long long *t_start;            // earliest CTA start (globaltimer)
     int *finished;                          // problems done
     int *timeout;                           // an idle CTA gave up
+    // CTA time (ns) and chunks per phase kind; slot PK_DONE holds the phase
+    // transitions (decide)
+    unsigned long long *phase_ns, *phase_chunks;
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -2096,13 +2099,19 @@ __global__ void __launch_bounds__(kPerThreads) k_persistent(const PLaunch L) {
         if (s_q < 0) continue;
         __threadfence();  // acquire: the phase's inputs, written by other CTAs
         PState &ps = L.states[s_q];
+        const unsigned long long tc0 = tid == 0 ? gtimer() : 0ull;
         run_chunk(ps, s_kind, s_robot, s_chunk, per_sm4, nn, wsum, &s_next, red);
         __threadfence();  // release: this chunk's results
         __syncthreads();
+        if (tid == 0) {
+            atomicAdd(L.phase_ns + s_kind, gtimer() - tc0);
+            atomicAdd(L.phase_chunks + s_kind, 1ull);
+        }
         if (tid == 0) s_last = atomicAdd(&ps.done, 1) == s_total - 1;
         __syncthreads();
         if (s_last) {
             __threadfence();
+            const unsigned long long td0 = tid == 0 ? gtimer() : 0ull;
             if (tid == 0) {
                 const unsigned long long now = gtimer();
                 PDecision d = decide(ps, s_kind, s_robot, now, deadline);
@@ -2128,11 +2137,22 @@ __global__ void __launch_bounds__(kPerThreads) k_persistent(const PLaunch L) {
                 __threadfence();
                 atomicExch(&ps.claim, s_word);  // publish the next phase
                 if (fin) atomicAdd(L.finished, 1);
+                atomicAdd(L.phase_ns + PK_DONE, gtimer() - td0);
+                atomicAdd(L.phase_chunks + PK_DONE, 1ull);
             }
         }
         __syncthreads();
     }
 }
+
+// Where the last persistent launch's CTA time went, per phase kind
+// (mrpop_plan_batch_phase_stats).
+constexpr int kPhaseKinds = PK_DONE + 1;
+static_assert(kPhaseKinds == MRPOP_PLAN_PHASES, "phase kinds of the header");
+static std::mutex g_phase_mu;
+static int64_t g_phase_ns[kPhaseKinds] = {};
+static int64_t g_phase_chunks[kPhaseKinds] = {};
+static int64_t g_phase_ctas = 0, g_phase_wall_ns = 0;
 
 // Test and diagnostic limits of the persistent launch (mrpop_set_persistent_limits).
 static std::atomic<int> g_per_ctas{0};
@@ -2325,9 +2345,12 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
         s.hist_floats = b.hist_floats;
     }
     PState *d_states = nullptr;
-    unsigned long long *d_aux = nullptr;  // [0] start time, [1] finished | timeout << 32
+    // [0] start time, [1] finished | timeout << 32, then CTA time and chunks
+    // per phase kind
+    unsigned long long *d_aux = nullptr;
+    constexpr int kAux = 2 + 2 * kPhaseKinds;
     PL_TRY(scratch_alloc((void **)&d_states, sizeof(PState) * n, st));
-    PL_TRY(scratch_alloc((void **)&d_aux, sizeof(unsigned long long) * 2, st));
+    PL_TRY(scratch_alloc((void **)&d_aux, sizeof(unsigned long long) * kAux, st));
     struct Release {
         void *a, *b;
         cudaStream_t s;
@@ -2337,7 +2360,7 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
         }
     } release{d_states, d_aux, st};
     PL_TRY(cudaMemcpyAsync(d_states, hs.data(), sizeof(PState) * n, cudaMemcpyHostToDevice, st));
-    const unsigned long long aux0[2] = {~0ull, (unsigned long long)finished0};
+    unsigned long long aux0[kAux] = {~0ull, (unsigned long long)finished0};
     PL_TRY(cudaMemcpyAsync(d_aux, aux0, sizeof(aux0), cudaMemcpyHostToDevice, st));
     PLaunch L{};
     L.states = d_states;
@@ -2349,6 +2372,8 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
     L.t_start = d_aux;
     L.finished = reinterpret_cast<int *>(d_aux + 1);
     L.timeout = reinterpret_cast<int *>(d_aux + 1) + 1;
+    L.phase_ns = d_aux + 2;
+    L.phase_chunks = d_aux + 2 + kPhaseKinds;
     // the launch, captured in a CUDA graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -2365,9 +2390,19 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
     if (exec) cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     PL_TRY(e);
-    unsigned long long aux[2];
+    unsigned long long aux[kAux];
+    const double t_wall = now_s() - t0 - t_launch;
     PL_TRY(cudaMemcpy(hs.data(), d_states, sizeof(PState) * n, cudaMemcpyDeviceToHost));
     PL_TRY(cudaMemcpy(aux, d_aux, sizeof(aux), cudaMemcpyDeviceToHost));
+    {
+        std::lock_guard<std::mutex> lock(g_phase_mu);
+        for (int k = 0; k < kPhaseKinds; ++k) {
+            g_phase_ns[k] = (int64_t)aux[2 + k];
+            g_phase_chunks[k] = (int64_t)aux[2 + kPhaseKinds + k];
+        }
+        g_phase_ctas = ctas;
+        g_phase_wall_ns = (int64_t)(t_wall * 1e9);
+    }
     const bool timeout = (aux[1] >> 32) != 0;
     // results and mirrors back to the host planners
     for (int i = 0; i < n; ++i) {
@@ -2762,6 +2797,20 @@ extern "C" mrpop_status mrpop_set_persistent_limits(int32_t ctas, int64_t idle_p
         return set_error(MRPOP_EINVAL, "mrpop_set_persistent_limits: negative limit");
     mrpop::g_per_ctas.store(ctas);
     mrpop::g_per_idle_polls.store(idle_polls);
+    return MRPOP_OK;
+}
+
+extern "C" mrpop_status mrpop_plan_batch_phase_stats(int64_t *ns, int64_t *chunks,
+                                                    int64_t *ctas_wall) {
+    if (!ns || !chunks || !ctas_wall)
+        return set_error(MRPOP_EINVAL, "mrpop_plan_batch_phase_stats: NULL argument");
+    std::lock_guard<std::mutex> lock(g_phase_mu);
+    for (int k = 0; k < kPhaseKinds; ++k) {
+        ns[k] = g_phase_ns[k];
+        chunks[k] = g_phase_chunks[k];
+    }
+    ctas_wall[0] = g_phase_ctas;
+    ctas_wall[1] = g_phase_wall_ns;
     return MRPOP_OK;
 }
 

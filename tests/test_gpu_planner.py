@@ -428,3 +428,22 @@ def test_planner_neighbors_kernel_parity(mp, orc, dof, N, Q, delta):
         assert (idx[i, kept:] == -1).all()
     if N > 2 * cap and delta >= 5:           # the cap is exercised on the wide radius
         assert cnt.max() > cap
+
+
+def test_plan_batch_phase_stats(mp, orc):
+    """The persistent launch accounts its CTA time by phase kind: ROADMAP and
+    search phases both ran, chunk counts are positive where time is, and the
+    busy time fits in the launch's CTA time."""
+    probs = [_planar_problem(mp, orc, s)[0] for s in (0, 1)]
+    mp.plan_batch(probs, 2.0, max_steps=40)
+    st = mp.plan_batch_phase_stats()
+    busy = sum(st[k][0] for k in mp.PLAN_PHASE_NAMES)
+    assert st["ctas"] > 0 and st["wall_ns"] > 0
+    assert 0 < busy <= st["ctas"] * st["wall_ns"]
+    for k in mp.PLAN_PHASE_NAMES:
+        ns, n = st[k]
+        assert n >= 0 and not (ns > 0 and n == 0)   # time only where chunks ran
+    assert st["roadmap_edge_check"][1] > 0 and st["search_sample"][1] > 0
+    assert st["phase_transitions"][1] > 0
+    for p in probs:
+        p.close()
