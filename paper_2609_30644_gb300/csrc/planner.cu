@@ -1637,8 +1637,7 @@ enum PKind : int {
 };
 constexpr int kPerThreads = 256;          // threads per persistent CTA (= kStepIters)
 constexpr int kPerWarps = kPerThreads / 32;
-constexpr int kPerEdges = 32;             // edges per validation chunk, at least
-constexpr int kPerEdgesMax = kStepIters;  // and at most
+constexpr int kPerEdges = 32;             // edges per validation chunk
 constexpr int kFineCap = 16384;           // sub-edges per fine re-check window
 constexpr int kTraceCap = 256;            // incumbents recorded per problem
 constexpr int kHistCap = 64;              // incumbent paths kept per problem
@@ -1661,7 +1660,6 @@ struct PState {
     double c_best, target;
     unsigned long long seed;
     int n_per_round, rcap;
-    int per_edges;             // edges per validation chunk (kPerEdges .. kPerEdgesMax)
     float res4;                // resolution / 4 (fine re-check)
     // incumbent candidate of the current step
     int cand_len, fine_M, fine_done, fine_cnt, fine_bad, accepted;
@@ -1708,11 +1706,11 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 __device__ __forceinline__ int chunks_of(int n, int per) { return n <= 0 ? 0 : (n + per - 1) / per; }
 
-// Validation of edges [chunk * per, chunk * per + per) of vp (count edges in all).
-__device__ __noinline__ void val_chunk(const VParams &vp, int chunk, int count, int per,
-                                       float4 *sm4, int *s_next) {
+// Validation of edges [chunk * 32, chunk * 32 + 32) of vp (count edges in all).
+__device__ __noinline__ void val_chunk(const VParams &vp, int chunk, int count, float4 *sm4,
+                                       int *s_next) {
     if (threadIdx.x == 0) *s_next = 0;
-    const int e0 = chunk * per, e1 = min(count, e0 + per);
+    const int e0 = chunk * kPerEdges, e1 = min(count, e0 + kPerEdges);
     vb::validate_body<vb::kVerdict, false, true>(vp, sm4, e0, e1, s_next);
     __syncthreads();
 }
@@ -1855,7 +1853,7 @@ __device__ void run_chunk(PState &ps, int kind, int r, int c, float4 *sm4, NnSha
     const int tid = threadIdx.x;
     switch (kind) {
         case PK_RM_SAMPLE: rmb_sample_body(ps.jobs[r], c * kPerThreads + tid); break;
-        case PK_RM_VALC: val_chunk(ps.vp[3 + r], c, ps.jobs[r].nc, ps.per_edges, sm4, s_next); break;
+        case PK_RM_VALC: val_chunk(ps.vp[3 + r], c, ps.jobs[r].nc, sm4, s_next); break;
         case PK_RM_APPEND: {
             RmJob &J = ps.jobs[r];
             append_valid(J.cand, J.cvalid, J.nc, J.dof, J.want, J.q, J.rcap, J.count);
@@ -1868,9 +1866,7 @@ __device__ void run_chunk(PState &ps, int kind, int r, int c, float4 *sm4, NnSha
         }
         case PK_RM_NB: rmb_neighbors_body(ps.jobs[r], c * kPerWarps + (tid >> 5)); break;
         case PK_RM_EDGES: rmb_edges_body(ps.jobs[r], c * kPerThreads + tid); break;
-        case PK_RM_VALE:
-            val_chunk(ps.vp[3 + ps.K + r], c, ps.jobs[r].emax, ps.per_edges, sm4, s_next);
-            break;
+        case PK_RM_VALE: val_chunk(ps.vp[3 + ps.K + r], c, ps.jobs[r].emax, sm4, s_next); break;
         case PK_RM_LINK: {
             const RmJob &J = ps.jobs[r];
             if (tid < 32) link_edges(J.evalid, J.ea, J.eb, J.m * kKmax, J.adj, J.deg);
@@ -1881,16 +1877,16 @@ __device__ void run_chunk(PState &ps, int kind, int r, int c, float4 *sm4, NnSha
         case PK_ST_SAMPLE: sample_body(S, tid); break;
         case PK_ST_NN0: nearest_body<0, kPerThreads>(S, c, nn); break;
         case PK_ST_ORACLE: oracle_body(S, tid); break;
-        case PK_ST_VAL1: val_chunk(ps.vp[0], c, kStepIters, ps.per_edges, sm4, s_next); break;
+        case PK_ST_VAL1: val_chunk(ps.vp[0], c, kStepIters, sm4, s_next); break;
         case PK_ST_INSERT: insert_body(S, wsum); break;
         case PK_ST_NN1: nearest_body<1, kPerThreads>(S, c, nn); break;
         case PK_ST_CONN: conn_prep_body(S, tid); break;
-        case PK_ST_VAL2: val_chunk(ps.vp[1], c, kStepIters, ps.per_edges, sm4, s_next); break;
+        case PK_ST_VAL2: val_chunk(ps.vp[1], c, kStepIters, sm4, s_next); break;
         case PK_ST_SOLUTION:
             solution_body(S, tid);
             solution_candidate(ps, red);
             break;
-        case PK_FINE_VAL: val_chunk(ps.vp[2], c, ps.fine_cnt, ps.per_edges, sm4, s_next); break;
+        case PK_FINE_VAL: val_chunk(ps.vp[2], c, ps.fine_cnt, sm4, s_next); break;
         case PK_FINE_ACCEPT: fine_accept(ps); break;
         default: break;
     }
@@ -1998,11 +1994,11 @@ __device__ PDecision decide(PState &ps, int kind, int r, unsigned long long now,
                             unsigned long long deadline) {
     switch (kind) {
         case PK_BEGIN: return begin_outer(ps, now, deadline);
-        case PK_RM_SAMPLE: return {phase_word(PK_RM_VALC, r, chunks_of(ps.jobs[r].nc, ps.per_edges)), 0};
+        case PK_RM_SAMPLE: return {phase_word(PK_RM_VALC, r, chunks_of(ps.jobs[r].nc, kPerEdges)), 0};
         case PK_RM_VALC: return {phase_word(PK_RM_APPEND, r, 1), 0};
         case PK_RM_APPEND: return {phase_word(PK_RM_NB, r, chunks_of(ps.jobs[r].m, kPerWarps)), 0};
         case PK_RM_NB: return {phase_word(PK_RM_EDGES, r, chunks_of(ps.jobs[r].emax, kPerThreads)), 0};
-        case PK_RM_EDGES: return {phase_word(PK_RM_VALE, r, chunks_of(ps.jobs[r].emax, ps.per_edges)), 0};
+        case PK_RM_EDGES: return {phase_word(PK_RM_VALE, r, chunks_of(ps.jobs[r].emax, kPerEdges)), 0};
         case PK_RM_VALE: return {phase_word(PK_RM_LINK, r, 1), 0};
         case PK_RM_LINK: {
             if (r + 1 < ps.K) return {round_setup(ps, r + 1), 0};
@@ -2030,19 +2026,19 @@ __device__ PDecision decide(PState &ps, int kind, int r, unsigned long long now,
         }
         case PK_ST_SAMPLE: return {phase_word(PK_ST_NN0, 0, kStepIters / kPQB), 0};
         case PK_ST_NN0: return {phase_word(PK_ST_ORACLE, 0, 1), 0};
-        case PK_ST_ORACLE: return {phase_word(PK_ST_VAL1, 0, kStepIters / ps.per_edges), 0};
+        case PK_ST_ORACLE: return {phase_word(PK_ST_VAL1, 0, kStepIters / kPerEdges), 0};
         case PK_ST_VAL1: return {phase_word(PK_ST_INSERT, 0, 1), 0};
         case PK_ST_INSERT: return {phase_word(PK_ST_NN1, 0, kStepIters / kPQB), 0};
         case PK_ST_NN1: return {phase_word(PK_ST_CONN, 0, 1), 0};
-        case PK_ST_CONN: return {phase_word(PK_ST_VAL2, 0, kStepIters / ps.per_edges), 0};
+        case PK_ST_CONN: return {phase_word(PK_ST_VAL2, 0, kStepIters / kPerEdges), 0};
         case PK_ST_VAL2: return {phase_word(PK_ST_SOLUTION, 0, 1), 0};
         case PK_ST_SOLUTION:
-            if (ps.fine_M > 0) return {phase_word(PK_FINE_VAL, 0, chunks_of(ps.fine_cnt, ps.per_edges)), 0};
+            if (ps.fine_M > 0) return {phase_word(PK_FINE_VAL, 0, chunks_of(ps.fine_cnt, kPerEdges)), 0};
             return after_step(ps, false, now, deadline);
         case PK_FINE_VAL: return {phase_word(PK_FINE_ACCEPT, 0, 1), 0};
         case PK_FINE_ACCEPT:
             if (ps.fine_bad) return after_step(ps, false, now, deadline);
-            if (!ps.accepted) return {phase_word(PK_FINE_VAL, 0, chunks_of(ps.fine_cnt, ps.per_edges)), 0};
+            if (!ps.accepted) return {phase_word(PK_FINE_VAL, 0, chunks_of(ps.fine_cnt, kPerEdges)), 0};
             return after_step(ps, true, now, deadline);
         default: return {phase_word(PK_DONE, 0, 0), 0};
     }
@@ -2288,13 +2284,6 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
     PL_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent, kPerThreads, smem));
     if (bps < 1) return set_error(MRPOP_EINVAL, "plan_batch: persistent kernel does not fit an SM");
     const int ctas = g_per_ctas.load() > 0 ? g_per_ctas.load() : sms * bps;
-    // Edges per validation chunk: small chunks let a few problems spread a
-    // phase over many CTAs; with many problems the CTAs have work anyway, and
-    // larger chunks keep a CTA's warps busy longer between phases (its edges
-    // are handed out warp by warp, so a chunk ends with its slowest edge).
-    // Verdicts do not depend on the chunking.
-    int per_edges = kPerEdges;
-    while (per_edges < kPerEdgesMax && (int64_t)n * (kStepIters / per_edges) > ctas) per_edges *= 2;
 
     // per-problem state from the host mirrors (each call starts with a
     // roadmap round, as Alg. 1 does)
@@ -2335,7 +2324,6 @@ static mrpop_status plan_batch_persistent(mrpop_problem *const *ps, int n, doubl
         s.target = run[i].target;
         s.seed = pl->seed;
         s.n_per_round = pl->n_per_round;
-        s.per_edges = per_edges;
         s.rcap = pl->rcap;
         s.res4 = 0.25f * pl->p->cfg.resolution;
         s.slot = b.slot;
