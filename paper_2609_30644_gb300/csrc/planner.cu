@@ -2078,7 +2078,10 @@ __global__ void __launch_bounds__(kPerThreads) k_persistent(const PLaunch L) {
                 s_robot = (int)((got >> 52) & 63);
                 s_total = tot;
                 s_chunk = c;
-                scan = q;  // stay with this problem while it has chunks
+                // the next claim starts at the next problem: the CTAs spread
+                // over the problems, so a phase with many chunks (a many-arm
+                // problem's long edges) runs on many CTAs at once
+                scan = (q + 1) % L.n;
             }
             if (s_q < 0) {
                 if (*(volatile int *)L.finished >= L.n) {
