@@ -208,7 +208,7 @@ mrpop_status nearest_dp(const float *tree, int N, int64_t ld, int dim, const flo
 // The ordering pass flags inputs outside the operand type's range (NaN and
 // infinities always) and the kernel then sends every pair to the exact check.
 constexpr int kTcWarps = 8;
-constexpr int kSliceAlign = 256;           // tree slices are whole tiles
+constexpr int kSliceAlign = 256;           // tree slices are whole tensor-core tiles
 constexpr int kTcThreads = kTcWarps * 32;
 constexpr int kTcQueries = kTcWarps * 32;  // queries per block
 constexpr float kTc = 1.125f / 256.f;      // TF32: folded into |x|^2
@@ -924,17 +924,18 @@ struct F32Shape {
     // packed FMAs (the multipliers kept twice) where two blocks still fit and
     // the tile's registers do not spill (they do below 8 dimensions)
     static constexpr bool PACKED = DIM >= 8 && DIM <= 21;
-    // vertices per shared-memory tile: two blocks of 256 threads fit an SM
-    static constexpr int VT = DIM <= 14 ? 256 : (DIM <= 21 && !PACKED) ? 128 : 64;
+    // vertices per shared-memory tile (six 64-vertex steps per barrier up to
+    // 14 dimensions) such that two blocks of 256 threads fit an SM
+    static constexpr int VT = DIM <= 14 ? 384 : (DIM <= 21 && !PACKED) ? 128 : 64;
     static constexpr int ROWS = DIM + 2;              // x_d, g, folded |x|^2
     static constexpr int AM = PACKED ? 2 : 1;         // copies of each -2 q_d
 };
 
 template <int DIM>
 constexpr size_t f32_smem_bytes() {
-    // -2 q [DIM][256] (twice when packed), q [DIM][256], two tiles
-    // [ROWS][VT], best d2, best position and bound [8][256] each
-    return sizeof(float) * ((size_t)(F32Shape<DIM>::AM + 1) * DIM * kTcQueries +
+    // -2 q [DIM][256] (twice when packed), two tiles [ROWS][VT], best d2,
+    // best position and bound [8][256] each
+    return sizeof(float) * ((size_t)F32Shape<DIM>::AM * DIM * kTcQueries +
                             (size_t)2 * F32Shape<DIM>::ROWS * F32Shape<DIM>::VT +
                             (size_t)3 * 8 * kTcQueries);
 }
@@ -988,9 +989,7 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, int ldt, const float *
     extern __shared__ __align__(16) float f32_sm[];
     // -2 q_d of query j at am[d][AM j .. AM j + AM - 1]
     float(*am)[AM * kTcQueries] = reinterpret_cast<float(*)[AM * kTcQueries]>(f32_sm);
-    float(*qsm)[kTcQueries] =
-        reinterpret_cast<float(*)[kTcQueries]>(f32_sm + AM * DIM * kTcQueries);
-    float *tiles = f32_sm + (AM + 1) * DIM * kTcQueries;          // [2][ROWS][VT]
+    float *tiles = f32_sm + AM * DIM * kTcQueries;                // [2][ROWS][VT]
     float(*sb_d2)[kTcQueries] =
         reinterpret_cast<float(*)[kTcQueries]>(tiles + 2 * ROWS * VT);  // [8][256]
     int(*sb_pos)[kTcQueries] = reinterpret_cast<int(*)[kTcQueries]>(sb_d2 + 8);
@@ -1043,17 +1042,22 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, int ldt, const float *
     };
     issue_tile(vs, 0);
 
-    tc_stage_queries<DIM>(qsm, queries, Q, qb);
+    // The queries themselves are not kept: within the filter's coordinate
+    // range [2^-60, 2^60] both -2 q_d and -0.5 (-2 q_d) are exact, so the exact
+    // check takes q_d back from the multipliers; in exact-only mode it reads
+    // the ordered queries from global memory instead.
     {
         const int j = tid;
+        const bool ok = qb + j < Q;
         float n2 = 0.f;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            const float v = qsm[d][j];
+            const float v = ok ? __ldg(queries + (size_t)d * Q + qb + j) : 0.f;
+            const float a = -2.f * v;
             if constexpr (AM == 2)
-                *reinterpret_cast<float2 *>(&am[d][2 * j]) = make_float2(-2.f * v, -2.f * v);
+                *reinterpret_cast<float2 *>(&am[d][2 * j]) = make_float2(a, a);
             else
-                am[d][j] = -2.f * v;
+                am[d][j] = a;
             n2 = fmaf(v, v, n2);
         }
         qn_s[j] = n2;
@@ -1204,10 +1208,19 @@ nearest_f32_kernel(const float *__restrict__ tree, int N, int ldt, const float *
                     // a vertex with g >= c is never admissible
                     if (!(g < cr)) continue;
                     float d2 = 0.f;
+                    if (exact_only) {
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        const float dq = qsm[d][qlr] - xs[d][vl];
-                        d2 = fmaf(dq, dq, d2);
+                        for (int d = 0; d < DIM; ++d) {
+                            const float dq = __ldg(queries + (size_t)d * Q + qb + qlr) - xs[d][vl];
+                            d2 = fmaf(dq, dq, d2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d) {
+                            // one rounding of q_d - x_d, as the plain difference
+                            const float dq = fmaf(-0.5f, am[d][AM * qlr], -xs[d][vl]);
+                            d2 = fmaf(dq, dq, d2);
+                        }
                     }
                     // filter of Alg. 2: g_v + |q - q_v| < c (strict); key (d^2,
                     // g, index), the running best keeps the vertex's position in
