@@ -220,7 +220,7 @@ def test_nearest_work_counts(mp, orc):
 
 @pytest.mark.parametrize("filt", FILTERS)
 @pytest.mark.parametrize("D,case", [(D, c) for D in (14, 21)
-                                    for c in ("offset", "tiny", "huge", "nan")]
+                                    for c in ("offset", "tiny", "huge", "nan", "colossal")]
                          + [(14, "scaled_down"), (14, "scaled_up"), (7, "scaled_down")])
 def test_nearest_filter_range(mp, orc, D, case, filt):
     """Both filters' error bounds are relative to |q|^2 + |x|^2: a box far
@@ -229,8 +229,10 @@ def test_nearest_filter_range(mp, orc, D, case, filt):
     from its largest magnitude: boxes shrunk by 1e-12 or grown by 1e15 must
     stay exact, as must a single tiny or huge coordinate.  For the FP32 and
     TF32 filters a nonzero coordinate below 2^-60 or above 2^60 turns the
-    filter off; a NaN does so for all.  Results must equal the small-batch
-    kernel's and the oracle's."""
+    filter off; a NaN does so for all.  A query coordinate of 3e38, shared
+    with its own vertex, makes -2 q overflow: the exact check must still see
+    the query itself (distance 0 to that vertex).  Results must equal the
+    small-batch kernel's and the oracle's."""
     N, Q = 1500, 2048
     lo, hi = -2.9 * np.ones(D), 2.9 * np.ones(D)
     tree = synth.random_tree(D, N, lo, hi, seed=31 + D, dup_frac=0.05)
@@ -245,6 +247,9 @@ def test_nearest_filter_range(mp, orc, D, case, filt):
         tree[2, 7] = np.float32(2.0 ** 61)
     elif case == "nan":
         tree[4, 11] = np.nan
+    elif case == "colossal":
+        qs[2, 9] = tree[2, 9] = np.float32(3e38)  # query 9 is vertex 9
+        cs[9] = np.float32(tree[D, 9]) + np.float32(1.0)  # and vertex 9 is admissible
     else:
         # every coordinate, the costs and the budgets scaled alike: the
         # nearest vertex is the same, distances scale by f
@@ -253,6 +258,8 @@ def test_nearest_filter_range(mp, orc, D, case, filt):
         qs *= f
         cs *= f
     big = mp.nearest(_dev(tree), _dev(qs), _dev(cs), filter=filt).cpu().numpy()
+    if case == "colossal":
+        assert big[9] == 9, big[9]
     small = np.concatenate([
         mp.nearest(_dev(tree), _dev(np.ascontiguousarray(qs[:, i:i + 1000])),
                    _dev(cs[i:i + 1000])).cpu().numpy() for i in range(0, Q, 1000)])
